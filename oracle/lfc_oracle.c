@@ -1,0 +1,1029 @@
+/*
+ * lfc_oracle.c -- plain, slow, single-threaded CPU oracle for the PC-bzip2
+ * compression path (Su et al., "PC-bzip2: a phase-space continuity enhanced
+ * lossless compression algorithm for light field microscopy data").
+ *
+ * TEST INFRASTRUCTURE. Only the test suite, the smoke check and the CPU
+ * baseline leg of the benchmark load this file. The CUDA library shares no
+ * code, header, table or constant generator with it, and neither includes the
+ * other.
+ *
+ * Each function states the passage it follows. Where the paper is silent the
+ * function states the reading it takes. Integer arithmetic throughout: the
+ * whole path is exact, so the CUDA path must reproduce these bytes exactly.
+ *
+ * Parity pins (what fixes each function other than itself):
+ *   lfc_orc_symbols / lfc_orc_inverse_symbols : exact inverse (round trip),
+ *       textbook lossless-JPEG predictor values on hand-made frames, the
+ *       ordering is a bijection on pixel indices.
+ *   lfc_orc_judge_last / lfc_orc_bigram      : brute force "generate every
+ *       rotation, stable sort by first byte, take the last column".
+ *   lfc_orc_log2_fx / lfc_orc_score          : closed forms (constant input
+ *       gives entropy 0; m equal bins give log2 m), libm log2 within 2^-28.
+ *   lfc_orc_bwt                              : brute-force rotation sort.
+ *   lfc_orc_huff_lengths                     : optimal prefix-code cost and
+ *       Kraft sum against an independent heap Huffman.
+ *   lfc_orc_bz2_stream                       : decoded by the stock bzip2
+ *       decoder to the exact input bytes.
+ *   lfc_orc_bz2_decode                       : decodes the stock bzip2
+ *       encoder's streams.
+ *   lfc_orc_crc32                            : CRC-32/BZIP2 check value.
+ *   The exact compressed bytes (table partition, refinement, tie rules) are
+ *   choices of this library that the paper and the bzip2 format leave free:
+ *   parity unpinned beyond stock-decoder acceptance and the properties above.
+ */
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+/* ------------------------------------------------------------------------ */
+/* Candidate id (Sec. 2.1.4: the predictor is one unsigned 8-bit integer).   */
+/* Library reading of the missing Fig. 3 table:                             */
+/*   bits 0-3 predictor function f (0 none, 1..7 lossless-JPEG set)         */
+/*   bits 4-5 domain (0 intra-lenslet, 1 inter-lenslet, 2 phase space)      */
+/*   bit  6   ordering (0 lenslet-major raw layout, 1 view-major)           */
+/*   bit  7   temporal delta against the previous frame                     */
+/* ------------------------------------------------------------------------ */
+#define ID_F(id) ((id) & 15)
+#define ID_DOMAIN(id) (((id) >> 4) & 3)
+#define ID_ORDER(id) (((id) >> 6) & 1)
+#define ID_TEMPORAL(id) (((id) >> 7) & 1)
+
+int lfc_orc_id_valid(int id)
+{
+    if (id < 0 || id > 255) return 0;
+    if (ID_F(id) > 7) return 0;
+    if (ID_DOMAIN(id) > 2) return 0;
+    if (ID_F(id) == 0 && ID_DOMAIN(id) != 0) return 0;
+    return 1;
+}
+
+/* Floor of x/2 for a signed integer, written out (no reliance on >>). */
+static int32_t floor_half(int32_t x)
+{
+    if (x >= 0) return x / 2;
+    return -((-x + 1) / 2);
+}
+
+/* The seven classic lossless-JPEG predictor functions (Sec. 3: "7 types of
+ * predictors mainly applied in traditional compression methods"; the paper
+ * names B+(A-C)/2 and (A+B)/2). A = left, B = top, C = top-left. */
+static int32_t jpeg_predict(int f, int32_t A, int32_t B, int32_t C)
+{
+    switch (f) {
+    case 1: return A;
+    case 2: return B;
+    case 3: return C;
+    case 4: return A + B - C;
+    case 5: return A + floor_half(B - C);
+    case 6: return B + floor_half(A - C);
+    case 7: return floor_half(A + B);
+    default: return 0;
+    }
+}
+
+/* Prediction in one 2-D grid with the lossless-JPEG boundary rule: the origin
+ * predicts 0, the first row predicts from the left neighbour, the first
+ * column from the top neighbour, everything else uses f. */
+static int32_t grid_predict(int f, int row, int col, int32_t A, int32_t B, int32_t C)
+{
+    if (row == 0 && col == 0) return 0;
+    if (row == 0) return A;
+    if (col == 0) return B;
+    return jpeg_predict(f, A, B, C);
+}
+
+static int32_t as_int16(uint32_t e16)
+{
+    e16 &= 0xFFFFu;
+    return e16 >= 32768u ? (int32_t)e16 - 65536 : (int32_t)e16;
+}
+
+/* Map a mod-2^16 residual to a non-negative symbol ("symbol images step
+ * means to convert the delta images to full positive images", Fig. 2a).
+ * Reading: zigzag of the residual taken as a signed 16-bit value. */
+static uint16_t zigzag16(uint32_t e16)
+{
+    int32_t s = as_int16(e16);
+    int32_t z = s >= 0 ? 2 * s : -2 * s - 1;
+    return (uint16_t)z;
+}
+
+static uint32_t unzigzag16(uint16_t z)
+{
+    int32_t s = (z & 1) ? -(((int32_t)z + 1) / 2) : ((int32_t)z / 2);
+    return (uint32_t)s & 0xFFFFu;
+}
+
+/* Base field value at pixel (y, x): the raw count, or with the temporal
+ * flag the signed 16-bit difference to the previous frame (time series,
+ * Sec. 3 and 4: temporal continuity). */
+static int32_t base_field(const uint16_t *X, const uint16_t *prev, int W, int y, int x, int temporal)
+{
+    int64_t k = (int64_t)y * W + x;
+    if (!temporal) return (int32_t)X[k];
+    return as_int16((uint32_t)X[k] - (uint32_t)prev[k]);
+}
+
+/* Intra-lenslet residual (Sec. 2.1.1: left, top and top-left neighbouring
+ * pixels inside the same microlens) of the base field at (y, x), mod 2^16. */
+static uint32_t intra_residual(int f, const uint16_t *X, const uint16_t *prev, int W, int p,
+                               int y, int x, int temporal)
+{
+    int v = y % p, u = x % p;
+    int32_t Xv = base_field(X, prev, W, y, x, temporal);
+    int32_t A = u > 0 ? base_field(X, prev, W, y, x - 1, temporal) : 0;
+    int32_t B = v > 0 ? base_field(X, prev, W, y - 1, x, temporal) : 0;
+    int32_t C = (u > 0 && v > 0) ? base_field(X, prev, W, y - 1, x - 1, temporal) : 0;
+    int32_t pred = grid_predict(f, v, u, A, B, C);
+    return (uint32_t)(Xv - pred) & 0xFFFFu;
+}
+
+/* Inter-lenslet residual (Sec. 2.1.1: the pixels in the same position of the
+ * left, top and top-left neighbouring microlenses) at (y, x), mod 2^16. */
+static uint32_t inter_residual(int f, const uint16_t *X, const uint16_t *prev, int W, int p,
+                               int y, int x, int temporal)
+{
+    int t = y / p, s = x / p;
+    int32_t Xv = base_field(X, prev, W, y, x, temporal);
+    int32_t A = s > 0 ? base_field(X, prev, W, y, x - p, temporal) : 0;
+    int32_t B = t > 0 ? base_field(X, prev, W, y - p, x, temporal) : 0;
+    int32_t C = (s > 0 && t > 0) ? base_field(X, prev, W, y - p, x - p, temporal) : 0;
+    int32_t pred = grid_predict(f, t, s, A, B, C);
+    return (uint32_t)(Xv - pred) & 0xFFFFu;
+}
+
+/* Phase-space residual (Sec. 2.1.1 and Fig. 1b: both neighbouring pixels and
+ * pixels in neighbouring microlenses). Reading: two stages, the intra
+ * residual field e1 (signed 16-bit) is predicted again across lenslets. */
+static uint32_t phase_residual(int f, const uint16_t *X, const uint16_t *prev, int W, int p,
+                               int y, int x, int temporal)
+{
+    int t = y / p, s = x / p;
+    int32_t E = as_int16(intra_residual(f, X, prev, W, p, y, x, temporal));
+    int32_t A = s > 0 ? as_int16(intra_residual(f, X, prev, W, p, y, x - p, temporal)) : 0;
+    int32_t B = t > 0 ? as_int16(intra_residual(f, X, prev, W, p, y - p, x, temporal)) : 0;
+    int32_t C = (s > 0 && t > 0) ? as_int16(intra_residual(f, X, prev, W, p, y - p, x - p, temporal)) : 0;
+    int32_t pred = grid_predict(f, t, s, A, B, C);
+    return (uint32_t)(E - pred) & 0xFFFFu;
+}
+
+/* Symbol of pixel (y, x) under candidate id (Fig. 2a: multiple predictors,
+ * then the symbol image). With f = 0 and no temporal flag the symbol is the
+ * raw count (plain bzip2, Sec. 4: "directly apply bzip2"). */
+static uint16_t pixel_symbol(int id, const uint16_t *X, const uint16_t *prev, int W, int p, int y, int x)
+{
+    int f = ID_F(id), dom = ID_DOMAIN(id), tmp = ID_TEMPORAL(id);
+    uint32_t e;
+    if (f == 0) {
+        if (!tmp) return X[(int64_t)y * W + x];
+        e = (uint32_t)base_field(X, prev, W, y, x, 1) & 0xFFFFu;
+    } else if (dom == 0) {
+        e = intra_residual(f, X, prev, W, p, y, x, tmp);
+    } else if (dom == 1) {
+        e = inter_residual(f, X, prev, W, p, y, x, tmp);
+    } else {
+        e = phase_residual(f, X, prev, W, p, y, x, tmp);
+    }
+    return zigzag16(e);
+}
+
+/* Stream position k -> pixel (y, x). Ordering 0 is the raw lenslet-major
+ * layout; ordering 1 is the view-major sub-aperture mosaic
+ * out[v*Ny + t][u*Nx + s] = in[t*p + v][s*p + u] (4-D phase space,
+ * Sec. 2.1 and Fig. 1a). */
+static void stream_to_pixel(int order, int W, int H, int p, int64_t k, int *y, int *x)
+{
+    int r = (int)(k / W), c = (int)(k % W);
+    if (order == 0) {
+        *y = r;
+        *x = c;
+        return;
+    }
+    int Nx = W / p, Ny = H / p;
+    int v = r / Ny, t = r % Ny, u = c / Nx, s = c % Nx;
+    *y = t * p + v;
+    *x = s * p + u;
+}
+
+static int geometry_ok(int W, int H, int p)
+{
+    if (W <= 0 || H <= 0 || p <= 0) return 0;
+    if (W % p != 0 || H % p != 0) return 0;
+    if ((int64_t)W * H * 2 > ((int64_t)1 << 26)) return 0;
+    return 1;
+}
+
+/* Symbol stream of a frame in the candidate's ordering: W*H uint16 symbols.
+ * Realigned to bytes it is (lo, hi) per symbol ("realign the 16bit predicted
+ * image as an 8bit data string", Sec. 2.1.2; byte order is a reading). */
+int lfc_orc_symbols(const uint16_t *X, const uint16_t *prev, int W, int H, int p, int id, uint16_t *out)
+{
+    if (!geometry_ok(W, H, p) || !lfc_orc_id_valid(id)) return -1;
+    if (ID_TEMPORAL(id) && !prev) return -1;
+    int64_t n = (int64_t)W * H;
+    for (int64_t k = 0; k < n; k++) {
+        int y, x;
+        stream_to_pixel(ID_ORDER(id), W, H, p, k, &y, &x);
+        out[k] = pixel_symbol(id, X, prev, W, p, y, x);
+    }
+    return 0;
+}
+
+/* Inverse of lfc_orc_symbols (Fig. 2b: the inverse predictor chosen by the
+ * header). Pixels are restored in raster order, which is causal for every
+ * domain: each neighbour used above lies above or to the left. */
+int lfc_orc_inverse_symbols(const uint16_t *Z, const uint16_t *prev, int W, int H, int p, int id, uint16_t *X)
+{
+    if (!geometry_ok(W, H, p) || !lfc_orc_id_valid(id)) return -1;
+    if (ID_TEMPORAL(id) && !prev) return -1;
+    int64_t n = (int64_t)W * H;
+    int f = ID_F(id), dom = ID_DOMAIN(id), tmp = ID_TEMPORAL(id), order = ID_ORDER(id);
+    uint16_t *zpix = (uint16_t *)malloc(sizeof(uint16_t) * n);
+    int32_t *F0 = (int32_t *)malloc(sizeof(int32_t) * n); /* base field */
+    int32_t *E1 = (int32_t *)malloc(sizeof(int32_t) * n); /* intra residual field (phase) */
+    if (!zpix || !F0 || !E1) { free(zpix); free(F0); free(E1); return -2; }
+    for (int64_t k = 0; k < n; k++) {
+        int y, x;
+        stream_to_pixel(order, W, H, p, k, &y, &x);
+        zpix[(int64_t)y * W + x] = Z[k];
+    }
+    for (int y = 0; y < H; y++) {
+        for (int x = 0; x < W; x++) {
+            int64_t k = (int64_t)y * W + x;
+            int v = y % p, u = x % p, t = y / p, s = x / p;
+            if (f == 0 && !tmp) {
+                X[k] = zpix[k];
+                continue;
+            }
+            uint32_t e = unzigzag16(zpix[k]);
+            int32_t base;
+            if (f == 0) {
+                base = as_int16(e);
+            } else if (dom == 0) {
+                int32_t A = u > 0 ? F0[k - 1] : 0, B = v > 0 ? F0[k - W] : 0;
+                int32_t C = (u > 0 && v > 0) ? F0[k - W - 1] : 0;
+                base = (int32_t)((e + (uint32_t)grid_predict(f, v, u, A, B, C)) & 0xFFFFu);
+            } else if (dom == 1) {
+                int32_t A = s > 0 ? F0[k - p] : 0, B = t > 0 ? F0[k - (int64_t)p * W] : 0;
+                int32_t C = (s > 0 && t > 0) ? F0[k - (int64_t)p * W - p] : 0;
+                base = (int32_t)((e + (uint32_t)grid_predict(f, t, s, A, B, C)) & 0xFFFFu);
+            } else {
+                int32_t A = s > 0 ? E1[k - p] : 0, B = t > 0 ? E1[k - (int64_t)p * W] : 0;
+                int32_t C = (s > 0 && t > 0) ? E1[k - (int64_t)p * W - p] : 0;
+                E1[k] = as_int16(e + (uint32_t)grid_predict(f, t, s, A, B, C));
+                int32_t a = u > 0 ? F0[k - 1] : 0, b = v > 0 ? F0[k - W] : 0;
+                int32_t c = (u > 0 && v > 0) ? F0[k - W - 1] : 0;
+                base = (int32_t)(((uint32_t)E1[k] + (uint32_t)grid_predict(f, v, u, a, b, c)) & 0xFFFFu);
+            }
+            /* keep the base field in its domain: signed for temporal deltas */
+            F0[k] = tmp ? as_int16((uint32_t)base) : base;
+            if (tmp)
+                X[k] = (uint16_t)(((uint32_t)F0[k] + prev[k]) & 0xFFFFu);
+            else
+                X[k] = (uint16_t)base;
+        }
+    }
+    free(zpix);
+    free(F0);
+    free(E1);
+    return 0;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Two-dimensional image entropy criterion (Sec. 2.1.2, Eq. (1), Fig. 2c).   */
+/* ------------------------------------------------------------------------ */
+
+/* Last column of the judge-BWT: rotations sorted by their first byte only,
+ * ties kept in generation order (rotation k starts at S[k]). */
+void lfc_orc_judge_last(const uint8_t *S, int64_t n, uint8_t *L)
+{
+    int64_t count[256], start[256];
+    for (int b = 0; b < 256; b++) count[b] = 0;
+    for (int64_t i = 0; i < n; i++) count[S[i]]++;
+    int64_t acc = 0;
+    for (int b = 0; b < 256; b++) { start[b] = acc; acc += count[b]; }
+    for (int64_t i = 0; i < n; i++) {
+        int64_t j = start[S[i]]++;           /* stable: increasing i */
+        L[j] = S[(i + n - 1) % n];           /* last byte of rotation i */
+    }
+}
+
+/* S16 = [x1x2, x2x3, ...]: histogram of adjacent pairs, first byte high. */
+void lfc_orc_bigram(const uint8_t *L, int64_t n, uint32_t *hist)
+{
+    for (int t = 0; t < 65536; t++) hist[t] = 0;
+    for (int64_t j = 0; j + 1 < n; j++) hist[((uint32_t)L[j] << 8) | L[j + 1]]++;
+}
+
+/* Fixed-point binary logarithm: 2^32 * log2(c) for c >= 1, integer part from
+ * the leading bit, 32 fraction bits by repeated squaring of the mantissa
+ * (binary logarithm by squaring; Knuth, TAOCP vol. 1, Sec. 1.2.2, Ex. 25).
+ * The mantissa is kept in Q62 with the square truncated back to Q62. */
+uint64_t lfc_orc_log2_fx(uint32_t c)
+{
+    if (c <= 1) return 0;
+    int k = 0;
+    while (((uint64_t)c >> (k + 1)) != 0) k++;
+    uint64_t y = (uint64_t)c << (62 - k); /* [2^62, 2^63) = [1, 2) */
+    uint64_t frac = 0;
+    for (int i = 0; i < 32; i++) {
+        unsigned __int128 sq = (unsigned __int128)y * y;
+        uint64_t z = (uint64_t)(sq >> 62); /* y^2 in Q62, [1, 4) */
+        frac <<= 1;
+        if (z >= ((uint64_t)1 << 63)) {
+            frac |= 1;
+            y = z >> 1;
+        } else {
+            y = z;
+        }
+    }
+    return ((uint64_t)k << 32) | frac;
+}
+
+/* Score of Eq. (1): sum over t of P_t * log2(P_t) in 2^-32 units. With N =
+ * n - 1 pairs, H = log2 N - score / (N 2^32); minimising H is maximising the
+ * score (reading of the unsigned Eq. (1): H = -sum p log p). */
+uint64_t lfc_orc_score(const uint32_t *hist)
+{
+    uint64_t s = 0;
+    for (int t = 0; t < 65536; t++)
+        if (hist[t] > 1) s += (uint64_t)hist[t] * lfc_orc_log2_fx(hist[t]);
+    return s;
+}
+
+/* Entropy criterion over a list of candidate ids (Fig. 2a multiple
+ * predictors; Sec. 4 "choose a suitable predictor or directly apply bzip2").
+ * Returns the best id: maximum score, ties to the lowest id. */
+int lfc_orc_judge(const uint16_t *X, const uint16_t *prev, int W, int H, int p,
+                  const uint8_t *ids, int K, uint64_t *scores)
+{
+    if (!geometry_ok(W, H, p) || K <= 0) return -1;
+    int64_t nsym = (int64_t)W * H, n = 2 * nsym;
+    uint16_t *z = (uint16_t *)malloc(sizeof(uint16_t) * nsym);
+    uint8_t *S = (uint8_t *)malloc(n);
+    uint8_t *L = (uint8_t *)malloc(n);
+    uint32_t *hist = (uint32_t *)malloc(sizeof(uint32_t) * 65536);
+    if (!z || !S || !L || !hist) { free(z); free(S); free(L); free(hist); return -2; }
+    int best = -1;
+    uint64_t best_score = 0;
+    for (int c = 0; c < K; c++) {
+        if (lfc_orc_symbols(X, prev, W, H, p, ids[c], z) != 0) { best = -1; break; }
+        for (int64_t k = 0; k < nsym; k++) {
+            S[2 * k] = (uint8_t)(z[k] & 0xFF);
+            S[2 * k + 1] = (uint8_t)(z[k] >> 8);
+        }
+        lfc_orc_judge_last(S, n, L);
+        lfc_orc_bigram(L, n, hist);
+        uint64_t sc = lfc_orc_score(hist);
+        if (scores) scores[c] = sc;
+        if (best < 0 || sc > best_score || (sc == best_score && ids[c] < best)) {
+            best = ids[c];
+            best_score = sc;
+        }
+    }
+    free(z); free(S); free(L); free(hist);
+    return best;
+}
+
+/* ------------------------------------------------------------------------ */
+/* bzip2 per block (Sec. 2.1.3: the chosen stream is bzip2-coded in blocks). */
+/* Format: the public bzip2 stream format (level 9).                         */
+/* ------------------------------------------------------------------------ */
+
+/* CRC-32/BZIP2: polynomial 0x04C11DB7, MSB first, init and final xor ~0. */
+uint32_t lfc_orc_crc32(const uint8_t *d, int64_t n)
+{
+    uint32_t crc = 0xFFFFFFFFu;
+    for (int64_t i = 0; i < n; i++) {
+        crc ^= (uint32_t)d[i] << 24;
+        for (int k = 0; k < 8; k++)
+            crc = (crc & 0x80000000u) ? (crc << 1) ^ 0x04C11DB7u : (crc << 1);
+    }
+    return ~crc;
+}
+
+/* Initial run-length step: a run of 4..255 equal bytes becomes the byte four
+ * times and a count byte (run - 4); longer runs are cut into 255-byte runs. */
+int64_t lfc_orc_rle1(const uint8_t *in, int64_t n, uint8_t *out)
+{
+    int64_t i = 0, o = 0;
+    while (i < n) {
+        uint8_t b = in[i];
+        int64_t run = 1;
+        while (i + run < n && in[i + run] == b && run < 255) run++;
+        if (run >= 4) {
+            out[o++] = b; out[o++] = b; out[o++] = b; out[o++] = b;
+            out[o++] = (uint8_t)(run - 4);
+        } else {
+            for (int64_t r = 0; r < run; r++) out[o++] = b;
+        }
+        i += run;
+    }
+    return o;
+}
+
+/* Burrows-Wheeler transform of a block: every cyclic rotation sorted, ties
+ * between identical rotations by start index; L[j] = blk[(SA[j]-1) mod m];
+ * origPtr = j with SA[j] = 0. Prefix doubling: after the round with shift h
+ * the ranks order rotations by their first 2h bytes; each round sorts by
+ * (rank[i], rank[i+h], i) with the library qsort. */
+static const int64_t *g_rank;
+static int64_t g_h, g_m;
+static int cmp_rot(const void *a, const void *b)
+{
+    int64_t i = *(const int64_t *)a, j = *(const int64_t *)b;
+    if (g_rank[i] != g_rank[j]) return g_rank[i] < g_rank[j] ? -1 : 1;
+    int64_t ri = g_rank[(i + g_h) % g_m], rj = g_rank[(j + g_h) % g_m];
+    if (ri != rj) return ri < rj ? -1 : 1;
+    return i < j ? -1 : (i > j);
+}
+
+int lfc_orc_bwt(const uint8_t *blk, int64_t m, uint8_t *L, int64_t *orig_ptr)
+{
+    if (m <= 0) return -1;
+    int64_t *sa = (int64_t *)malloc(sizeof(int64_t) * m);
+    int64_t *rank = (int64_t *)malloc(sizeof(int64_t) * m);
+    int64_t *nr = (int64_t *)malloc(sizeof(int64_t) * m);
+    if (!sa || !rank || !nr) { free(sa); free(rank); free(nr); return -2; }
+    for (int64_t i = 0; i < m; i++) { sa[i] = i; rank[i] = blk[i]; }
+    int64_t cover = 1; /* rank orders rotations by their first `cover` bytes */
+    for (;;) {
+        g_rank = rank;
+        g_h = cover;
+        g_m = m;
+        /* (rank[i], rank[i + cover]) orders by the first 2 * cover bytes */
+        qsort(sa, (size_t)m, sizeof(int64_t), cmp_rot);
+        int64_t distinct = 1;
+        nr[sa[0]] = 0;
+        for (int64_t j = 1; j < m; j++) {
+            int64_t a = sa[j - 1], b = sa[j];
+            int same = rank[a] == rank[b] && rank[(a + cover) % m] == rank[(b + cover) % m];
+            nr[b] = same ? nr[a] : j;
+            if (!same) distinct++;
+        }
+        memcpy(rank, nr, sizeof(int64_t) * m);
+        cover *= 2;
+        if (distinct == m || cover >= m) break;
+    }
+    for (int64_t j = 0; j < m; j++) {
+        L[j] = blk[(sa[j] + m - 1) % m];
+        if (sa[j] == 0) *orig_ptr = j;
+    }
+    free(sa); free(rank); free(nr);
+    return 0;
+}
+
+/* Move-to-front over the bytes in use (initial list ascending), zero runs
+ * coded in bijective base 2 as RUNA (0) / RUNB (1), other MTF index k coded
+ * as k + 1, then EOB = nInUse + 1. Returns the number of symbols. */
+int64_t lfc_orc_mtf_rle2(const uint8_t *L, int64_t m, uint16_t *sym, uint8_t *in_use, uint32_t *freq)
+{
+    int n_in_use = 0;
+    uint8_t to_seq[256], list[256];
+    for (int b = 0; b < 256; b++) in_use[b] = 0;
+    for (int64_t i = 0; i < m; i++) in_use[L[i]] = 1;
+    for (int b = 0; b < 256; b++)
+        if (in_use[b]) to_seq[b] = (uint8_t)n_in_use++;
+    for (int k = 0; k < n_in_use; k++) list[k] = (uint8_t)k;
+    int alpha = n_in_use + 2;
+    for (int s = 0; s < 258; s++) freq[s] = 0;
+    int64_t o = 0, zrun = 0;
+    for (int64_t i = 0; i <= m; i++) {
+        int j = 0;
+        if (i < m) {
+            uint8_t s = to_seq[L[i]];
+            while (list[j] != s) j++;
+            for (int q = j; q > 0; q--) list[q] = list[q - 1];
+            list[0] = s;
+            if (j == 0) { zrun++; continue; }
+        }
+        if (zrun > 0) {
+            /* bijective base 2: digit k of the run is bit k of (run + 1) */
+            int64_t r1 = zrun + 1;
+            int digits = 0;
+            while ((r1 >> (digits + 1)) != 0) digits++;
+            for (int k = 0; k < digits; k++) {
+                uint16_t d = (uint16_t)((r1 >> k) & 1); /* 0 RUNA, 1 RUNB */
+                sym[o++] = d;
+                freq[d]++;
+            }
+            zrun = 0;
+        }
+        if (i < m) {
+            sym[o++] = (uint16_t)(j + 1);
+            freq[j + 1]++;
+        }
+    }
+    sym[o++] = (uint16_t)(alpha - 1); /* EOB */
+    freq[alpha - 1]++;
+    return o;
+}
+
+/* Huffman code lengths. Weights are max(freq, 1). Each step joins the two
+ * nodes with the smallest (weight, key); leaves have key = symbol, the k-th
+ * joined node has key alpha + k, the first chosen becomes the left child.
+ * If the longest code exceeds max_len every weight w becomes 1 + w/2 and the
+ * tree is built again. O(alpha^2) selection: plain, slow, obvious. */
+void lfc_orc_huff_lengths(const uint32_t *freq, int alpha, int max_len, uint8_t *len)
+{
+    uint64_t w[258];
+    uint64_t wt[2 * 258];
+    int parent[2 * 258], alive[2 * 258];
+    for (int i = 0; i < alpha; i++) w[i] = freq[i] ? freq[i] : 1;
+    for (;;) {
+        int nodes = alpha;
+        for (int i = 0; i < alpha; i++) { wt[i] = w[i]; alive[i] = 1; parent[i] = -1; }
+        for (int k = 0; k < alpha - 1; k++) {
+            int pick[2];
+            for (int q = 0; q < 2; q++) {
+                int best = -1;
+                for (int i = 0; i < nodes; i++) {
+                    if (!alive[i]) continue;
+                    if (best < 0 || wt[i] < wt[best]) best = i; /* ties: lower key first */
+                }
+                pick[q] = best;
+                alive[best] = 0;
+            }
+            wt[nodes] = wt[pick[0]] + wt[pick[1]];
+            parent[nodes] = -1;
+            alive[nodes] = 1;
+            parent[pick[0]] = nodes;
+            parent[pick[1]] = nodes;
+            nodes++;
+        }
+        int longest = 0;
+        for (int i = 0; i < alpha; i++) {
+            int d = 0;
+            for (int q = i; parent[q] >= 0; q = parent[q]) d++;
+            len[i] = (uint8_t)d;
+            if (d > longest) longest = d;
+        }
+        if (longest <= max_len) return;
+        for (int i = 0; i < alpha; i++) w[i] = 1 + w[i] / 2;
+    }
+}
+
+/* MSB-first bit writer. */
+typedef struct { uint8_t *buf; int64_t cap, nbits; int overflow; } bitw;
+static void put_bits(bitw *b, uint32_t v, int n)
+{
+    for (int k = n - 1; k >= 0; k--) {
+        int64_t byte = b->nbits >> 3;
+        if (byte >= b->cap) { b->overflow = 1; b->nbits++; continue; }
+        if ((b->nbits & 7) == 0) b->buf[byte] = 0;
+        if ((v >> k) & 1) b->buf[byte] |= (uint8_t)(0x80u >> (b->nbits & 7));
+        b->nbits++;
+    }
+}
+
+/* Number of Huffman tables from the symbol count (a choice the format leaves
+ * free; the thresholds follow common bzip2 practice). */
+static int n_groups_for(int64_t n_mtf)
+{
+    if (n_mtf < 200) return 2;
+    if (n_mtf < 600) return 3;
+    if (n_mtf < 1200) return 4;
+    if (n_mtf < 2400) return 5;
+    return 6;
+}
+
+/* One standalone level-9 bzip2 stream holding exactly one block with the
+ * bytes in[0..n). Returns the stream length in bytes, or -1 if cap is too
+ * small, -2 on bad input. Steps, in order: CRC of the input, RLE1, BWT,
+ * MTF/RLE2, table choice (initial partition by cumulative frequency, four
+ * refinement passes: each 50-symbol group picks the cheapest table, ties to
+ * the lower table, then every table is rebuilt from its groups' counts with
+ * a 17-bit length limit), canonical codes, bit packing. */
+int64_t lfc_orc_bz2_stream(const uint8_t *in, int64_t n, uint8_t *out, int64_t cap)
+{
+    if (n <= 0 || n > 720000) return -2;
+    uint32_t crc = lfc_orc_crc32(in, n);
+    uint8_t *r1 = (uint8_t *)malloc((size_t)(n + n / 4 + 8));
+    int64_t m = lfc_orc_rle1(in, n, r1);
+    if (m > 900000) { free(r1); return -2; }
+    uint8_t *L = (uint8_t *)malloc((size_t)m);
+    int64_t orig = 0;
+    lfc_orc_bwt(r1, m, L, &orig);
+    uint16_t *sym = (uint16_t *)malloc(sizeof(uint16_t) * (size_t)(m + 1));
+    uint8_t in_use[256];
+    uint32_t freq[258];
+    int64_t n_mtf = lfc_orc_mtf_rle2(L, m, sym, in_use, freq);
+    int n_in_use = 0;
+    for (int b = 0; b < 256; b++) n_in_use += in_use[b];
+    int alpha = n_in_use + 2;
+
+    int n_groups = n_groups_for(n_mtf);
+    int64_t n_sel = (n_mtf + 49) / 50;
+    uint8_t len[6][258];
+    uint8_t *sel = (uint8_t *)malloc((size_t)n_sel);
+    /* initial tables: table g covers the symbols whose cumulative count
+     * before them falls in the g-th equal share of n_mtf */
+    {
+        int64_t cum = 0;
+        for (int v = 0; v < alpha; v++) {
+            int64_t g = cum * n_groups / n_mtf;
+            if (g > n_groups - 1) g = n_groups - 1;
+            for (int t = 0; t < n_groups; t++) len[t][v] = (uint8_t)(t == g ? 0 : 15);
+            cum += freq[v];
+        }
+    }
+    for (int iter = 0; iter < 4; iter++) {
+        uint32_t rfreq[6][258];
+        memset(rfreq, 0, sizeof(rfreq));
+        for (int64_t gi = 0; gi < n_sel; gi++) {
+            int64_t a = gi * 50, e = a + 50 < n_mtf ? a + 50 : n_mtf;
+            int bt = 0;
+            uint32_t bc = 0;
+            for (int t = 0; t < n_groups; t++) {
+                uint32_t cost = 0;
+                for (int64_t i = a; i < e; i++) cost += len[t][sym[i]];
+                if (t == 0 || cost < bc) { bc = cost; bt = t; }
+            }
+            sel[gi] = (uint8_t)bt;
+            for (int64_t i = a; i < e; i++) rfreq[bt][sym[i]]++;
+        }
+        for (int t = 0; t < n_groups; t++) lfc_orc_huff_lengths(rfreq[t], alpha, 17, len[t]);
+    }
+    /* canonical codes: by length, then by symbol */
+    uint32_t code[6][258];
+    for (int t = 0; t < n_groups; t++) {
+        uint32_t next = 0;
+        for (int l = 1; l <= 20; l++) {
+            for (int v = 0; v < alpha; v++)
+                if (len[t][v] == l) code[t][v] = next++;
+            next <<= 1;
+        }
+    }
+
+    bitw bw = { out, cap, 0, 0 };
+    put_bits(&bw, 'B', 8); put_bits(&bw, 'Z', 8); put_bits(&bw, 'h', 8); put_bits(&bw, '9', 8);
+    put_bits(&bw, 0x314159, 24); put_bits(&bw, 0x265359, 24);
+    put_bits(&bw, crc, 32);
+    put_bits(&bw, 0, 1);
+    put_bits(&bw, (uint32_t)orig, 24);
+    uint32_t used16 = 0;
+    for (int i = 0; i < 16; i++)
+        for (int j = 0; j < 16; j++)
+            if (in_use[i * 16 + j]) used16 |= 1u << (15 - i);
+    put_bits(&bw, used16, 16);
+    for (int i = 0; i < 16; i++) {
+        if (!(used16 & (1u << (15 - i)))) continue;
+        uint32_t bits = 0;
+        for (int j = 0; j < 16; j++)
+            if (in_use[i * 16 + j]) bits |= 1u << (15 - j);
+        put_bits(&bw, bits, 16);
+    }
+    put_bits(&bw, (uint32_t)n_groups, 3);
+    put_bits(&bw, (uint32_t)n_sel, 15);
+    {
+        uint8_t lst[6];
+        for (int t = 0; t < n_groups; t++) lst[t] = (uint8_t)t;
+        for (int64_t gi = 0; gi < n_sel; gi++) {
+            int j = 0;
+            while (lst[j] != sel[gi]) j++;
+            for (int q = j; q > 0; q--) lst[q] = lst[q - 1];
+            lst[0] = sel[gi];
+            for (int q = 0; q < j; q++) put_bits(&bw, 1, 1);
+            put_bits(&bw, 0, 1);
+        }
+    }
+    for (int t = 0; t < n_groups; t++) {
+        int cur = len[t][0];
+        put_bits(&bw, (uint32_t)cur, 5);
+        for (int v = 0; v < alpha; v++) {
+            while (cur < len[t][v]) { put_bits(&bw, 2, 2); cur++; }
+            while (cur > len[t][v]) { put_bits(&bw, 3, 2); cur--; }
+            put_bits(&bw, 0, 1);
+        }
+    }
+    for (int64_t i = 0; i < n_mtf; i++) {
+        int t = sel[i / 50];
+        put_bits(&bw, code[t][sym[i]], len[t][sym[i]]);
+    }
+    put_bits(&bw, 0x177245, 24); put_bits(&bw, 0x385090, 24);
+    put_bits(&bw, crc, 32); /* combined CRC of a one-block stream */
+    while (bw.nbits & 7) put_bits(&bw, 0, 1);
+
+    free(r1); free(L); free(sym); free(sel);
+    if (bw.overflow) return -1;
+    return bw.nbits >> 3;
+}
+
+/* ------------------------------------------------------------------------ */
+/* bzip2 decoder (any number of blocks and streams back to back).            */
+/* ------------------------------------------------------------------------ */
+typedef struct { const uint8_t *buf; int64_t n, pos; int err; } bitr;
+static uint32_t get_bits(bitr *r, int k)
+{
+    uint32_t v = 0;
+    for (int i = 0; i < k; i++) {
+        int64_t byte = r->pos >> 3;
+        if (byte >= r->n) { r->err = 1; return 0; }
+        v = (v << 1) | ((r->buf[byte] >> (7 - (r->pos & 7))) & 1u);
+        r->pos++;
+    }
+    return v;
+}
+
+/* Returns the decoded length, -1 on a corrupt stream, -3 if cap is small. */
+int64_t lfc_orc_bz2_decode(const uint8_t *in, int64_t n, uint8_t *out, int64_t cap)
+{
+    bitr r = { in, n, 0, 0 };
+    int64_t o = 0;
+    uint8_t *tt = (uint8_t *)malloc(900000);
+    int64_t *cnt_before = (int64_t *)malloc(sizeof(int64_t) * 900000);
+    int64_t result = -1;
+    if (!tt || !cnt_before) goto done;
+    while ((r.pos >> 3) < n) {
+        if (get_bits(&r, 8) != 'B' || get_bits(&r, 8) != 'Z' || get_bits(&r, 8) != 'h') goto done;
+        uint32_t lvl = get_bits(&r, 8);
+        if (r.err || lvl < '1' || lvl > '9') goto done;
+        int64_t block_max = 100000 * (int64_t)(lvl - '0');
+        uint32_t combined = 0;
+        for (;;) {
+            uint32_t m1 = get_bits(&r, 24), m2 = get_bits(&r, 24);
+            if (r.err) goto done;
+            if (m1 == 0x177245 && m2 == 0x385090) {
+                uint32_t stored = get_bits(&r, 32);
+                if (r.err || stored != combined) goto done;
+                r.pos = (r.pos + 7) & ~(int64_t)7;
+                break;
+            }
+            if (m1 != 0x314159 || m2 != 0x265359) goto done;
+            uint32_t bcrc = get_bits(&r, 32);
+            if (get_bits(&r, 1) != 0) goto done; /* randomised blocks not produced */
+            int64_t orig = get_bits(&r, 24);
+            uint32_t used16 = get_bits(&r, 16);
+            uint8_t seq_to_unseq[256];
+            int n_in_use = 0;
+            for (int i = 0; i < 16; i++) {
+                if (!(used16 & (1u << (15 - i)))) continue;
+                uint32_t bits = get_bits(&r, 16);
+                for (int j = 0; j < 16; j++)
+                    if (bits & (1u << (15 - j))) seq_to_unseq[n_in_use++] = (uint8_t)(i * 16 + j);
+            }
+            if (r.err || n_in_use == 0) goto done;
+            int alpha = n_in_use + 2;
+            int n_groups = (int)get_bits(&r, 3);
+            int n_sel = (int)get_bits(&r, 15);
+            if (r.err || n_groups < 2 || n_groups > 6 || n_sel < 1) goto done;
+            uint8_t *sel = (uint8_t *)malloc((size_t)n_sel);
+            {
+                uint8_t lst[6];
+                for (int t = 0; t < n_groups; t++) lst[t] = (uint8_t)t;
+                for (int i = 0; i < n_sel; i++) {
+                    int j = 0;
+                    while (get_bits(&r, 1)) { j++; if (j >= n_groups) { r.err = 1; break; } }
+                    if (r.err) break;
+                    uint8_t v = lst[j];
+                    for (int q = j; q > 0; q--) lst[q] = lst[q - 1];
+                    lst[0] = v;
+                    sel[i] = v;
+                }
+            }
+            uint8_t len[6][258];
+            for (int t = 0; t < n_groups && !r.err; t++) {
+                int cur = (int)get_bits(&r, 5);
+                for (int v = 0; v < alpha && !r.err; v++) {
+                    for (;;) {
+                        if (cur < 1 || cur > 20) { r.err = 1; break; }
+                        if (!get_bits(&r, 1)) break;
+                        cur += get_bits(&r, 1) ? -1 : 1;
+                    }
+                    len[t][v] = (uint8_t)cur;
+                }
+            }
+            if (r.err) { free(sel); goto done; }
+            /* canonical decoding: codes of length l are consecutive from
+             * first[l], symbols of that length in increasing order */
+            uint32_t first[6][22];
+            int32_t count[6][22], base[6][22];
+            uint16_t perm[6][258];
+            for (int t = 0; t < n_groups; t++) {
+                uint32_t next = 0;
+                int np = 0;
+                for (int l = 1; l <= 20; l++) {
+                    first[t][l] = next;
+                    base[t][l] = np;
+                    count[t][l] = 0;
+                    for (int v = 0; v < alpha; v++)
+                        if (len[t][v] == l) { perm[t][np++] = (uint16_t)v; count[t][l]++; next++; }
+                    next <<= 1;
+                }
+            }
+            uint8_t list[256];
+            for (int k = 0; k < n_in_use; k++) list[k] = (uint8_t)k;
+            int64_t nblock = 0, gi = 0, in_group = 0;
+            int64_t run = 0, run_weight = 1;
+            int eob = 0;
+            while (!eob) {
+                if (in_group == 0) {
+                    if (gi >= n_sel) { r.err = 1; break; }
+                    in_group = 50;
+                    gi++;
+                }
+                int t = sel[gi - 1];
+                in_group--;
+                /* read one code: extend bit by bit until it matches */
+                uint32_t c = 0;
+                int l = 0, s = -1;
+                while (s < 0) {
+                    c = (c << 1) | get_bits(&r, 1);
+                    l++;
+                    if (r.err || l > 20) { r.err = 1; break; }
+                    if (c >= first[t][l] && c - first[t][l] < (uint32_t)count[t][l])
+                        s = perm[t][base[t][l] + (int32_t)(c - first[t][l])];
+                }
+                if (r.err) break;
+                if (s <= 1) { /* RUNA / RUNB */
+                    run += (s + 1) * run_weight;
+                    run_weight <<= 1;
+                    if (run > block_max) { r.err = 1; break; }
+                    continue;
+                }
+                if (run > 0) {
+                    if (nblock + run > block_max) { r.err = 1; break; }
+                    uint8_t b = seq_to_unseq[list[0]];
+                    for (int64_t q = 0; q < run; q++) tt[nblock++] = b;
+                    run = 0;
+                    run_weight = 1;
+                }
+                if (s == alpha - 1) { eob = 1; break; }
+                int j = s - 1;
+                if (j >= n_in_use) { r.err = 1; break; }
+                uint8_t v = list[j];
+                for (int q = j; q > 0; q--) list[q] = list[q - 1];
+                list[0] = v;
+                if (nblock >= block_max) { r.err = 1; break; }
+                tt[nblock++] = seq_to_unseq[v];
+            }
+            free(sel);
+            if (r.err || orig >= nblock) goto done;
+            /* inverse BWT: LF mapping T[j] = C[L[j]] + occ(L[j], j) */
+            {
+                int64_t C[256], seen[256];
+                for (int b = 0; b < 256; b++) { C[b] = 0; seen[b] = 0; }
+                for (int64_t j = 0; j < nblock; j++) C[tt[j]]++;
+                int64_t acc = 0;
+                for (int b = 0; b < 256; b++) { int64_t c0 = C[b]; C[b] = acc; acc += c0; }
+                for (int64_t j = 0; j < nblock; j++) cnt_before[j] = C[tt[j]] + seen[tt[j]]++;
+                /* walk backwards from the row of the original string */
+                uint8_t *blk = (uint8_t *)malloc((size_t)nblock);
+                int64_t j = orig;
+                for (int64_t k = nblock - 1; k >= 0; k--) {
+                    blk[k] = tt[j];
+                    j = cnt_before[j];
+                }
+                /* inverse RLE1 into out, CRC over the produced bytes */
+                int64_t o0 = o, i = 0;
+                int same = 0;
+                int last = -1;
+                while (i < nblock) {
+                    uint8_t b = blk[i++];
+                    if (o >= cap) { free(blk); result = -3; goto done; }
+                    out[o++] = b;
+                    same = (b == last) ? same + 1 : 1;
+                    last = b;
+                    if (same == 4) {
+                        if (i >= nblock) { free(blk); goto done; }
+                        int extra = blk[i++];
+                        if (o + extra > cap) { free(blk); result = -3; goto done; }
+                        for (int q = 0; q < extra; q++) out[o++] = b;
+                        same = 0;
+                        last = -1;
+                    }
+                }
+                free(blk);
+                uint32_t got = lfc_orc_crc32(out + o0, o - o0);
+                if (got != bcrc) goto done;
+                combined = ((combined << 1) | (combined >> 31)) ^ bcrc;
+            }
+        }
+    }
+    result = o;
+done:
+    free(tt);
+    free(cnt_before);
+    return result;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Container (Sec. 2.1.4 header with the 8-bit predictor id; Sec. 2.1.3     */
+/* block information). Little-endian fields:                                 */
+/*   0 "LFC1"  4 u16 version=1  6 u16 flags (bit0 temporal)                 */
+/*   8 u32 W  12 u32 H  16 u32 p  20 u8 id  21..23 zero                     */
+/*   24 u32 block_bytes  28 u32 n_blocks  32 u32 CRC-32/BZIP2 of raw frame  */
+/*   36 u32 header_bytes = 40 + 4 n_blocks  40 u32 stream bytes per block   */
+/*   then the standalone bzip2 streams of the blocks, in order.             */
+/* ------------------------------------------------------------------------ */
+static void wr32(uint8_t *p, uint32_t v) { p[0] = (uint8_t)v; p[1] = (uint8_t)(v >> 8); p[2] = (uint8_t)(v >> 16); p[3] = (uint8_t)(v >> 24); }
+static void wr16(uint8_t *p, uint32_t v) { p[0] = (uint8_t)v; p[1] = (uint8_t)(v >> 8); }
+static uint32_t rd32(const uint8_t *p) { return (uint32_t)p[0] | ((uint32_t)p[1] << 8) | ((uint32_t)p[2] << 16) | ((uint32_t)p[3] << 24); }
+static uint32_t rd16(const uint8_t *p) { return (uint32_t)p[0] | ((uint32_t)p[1] << 8); }
+
+/* Compress one frame with a given candidate id. Returns the container size,
+ * -1 if cap is too small, -2 on bad arguments. */
+int64_t lfc_orc_compress_id(const uint16_t *X, const uint16_t *prev, int W, int H, int p, int id,
+                            int block_bytes, uint8_t *out, int64_t cap)
+{
+    if (!geometry_ok(W, H, p) || !lfc_orc_id_valid(id)) return -2;
+    if (block_bytes <= 0 || block_bytes > 720000) return -2;
+    if (ID_TEMPORAL(id) && !prev) return -2;
+    int64_t nsym = (int64_t)W * H, n = 2 * nsym;
+    int64_t n_blocks = (n + block_bytes - 1) / block_bytes;
+    int64_t hdr = 40 + 4 * n_blocks;
+    if (cap < hdr) return -1;
+    uint16_t *z = (uint16_t *)malloc(sizeof(uint16_t) * nsym);
+    uint8_t *S = (uint8_t *)malloc((size_t)n);
+    uint8_t *raw = (uint8_t *)malloc((size_t)n);
+    lfc_orc_symbols(X, prev, W, H, p, id, z);
+    for (int64_t k = 0; k < nsym; k++) {
+        S[2 * k] = (uint8_t)(z[k] & 0xFF);
+        S[2 * k + 1] = (uint8_t)(z[k] >> 8);
+        raw[2 * k] = (uint8_t)(X[k] & 0xFF);
+        raw[2 * k + 1] = (uint8_t)(X[k] >> 8);
+    }
+    memcpy(out, "LFC1", 4);
+    wr16(out + 4, 1);
+    wr16(out + 6, ID_TEMPORAL(id) ? 1u : 0u);
+    wr32(out + 8, (uint32_t)W);
+    wr32(out + 12, (uint32_t)H);
+    wr32(out + 16, (uint32_t)p);
+    out[20] = (uint8_t)id; out[21] = 0; out[22] = 0; out[23] = 0;
+    wr32(out + 24, (uint32_t)block_bytes);
+    wr32(out + 28, (uint32_t)n_blocks);
+    wr32(out + 32, lfc_orc_crc32(raw, n));
+    wr32(out + 36, (uint32_t)hdr);
+    int64_t o = hdr;
+    int64_t ret = 0;
+    for (int64_t b = 0; b < n_blocks; b++) {
+        int64_t a = b * block_bytes, e = a + block_bytes < n ? a + block_bytes : n;
+        int64_t s = lfc_orc_bz2_stream(S + a, e - a, out + o, cap - o);
+        if (s < 0) { ret = -1; break; }
+        wr32(out + 40 + 4 * b, (uint32_t)s);
+        o += s;
+    }
+    free(z); free(S); free(raw);
+    return ret < 0 ? ret : o;
+}
+
+/* Judge over ids[0..K) then compress with the winner (Fig. 1c pipeline). */
+int64_t lfc_orc_compress(const uint16_t *X, const uint16_t *prev, int W, int H, int p,
+                         const uint8_t *ids, int K, int block_bytes, uint8_t *out, int64_t cap,
+                         int *chosen)
+{
+    int best = lfc_orc_judge(X, prev, W, H, p, ids, K, 0);
+    if (best < 0) return -2;
+    if (chosen) *chosen = best;
+    return lfc_orc_compress_id(X, prev, W, H, p, best, block_bytes, out, cap);
+}
+
+/* Header parse: fills W, H, p, id; returns 0 or -1 when malformed. */
+int lfc_orc_container_info(const uint8_t *in, int64_t n, int *W, int *H, int *p, int *id)
+{
+    if (n < 40 || memcmp(in, "LFC1", 4) != 0 || rd16(in + 4) != 1) return -1;
+    *W = (int)rd32(in + 8);
+    *H = (int)rd32(in + 12);
+    *p = (int)rd32(in + 16);
+    *id = in[20];
+    return 0;
+}
+
+/* Decompress one container (Fig. 2b: unpack header, bzip2-decode, inverse
+ * predictor by the header's id). Returns 0, or -1 on a corrupt container. */
+int lfc_orc_decompress(const uint8_t *in, int64_t n, const uint16_t *prev, uint16_t *X)
+{
+    int W, H, p, id;
+    if (lfc_orc_container_info(in, n, &W, &H, &p, &id) != 0) return -1;
+    if (!geometry_ok(W, H, p) || !lfc_orc_id_valid(id)) return -1;
+    if (((rd16(in + 6) & 1) != 0) != (ID_TEMPORAL(id) != 0)) return -1;
+    if (ID_TEMPORAL(id) && !prev) return -1;
+    int64_t nsym = (int64_t)W * H, nbytes = 2 * nsym;
+    int64_t bb = rd32(in + 24), nb = rd32(in + 28);
+    if (bb <= 0 || bb > 720000 || nb != (nbytes + bb - 1) / bb) return -1;
+    int64_t hdr = rd32(in + 36);
+    if (hdr != 40 + 4 * nb || hdr > n) return -1;
+    uint8_t *S = (uint8_t *)malloc((size_t)nbytes);
+    uint16_t *z = (uint16_t *)malloc(sizeof(uint16_t) * nsym);
+    int64_t o = hdr;
+    int rc = 0;
+    for (int64_t b = 0; b < nb && rc == 0; b++) {
+        int64_t sz = rd32(in + 40 + 4 * b);
+        int64_t want = (b + 1) * bb < nbytes ? bb : nbytes - b * bb;
+        if (sz > n - o) { rc = -1; break; }
+        int64_t got = lfc_orc_bz2_decode(in + o, sz, S + b * bb, want);
+        if (got != want) rc = -1;
+        o += sz;
+    }
+    if (rc == 0) {
+        for (int64_t k = 0; k < nsym; k++) z[k] = (uint16_t)(S[2 * k] | ((uint16_t)S[2 * k + 1] << 8));
+        lfc_orc_inverse_symbols(z, prev, W, H, p, id, X);
+        uint8_t *raw = S; /* reuse as the raw frame bytes */
+        for (int64_t k = 0; k < nsym; k++) { raw[2 * k] = (uint8_t)(X[k] & 0xFF); raw[2 * k + 1] = (uint8_t)(X[k] >> 8); }
+        if (lfc_orc_crc32(raw, nbytes) != rd32(in + 32)) rc = -1;
+    }
+    free(S);
+    free(z);
+    return rc;
+}
