@@ -1,0 +1,220 @@
+/*
+ * lfc.h -- C ABI of liblfc, a GB300 (sm_103a) implementation of the PC-bzip2
+ * compression path for raw light-field microscopy frames (Su et al.,
+ * "PC-bzip2: a phase-space continuity enhanced lossless compression
+ * algorithm for light field microscopy data").
+ *
+ * Pipeline (Fig. 1c and Fig. 2 of the paper): predict every candidate
+ * (Sec. 2.1.1), score each by the two-dimensional image entropy of Eq. (1)
+ * (Sec. 2.1.2), keep the best, bzip2-code the chosen stream in independent
+ * blocks (Sec. 2.1.3) and pack a header holding the 8-bit predictor id
+ * (Sec. 2.1.4). Every stage runs in this library's CUDA kernels.
+ *
+ * Conventions for every entry point:
+ *  - Pointers named d_* are device pointers, h_* are host pointers.
+ *  - The caller owns every input and output buffer. A plan owns its
+ *    workspace, allocated once by lfc_plan_create; no other call allocates
+ *    device memory.
+ *  - Calls are asynchronous on the plan's stream unless they say otherwise;
+ *    results are ready once that stream is synchronised.
+ *  - The return value is an lfc_status. On LFC_ERR_* nothing is guaranteed
+ *    about outputs. lfc_plan_last_error gives a one-line reason.
+ *  - All integers in formats are little-endian. The arithmetic is integer
+ *    throughout and bit-exact; no call has a CPU fallback.
+ */
+#ifndef LFC_H
+#define LFC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    LFC_OK = 0,
+    LFC_ERR_INVALID_ARG = 1,   /* argument outside its documented range */
+    LFC_ERR_CAPACITY = 2,      /* an output buffer is smaller than required */
+    LFC_ERR_CORRUPT = 3,       /* a container or bzip2 stream failed a check */
+    LFC_ERR_CUDA = 4,          /* a CUDA runtime call failed */
+    LFC_ERR_TIMEOUT = 5,       /* a bounded device wait gave up */
+    LFC_ERR_UNIMPLEMENTED = 6, /* feature not built */
+    LFC_ERR_NOMEM = 7          /* workspace allocation failed at plan creation */
+} lfc_status;
+
+/* Candidate (predictor) id: one unsigned 8-bit integer, stored in the header
+ * (Sec. 2.1.4). The paper's mapping table (Fig. 3) is not available; this
+ * library's layout is
+ *   bits 0-3  f: 0 none, 1 A, 2 B, 3 C, 4 A+B-C, 5 A+(B-C)/2, 6 B+(A-C)/2,
+ *             7 (A+B)/2  -- the lossless-JPEG set of Sec. 3 / Fig. 3b, with
+ *             A = left, B = top, C = top-left and floor division;
+ *   bits 4-5  domain: 0 intra-lenslet (neighbouring pixels in one microlens),
+ *             1 inter-lenslet (same pixel of the neighbouring microlenses),
+ *             2 phase space (intra residual predicted again across
+ *             microlenses) -- Sec. 2.1.1, Fig. 1b, Fig. 3c;
+ *   bit  6    ordering: 0 raw lenslet-major layout, 1 view-major mosaic
+ *             out[v*Ny + t][u*Nx + s] = in[t*p + v][s*p + u];
+ *   bit  7    temporal: predict the difference to the previous raw frame.
+ * Valid ids: f <= 7, domain <= 2, and f == 0 only with domain 0. */
+#define LFC_ID(f, domain, ordering, temporal) \
+    ((uint8_t)((f) | ((domain) << 4) | ((ordering) << 6) | ((temporal) << 7)))
+
+/* Largest input block per bzip2 stream. RLE1 grows a block by at most 5/4,
+ * so a block always fits one level-9 bzip2 block (900000 bytes). */
+#define LFC_MAX_BLOCK_BYTES 720000
+
+typedef struct lfc_plan_s *lfc_plan;
+
+typedef struct {
+    /* Largest frame the plan serves (workspace sizing). width and height
+     * must be multiples of pitch; 2 * width * height <= 2^26. */
+    int32_t width, height, pitch;
+    /* Most frames one call may pass. */
+    int32_t max_frames;
+    /* Candidate set, one bit per id (bit id % 64 of word id / 64). All zero
+     * selects the default set: f in {0, 4, 5, 6, 7} x 3 domains (f = 0 only
+     * in domain 0) x 2 orderings = 26 ids, plus the same 26 with the temporal
+     * bit for frames that carry a previous frame. Temporal ids in the mask
+     * apply only to frames with prev != NULL. */
+    uint64_t candidate_mask[4];
+    /* Nonzero enables temporal candidates for frames that pass prev. */
+    int32_t temporal;
+    /* Informational for callers building series (keyframe every G frames:
+     * pass prev = NULL on keyframes). Default 16. */
+    int32_t keyframe_interval;
+    /* Input bytes per bzip2 block; 0 selects 720000. 1 .. 720000. */
+    int32_t block_bytes;
+    /* Learned proposal: judge only the top-k ids of the proposal network,
+     * all ids if its top probability is below tau. 0 = exhaustive. */
+    int32_t topk;
+    float tau;
+} lfc_config;
+
+/* One raw frame: row-major height x width uint16 counts in device memory,
+ * width and height multiples of pitch. prev, when not NULL, is the previous
+ * raw frame of the series (same geometry) and enables temporal ids. */
+typedef struct {
+    const uint16_t *data;
+    const uint16_t *prev;
+    int32_t width, height, pitch;
+    int32_t reserved; /* must be 0 */
+} lfc_frame;
+
+/* Creates a plan bound to cuda_stream (a cudaStream_t; NULL = legacy default
+ * stream) on the current device, allocating all workspace the other calls
+ * need for frames up to config->width x height and config->max_frames per
+ * call. Synchronous. Errors: INVALID_ARG, NOMEM, CUDA. */
+int lfc_plan_create(const lfc_config *config, void *cuda_stream, lfc_plan *out);
+
+/* Frees the plan and its workspace after synchronising its stream. */
+void lfc_plan_destroy(lfc_plan plan);
+
+/* One-line description of the last error the plan reported. */
+const char *lfc_plan_last_error(lfc_plan plan);
+
+/* Two-dimensional image entropy criterion (Sec. 2.1.2, Eq. (1), Fig. 2c).
+ * For each frame and each candidate id: the symbol stream (prediction,
+ * symbol map, ordering, 16-to-8-bit realign as (lo, hi) per symbol) is
+ * sorted by the first byte of every rotation only, ties in generation
+ * order; adjacent bytes of the last column form 16-bit values; their
+ * histogram P_t gives score = sum_t P_t * L2(P_t), L2(c) = 2^32 log2(c) in
+ * fixed point (leading-bit integer part, 32 fraction bits by repeated
+ * squaring in Q62). Lower entropy = higher score; the best id is the
+ * highest score, ties to the lowest id.
+ *   h_frames   host array of n frames (device data).
+ *   d_choice   device, n bytes: best id per frame.
+ *   d_scores   device, n * 256 uint64 or NULL: score of id c of frame i at
+ *              [i * 256 + c]; entries of ids not judged are left untouched.
+ * Errors: INVALID_ARG (n > max_frames, geometry beyond the plan), CUDA. */
+int lfc_judge(lfc_plan plan, const lfc_frame *h_frames, int n, uint8_t *d_choice, uint64_t *d_scores);
+
+/* Symbol stream of one frame under candidate id (Sec. 2.1.1 prediction,
+ * Fig. 2a symbol image, the id's ordering): width * height uint16 symbols
+ * in stream order written to d_out. Errors: INVALID_ARG, CUDA. */
+int lfc_symbols(lfc_plan plan, const lfc_frame *h_frame, int id, uint16_t *d_out);
+
+/* Bytes one frame's container can take at most (header + worst-case bzip2
+ * streams of every block). block_bytes 0 selects 720000. */
+size_t lfc_max_compressed_bytes(int32_t width, int32_t height, int32_t block_bytes);
+
+/* Compresses n frames (Fig. 1c): judge (unless d_choice is given), emit the
+ * chosen stream, split it into block_bytes blocks (Sec. 2.1.3) and code each
+ * as a standalone level-9 bzip2 stream (RLE1, BWT of the full rotation sort,
+ * MTF over the bytes in use, RUNA/RUNB zero runs, 2-6 Huffman tables chosen
+ * per 50 symbols, bit packing, block CRC-32/BZIP2), then the container:
+ *   0 "LFC1" | 4 u16 version 1 | 6 u16 flags (bit 0 temporal) | 8 u32 W |
+ *   12 u32 H | 16 u32 pitch | 20 u8 id, 3 zero bytes | 24 u32 block_bytes |
+ *   28 u32 n_blocks | 32 u32 CRC-32/BZIP2 of the raw frame bytes |
+ *   36 u32 header bytes (40 + 4 n_blocks) | 40 u32 stream bytes per block |
+ *   streams back to back.
+ * Frame i's container is written at d_out + sum_{j<i} lfc_max_compressed_
+ * bytes(W_j, H_j, block_bytes); its size goes to d_out_sizes[i].
+ *   d_choice    device n ids to use, or NULL to run lfc_judge first.
+ *   out_cap     bytes available at d_out; CAPACITY if below the slot sum.
+ * The call blocks the host until the stream has finished the BWT rounds
+ * (it reads per-round active counts). Errors: INVALID_ARG, CAPACITY, CUDA. */
+int lfc_compress(lfc_plan plan, const lfc_frame *h_frames, int n, const uint8_t *d_choice,
+                 uint8_t *d_out, size_t out_cap, uint64_t *d_out_sizes);
+
+/* Standalone bzip2 streams of arbitrary byte blocks (the coder stage of
+ * lfc_compress on its own). Block b is d_in[h_offsets[b] .. + h_sizes[b]),
+ * 1 <= size <= 720000 and n_blocks <= the plan's block capacity
+ * (lfc_plan_block_capacity). Stream b is written at d_out + b * out_stride,
+ * its byte count to d_stream_sizes[b]; out_stride must be at least
+ * lfc_max_stream_bytes(max size). Errors: INVALID_ARG, CAPACITY, CUDA. */
+int lfc_bzip2_encode(lfc_plan plan, const uint8_t *d_in, const uint64_t *h_offsets,
+                     const uint32_t *h_sizes, int n_blocks, uint8_t *d_out, size_t out_stride,
+                     uint32_t *d_stream_sizes);
+
+/* Worst-case bytes of one stream holding block_bytes input bytes. */
+size_t lfc_max_stream_bytes(int32_t block_bytes);
+
+/* Blocks one lfc_compress / lfc_bzip2_encode pass can hold. */
+int lfc_plan_block_capacity(lfc_plan plan);
+
+/* Decompresses n containers (Fig. 2b: unpack the header, bzip2-decode every
+ * block, inverse predictor chosen by the header's id). Container i is
+ * h_in[i] (device) of h_in_sizes[i] bytes; the frame goes to h_out[i]
+ * (device, width * height uint16 of that container). Temporal containers
+ * need h_prev[i] (device previous raw frame); h_prev may be NULL when no
+ * container is temporal. h_prev[i] may point at h_out[j] for j < i: frames
+ * are restored in index order. Synchronous: the host reads the headers.
+ * Errors: INVALID_ARG, CORRUPT (bad header, stream, CRC), CUDA. */
+int lfc_decompress(lfc_plan plan, const uint8_t *const *h_in, const uint64_t *h_in_sizes, int n,
+                   uint16_t *const *h_out, const uint16_t *const *h_prev);
+
+/* Stage timing (tracing). With timing enabled the plan records CUDA events on
+ * its stream around each stage below and accumulates their device time; the
+ * counters only change while enabled. lfc_plan_set_timing also zeroes them.
+ * lfc_plan_timing synchronises the plan's stream, then writes n_stages
+ * accumulated milliseconds to ms (host) and span counts to spans (host, may
+ * be NULL). Errors: INVALID_ARG, CUDA. */
+enum {
+    LFC_STAGE_JUDGE_HIST = 0, /* judge-BWT pair histograms (one kernel) */
+    LFC_STAGE_JUDGE_SCORE,    /* segment fixup, entropy scores, argmax */
+    LFC_STAGE_EMIT,           /* chosen symbol streams */
+    LFC_STAGE_CRC,            /* raw-frame and block CRCs */
+    LFC_STAGE_RLE1,
+    LFC_STAGE_BWT_SORT8,      /* 8-byte prefix radix sort */
+    LFC_STAGE_BWT_REFINE,     /* prefix-doubling rounds */
+    LFC_STAGE_BWT_OUT,        /* last column, origin, bytes in use */
+    LFC_STAGE_MTF,            /* MTF and RUNA/RUNB coding */
+    LFC_STAGE_HUFFMAN,
+    LFC_STAGE_PACK,
+    LFC_STAGE_CONTAINER,
+    LFC_NUM_STAGES
+};
+int lfc_plan_set_timing(lfc_plan plan, int enable);
+int lfc_plan_timing(lfc_plan plan, double *ms, int64_t *spans, int n_stages);
+
+/* Kernel launches this plan has issued since creation (host counter). */
+int64_t lfc_plan_launch_count(lfc_plan plan);
+
+/* Text of a status code. */
+const char *lfc_status_string(int status);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* LFC_H */

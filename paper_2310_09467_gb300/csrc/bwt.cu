@@ -1,0 +1,477 @@
+// bwt.cu -- RLE1 and the Burrows-Wheeler transform of every bzip2 block
+// (Sec. 2.1.3 codes the chosen stream with bzip2; the block format is the
+// public bzip2 format).
+//
+// BWT = sort of all cyclic rotations, ties between identical rotations by
+// start index. Two phases over all blocks of a pass at once, one CTA per
+// (4096-element tile, block), block-major so a block's bytes and suffix
+// array stay in L2 while its tiles run:
+//  1. LSD radix sort of the start positions by their first 8 bytes: 8 stable
+//     passes, 8-bit digits gathered from the block (no keys are stored).
+//  2. Prefix doubling on the groups still tied: rank[i] = head position of
+//     i's group in the suffix array; each round sorts the tied elements by
+//     (rank[i], rank[i + h]) with 5 stable 8-bit LSD passes over the 40-bit
+//     key (m < 2^20), splits groups, and doubles h. Groups left when h >= m
+//     hold identical rotations, already in start-index order (every pass is
+//     stable and the first starts from the identity).
+#include "lfc_common.cuh"
+
+namespace lfc {
+
+constexpr int kSortThreads = 256;
+constexpr int kPerThread = kTile / kSortThreads;  // 16
+
+// ------------------------------------------------------------------ RLE1
+// One CTA (1024 threads) per block: run starts are compacted, every run's
+// coded length (a run of L bytes is cut into 255-byte runs; a run of 4..255
+// becomes 4 bytes + count, shorter ones stay literal) is prefix-summed, and
+// the runs are written.
+__global__ void __launch_bounds__(1024) rle1_kernel(const BlockDesc *__restrict__ blocks, BlockState *__restrict__ st,
+                                                    uint8_t *__restrict__ rle_all, int32_t *__restrict__ scratch_all) {
+    __shared__ int32_t sh[33];
+    const int b = blockIdx.x;
+    const BlockDesc B = blocks[b];
+    const uint8_t *src = B.src;
+    const int n = B.len;
+    uint8_t *out = rle_all + (size_t)b * kBlockCap;
+    int32_t *runs = scratch_all + (size_t)b * kBlockCap;
+    const int T = blockDim.x;
+    const int per = (n + T - 1) / T;
+    const int a = min(n, (int)threadIdx.x * per), e = min(n, a + per);
+    int cnt = 0;
+    for (int i = a; i < e; i++) cnt += (i == 0 || src[i] != src[i - 1]);
+    int total_runs;
+    int off = block_excl_sum<int>(cnt, sh, &total_runs);
+    for (int i = a; i < e; i++)
+        if (i == 0 || src[i] != src[i - 1]) runs[off++] = i;
+    __syncthreads();
+    // coded length per run
+    const int perR = (total_runs + T - 1) / T;
+    const int ra = min(total_runs, (int)threadIdx.x * perR), re = min(total_runs, ra + perR);
+    int bytes = 0;
+    for (int r = ra; r < re; r++) {
+        const int L = (r + 1 < total_runs ? runs[r + 1] : n) - runs[r];
+        const int q = L / 255, rem = L % 255;
+        bytes += rem >= 4 ? 5 * (q + 1) : 5 * q + rem;
+    }
+    int total_out;
+    int o = block_excl_sum<int>(bytes, sh, &total_out);
+    for (int r = ra; r < re; r++) {
+        const int s0 = runs[r];
+        const int L = (r + 1 < total_runs ? runs[r + 1] : n) - s0;
+        const uint8_t v = src[s0];
+        const int q = L / 255, rem = L % 255;
+        for (int c = 0; c < q; c++) {
+            out[o] = v; out[o + 1] = v; out[o + 2] = v; out[o + 3] = v; out[o + 4] = 251;
+            o += 5;
+        }
+        if (rem >= 4) {
+            out[o] = v; out[o + 1] = v; out[o + 2] = v; out[o + 3] = v; out[o + 4] = (uint8_t)(rem - 4);
+            o += 5;
+        } else {
+            for (int c = 0; c < rem; c++) out[o++] = v;
+        }
+    }
+    if (threadIdx.x == 0) st[b].m = total_out;
+}
+
+cudaError_t launch_rle1(lfc_plan P, int nblocks) {
+    Workspace &ws = P->ws;
+    rle1_kernel<<<nblocks, 1024, 0, P->stream>>>(ws.blocks, ws.bstate, ws.rle, ws.sa2);
+    count_launches(P, 1);
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------------------ sort keys
+// MODE 0: element = start position, digit = byte (7 - pass) of its 8-byte
+//         prefix. MODE 1: element = start position of a tied element, digit
+//         = byte `pass` of (rank[v] << 20 | rank[(v + h) mod m]).
+template <int MODE>
+__device__ __forceinline__ uint32_t sort_digit(int32_t v, int pass, const uint8_t *rle, const int32_t *rank, int m, int h) {
+    if (MODE == 0) {
+        int i = v + (7 - pass);
+        while (i >= m) i -= m;
+        return rle[i];
+    } else {
+        int j = v + h;
+        if (j >= m) j -= m;
+        const uint64_t key = ((uint64_t)(uint32_t)rank[v] << 20) | (uint32_t)rank[j];
+        return (uint32_t)(key >> (8 * pass)) & 255u;
+    }
+}
+
+template <int MODE>
+__device__ __forceinline__ int sort_count(const BlockState &s, int h) {
+    if (MODE == 0) return s.m;
+    return h < s.m ? s.n_act : 0;
+}
+
+// Per-tile digit histogram, stored digit-major: cnt[b][digit][tile].
+template <int MODE>
+__global__ void __launch_bounds__(kSortThreads) radix_hist_kernel(int pass, int h, const BlockState *__restrict__ st,
+                                                                  const int32_t *__restrict__ in_all, const uint8_t *__restrict__ rle_all,
+                                                                  const int32_t *__restrict__ rank_all, uint32_t *__restrict__ cnt_all) {
+    __shared__ uint32_t hst[256];
+    const int b = blockIdx.y, tile = blockIdx.x;
+    const BlockState s = st[b];
+    const int n = sort_count<MODE>(s, h);
+    if (tile * kTile >= n) return;
+    hst[threadIdx.x] = 0;
+    __syncthreads();
+    const int32_t *in = in_all + (size_t)b * kBlockCap;
+    const uint8_t *rle = rle_all + (size_t)b * kBlockCap;
+    const int32_t *rank = rank_all + (size_t)b * kBlockCap;
+    for (int i = 0; i < kPerThread; i++) {
+        const int k = tile * kTile + i * kSortThreads + threadIdx.x;
+        const bool ok = k < n;
+        uint32_t d = 0;
+        if (ok) {
+            const int32_t v = (MODE == 0 && pass == 0) ? k : in[k];
+            d = sort_digit<MODE>(v, pass, rle, rank, s.m, h);
+        }
+        const uint32_t mm = __match_any_sync(LFC_FULL, ok ? d : 256u + lane_id());
+        if (ok && (mm & lanemask_lt()) == 0) atomicAdd(&hst[d], (uint32_t)__popc(mm));
+    }
+    __syncthreads();
+    cnt_all[((size_t)b * 256 + threadIdx.x) * kTilesPerBlock + tile] = hst[threadIdx.x];
+}
+
+// Exclusive scan of a block's counts in (digit, tile) order, in place.
+template <int MODE>
+__global__ void __launch_bounds__(1024) radix_scan_kernel(int h, const BlockState *__restrict__ st, uint32_t *__restrict__ cnt_all) {
+    __shared__ uint32_t sh[33];
+    const int b = blockIdx.x;
+    const int n = sort_count<MODE>(st[b], h);
+    if (n == 0) return;
+    const int nt = (n + kTile - 1) / kTile;
+    const int total = 256 * nt;
+    uint32_t *cnt = cnt_all + (size_t)b * 256 * kTilesPerBlock;
+    const int per = (total + blockDim.x - 1) / blockDim.x;
+    const int a = min(total, (int)threadIdx.x * per), e = min(total, a + per);
+    uint32_t sum = 0;
+    for (int q = a; q < e; q++) sum += cnt[(q / nt) * kTilesPerBlock + q % nt];
+    uint32_t off = block_excl_sum<uint32_t>(sum, sh, nullptr);
+    for (int q = a; q < e; q++) {
+        uint32_t &c = cnt[(q / nt) * kTilesPerBlock + q % nt];
+        const uint32_t v = c;
+        c = off;
+        off += v;
+    }
+}
+
+// Stable scatter: warp w owns elements [w*512, (w+1)*512) of the tile, taken
+// 32 at a time in order; equal digits are ranked with __match_any_sync and a
+// per-warp running count, then offset by earlier warps' counts.
+template <int MODE>
+__global__ void __launch_bounds__(kSortThreads) radix_scatter_kernel(int pass, int h, const BlockState *__restrict__ st,
+                                                                     const int32_t *__restrict__ in_all, int32_t *__restrict__ out_all,
+                                                                     const uint8_t *__restrict__ rle_all, const int32_t *__restrict__ rank_all,
+                                                                     const uint32_t *__restrict__ cnt_all) {
+    constexpr int NW = kSortThreads / 32;
+    __shared__ uint32_t wcnt[NW][256];
+    __shared__ uint32_t base[256];
+    const int b = blockIdx.y, tile = blockIdx.x;
+    const BlockState s = st[b];
+    const int n = sort_count<MODE>(s, h);
+    if (tile * kTile >= n) return;
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (int i = threadIdx.x; i < NW * 256; i += kSortThreads) (&wcnt[0][0])[i] = 0;
+    base[threadIdx.x] = cnt_all[((size_t)b * 256 + threadIdx.x) * kTilesPerBlock + tile];
+    __syncthreads();
+    const int32_t *in = in_all + (size_t)b * kBlockCap;
+    int32_t *out = out_all + (size_t)b * kBlockCap;
+    const uint8_t *rle = rle_all + (size_t)b * kBlockCap;
+    const int32_t *rank = rank_all + (size_t)b * kBlockCap;
+    int32_t vals[kPerThread];
+    uint32_t digs[kPerThread], rnk[kPerThread];
+#pragma unroll
+    for (int r = 0; r < kPerThread; r++) {
+        const int k = tile * kTile + w * 512 + r * 32 + lane;
+        const bool ok = k < n;
+        int32_t v = 0;
+        uint32_t d = 0;
+        if (ok) {
+            v = (MODE == 0 && pass == 0) ? k : in[k];
+            d = sort_digit<MODE>(v, pass, rle, rank, s.m, h);
+        }
+        const uint32_t mm = __match_any_sync(LFC_FULL, ok ? d : 256u + lane);
+        uint32_t before = 0;
+        if (ok) before = wcnt[w][d];
+        __syncwarp();
+        if (ok && (mm & lanemask_gt()) == 0) wcnt[w][d] = before + __popc(mm);
+        __syncwarp();
+        vals[r] = v;
+        digs[r] = ok ? d : 0xFFFFFFFFu;
+        rnk[r] = before + __popc(mm & lanemask_lt());
+    }
+    __syncthreads();
+    {   // per digit: exclusive prefix over warps, plus the tile's global offset
+        const int d = threadIdx.x;
+        uint32_t acc = base[d];
+        for (int ww = 0; ww < NW; ww++) {
+            const uint32_t c = wcnt[ww][d];
+            wcnt[ww][d] = acc;
+            acc += c;
+        }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int r = 0; r < kPerThread; r++)
+        if (digs[r] != 0xFFFFFFFFu) out[wcnt[w][digs[r]] + rnk[r]] = vals[r];
+}
+
+// ---------------------------------------------------------- group heads
+__device__ __forceinline__ uint64_t key8(const uint8_t *rle, int m, int v) {
+    uint64_t k = 0;
+    int i = v;
+#pragma unroll
+    for (int q = 0; q < 8; q++) {
+        k = (k << 8) | rle[i];
+        if (++i == m) i = 0;
+    }
+    return k;
+}
+
+__device__ __forceinline__ uint64_t key40(const int32_t *rank, int m, int v, int h) {
+    int j = v + h;
+    if (j >= m) j -= m;
+    return ((uint64_t)(uint32_t)rank[v] << 20) | (uint32_t)rank[j];
+}
+
+// Head flags of elements [k, k + 16) of a thread, MODE 0 over the suffix
+// array (m elements), MODE 1 over the sorted tied elements (n_act).
+template <int MODE>
+__device__ __forceinline__ uint64_t elem_key(int k, const int32_t *sorted, const uint8_t *rle, const int32_t *rank, int m, int h) {
+    const int32_t v = sorted[k];
+    return MODE == 0 ? key8(rle, m, v) : key40(rank, m, v, h);
+}
+
+// Pass A: per tile, the largest head position and the number of elements
+// that stay tied. Head flags go to flags[] for pass B.
+template <int MODE>
+__global__ void __launch_bounds__(kSortThreads) heads_tile_kernel(int h, const BlockState *__restrict__ st,
+                                                                  const int32_t *__restrict__ sorted_all, const int32_t *__restrict__ act_all,
+                                                                  const uint8_t *__restrict__ rle_all, const int32_t *__restrict__ rank_all,
+                                                                  uint8_t *__restrict__ flags_all, int32_t *__restrict__ aux_all) {
+    const int b = blockIdx.y, tile = blockIdx.x;
+    const BlockState s = st[b];
+    const int n = sort_count<MODE>(s, h);
+    if (tile * kTile >= n) return;
+    const int32_t *sorted = sorted_all + (size_t)b * kBlockCap;
+    const int32_t *act = act_all + (size_t)b * kBlockCap;
+    const uint8_t *rle = rle_all + (size_t)b * kBlockCap;
+    const int32_t *rank = rank_all + (size_t)b * kBlockCap;
+    uint8_t *flags = flags_all + (size_t)b * kBlockCap;
+    const int k0 = tile * kTile + threadIdx.x * kPerThread;
+    int hmax = -1, tied = 0;
+    if (k0 < n) {
+        const int k1 = min(n, k0 + kPerThread);
+        uint64_t prevk = k0 > 0 ? elem_key<MODE>(k0 - 1, sorted, rle, rank, s.m, h) : 0;
+        uint64_t cur = elem_key<MODE>(k0, sorted, rle, rank, s.m, h);
+        bool curhead = (k0 == 0) || cur != prevk;
+        for (int k = k0; k < k1; k++) {
+            bool nexthead = true;
+            uint64_t nk = 0;
+            if (k + 1 < n) {
+                nk = elem_key<MODE>(k + 1, sorted, rle, rank, s.m, h);
+                nexthead = nk != cur;
+            }
+            flags[k] = (uint8_t)curhead;
+            if (curhead) hmax = MODE == 0 ? k : act[k];
+            tied += !(curhead && nexthead);
+            cur = nk;
+            curhead = nexthead;
+        }
+    }
+    int mine = hmax;  // last head position among this thread's elements
+    for (int o = 16; o > 0; o >>= 1) mine = max(mine, __shfl_xor_sync(LFC_FULL, mine, o));
+    for (int o = 16; o > 0; o >>= 1) tied += __shfl_xor_sync(LFC_FULL, tied, o);
+    __shared__ int32_t wm[kSortThreads / 32], wt[kSortThreads / 32];
+    if ((threadIdx.x & 31) == 0) { wm[threadIdx.x >> 5] = mine; wt[threadIdx.x >> 5] = tied; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int mx = -1, tt = 0;
+        for (int i = 0; i < kSortThreads / 32; i++) { mx = max(mx, wm[i]); tt += wt[i]; }
+        int32_t *aux = aux_all + ((size_t)b * kTilesPerBlock + tile) * 4;
+        aux[0] = mx;
+        aux[1] = tt;
+    }
+}
+
+// Pass across tiles of a block: exclusive max of head positions, exclusive
+// sum of tied counts, total tied count of the block.
+template <int MODE>
+__global__ void __launch_bounds__(256) heads_scan_kernel(int h, BlockState *__restrict__ st, int32_t *__restrict__ aux_all,
+                                                         int32_t *__restrict__ counters) {
+    __shared__ int32_t shm[33];
+    __shared__ int32_t shs[33];
+    const int b = blockIdx.x;
+    const int n = sort_count<MODE>(st[b], h);
+    int32_t *aux = aux_all + (size_t)b * kTilesPerBlock * 4;
+    const int nt = (n + kTile - 1) / kTile;
+    // nt <= 220 < 256: one tile per thread
+    const int t = threadIdx.x;
+    const int mx = t < nt ? aux[t * 4 + 0] : -1;
+    const int cn = t < nt ? aux[t * 4 + 1] : 0;
+    const int exm = block_excl_max(mx, shm);
+    int total;
+    const int exs = block_excl_sum<int>(cn, shs, &total);
+    if (t < nt) { aux[t * 4 + 2] = exm; aux[t * 4 + 3] = exs; }
+    if (t == 0) {
+        st[b].n_act_next = total;
+        if (total) { atomicAdd(&counters[0], total); atomicMax(&counters[1], total); }
+    }
+}
+
+// Pass B: rank[v] = head position of v's group; the suffix array takes the
+// sorted tied elements (MODE 1); elements still tied are compacted into the
+// next round's lists.
+template <int MODE>
+__global__ void __launch_bounds__(kSortThreads) heads_apply_kernel(int h, const BlockState *__restrict__ st,
+                                                                   const int32_t *__restrict__ sorted_all, const int32_t *__restrict__ act_all,
+                                                                   const uint8_t *__restrict__ flags_all, const int32_t *__restrict__ aux_all,
+                                                                   int32_t *__restrict__ rank_all, int32_t *__restrict__ sa_all,
+                                                                   int32_t *__restrict__ act_out_all, int32_t *__restrict__ val_out_all) {
+    __shared__ int32_t shm[33];
+    __shared__ int32_t shs[33];
+    const int b = blockIdx.y, tile = blockIdx.x;
+    const BlockState s = st[b];
+    const int n = sort_count<MODE>(s, h);
+    if (tile * kTile >= n) return;
+    const size_t bo = (size_t)b * kBlockCap;
+    const int32_t *sorted = sorted_all + bo;
+    const int32_t *act = act_all + bo;
+    const uint8_t *flags = flags_all + bo;
+    const int32_t *aux = aux_all + ((size_t)b * kTilesPerBlock + tile) * 4;
+    int32_t *rank = rank_all + bo;
+    int32_t *sa = sa_all + bo;
+    int32_t *act_out = act_out_all + bo;
+    int32_t *val_out = val_out_all + bo;
+    const int k0 = tile * kTile + threadIdx.x * kPerThread;
+    const int k1 = min(n, k0 + kPerThread);
+    int mine = -1, tied = 0;
+    for (int k = k0; k < k1; k++) {
+        const bool hd = flags[k];
+        const bool nh = (k + 1 >= n) || flags[k + 1];
+        if (hd) mine = MODE == 0 ? k : act[k];
+        tied += !(hd && nh);
+    }
+    int carry = block_excl_max(mine, shm);
+    carry = max(carry, aux[2]);
+    int off = block_excl_sum<int>(tied, shs, nullptr) + aux[3];
+    for (int k = k0; k < k1; k++) {
+        const bool hd = flags[k];
+        const bool nh = (k + 1 >= n) || flags[k + 1];
+        const int pos = MODE == 0 ? k : act[k];
+        if (hd) carry = pos;
+        const int32_t v = sorted[k];
+        rank[v] = carry;
+        if (MODE == 1) sa[pos] = v;
+        if (!(hd && nh)) {
+            act_out[off] = pos;
+            val_out[off] = v;
+            off++;
+        }
+    }
+}
+
+__global__ void commit_round_kernel(BlockState *st, int nblocks) {
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b < nblocks) { st[b].n_act = st[b].n_act_next; st[b].n_act_next = 0; }
+}
+
+// L[j] = block[(SA[j] - 1) mod m]; origPtr = j with SA[j] = 0; bytes in use.
+__global__ void __launch_bounds__(kSortThreads) bwt_output_kernel(BlockState *__restrict__ st, const int32_t *__restrict__ sa_all,
+                                                                  const uint8_t *__restrict__ rle_all, uint8_t *__restrict__ L_all) {
+    __shared__ uint32_t used[8];
+    const int b = blockIdx.y, tile = blockIdx.x;
+    const int m = st[b].m;
+    if (tile * kTile >= m) return;
+    if (threadIdx.x < 8) used[threadIdx.x] = 0;
+    __syncthreads();
+    const size_t bo = (size_t)b * kBlockCap;
+    for (int i = 0; i < kPerThread; i++) {
+        const int j = tile * kTile + i * kSortThreads + threadIdx.x;
+        if (j < m) {
+            const int v = sa_all[bo + j];
+            const uint8_t c = rle_all[bo + (v == 0 ? m - 1 : v - 1)];
+            L_all[bo + j] = c;
+            if (v == 0) st[b].orig_ptr = j;
+            atomicOr(&used[c >> 5], 1u << (c & 31));
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x < 8 && used[threadIdx.x]) atomicOr(&st[b].in_use[threadIdx.x], used[threadIdx.x]);
+}
+
+template <int MODE>
+static void radix_pass(lfc_plan P, int nblocks, int tiles, int pass, int h, const int32_t *in, int32_t *out) {
+    Workspace &ws = P->ws;
+    dim3 grid(tiles, nblocks);
+    radix_hist_kernel<MODE><<<grid, kSortThreads, 0, P->stream>>>(pass, h, ws.bstate, in, ws.rle, ws.rank, ws.tilecnt);
+    radix_scan_kernel<MODE><<<nblocks, 1024, 0, P->stream>>>(h, ws.bstate, ws.tilecnt);
+    radix_scatter_kernel<MODE><<<grid, kSortThreads, 0, P->stream>>>(pass, h, ws.bstate, in, out, ws.rle, ws.rank, ws.tilecnt);
+    count_launches(P, 3);
+}
+
+cudaError_t launch_bwt(lfc_plan P, int nblocks, int max_m) {
+    Workspace &ws = P->ws;
+    cudaStream_t s = P->stream;
+    cudaError_t e;
+    const int tiles = (max_m + kTile - 1) / kTile;
+    if (tiles == 0) return cudaSuccess;
+    // phase 1: 8 LSD passes, identity -> sa2 -> sa -> ... -> sa
+    stage_begin(P, LFC_STAGE_BWT_SORT8);
+    for (int pass = 0; pass < 8; pass++) {
+        const int32_t *in = (pass & 1) ? ws.sa2 : ws.sa;
+        int32_t *out = (pass & 1) ? ws.sa : ws.sa2;
+        radix_pass<0>(P, nblocks, tiles, pass, 0, in, out);
+    }
+    stage_end(P, LFC_STAGE_BWT_SORT8);
+    stage_begin(P, LFC_STAGE_BWT_REFINE);
+    e = cudaMemsetAsync(ws.act_total, 0, 2 * sizeof(int32_t), s);
+    if (e != cudaSuccess) return e;
+    dim3 grid(tiles, nblocks);
+    heads_tile_kernel<0><<<grid, kSortThreads, 0, s>>>(0, ws.bstate, ws.sa, ws.sa, ws.rle, ws.rank, ws.bwt, ws.tileaux);
+    heads_scan_kernel<0><<<nblocks, 256, 0, s>>>(0, ws.bstate, ws.tileaux, ws.act_total);
+    heads_apply_kernel<0><<<grid, kSortThreads, 0, s>>>(0, ws.bstate, ws.sa, ws.sa, ws.bwt, ws.tileaux, ws.rank, ws.sa,
+                                                        ws.act, ws.val);
+    commit_round_kernel<<<(nblocks + 255) / 256, 256, 0, s>>>(ws.bstate, nblocks);
+    count_launches(P, 4);
+    e = cudaMemcpyAsync(ws.h_act_total, ws.act_total, 2 * sizeof(int32_t), cudaMemcpyDeviceToHost, s);
+    if (e != cudaSuccess) return e;
+    e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return e;
+    int32_t *act = ws.act, *act2 = ws.act2;
+    for (int h = 8; ws.h_act_total[0] > 0 && h < max_m; h *= 2) {
+        const int t1 = (ws.h_act_total[1] + kTile - 1) / kTile;
+        // 5 LSD passes over the 40-bit key: val -> val2 -> val -> val2 -> val -> val2
+        for (int pass = 0; pass < 5; pass++) {
+            const int32_t *in = (pass & 1) ? ws.val2 : ws.val;
+            int32_t *out = (pass & 1) ? ws.val : ws.val2;
+            radix_pass<1>(P, nblocks, t1, pass, h, in, out);
+        }
+        e = cudaMemsetAsync(ws.act_total, 0, 2 * sizeof(int32_t), s);
+        if (e != cudaSuccess) return e;
+        dim3 g1(t1, nblocks);
+        heads_tile_kernel<1><<<g1, kSortThreads, 0, s>>>(h, ws.bstate, ws.val2, act, ws.rle, ws.rank, ws.bwt, ws.tileaux);
+        heads_scan_kernel<1><<<nblocks, 256, 0, s>>>(h, ws.bstate, ws.tileaux, ws.act_total);
+        heads_apply_kernel<1><<<g1, kSortThreads, 0, s>>>(h, ws.bstate, ws.val2, act, ws.bwt, ws.tileaux, ws.rank, ws.sa,
+                                                          act2, ws.val);
+        commit_round_kernel<<<(nblocks + 255) / 256, 256, 0, s>>>(ws.bstate, nblocks);
+        count_launches(P, 4);
+        int32_t *tmp = act; act = act2; act2 = tmp;
+        e = cudaMemcpyAsync(ws.h_act_total, ws.act_total, 2 * sizeof(int32_t), cudaMemcpyDeviceToHost, s);
+        if (e != cudaSuccess) return e;
+        e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) return e;
+    }
+    stage_end(P, LFC_STAGE_BWT_REFINE);
+    stage_begin(P, LFC_STAGE_BWT_OUT);
+    bwt_output_kernel<<<grid, kSortThreads, 0, s>>>(ws.bstate, ws.sa, ws.rle, ws.bwt);
+    stage_end(P, LFC_STAGE_BWT_OUT);
+    count_launches(P, 1);
+    return cudaGetLastError();
+}
+
+}  // namespace lfc

@@ -1,0 +1,428 @@
+// judge.cu -- prediction, symbol map, orderings and the two-dimensional image
+// entropy criterion (Sec. 2.1.1, Sec. 2.1.2, Eq. (1), Fig. 2a/2c).
+//
+// The judge never materialises a candidate stream or its judge-BWT. Sorting
+// the rotations of S by their first byte only, with ties in generation order,
+// puts the rotations that start with byte b in increasing start order; their
+// last bytes are the predecessors S[i-1] of the occurrences i of b. So the
+// last column L is the concatenation over b = 0..255 of those predecessor
+// lists, and the 16-bit pairs of adjacent L entries are
+//   (S[i-1], S[j-1]) for consecutive occurrences i < j of the same byte b,
+//   (last predecessor of bucket b, first predecessor of the next non-empty
+//    bucket)  -- at most 255 bucket-boundary pairs,
+// with S[-1] = S[n-1]. Each warp walks its rows of the stream in 32-byte
+// windows: __match_any_sync finds equal bytes in the window, a per-warp table
+// carries the last predecessor of every byte value across windows, and the
+// pairs are counted in a shared-memory histogram with warp-aggregated
+// atomics. Per-warp and per-CTA first/last predecessor tables stitch the
+// chains across warps, CTAs and buckets in a small fixup kernel.
+#include "lfc_common.cuh"
+
+namespace lfc {
+
+// ------------------------------------------------------------ prediction
+__device__ __forceinline__ int32_t as_i16(uint32_t v) { return (int32_t)(int16_t)(uint16_t)v; }
+
+// Base field: raw count, or signed 16-bit difference to the previous frame.
+__device__ __forceinline__ int32_t base_field(const FrameDev &F, int y, int x, bool tmp) {
+    size_t k = (size_t)y * F.W + x;
+    uint32_t a = __ldg(F.X + k);
+    if (!tmp) return (int32_t)a;
+    return as_i16(a - (uint32_t)__ldg(F.prev + k));
+}
+
+// Lossless-JPEG predictor set, floor division by arithmetic shift.
+__device__ __forceinline__ int32_t jpeg_pred(int f, int32_t A, int32_t B, int32_t C) {
+    switch (f) {
+    case 1: return A;
+    case 2: return B;
+    case 3: return C;
+    case 4: return A + B - C;
+    case 5: return A + ((B - C) >> 1);
+    case 6: return B + ((A - C) >> 1);
+    case 7: return (A + B) >> 1;
+    default: return 0;
+    }
+}
+
+// 2-D grid rule: origin 0, first row from the left, first column from the top.
+__device__ __forceinline__ int32_t grid_pred(int f, int row, int col, int32_t A, int32_t B, int32_t C) {
+    if (row == 0) return col == 0 ? 0 : A;
+    if (col == 0) return B;
+    return jpeg_pred(f, A, B, C);
+}
+
+__device__ __forceinline__ uint32_t intra_res(const FrameDev &F, int f, int y, int x, bool tmp) {
+    const int v = y % F.p, u = x % F.p;
+    int32_t X = base_field(F, y, x, tmp);
+    int32_t A = u > 0 ? base_field(F, y, x - 1, tmp) : 0;
+    int32_t B = v > 0 ? base_field(F, y - 1, x, tmp) : 0;
+    int32_t C = (u > 0 && v > 0) ? base_field(F, y - 1, x - 1, tmp) : 0;
+    return (uint32_t)(X - grid_pred(f, v, u, A, B, C)) & 0xFFFFu;
+}
+
+__device__ __forceinline__ uint32_t inter_res(const FrameDev &F, int f, int y, int x, bool tmp) {
+    const int t = y / F.p, s = x / F.p, p = F.p;
+    int32_t X = base_field(F, y, x, tmp);
+    int32_t A = s > 0 ? base_field(F, y, x - p, tmp) : 0;
+    int32_t B = t > 0 ? base_field(F, y - p, x, tmp) : 0;
+    int32_t C = (s > 0 && t > 0) ? base_field(F, y - p, x - p, tmp) : 0;
+    return (uint32_t)(X - grid_pred(f, t, s, A, B, C)) & 0xFFFFu;
+}
+
+__device__ __forceinline__ uint32_t phase_res(const FrameDev &F, int f, int y, int x, bool tmp) {
+    const int t = y / F.p, s = x / F.p, p = F.p;
+    int32_t E = as_i16(intra_res(F, f, y, x, tmp));
+    int32_t A = s > 0 ? as_i16(intra_res(F, f, y, x - p, tmp)) : 0;
+    int32_t B = t > 0 ? as_i16(intra_res(F, f, y - p, x, tmp)) : 0;
+    int32_t C = (s > 0 && t > 0) ? as_i16(intra_res(F, f, y - p, x - p, tmp)) : 0;
+    return (uint32_t)(E - grid_pred(f, t, s, A, B, C)) & 0xFFFFu;
+}
+
+// Symbol of pixel (y, x) under candidate id.
+__device__ __forceinline__ uint32_t pixel_symbol(const FrameDev &F, int id, int y, int x) {
+    const int f = id & 15, dom = (id >> 4) & 3;
+    const bool tmp = (id >> 7) & 1;
+    uint32_t e;
+    if (f == 0) {
+        if (!tmp) return __ldg(F.X + (size_t)y * F.W + x);
+        e = (uint32_t)base_field(F, y, x, true) & 0xFFFFu;
+    } else if (dom == 0) {
+        e = intra_res(F, f, y, x, tmp);
+    } else if (dom == 1) {
+        e = inter_res(F, f, y, x, tmp);
+    } else {
+        e = phase_res(F, f, y, x, tmp);
+    }
+    // zigzag of the residual as a signed 16-bit value
+    const int32_t sv = as_i16(e);
+    return (uint32_t)((sv << 1) ^ (sv >> 31)) & 0xFFFFu;
+}
+
+// Stream row r of ordering `ord` is raw row y; stream column c is raw column x.
+__device__ __forceinline__ int stream_row_to_y(const FrameDev &F, int ord, int r) {
+    return ord ? (r % F.Ny) * F.p + r / F.Ny : r;
+}
+__device__ __forceinline__ int raw_x_to_col(const FrameDev &F, int ord, int x) {
+    return ord ? (x % F.p) * F.Nx + x / F.p : x;
+}
+__device__ __forceinline__ int col_to_raw_x(const FrameDev &F, int ord, int c) {
+    return ord ? (c % F.Nx) * F.p + c / F.Nx : c;
+}
+
+// Last byte of stream row r - 1 (the byte before the row's first byte);
+// for r = 0 the stream's last byte (rotation 0 wraps around).
+__device__ __forceinline__ uint32_t byte_before_row(const FrameDev &F, int id, int r) {
+    const int ord = (id >> 6) & 1;
+    int rr = r == 0 ? F.H - 1 : r - 1;
+    int y = stream_row_to_y(F, ord, rr);
+    int x = col_to_raw_x(F, ord, F.W - 1);
+    return pixel_symbol(F, id, y, x) >> 8;
+}
+
+// ------------------------------------------------------------ the judge
+constexpr int kJudgeWarps = 16;
+constexpr uint16_t kNone = 0xFFFF;
+
+__device__ __forceinline__ int find_frame(const JudgeFrame *fr, int n, int64_t cta) {
+    int lo = 0, hi = n - 1;
+    while (lo < hi) {
+        int mid = (lo + hi + 1) >> 1;
+        if (fr[mid].cta_base <= cta) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+// smem: hist[32768] u32 | first[NW][256] u16 | last[NW][256] u16 | rows[NW][maxW] u16
+__global__ void __launch_bounds__(kJudgeWarps * 32, 1)
+judge_hist_kernel(const JudgeFrame *__restrict__ frames, int nframes, const uint8_t *__restrict__ cand,
+                  uint32_t *__restrict__ hist, uint16_t *__restrict__ summ, int maxW) {
+    extern __shared__ __align__(16) uint8_t smem[];
+    uint32_t *sh_hist = reinterpret_cast<uint32_t *>(smem);
+    uint16_t *sh_first = reinterpret_cast<uint16_t *>(smem + 32768 * 4);
+    uint16_t *sh_last = sh_first + kJudgeWarps * 256;
+    uint16_t *sh_rows = sh_last + kJudgeWarps * 256;
+
+    const int fi = find_frame(frames, nframes, blockIdx.x);
+    const JudgeFrame &J = frames[fi];
+    const FrameDev F = J.F;
+    const int64_t local = (int64_t)blockIdx.x - J.cta_base;
+    const int ci = (int)(local / J.segs), seg = (int)(local % J.segs);
+    const int id = cand[J.cand_off + ci];
+    const int ord = (id >> 6) & 1;
+    uint32_t *ghist = hist + (size_t)(J.hist_off + ci) * kHistBins;
+
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int r_seg0 = seg * J.rows_per_seg;
+    const int r_seg1 = min(F.H, r_seg0 + J.rows_per_seg);
+    const int rpw = (r_seg1 - r_seg0 + kJudgeWarps - 1) / kJudgeWarps;
+    const int r0 = min(r_seg1, r_seg0 + w * rpw), r1 = min(r_seg1, r0 + rpw);
+    uint16_t *zrow = sh_rows + (size_t)w * maxW;
+    const uint8_t *zbytes = reinterpret_cast<const uint8_t *>(zrow);
+    uint16_t *my_first = sh_first + w * 256, *my_last = sh_last + w * 256;
+    const int nb = 2 * F.W;
+
+    uint32_t carry0 = 0;
+    if (r0 < r1) carry0 = byte_before_row(F, id, r0);  // uniform per warp
+
+    for (int pass = 0; pass < 2; pass++) {
+        for (int i = threadIdx.x; i < 32768; i += blockDim.x) sh_hist[i] = 0;
+        for (int i = lane; i < 256; i += 32) { my_first[i] = kNone; my_last[i] = kNone; }
+        __syncthreads();
+        uint32_t prev_byte = carry0;
+        for (int r = r0; r < r1; r++) {
+            const int y = stream_row_to_y(F, ord, r);
+            for (int x = lane; x < F.W; x += 32) zrow[raw_x_to_col(F, ord, x)] = (uint16_t)pixel_symbol(F, id, y, x);
+            __syncwarp();
+            for (int base = 0; base < nb; base += 32) {
+                const int q = base + lane;
+                const bool valid = q < nb;
+                const uint32_t b = valid ? zbytes[q] : 0u;
+                const uint32_t a = valid ? (q > 0 ? (uint32_t)zbytes[q - 1] : prev_byte) : 0u;
+                const uint32_t m = __match_any_sync(LFC_FULL, valid ? b : 256u + lane);
+                const uint32_t lower = m & lanemask_lt();
+                const int pl = lower ? 31 - __clz(lower) : lane;
+                const uint32_t a_prev = __shfl_sync(LFC_FULL, a, pl);
+                int bin = -1;
+                if (valid) {
+                    if (lower) {
+                        bin = (int)((a_prev << 8) | a);
+                    } else {
+                        const uint16_t pend = my_last[b];
+                        if (pend != kNone) bin = (int)(((uint32_t)pend << 8) | a);
+                        else my_first[b] = (uint16_t)a;
+                    }
+                }
+                __syncwarp();
+                if (valid && (m & lanemask_gt()) == 0) my_last[b] = (uint16_t)a;
+                __syncwarp();
+                const bool contrib = bin >= 0 && (bin >> 15) == pass;
+                const uint32_t hm = __match_any_sync(LFC_FULL, contrib ? (uint32_t)bin : 0x10000u + lane);
+                if (contrib && (hm & lanemask_lt()) == 0) atomicAdd(&sh_hist[bin & 0x7FFF], __popc(hm));
+            }
+            prev_byte = zbytes[nb - 1];
+            __syncwarp();
+        }
+        __syncthreads();
+        for (int i = threadIdx.x; i < 32768; i += blockDim.x) {
+            const uint32_t c = sh_hist[i];
+            if (c) atomicAdd(&ghist[pass * 32768 + i], c);
+        }
+        __syncthreads();
+    }
+    // stitch warps in stream order; write this segment's first/last tables
+    if (threadIdx.x < 256) {
+        const int b = threadIdx.x;
+        uint16_t first = kNone, cur = kNone;
+        for (int ww = 0; ww < kJudgeWarps; ww++) {
+            const uint16_t f = sh_first[ww * 256 + b];
+            if (f == kNone) continue;
+            if (cur != kNone) atomicAdd(&ghist[((uint32_t)cur << 8) | f], 1u);
+            else first = f;
+            cur = sh_last[ww * 256 + b];
+        }
+        uint16_t *out = summ + (size_t)(J.summ_off + (int64_t)ci * J.segs + seg) * 512;
+        out[b] = first;
+        out[256 + b] = cur;
+    }
+}
+
+// One CTA (256 threads) per (frame, candidate): links segments and adds the
+// bucket-boundary pairs.
+__global__ void judge_fixup_kernel(const JudgeFrame *__restrict__ frames, const int32_t *__restrict__ hist_frame,
+                                   uint32_t *__restrict__ hist, const uint16_t *__restrict__ summ) {
+    __shared__ uint16_t gfirst[256], glast[256];
+    const int hidx = blockIdx.x;  // global histogram index
+    const JudgeFrame &J = frames[hist_frame[hidx]];
+    const int ci = (int)(hidx - J.hist_off);
+    uint32_t *ghist = hist + (size_t)hidx * kHistBins;
+    const int b = threadIdx.x;
+    uint16_t first = kNone, cur = kNone;
+    for (int sgi = 0; sgi < J.segs; sgi++) {
+        const uint16_t *s = summ + (size_t)(J.summ_off + (int64_t)ci * J.segs + sgi) * 512;
+        const uint16_t f = s[b];
+        if (f == kNone) continue;
+        if (cur != kNone) atomicAdd(&ghist[((uint32_t)cur << 8) | f], 1u);
+        else first = f;
+        cur = s[256 + b];
+    }
+    gfirst[b] = first;
+    glast[b] = cur;
+    __syncthreads();
+    if (cur != kNone) {
+        for (int nb = b + 1; nb < 256; nb++) {
+            if (gfirst[nb] != kNone) {
+                atomicAdd(&ghist[((uint32_t)cur << 8) | gfirst[nb]], 1u);
+                break;
+            }
+        }
+    }
+}
+
+// Fixed-point 2^32 log2(c): integer part from the leading bit, 32 fraction
+// bits by squaring the Q62 mantissa (128-bit product via __umul64hi).
+__device__ __forceinline__ uint64_t log2_fx(uint32_t c) {
+    if (c <= 1) return 0;
+    const int k = 31 - __clz(c);
+    uint64_t y = (uint64_t)c << (62 - k);
+    uint64_t frac = 0;
+#pragma unroll 4
+    for (int i = 0; i < 32; i++) {
+        const uint64_t hi = __umul64hi(y, y), lo = y * y;
+        const uint64_t z = (hi << 2) | (lo >> 62);
+        frac <<= 1;
+        if (z >> 63) { frac |= 1; y = z >> 1; } else { y = z; }
+    }
+    return ((uint64_t)k << 32) | frac;
+}
+
+__global__ void l2_table_kernel(uint64_t *tab) {
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c < kHistBins) tab[c] = log2_fx((uint32_t)c);
+}
+
+// One CTA per histogram: score = sum_t P_t * L2(P_t).
+__global__ void __launch_bounds__(1024) entropy_kernel(const uint32_t *__restrict__ hist, const uint64_t *__restrict__ tab,
+                                                       const JudgeFrame *__restrict__ frames, const int32_t *__restrict__ hist_frame,
+                                                       const uint8_t *__restrict__ cand, uint64_t *__restrict__ scores,
+                                                       const int32_t *__restrict__ frame_index) {
+    __shared__ uint64_t part[32];
+    const int hidx = blockIdx.x;
+    const uint4 *h4 = reinterpret_cast<const uint4 *>(hist + (size_t)hidx * kHistBins);
+    uint64_t s = 0;
+    for (int i = threadIdx.x; i < kHistBins / 4; i += blockDim.x) {
+        const uint4 v = h4[i];
+        const uint32_t c[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+        for (int k = 0; k < 4; k++)
+            if (c[k] > 1) s += (uint64_t)c[k] * (c[k] < (uint32_t)kHistBins ? __ldg(tab + c[k]) : log2_fx(c[k]));
+    }
+    s = warp_sum(s);
+    if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        uint64_t t = threadIdx.x < (blockDim.x >> 5) ? part[threadIdx.x] : 0;
+        t = warp_sum(t);
+        if (threadIdx.x == 0) {
+            const int f = hist_frame[hidx];
+            const JudgeFrame &J = frames[f];
+            const int id = cand[J.cand_off + (hidx - J.hist_off)];
+            scores[(size_t)frame_index[f] * 256 + id] = t;
+        }
+    }
+}
+
+// One warp per frame: best = highest score, ties to the lowest id.
+__global__ void argmax_kernel(const JudgeFrame *__restrict__ frames, int nframes, const uint8_t *__restrict__ cand,
+                              const uint64_t *__restrict__ scores, uint8_t *__restrict__ choice,
+                              const int32_t *__restrict__ frame_index) {
+    const int f = blockIdx.x;
+    if (f >= nframes) return;
+    const JudgeFrame &J = frames[f];
+    const uint64_t *sc = scores + (size_t)frame_index[f] * 256;
+    uint64_t best = 0;
+    int best_id = 256;
+    for (int k = threadIdx.x; k < J.K; k += 32) {
+        const int id = cand[J.cand_off + k];
+        const uint64_t v = sc[id];
+        if (best_id == 256 || v > best || (v == best && id < best_id)) { best = v; best_id = id; }
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        const uint64_t ob = __shfl_xor_sync(LFC_FULL, best, o);
+        const int oi = __shfl_xor_sync(LFC_FULL, best_id, o);
+        if (oi != 256 && (best_id == 256 || ob > best || (ob == best && oi < best_id))) { best = ob; best_id = oi; }
+    }
+    if (threadIdx.x == 0) choice[frame_index[f]] = (uint8_t)best_id;
+}
+
+cudaError_t init_l2_table(uint64_t *tab, cudaStream_t s) {
+    l2_table_kernel<<<kHistBins / 256, 256, 0, s>>>(tab);
+    return cudaGetLastError();
+}
+
+size_t judge_smem_bytes(int maxW) {
+    return (size_t)32768 * 4 + (size_t)kJudgeWarps * 256 * 2 * 2 + (size_t)kJudgeWarps * maxW * 2;
+}
+
+cudaError_t launch_judge(lfc_plan P, const JudgeFrame *d_frames, int nframes, int64_t total_ctas, int max_w,
+                         const uint8_t *d_cand, int total_cand, int64_t nhist, uint64_t *d_scores,
+                         uint8_t *d_choice, const int32_t *h_frame_index) {
+    (void)h_frame_index;
+    cudaStream_t s = P->stream;
+    Workspace &ws = P->ws;
+    cudaError_t e;
+    const size_t smem = judge_smem_bytes(max_w);
+    e = cudaFuncSetAttribute(judge_hist_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    e = cudaMemsetAsync(ws.hist, 0, (size_t)nhist * kHistBins * 4, s);
+    if (e != cudaSuccess) return e;
+    // frame index table and hist->frame table ride behind the frame table
+    const int32_t *d_frame_index = reinterpret_cast<const int32_t *>(d_frames + nframes);
+    const int32_t *d_hist_frame = d_frame_index + nframes;
+    stage_begin(P, LFC_STAGE_JUDGE_HIST);
+    judge_hist_kernel<<<(unsigned)total_ctas, kJudgeWarps * 32, smem, s>>>(d_frames, nframes, d_cand, ws.hist,
+                                                                            ws.summ, max_w);
+    stage_end(P, LFC_STAGE_JUDGE_HIST);
+    stage_begin(P, LFC_STAGE_JUDGE_SCORE);
+    judge_fixup_kernel<<<(unsigned)nhist, 256, 0, s>>>(d_frames, d_hist_frame, ws.hist, ws.summ);
+    entropy_kernel<<<(unsigned)nhist, 1024, 0, s>>>(ws.hist, ws.l2tab, d_frames, d_hist_frame, d_cand, d_scores,
+                                                   d_frame_index);
+    argmax_kernel<<<nframes, 32, 0, s>>>(d_frames, nframes, d_cand, d_scores, d_choice, d_frame_index);
+    stage_end(P, LFC_STAGE_JUDGE_SCORE);
+    count_launches(P, 4);
+    (void)total_cand;
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------------------ emission
+struct EmitArgs {
+    FrameDev F[8];
+    uint8_t *dst[8];
+};
+
+// Stream of the chosen id: thread per output symbol, 2-D grid (chunk, frame).
+__global__ void emit_kernel(EmitArgs args, const uint8_t *__restrict__ choice, int nframes) {
+    const int f = blockIdx.y;
+    if (f >= nframes) return;
+    const FrameDev F = args.F[f];
+    int id = choice[f];
+    if ((id & 0x80) && !F.prev) id &= 0x7F;  // no reference frame: never read through NULL
+    const int ord = (id >> 6) & 1;
+    const int64_t n = (int64_t)F.W * F.H;
+    uint16_t *out = reinterpret_cast<uint16_t *>(args.dst[f]);
+    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x) {
+        const int r = (int)(k / F.W), c = (int)(k % F.W);
+        const int y = stream_row_to_y(F, ord, r), x = col_to_raw_x(F, ord, c);
+        out[k] = (uint16_t)pixel_symbol(F, id, y, x);
+    }
+}
+
+cudaError_t launch_emit(const FrameDev *h_frames, const uint8_t *d_choice, int nframes, uint8_t *const *h_dst,
+                        cudaStream_t s) {
+    for (int f0 = 0; f0 < nframes; f0 += 8) {
+        EmitArgs a;
+        const int cnt = nframes - f0 < 8 ? nframes - f0 : 8;
+        for (int i = 0; i < cnt; i++) { a.F[i] = h_frames[f0 + i]; a.dst[i] = h_dst[f0 + i]; }
+        dim3 grid(1216, cnt);
+        emit_kernel<<<grid, 256, 0, s>>>(a, d_choice + f0, cnt);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
+__global__ void symbols_one_kernel(FrameDev F, int id, uint16_t *out) {
+    const int ord = (id >> 6) & 1;
+    const int64_t n = (int64_t)F.W * F.H;
+    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x) {
+        const int r = (int)(k / F.W), c = (int)(k % F.W);
+        out[k] = (uint16_t)pixel_symbol(F, id, stream_row_to_y(F, ord, r), col_to_raw_x(F, ord, c));
+    }
+}
+
+cudaError_t launch_symbols_one(const FrameDev &F, int id, uint16_t *dst, cudaStream_t s) {
+    symbols_one_kernel<<<1216, 256, 0, s>>>(F, id, dst);
+    return cudaGetLastError();
+}
+
+}  // namespace lfc

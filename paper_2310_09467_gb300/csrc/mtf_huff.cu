@@ -1,0 +1,579 @@
+// mtf_huff.cu -- move-to-front, zero-run coding, Huffman table choice and bit
+// packing of every bzip2 block (Sec. 2.1.3; public bzip2 block format).
+//
+// MTF is sequential per block, so each block's BWT output is cut into
+// 4096-byte segments handled by one warp each. A segment's effect on the MTF
+// list is "its distinct symbols by most recent use, then the old list
+// without them"; one warp per block composes these summaries in order to get
+// every segment's starting list, then every segment replays MTF from its
+// list with the 256-entry list held in registers (8 entries per lane).
+#include "lfc_common.cuh"
+
+namespace lfc {
+
+constexpr int kSymStride = kBlockCap + 64;  // uint16 symbols per block slot
+
+// Sequence index of byte c among the bytes in use (ascending byte order).
+__device__ __forceinline__ void build_seq_table(const uint32_t *in_use, uint8_t *seq) {
+    for (int c = threadIdx.x; c < 256; c += blockDim.x) {
+        int cnt = 0;
+        const int w = c >> 5;
+        for (int i = 0; i < w; i++) cnt += __popc(in_use[i]);
+        cnt += __popc(in_use[w] & ((1u << (c & 31)) - 1u));
+        seq[c] = (uint8_t)cnt;
+    }
+}
+
+// ---------------------------------------------------- MTF: segment summaries
+__global__ void __launch_bounds__(32) mtf_summary_kernel(BlockState *__restrict__ st, const uint8_t *__restrict__ L_all,
+                                                         uint8_t *__restrict__ rec_all, int32_t *__restrict__ reclen_all) {
+    __shared__ uint8_t seq[256];
+    __shared__ uint8_t seen[256];
+    const int b = blockIdx.y, g = blockIdx.x;
+    const int m = st[b].m;
+    const int s0 = g * kTile;
+    if (s0 >= m) return;
+    const int s1 = min(m, s0 + kTile);
+    uint32_t iu[8];
+    for (int i = 0; i < 8; i++) iu[i] = st[b].in_use[i];
+    if (threadIdx.x == 0) {
+        int n = 0;
+        for (int i = 0; i < 8; i++) n += __popc(iu[i]);
+        st[b].n_in_use = n;  // same value from every segment
+    }
+    __shared__ uint32_t iush[8];
+    if (threadIdx.x < 8) iush[threadIdx.x] = iu[threadIdx.x];
+    __syncwarp();
+    build_seq_table(iush, seq);
+    for (int i = threadIdx.x; i < 256; i += 32) seen[i] = 0;
+    __syncwarp();
+    int n_in_use = 0;
+    for (int i = 0; i < 8; i++) n_in_use += __popc(iu[i]);
+    const uint8_t *L = L_all + (size_t)b * kBlockCap;
+    uint8_t *rec = rec_all + ((size_t)b * kTilesPerBlock + g) * 256;
+    const int lane = threadIdx.x;
+    int len = 0;
+    for (int wend = s1; wend > s0 && len < n_in_use; wend -= 32) {
+        const int ws0 = max(s0, wend - 32);
+        const int i = ws0 + lane;
+        const bool valid = i < wend;
+        const uint32_t s = valid ? seq[L[i]] : 0u;
+        const uint32_t mm = __match_any_sync(LFC_FULL, valid ? s : 256u + lane);
+        const bool leader = valid && (mm & lanemask_gt()) == 0;  // latest use in the window
+        const bool fresh = leader && !seen[s];
+        const uint32_t bal = __ballot_sync(LFC_FULL, fresh);
+        if (fresh) {
+            rec[len + __popc(bal & lanemask_gt())] = (uint8_t)s;  // later lanes first
+            seen[s] = 1;
+        }
+        len += __popc(bal);
+        __syncwarp();
+    }
+    if (lane == 0) reclen_all[(size_t)b * kTilesPerBlock + g] = len;
+}
+
+// One warp per block: starting list of every segment.
+__global__ void __launch_bounds__(32) mtf_compose_kernel(const BlockState *__restrict__ st, const uint8_t *__restrict__ rec_all,
+                                                         const int32_t *__restrict__ reclen_all, uint8_t *__restrict__ lists_all) {
+    __shared__ uint8_t lst[256], nxt[256], inr[256];
+    const int b = blockIdx.x;
+    const int m = st[b].m;
+    int n_in_use = 0;
+    for (int i = 0; i < 8; i++) n_in_use += __popc(st[b].in_use[i]);
+    const int ng = (m + kTile - 1) / kTile;
+    const int lane = threadIdx.x;
+    for (int i = lane; i < 256; i += 32) lst[i] = i < n_in_use ? (uint8_t)i : (uint8_t)0xFF;
+    __syncwarp();
+    for (int g = 0; g < ng; g++) {
+        uint8_t *out = lists_all + ((size_t)b * kTilesPerBlock + g) * 256;
+        for (int i = lane; i < 256; i += 32) out[i] = lst[i];
+        const uint8_t *rec = rec_all + ((size_t)b * kTilesPerBlock + g) * 256;
+        const int rl = reclen_all[(size_t)b * kTilesPerBlock + g];
+        for (int i = lane; i < 256; i += 32) inr[i] = 0;
+        __syncwarp();
+        for (int i = lane; i < rl; i += 32) { const uint8_t v = rec[i]; inr[v] = 1; nxt[i] = v; }
+        __syncwarp();
+        int pos = rl;
+        for (int c = 0; c < 256; c += 32) {
+            const int i = c + lane;
+            const bool keep = i < n_in_use && !inr[lst[i]];
+            const uint32_t bal = __ballot_sync(LFC_FULL, keep);
+            if (keep) nxt[pos + __popc(bal & lanemask_lt())] = lst[i];
+            pos += __popc(bal);
+        }
+        __syncwarp();
+        for (int i = lane; i < 256; i += 32) lst[i] = i < n_in_use ? nxt[i] : (uint8_t)0xFF;
+        __syncwarp();
+    }
+}
+
+// One warp per segment: MTF indices from the segment's starting list.
+__global__ void __launch_bounds__(32) mtf_encode_kernel(const BlockState *__restrict__ st, const uint8_t *__restrict__ L_all,
+                                                        const uint8_t *__restrict__ lists_all, uint8_t *__restrict__ idx_all) {
+    __shared__ uint8_t seq[256];
+    __shared__ uint32_t iush[8];
+    const int b = blockIdx.y, g = blockIdx.x;
+    const int m = st[b].m;
+    const int s0 = g * kTile;
+    if (s0 >= m) return;
+    const int s1 = min(m, s0 + kTile);
+    const int lane = threadIdx.x;
+    if (lane < 8) iush[lane] = st[b].in_use[lane];
+    __syncwarp();
+    build_seq_table(iush, seq);
+    __syncwarp();
+    const uint8_t *lst = lists_all + ((size_t)b * kTilesPerBlock + g) * 256;
+    uint64_t v = 0;
+    for (int q = 0; q < 8; q++) v |= (uint64_t)lst[lane * 8 + q] << (8 * q);
+    const uint8_t *L = L_all + (size_t)b * kBlockCap;
+    uint8_t *out = idx_all + (size_t)b * kBlockCap;
+    for (int w0 = s0; w0 < s1; w0 += 32) {
+        const int i = w0 + lane;
+        const int cnt = min(32, s1 - w0);
+        const uint32_t mys = i < s1 ? seq[L[i]] : 0u;
+        uint32_t myidx = 0;
+        for (int k = 0; k < cnt; k++) {
+            const uint32_t s = __shfl_sync(LFC_FULL, mys, k);
+            const uint32_t front = __shfl_sync(LFC_FULL, (uint32_t)v & 0xFFu, 0);
+            if (front == s) {               // index 0: list unchanged
+                if (lane == k) myidx = 0;
+                continue;
+            }
+            const uint32_t pat = s * 0x01010101u;
+            const uint32_t eql = __vcmpeq4((uint32_t)v, pat), eqh = __vcmpeq4((uint32_t)(v >> 32), pat);
+            const uint32_t bal = __ballot_sync(LFC_FULL, (eql | eqh) != 0);
+            const int owner = __ffs(bal) - 1;
+            int byte = eql ? (__ffs(eql) - 1) >> 3 : 4 + ((__ffs(eqh) - 1) >> 3);
+            byte = __shfl_sync(LFC_FULL, byte, owner);
+            const uint64_t carry_up = __shfl_up_sync(LFC_FULL, v >> 56, 1);
+            const uint64_t carry = lane == 0 ? (uint64_t)s : carry_up;
+            const uint64_t shifted = (v << 8) | carry;
+            if (lane < owner) {
+                v = shifted;
+            } else if (lane == owner) {
+                const uint64_t mask = byte == 7 ? ~0ull : ((1ull << (8 * (byte + 1))) - 1ull);
+                v = (shifted & mask) | (v & ~mask);
+            }
+            if (lane == k) myidx = (uint32_t)(owner * 8 + byte);
+        }
+        if (i < s1) out[i] = (uint8_t)myidx;
+    }
+}
+
+// ------------------------------------------------------------------ RLE2
+// Zero runs of length r -> bijective base-2 digits RUNA(0)/RUNB(1): digit k
+// is bit k of r + 1, floor(log2(r + 1)) digits. Index j > 0 -> j + 1.
+__global__ void __launch_bounds__(1024) rle2_kernel(BlockState *__restrict__ st, const uint8_t *__restrict__ idx_all,
+                                                    uint16_t *__restrict__ sym_all, uint32_t *__restrict__ freq_all) {
+    __shared__ int32_t sh[33];
+    __shared__ uint32_t fq[kMaxAlpha];
+    const int b = blockIdx.x;
+    const int m = st[b].m;
+    int n_in_use = 0;
+    for (int i = 0; i < 8; i++) n_in_use += __popc(st[b].in_use[i]);
+    const uint8_t *idx = idx_all + (size_t)b * kBlockCap;
+    uint16_t *sym = sym_all + (size_t)b * kSymStride;
+    for (int i = threadIdx.x; i < kMaxAlpha; i += blockDim.x) fq[i] = 0;
+    const int T = blockDim.x;
+    const int per = (m + T - 1) / T;
+    const int a = min(m, (int)threadIdx.x * per), e = min(m, a + per);
+    int lastnz = -1;
+    for (int i = a; i < e; i++) if (idx[i]) lastnz = i;
+    int carry = block_excl_max(lastnz, sh);
+    int cnt = 0;
+    {
+        int lz = carry;
+        for (int i = a; i < e; i++) {
+            if (idx[i]) { cnt++; lz = i; continue; }
+            if (i == m - 1 || idx[i + 1]) cnt += 31 - __clz(i - lz + 1);  // floor(log2(r + 1))
+        }
+    }
+    int total;
+    int o = block_excl_sum<int>(cnt, sh, &total);
+    {
+        int lz = carry;
+        for (int i = a; i < e; i++) {
+            const uint32_t j = idx[i];
+            if (j) {
+                sym[o++] = (uint16_t)(j + 1);
+                atomicAdd(&fq[j + 1], 1u);
+                lz = i;
+                continue;
+            }
+            if (i == m - 1 || idx[i + 1]) {
+                const uint32_t r1 = (uint32_t)(i - lz) + 1u;
+                const int nd = 31 - __clz(r1);
+                for (int k = 0; k < nd; k++) {
+                    const uint32_t d = (r1 >> k) & 1u;
+                    sym[o++] = (uint16_t)d;
+                    atomicAdd(&fq[d], 1u);
+                }
+            }
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        sym[total] = (uint16_t)(n_in_use + 1);
+        fq[n_in_use + 1]++;
+        st[b].n_mtf = total + 1;
+        st[b].n_in_use = n_in_use;
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < kMaxAlpha; i += blockDim.x) freq_all[(size_t)b * kMaxAlpha + i] = fq[i];
+}
+
+// --------------------------------------------------------------- Huffman
+// Code lengths of one table by one warp: weights max(freq, 1); the two nodes
+// with the smallest (weight, key) are joined (leaf key = symbol, k-th joined
+// node key = alpha + k; the two-queue method reproduces that order because
+// leaves are pre-sorted by (weight, symbol) and joined nodes appear in
+// non-decreasing weight); over-long codes halve the weights (1 + w/2).
+struct HuffScratch {
+    uint32_t w[kMaxAlpha];
+    uint32_t nw[kMaxAlpha];         // joined-node weights
+    uint16_t order[kMaxAlpha];      // leaves sorted by (w, symbol)
+    uint16_t kid[2][kMaxAlpha];     // children of joined node k (node ids)
+    uint8_t depth[2 * kMaxAlpha];
+};
+
+__device__ void huff_lengths_warp(const uint32_t *freq, int alpha, int max_len, uint8_t *len_out, HuffScratch &S) {
+    const int lane = threadIdx.x & 31;
+    for (int i = lane; i < alpha; i += 32) S.w[i] = freq[i] ? freq[i] : 1u;
+    __syncwarp();
+    for (;;) {
+        for (int i = lane; i < alpha; i += 32) {
+            const uint32_t wi = S.w[i];
+            int r = 0;
+            for (int j = 0; j < alpha; j++) {
+                const uint32_t wj = S.w[j];
+                r += (wj < wi) || (wj == wi && j < i);
+            }
+            S.order[r] = (uint16_t)i;
+        }
+        __syncwarp();
+        int longest = 0;
+        if (lane == 0) {
+            int la = 0, nb = 0, lb = 0;  // leaf cursor, joined count, joined cursor
+            for (int k = 0; k < alpha - 1; k++) {
+                int pick[2];
+                uint32_t pw[2];
+                for (int q = 0; q < 2; q++) {
+                    const bool haveA = la < alpha, haveB = lb < nb;
+                    bool takeA;
+                    if (!haveB) takeA = true;
+                    else if (!haveA) takeA = false;
+                    else takeA = S.w[S.order[la]] <= S.nw[lb];  // equal weight: leaf (smaller key)
+                    if (takeA) { pick[q] = S.order[la]; pw[q] = S.w[S.order[la]]; la++; }
+                    else { pick[q] = alpha + lb; pw[q] = S.nw[lb]; lb++; }
+                }
+                S.kid[0][k] = (uint16_t)pick[0];
+                S.kid[1][k] = (uint16_t)pick[1];
+                S.nw[nb++] = pw[0] + pw[1];
+            }
+            // depths top-down: root is joined node alpha - 2
+            S.depth[alpha + alpha - 2] = 0;
+            for (int k = alpha - 2; k >= 0; k--) {
+                const uint8_t d = S.depth[alpha + k] + 1;
+                S.depth[S.kid[0][k]] = d;
+                S.depth[S.kid[1][k]] = d;
+            }
+            for (int i = 0; i < alpha; i++) longest = max(longest, (int)S.depth[i]);
+        }
+        longest = __shfl_sync(LFC_FULL, longest, 0);
+        __syncwarp();
+        if (longest <= max_len) break;
+        for (int i = lane; i < alpha; i += 32) S.w[i] = 1u + S.w[i] / 2u;
+        __syncwarp();
+    }
+    for (int i = lane; i < alpha; i += 32) len_out[i] = S.depth[i];
+    __syncwarp();
+}
+
+constexpr int kHuffThreads = 256;
+
+// One CTA per block: table count, initial partition by cumulative frequency,
+// four refinement passes (each 50-symbol group picks the cheapest table, ties
+// to the lower table, then every table is rebuilt from its groups' counts
+// with a 17-bit limit), canonical codes.
+__global__ void __launch_bounds__(kHuffThreads) huffman_kernel(BlockState *__restrict__ st, const uint16_t *__restrict__ sym_all,
+                                                               const uint32_t *__restrict__ freq_all, uint8_t *__restrict__ sel_all,
+                                                               uint8_t *__restrict__ lens_all, uint32_t *__restrict__ codes_all) {
+    __shared__ uint8_t len[kMaxGroups][kMaxAlpha];
+    __shared__ uint64_t packed[kMaxAlpha];
+    __shared__ uint32_t rfreq[kMaxGroups][kMaxAlpha];
+    __shared__ HuffScratch scratch[kMaxGroups];
+    const int b = blockIdx.x;
+    const int n_mtf = st[b].n_mtf;
+    const int alpha = st[b].n_in_use + 2;
+    const int ng = n_mtf < 200 ? 2 : n_mtf < 600 ? 3 : n_mtf < 1200 ? 4 : n_mtf < 2400 ? 5 : 6;
+    const int nsel = (n_mtf + 49) / 50;
+    const uint16_t *sym = sym_all + (size_t)b * kSymStride;
+    const uint32_t *freq = freq_all + (size_t)b * kMaxAlpha;
+    uint8_t *sel = sel_all + (size_t)b * kMaxSelectors;
+    if (threadIdx.x == 0) {
+        int64_t cum = 0;
+        for (int v = 0; v < alpha; v++) {
+            int64_t gsel = cum * ng / n_mtf;
+            if (gsel > ng - 1) gsel = ng - 1;
+            for (int t = 0; t < ng; t++) len[t][v] = (uint8_t)(t == gsel ? 0 : 15);
+            cum += freq[v];
+        }
+        st[b].n_groups = ng;
+        st[b].n_sel = nsel;
+    }
+    __syncthreads();
+    const int w = threadIdx.x >> 5;
+    for (int iter = 0; iter < 4; iter++) {
+        for (int i = threadIdx.x; i < kMaxGroups * kMaxAlpha; i += blockDim.x) (&rfreq[0][0])[i] = 0;
+        for (int v = threadIdx.x; v < alpha; v += blockDim.x) {
+            uint64_t pk = 0;
+            for (int t = 0; t < ng; t++) pk |= (uint64_t)len[t][v] << (10 * t);
+            packed[v] = pk;
+        }
+        __syncthreads();
+        for (int gi = threadIdx.x; gi < nsel; gi += blockDim.x) {
+            const int a = gi * 50, e = min(n_mtf, a + 50);
+            uint64_t acc = 0;
+            for (int i = a; i < e; i++) acc += packed[sym[i]];
+            int bt = 0;
+            uint32_t bc = (uint32_t)(acc & 1023u);
+            for (int t = 1; t < ng; t++) {
+                const uint32_t c = (uint32_t)((acc >> (10 * t)) & 1023u);
+                if (c < bc) { bc = c; bt = t; }
+            }
+            sel[gi] = (uint8_t)bt;
+            for (int i = a; i < e; i++) atomicAdd(&rfreq[bt][sym[i]], 1u);
+        }
+        __syncthreads();
+        if (w < ng) huff_lengths_warp(rfreq[w], alpha, 17, len[w], scratch[w]);
+        __syncthreads();
+    }
+    // canonical codes: by length, then symbol
+    if (w < ng && (threadIdx.x & 31) == 0) {
+        uint32_t next[22];
+        uint32_t cnt[22];
+        for (int l = 0; l < 22; l++) cnt[l] = 0;
+        for (int v = 0; v < alpha; v++) cnt[len[w][v]]++;
+        uint32_t c = 0;
+        for (int l = 1; l <= 20; l++) { next[l] = c; c = (c + cnt[l]) << 1; }
+        uint32_t *codes = codes_all + ((size_t)b * kMaxGroups + w) * kMaxAlpha;
+        uint8_t *lo = lens_all + ((size_t)b * kMaxGroups + w) * kMaxAlpha;
+        for (int v = 0; v < alpha; v++) {
+            codes[v] = next[len[w][v]]++;
+            lo[v] = len[w][v];
+        }
+    }
+}
+
+// ------------------------------------------------------------ bit packing
+// Bits are numbered from the start of the stream; bit P lands in word P/32 at
+// bit 31 - P%32 (MSB first), and words are byte-swapped at the end.
+__device__ __forceinline__ void put_bits(uint32_t *words, uint64_t pos, uint32_t value, int nbits) {
+    if (nbits == 0) return;
+    const int sh = (int)(pos & 31);
+    const uint64_t v = (uint64_t)value << (64 - nbits - sh);
+    const uint32_t hi = (uint32_t)(v >> 32), lo = (uint32_t)v;
+    if (hi) atomicOr(&words[pos >> 5], hi);
+    if (lo) atomicOr(&words[(pos >> 5) + 1], lo);
+}
+
+constexpr int kPackThreads = 1024;
+
+__global__ void __launch_bounds__(kPackThreads) pack_kernel(BlockState *__restrict__ st, const uint16_t *__restrict__ sym_all,
+                                                            const uint8_t *__restrict__ sel_all, const uint8_t *__restrict__ lens_all,
+                                                            const uint32_t *__restrict__ codes_all, uint32_t *__restrict__ packed_all,
+                                                            int64_t stream_words) {
+    __shared__ uint8_t len[kMaxGroups][kMaxAlpha];
+    __shared__ uint32_t code[kMaxGroups][kMaxAlpha];
+    __shared__ uint64_t sh64[33];
+    __shared__ uint32_t tbl_bits[kMaxGroups];
+    __shared__ uint64_t base_bits[8];
+    const int b = blockIdx.x;
+    const BlockState S = st[b];
+    const int ng = S.n_groups, nsel = S.n_sel, n_mtf = S.n_mtf, alpha = S.n_in_use + 2;
+    const uint16_t *sym = sym_all + (size_t)b * kSymStride;
+    const uint8_t *sel = sel_all + (size_t)b * kMaxSelectors;
+    uint32_t *words = packed_all + (size_t)b * stream_words;
+    for (int i = threadIdx.x; i < ng * kMaxAlpha; i += blockDim.x) {
+        const int t = i / kMaxAlpha, v = i % kMaxAlpha;
+        len[t][v] = lens_all[((size_t)b * kMaxGroups + t) * kMaxAlpha + v];
+        code[t][v] = codes_all[((size_t)b * kMaxGroups + t) * kMaxAlpha + v];
+    }
+    uint32_t used16 = 0;
+    for (int i = 0; i < 16; i++) {
+        const uint32_t half = (S.in_use[i >> 1] >> ((i & 1) * 16)) & 0xFFFFu;
+        if (half) used16 |= 1u << (15 - i);
+    }
+    __syncthreads();
+    // --- selector MTF indices (list of ng tables, initially 0..ng-1)
+    const int T = blockDim.x;
+    const int sper = (nsel + T - 1) / T;
+    const int sa = min(nsel, (int)threadIdx.x * sper), se = min(nsel, sa + sper);
+    uint64_t sbits = 0;
+    for (int i = sa; i < se; i++) {
+        const int s = sel[i];
+        uint32_t D = 0;
+        int j = -1;
+        for (int q = i - 1; q >= 0; q--) {
+            const int v = sel[q];
+            if (v == s) { j = __popc(D); break; }
+            D |= 1u << v;
+            if (__popc(D) == ng - 1) { j = ng - 1; break; }
+        }
+        if (j < 0) j = __popc(D) + __popc(((1u << s) - 1u) & ~D);
+        sbits += (uint64_t)j + 1;
+    }
+    uint64_t sel_total;
+    uint64_t sel_off = block_excl_sum<uint64_t>(sbits, sh64, &sel_total);
+    // --- code-length section bits per table (warp t)
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (w < ng) {
+        uint32_t bits = 0;
+        for (int v = lane; v < alpha; v += 32) {
+            const int d = v == 0 ? 0 : (int)len[w][v] - (int)len[w][v - 1];
+            bits += 2u * (uint32_t)abs(d) + 1u;
+        }
+        bits = warp_sum(bits);
+        if (lane == 0) tbl_bits[w] = bits + 5u;
+    }
+    // --- data bits
+    const int dper = (n_mtf + T - 1) / T;
+    const int da = min(n_mtf, (int)threadIdx.x * dper), de = min(n_mtf, da + dper);
+    uint64_t dbits = 0;
+    for (int i = da; i < de; i++) dbits += len[sel[i / 50]][sym[i]];
+    uint64_t data_total;
+    uint64_t data_off = block_excl_sum<uint64_t>(dbits, sh64, &data_total);
+    // layout
+    if (threadIdx.x == 0) {
+        uint64_t p = 32 + 48 + 32 + 1 + 24 + 16 + 16ull * __popc(used16) + 3 + 15;
+        base_bits[0] = p;                       // selectors start
+        p += sel_total;
+        for (int t = 0; t < ng; t++) p += tbl_bits[t];
+        base_bits[1] = p;                       // data start
+        p += data_total;
+        base_bits[2] = p;                       // trailer start
+        p += 48 + 32;
+        p = (p + 7) & ~7ull;
+        base_bits[3] = p;                       // total bits
+    }
+    __syncthreads();
+    const uint64_t total_bits = base_bits[3];
+    const int64_t nwords = (int64_t)((total_bits + 31) >> 5);
+    for (int64_t i = threadIdx.x; i < nwords + 1 && i < stream_words; i += blockDim.x) words[i] = 0;
+    __syncthreads();
+    // --- header (thread 0)
+    if (threadIdx.x == 0) {
+        uint64_t p = 0;
+        put_bits(words, p, 0x425A6839u, 32); p += 32;  // "BZh9"
+        put_bits(words, p, 0x314159u, 24); p += 24;
+        put_bits(words, p, 0x265359u, 24); p += 24;
+        put_bits(words, p, S.crc, 32); p += 32;
+        put_bits(words, p, 0, 1); p += 1;
+        put_bits(words, p, (uint32_t)S.orig_ptr, 24); p += 24;
+        put_bits(words, p, used16, 16); p += 16;
+        for (int i = 0; i < 16; i++) {
+            if (!(used16 & (1u << (15 - i)))) continue;
+            const uint32_t half = (S.in_use[i >> 1] >> ((i & 1) * 16)) & 0xFFFFu;
+            put_bits(words, p, __brev(half) >> 16, 16);  // byte 16i+j -> bit 15-j
+            p += 16;
+        }
+        put_bits(words, p, (uint32_t)ng, 3); p += 3;
+        put_bits(words, p, (uint32_t)nsel, 15); p += 15;
+        // trailer
+        uint64_t q = base_bits[2];
+        put_bits(words, q, 0x177245u, 24); q += 24;
+        put_bits(words, q, 0x385090u, 24); q += 24;
+        put_bits(words, q, S.crc, 32);
+    }
+    // --- selectors
+    {
+        uint64_t p = base_bits[0] + sel_off;
+        for (int i = sa; i < se; i++) {
+            const int s = sel[i];
+            uint32_t D = 0;
+            int j = -1;
+            for (int q = i - 1; q >= 0; q--) {
+                const int v = sel[q];
+                if (v == s) { j = __popc(D); break; }
+                D |= 1u << v;
+                if (__popc(D) == ng - 1) { j = ng - 1; break; }
+            }
+            if (j < 0) j = __popc(D) + __popc(((1u << s) - 1u) & ~D);
+            put_bits(words, p, ((1u << j) - 1u) << 1, j + 1);
+            p += (uint64_t)j + 1;
+        }
+    }
+    // --- code lengths (warp t, lane 0: sequential deltas)
+    if (w < ng && lane == 0) {
+        uint64_t p = base_bits[0] + sel_total;
+        for (int t = 0; t < w; t++) p += tbl_bits[t];
+        int cur = len[w][0];
+        put_bits(words, p, (uint32_t)cur, 5); p += 5;
+        for (int v = 0; v < alpha; v++) {
+            const int target = len[w][v];
+            while (cur < target) { put_bits(words, p, 2u, 2); p += 2; cur++; }
+            while (cur > target) { put_bits(words, p, 3u, 2); p += 2; cur--; }
+            p += 1;  // '0'
+        }
+    }
+    // --- data: each thread packs its span into whole words; only the span's
+    // first and last words are shared with neighbours (atomicOr)
+    {
+        const uint64_t p0 = base_bits[1] + data_off, p1 = p0 + dbits;
+        uint64_t acc = 0;   // pending bits, left-aligned
+        int nacc = 0;
+        uint64_t wpos = p0 & ~31ull;  // bit position of the word being built
+        nacc = (int)(p0 - wpos);      // leading bits owned by the previous span (zeros)
+        for (int i = da; i < de; i++) {
+            const int t = sel[i / 50];
+            const uint32_t s = sym[i];
+            const int l = len[t][s];
+            acc |= (uint64_t)code[t][s] << (64 - nacc - l);
+            nacc += l;
+            if (nacc >= 32) {
+                const uint32_t word = (uint32_t)(acc >> 32);
+                if (wpos < p0) atomicOr(&words[wpos >> 5], word);
+                else words[wpos >> 5] = word;
+                acc <<= 32;
+                nacc -= 32;
+                wpos += 32;
+            }
+        }
+        if (nacc > 0 && p1 > p0) atomicOr(&words[wpos >> 5], (uint32_t)(acc >> 32));
+    }
+    __syncthreads();
+    for (int64_t i = threadIdx.x; i < nwords; i += blockDim.x) words[i] = __byte_perm(words[i], 0, 0x0123);
+    if (threadIdx.x == 0) {
+        st[b].stream_bits = (uint32_t)total_bits;
+        st[b].stream_bytes = (uint32_t)(total_bits >> 3);
+    }
+}
+
+cudaError_t launch_mtf_rle2(lfc_plan P, int nblocks) {
+    Workspace &ws = P->ws;
+    cudaStream_t s = P->stream;
+    dim3 grid(kTilesPerBlock, nblocks);
+    mtf_summary_kernel<<<grid, 32, 0, s>>>(ws.bstate, ws.bwt, ws.mtfrec, ws.mtfreclen);
+    mtf_compose_kernel<<<nblocks, 32, 0, s>>>(ws.bstate, ws.mtfrec, ws.mtfreclen, ws.mtflists);
+    mtf_encode_kernel<<<grid, 32, 0, s>>>(ws.bstate, ws.bwt, ws.mtflists, ws.mtfidx);
+    rle2_kernel<<<nblocks, 1024, 0, s>>>(ws.bstate, ws.mtfidx, ws.sym, ws.freq);
+    count_launches(P, 4);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_huffman(lfc_plan P, int nblocks) {
+    Workspace &ws = P->ws;
+    huffman_kernel<<<nblocks, kHuffThreads, 0, P->stream>>>(ws.bstate, ws.sym, ws.freq, ws.sel, ws.lens, ws.codes);
+    count_launches(P, 1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_pack(lfc_plan P, int nblocks) {
+    Workspace &ws = P->ws;
+    pack_kernel<<<nblocks, kPackThreads, 0, P->stream>>>(ws.bstate, ws.sym, ws.sel, ws.lens, ws.codes, ws.packed,
+                                                         ws.stream_words);
+    count_launches(P, 1);
+    return cudaGetLastError();
+}
+
+}  // namespace lfc

@@ -1,0 +1,285 @@
+"""Python binding of liblfc (include/lfc.h): argument marshalling only.
+
+Every step of the compression path runs in the CUDA library; this module
+passes device pointers (``tensor.data_ptr()``), sizes and the current CUDA
+stream. It never computes any part of the method itself, and it has no CPU
+fallback: if ``liblfc.so`` is missing it raises.
+
+Frames are 2-D CUDA tensors of 2-byte elements (int16 or uint16 views of the
+uint16 counts), row-major, height x width.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+SO_PATH = os.path.join(_HERE, "_build", "liblfc.so")
+
+LFC_OK = 0
+STATUS = {0: "LFC_OK", 1: "LFC_ERR_INVALID_ARG", 2: "LFC_ERR_CAPACITY", 3: "LFC_ERR_CORRUPT",
+          4: "LFC_ERR_CUDA", 5: "LFC_ERR_TIMEOUT", 6: "LFC_ERR_UNIMPLEMENTED", 7: "LFC_ERR_NOMEM"}
+
+# every symbol include/lfc.h declares
+EXPORTS = ["lfc_plan_create", "lfc_plan_destroy", "lfc_plan_last_error", "lfc_judge", "lfc_symbols",
+           "lfc_max_compressed_bytes", "lfc_compress", "lfc_bzip2_encode", "lfc_max_stream_bytes",
+           "lfc_plan_block_capacity", "lfc_decompress", "lfc_status_string", "lfc_plan_set_timing",
+           "lfc_plan_timing", "lfc_plan_launch_count"]
+
+STAGES = ["judge_hist", "judge_score", "emit", "crc", "rle1", "bwt_sort8", "bwt_refine", "bwt_out", "mtf",
+          "huffman", "pack", "container"]
+
+
+class LfcError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__("%s: %s" % (STATUS.get(status, status), msg))
+        self.status = status
+
+
+class Config(ctypes.Structure):
+    _fields_ = [("width", ctypes.c_int32), ("height", ctypes.c_int32), ("pitch", ctypes.c_int32),
+                ("max_frames", ctypes.c_int32), ("candidate_mask", ctypes.c_uint64 * 4),
+                ("temporal", ctypes.c_int32), ("keyframe_interval", ctypes.c_int32),
+                ("block_bytes", ctypes.c_int32), ("topk", ctypes.c_int32), ("tau", ctypes.c_float)]
+
+
+class Frame(ctypes.Structure):
+    _fields_ = [("data", ctypes.c_void_p), ("prev", ctypes.c_void_p), ("width", ctypes.c_int32),
+                ("height", ctypes.c_int32), ("pitch", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+
+
+_lib = None
+
+
+def load():
+    """Load liblfc.so; raises if it has not been built."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(SO_PATH):
+        raise RuntimeError("liblfc.so not built (%s): run __graft_entry__.build()" % SO_PATH)
+    lib = ctypes.CDLL(SO_PATH)
+    P, i32, u64, sz = ctypes.c_void_p, ctypes.c_int, ctypes.c_uint64, ctypes.c_size_t
+    sig = {
+        "lfc_plan_create": (i32, [ctypes.POINTER(Config), P, ctypes.POINTER(P)]),
+        "lfc_plan_destroy": (None, [P]),
+        "lfc_plan_last_error": (ctypes.c_char_p, [P]),
+        "lfc_judge": (i32, [P, ctypes.POINTER(Frame), i32, P, P]),
+        "lfc_symbols": (i32, [P, ctypes.POINTER(Frame), i32, P]),
+        "lfc_max_compressed_bytes": (sz, [ctypes.c_int32, ctypes.c_int32, ctypes.c_int32]),
+        "lfc_compress": (i32, [P, ctypes.POINTER(Frame), i32, P, P, sz, P]),
+        "lfc_bzip2_encode": (i32, [P, P, ctypes.POINTER(u64), ctypes.POINTER(ctypes.c_uint32), i32, P, sz, P]),
+        "lfc_max_stream_bytes": (sz, [ctypes.c_int32]),
+        "lfc_plan_block_capacity": (i32, [P]),
+        "lfc_decompress": (i32, [P, ctypes.POINTER(P), ctypes.POINTER(u64), i32, ctypes.POINTER(P),
+                                 ctypes.POINTER(P)]),
+        "lfc_status_string": (ctypes.c_char_p, [i32]),
+        "lfc_plan_set_timing": (i32, [P, i32]),
+        "lfc_plan_timing": (i32, [P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int64), i32]),
+        "lfc_plan_launch_count": (ctypes.c_int64, [P]),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+def max_compressed_bytes(width: int, height: int, block_bytes: int = 0) -> int:
+    return int(load().lfc_max_compressed_bytes(width, height, block_bytes))
+
+
+def max_stream_bytes(block_bytes: int) -> int:
+    return int(load().lfc_max_stream_bytes(block_bytes))
+
+
+def mask_from_ids(ids):
+    m = [0, 0, 0, 0]
+    for i in ids:
+        m[i >> 6] |= 1 << (i & 63)
+    return m
+
+
+def _torch():
+    import torch
+    return torch
+
+
+def _ptr(t):
+    return None if t is None else ctypes.c_void_p(t.data_ptr())
+
+
+class Plan:
+    """One plan = workspace for frames up to width x height, max_frames per call."""
+
+    def __init__(self, width, height, pitch, max_frames=1, candidate_ids=None, temporal=False,
+                 block_bytes=0, keyframe_interval=16, stream=None):
+        torch = _torch()
+        self.lib = load()
+        cfg = Config()
+        cfg.width, cfg.height, cfg.pitch, cfg.max_frames = width, height, pitch, max_frames
+        m = mask_from_ids(candidate_ids) if candidate_ids else [0, 0, 0, 0]
+        for i in range(4):
+            cfg.candidate_mask[i] = m[i]
+        cfg.temporal = 1 if temporal else 0
+        cfg.keyframe_interval = keyframe_interval
+        cfg.block_bytes = block_bytes
+        cfg.topk, cfg.tau = 0, 0.0
+        self.cfg = cfg
+        self.block_bytes = block_bytes or 720000
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        h = ctypes.c_void_p()
+        rc = self.lib.lfc_plan_create(ctypes.byref(cfg), ctypes.c_void_p(self.stream.cuda_stream), ctypes.byref(h))
+        if rc != LFC_OK:
+            raise LfcError(rc, "lfc_plan_create")
+        self.h = h
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.lfc_plan_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _check(self, rc, what):
+        if rc != LFC_OK:
+            msg = self.lib.lfc_plan_last_error(self.h)
+            raise LfcError(rc, "%s: %s" % (what, msg.decode() if msg else ""))
+
+    def set_timing(self, enable=True):
+        self._check(self.lib.lfc_plan_set_timing(self.h, 1 if enable else 0), "lfc_plan_set_timing")
+
+    def timing(self):
+        """Accumulated device milliseconds and span counts per stage (synchronises)."""
+        n = len(STAGES)
+        ms = (ctypes.c_double * n)()
+        sp = (ctypes.c_int64 * n)()
+        self._check(self.lib.lfc_plan_timing(self.h, ms, sp, n), "lfc_plan_timing")
+        return {k: (ms[i], sp[i]) for i, k in enumerate(STAGES)}
+
+    def launch_count(self):
+        return int(self.lib.lfc_plan_launch_count(self.h))
+
+    @property
+    def block_capacity(self):
+        return int(self.lib.lfc_plan_block_capacity(self.h))
+
+    @staticmethod
+    def _frames(frames, pitch, prevs=None):
+        arr = (Frame * len(frames))()
+        for i, f in enumerate(frames):
+            assert f.is_cuda and f.dim() == 2 and f.element_size() == 2 and f.is_contiguous()
+            arr[i].data = f.data_ptr()
+            pv = None if prevs is None else prevs[i]
+            arr[i].prev = pv.data_ptr() if pv is not None else None
+            arr[i].height, arr[i].width = f.shape
+            arr[i].pitch = pitch if isinstance(pitch, int) else pitch[i]
+            arr[i].reserved = 0
+        return arr
+
+    # ------------------------------------------------------------- calls
+    def judge(self, frames, pitch, prevs=None, choice=None, scores=None):
+        """Returns (choice uint8[n], scores int64[n, 256] holding uint64 bits)."""
+        torch = _torch()
+        n = len(frames)
+        arr = self._frames(frames, pitch, prevs)
+        if choice is None:
+            choice = torch.empty(n, dtype=torch.uint8, device=frames[0].device)
+        if scores is None:
+            scores = torch.zeros((n, 256), dtype=torch.int64, device=frames[0].device)
+        self._check(self.lib.lfc_judge(self.h, arr, n, _ptr(choice), _ptr(scores)), "lfc_judge")
+        return choice, scores
+
+    def symbols(self, frame, pitch, cid, prev=None, out=None):
+        torch = _torch()
+        arr = self._frames([frame], pitch, None if prev is None else [prev])
+        if out is None:
+            out = torch.empty(frame.numel(), dtype=torch.int16, device=frame.device)
+        self._check(self.lib.lfc_symbols(self.h, arr, cid, _ptr(out)), "lfc_symbols")
+        return out
+
+    def slots(self, frames):
+        offs, o = [], 0
+        for f in frames:
+            offs.append(o)
+            o += max_compressed_bytes(f.shape[1], f.shape[0], self.block_bytes)
+        return offs, o
+
+    def compress(self, frames, pitch, prevs=None, choice=None, out=None, sizes=None):
+        """Compress on the device. Returns (out uint8 buffer, sizes int64[n], slot offsets)."""
+        torch = _torch()
+        n = len(frames)
+        arr = self._frames(frames, pitch, prevs)
+        offs, total = self.slots(frames)
+        if out is None:
+            out = torch.empty(total, dtype=torch.uint8, device=frames[0].device)
+        if sizes is None:
+            sizes = torch.empty(n, dtype=torch.int64, device=frames[0].device)
+        rc = self.lib.lfc_compress(self.h, arr, n, _ptr(choice), _ptr(out), out.numel(), _ptr(sizes))
+        self._check(rc, "lfc_compress")
+        return out, sizes, offs
+
+    def compress_to_bytes(self, frames, pitch, prevs=None, choice=None):
+        out, sizes, offs = self.compress(frames, pitch, prevs, choice)
+        sz = sizes.cpu().numpy()
+        host = out.cpu().numpy()
+        return [host[o:o + int(s)].tobytes() for o, s in zip(offs, sz)]
+
+    def bzip2_encode(self, data, offsets, sizes_in, out=None, stride=None):
+        """Device bytes ``data`` (uint8 tensor) split at offsets/sizes -> streams."""
+        torch = _torch()
+        nb = len(offsets)
+        offs = (ctypes.c_uint64 * nb)(*[int(o) for o in offsets])
+        szs = (ctypes.c_uint32 * nb)(*[int(s) for s in sizes_in])
+        if stride is None:
+            stride = max_stream_bytes(max(int(s) for s in sizes_in))
+        if out is None:
+            out = torch.empty(nb * stride, dtype=torch.uint8, device=data.device)
+        ss = torch.empty(nb, dtype=torch.int32, device=data.device)
+        rc = self.lib.lfc_bzip2_encode(self.h, _ptr(data), offs, szs, nb, _ptr(out), stride, _ptr(ss))
+        self._check(rc, "lfc_bzip2_encode")
+        return out, ss, stride
+
+    def bzip2_encode_bytes(self, blocks):
+        torch = _torch()
+        buf = b"".join(blocks)
+        data = torch.from_numpy(np.frombuffer(buf, dtype=np.uint8).copy()).cuda()
+        offs, o = [], 0
+        for b in blocks:
+            offs.append(o)
+            o += len(b)
+        out, ss, stride = self.bzip2_encode(data, offs, [len(b) for b in blocks])
+        host = out.cpu().numpy()
+        sz = ss.cpu().numpy()
+        return [host[i * stride:i * stride + int(sz[i])].tobytes() for i in range(len(blocks))]
+
+    def decompress(self, blobs, outs, prevs=None):
+        """blobs: list of uint8 CUDA tensors (one container each); outs: frame tensors."""
+        n = len(blobs)
+        ins = (ctypes.c_void_p * n)(*[b.data_ptr() for b in blobs])
+        szs = (ctypes.c_uint64 * n)(*[b.numel() for b in blobs])
+        os_ = (ctypes.c_void_p * n)(*[o.data_ptr() for o in outs])
+        pv = None
+        if prevs is not None:
+            pv = (ctypes.c_void_p * n)(*[(p.data_ptr() if p is not None else None) for p in prevs])
+        rc = self.lib.lfc_decompress(self.h, ins, szs, n, os_, pv)
+        self._check(rc, "lfc_decompress")
+        return outs
+
+
+def to_device_frame(arr: np.ndarray, device="cuda"):
+    """uint16 numpy frame -> contiguous int16 CUDA tensor holding the same bits."""
+    torch = _torch()
+    a = np.ascontiguousarray(arr, dtype=np.uint16).view(np.int16)
+    return torch.from_numpy(a.copy()).to(device)
+
+
+def from_device_frame(t) -> np.ndarray:
+    return t.cpu().numpy().view(np.uint16)

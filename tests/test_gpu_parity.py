@@ -1,0 +1,122 @@
+"""GPU parity: the CUDA path (through the C ABI) against the CPU oracle.
+
+All of the path is integer work, so every comparison is bit-exact: symbol
+streams, uint64 entropy scores, chosen ids, bzip2 stream bytes and whole
+containers. Sizes span several tiles, CTAs and blocks with ragged tails.
+"""
+import bz2
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2310_09467_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def lfc():
+    import torch
+    from paper_2310_09467_gb300 import build, lfc as L
+    build.build()
+    torch.cuda.init()
+    return L
+
+
+def _frames():
+    return [
+        (synth.beads(195, 195, 13, peak=2000.0, seed=0), 13),
+        (synth.beads(150, 135, 15, peak=20.0, seed=1), 15),
+        (synth.cells(210, 195, 15, seed=3), 15),
+        (synth.beads(390, 260, 13, peak=200.0, seed=5), 13),
+    ]
+
+
+def test_symbols_all_ids(lfc):
+    rng = np.random.default_rng(0)
+    p = 5
+    fr = rng.integers(0, 65536, (7 * p, 9 * p), dtype=np.uint16)
+    fr[0, :3] = [0, 65535, 0]
+    prev = rng.integers(0, 65536, fr.shape, dtype=np.uint16)
+    plan = lfc.Plan(fr.shape[1], fr.shape[0], p, temporal=True)
+    d, dp = lfc.to_device_frame(fr), lfc.to_device_frame(prev)
+    for cid in range(256):
+        if not oracle.id_valid(cid):
+            continue
+        pv = prev if cid >> 7 else None
+        got = plan.symbols(d, p, cid, prev=dp if pv is not None else None).cpu().numpy().view(np.uint16)
+        assert np.array_equal(got, oracle.symbols(fr, p, cid, prev=pv)), cid
+
+
+@pytest.mark.parametrize("k", range(4))
+def test_judge_scores_and_choice(lfc, k):
+    fr, p = _frames()[k]
+    plan = lfc.Plan(fr.shape[1], fr.shape[0], p)
+    choice, scores = plan.judge([lfc.to_device_frame(fr)], p)
+    ids = oracle.default_ids()
+    best, ref = oracle.judge(fr, p, ids)
+    got = scores.cpu().numpy().view(np.uint64)[0]
+    assert [int(got[i]) for i in ids] == ref
+    assert int(choice.cpu()[0]) == best
+
+
+def test_judge_batch_uneven_and_temporal(lfc):
+    vs = synth.VesselSeries(180, 165, 15, seed=4)
+    f0, f1 = vs.frame(0), vs.frame(1)
+    other = synth.beads(195, 195, 13, peak=2000.0, seed=9)
+    plan = lfc.Plan(195, 195, 13, max_frames=3, temporal=True)
+    ds = [lfc.to_device_frame(x) for x in (f0, f1, other)]
+    pitches = [15, 15, 13]
+    choice, scores = plan.judge(ds, pitches, prevs=[None, ds[0], None])
+    sc = scores.cpu().numpy().view(np.uint64)
+    ch = choice.cpu().numpy()
+    for i, (fr, pv, p) in enumerate([(f0, None, 15), (f1, f0, 15), (other, None, 13)]):
+        ids = oracle.default_ids(pv is not None)
+        best, ref = oracle.judge(fr, p, ids, prev=pv)
+        assert [int(sc[i][c]) for c in ids] == ref, i
+        assert int(ch[i]) == best
+
+
+def _coder_inputs():
+    rng = np.random.default_rng(7)
+    yield [b"a"]
+    yield [b"ab", b"abab" * 3, b"\x00" * 1000, bytes(range(256)) * 3]
+    yield [bytes(rng.integers(0, 256, 5000, dtype=np.uint8)), bytes(rng.integers(0, 3, 70001, dtype=np.uint8))]
+    yield [bytes(np.repeat(rng.integers(0, 256, 3000, dtype=np.uint8), rng.integers(1, 300, 3000))[:300000])]
+    yield [b"aaaabbbb" * 90000]                                   # 720000 -> 900000 after RLE1
+    yield [bytes(rng.integers(0, 256, 720000, dtype=np.uint8)), b"xyz" * 240000]
+    yield [bytes(rng.integers(0, 2, 250000, dtype=np.uint8) * 255)]
+
+
+@pytest.mark.parametrize("case", range(7))
+def test_bzip2_encode_bytes_identical(lfc, case):
+    blocks = list(_coder_inputs())[case]
+    plan = lfc.Plan(195, 195, 13, max_frames=4)
+    got = plan.bzip2_encode_bytes(blocks)
+    for g, b in zip(got, blocks):
+        assert g == oracle.bz2_stream(b)
+        assert bz2.decompress(g) == b
+
+
+@pytest.mark.parametrize("k", range(4))
+def test_compress_container_identical(lfc, k):
+    fr, p = _frames()[k]
+    plan = lfc.Plan(fr.shape[1], fr.shape[0], p, block_bytes=20000)
+    blob = plan.compress_to_bytes([lfc.to_device_frame(fr)], p)[0]
+    best, _ = oracle.judge(fr, p)
+    assert blob == oracle.compress_id(fr, p, best, block_bytes=20000)
+    assert np.array_equal(oracle.decompress(blob), fr)
+
+
+def test_compress_batch_temporal(lfc):
+    vs = synth.VesselSeries(180, 180, 15, seed=11)
+    frs = [vs.frame(k) for k in range(3)]
+    plan = lfc.Plan(180, 180, 15, max_frames=3, temporal=True, block_bytes=30000)
+    ds = [lfc.to_device_frame(x) for x in frs]
+    blobs = plan.compress_to_bytes(ds, 15, prevs=[None, ds[0], ds[1]])
+    for i, blob in enumerate(blobs):
+        pv = frs[i - 1] if i else None
+        best, _ = oracle.judge(frs[i], 15, prev=pv)
+        assert blob == oracle.compress_id(frs[i], 15, best, prev=pv, block_bytes=30000)
+        assert np.array_equal(oracle.decompress(blob, prev=pv), frs[i])
