@@ -144,7 +144,7 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="lfc", choices=["lfc", "reference"])
-    ap.add_argument("--per-kind", type=int, default=6)
+    ap.add_argument("--per-kind", type=int, default=4)
     ap.add_argument("--no-cpu", action="store_true")
     args = ap.parse_args()
     if args.impl == "reference":

@@ -176,13 +176,16 @@ int lfc_plan_block_capacity(lfc_plan plan);
 /* Decompresses n containers (Fig. 2b: unpack the header, bzip2-decode every
  * block, inverse predictor chosen by the header's id). Container i is
  * h_in[i] (device) of h_in_sizes[i] bytes; the frame goes to h_out[i]
- * (device, width * height uint16 of that container). Temporal containers
- * need h_prev[i] (device previous raw frame); h_prev may be NULL when no
- * container is temporal. h_prev[i] may point at h_out[j] for j < i: frames
- * are restored in index order. Synchronous: the host reads the headers.
- * Errors: INVALID_ARG, CORRUPT (bad header, stream, CRC), CUDA. */
+ * (device), which holds h_out_bytes[i] bytes (CAPACITY below 2 * W * H of the
+ * container). Temporal containers need h_prev[i] (device previous raw frame
+ * of the same geometry); h_prev may be NULL when no container is temporal.
+ * h_prev[i] may point at h_out[j] for j < i: frames are restored in index
+ * order. Every read of a container is bounds-checked, so a corrupt container
+ * returns CORRUPT (bad header, block stream, block CRC or frame CRC) and
+ * never reads or writes outside the buffers. Synchronous: the host reads
+ * the headers. Errors: INVALID_ARG, CAPACITY, CORRUPT, CUDA. */
 int lfc_decompress(lfc_plan plan, const uint8_t *const *h_in, const uint64_t *h_in_sizes, int n,
-                   uint16_t *const *h_out, const uint16_t *const *h_prev);
+                   uint16_t *const *h_out, const uint64_t *h_out_bytes, const uint16_t *const *h_prev);
 
 /* Stage timing (tracing). With timing enabled the plan records CUDA events on
  * its stream around each stage below and accumulates their device time; the

@@ -506,8 +506,102 @@ extern "C" int lfc_compress(lfc_plan P, const lfc_frame *frames, int n, const ui
     return LFC_OK;
 }
 
+static uint32_t rd32h(const uint8_t *p) {
+    return (uint32_t)p[0] | ((uint32_t)p[1] << 8) | ((uint32_t)p[2] << 16) | ((uint32_t)p[3] << 24);
+}
+
 extern "C" int lfc_decompress(lfc_plan P, const uint8_t *const *h_in, const uint64_t *h_in_sizes, int n,
-                              uint16_t *const *h_out, const uint16_t *const *h_prev) {
-    (void)h_in; (void)h_in_sizes; (void)n; (void)h_out; (void)h_prev;
-    return fail(P, LFC_ERR_UNIMPLEMENTED, "lfc_decompress: not built yet");
+                              uint16_t *const *h_out, const uint64_t *h_out_bytes, const uint16_t *const *h_prev) {
+    if (!P || !h_in || !h_in_sizes || !h_out || !h_out_bytes || n < 1)
+        return fail(P, LFC_ERR_INVALID_ARG, "lfc_decompress: bad arguments");
+    if (n > P->cfg.max_frames) return fail(P, LFC_ERR_INVALID_ARG, "lfc_decompress: n > max_frames");
+    Workspace &ws = P->ws;
+    struct Hdr { int W, H, p, id, bb, nb; uint32_t crc; std::vector<uint32_t> sizes; };
+    std::vector<Hdr> hd(n);
+    // headers: the host reads them (two small synchronous copies per container)
+    for (int i = 0; i < n; i++) {
+        if (!h_in[i] || !h_out[i]) return fail(P, LFC_ERR_INVALID_ARG, "lfc_decompress: NULL buffer");
+        if (h_in_sizes[i] < 40) return fail(P, LFC_ERR_CORRUPT, "container shorter than its header");
+        uint8_t h[40];
+        CK(cudaMemcpyAsync(h, h_in[i], 40, cudaMemcpyDeviceToHost, P->stream));
+        CK(cudaStreamSynchronize(P->stream));
+        Hdr &H = hd[i];
+        if (memcmp(h, "LFC1", 4) != 0 || h[4] != 1 || h[5] != 0) return fail(P, LFC_ERR_CORRUPT, "bad magic or version");
+        H.W = (int)rd32h(h + 8);
+        H.H = (int)rd32h(h + 12);
+        H.p = (int)rd32h(h + 16);
+        H.id = h[20];
+        H.bb = (int)rd32h(h + 24);
+        H.nb = (int)rd32h(h + 28);
+        H.crc = rd32h(h + 32);
+        const uint32_t hdr = rd32h(h + 36);
+        if (rd32h(h + 8) > 65536 || rd32h(h + 12) > 65536 || !geometry_ok(H.W, H.H, H.p) || !id_valid(H.id))
+            return fail(P, LFC_ERR_CORRUPT, "bad geometry or id");
+        if ((int64_t)H.W * H.H > (int64_t)P->cfg.width * P->cfg.height || H.W > P->cfg.width)
+            return fail(P, LFC_ERR_INVALID_ARG, "container frame larger than the plan");
+        if (((h[6] & 1) != 0) != ((H.id & 0x80) != 0) || h[7] != 0 || h[21] || h[22] || h[23])
+            return fail(P, LFC_ERR_CORRUPT, "bad flags");
+        if (H.bb < 1 || H.bb > kMaxBlockBytes) return fail(P, LFC_ERR_CORRUPT, "bad block size");
+        const int64_t nbytes = 2LL * H.W * H.H;
+        if (H.nb != (nbytes + H.bb - 1) / H.bb || hdr != 40u + 4u * (uint32_t)H.nb || hdr > h_in_sizes[i])
+            return fail(P, LFC_ERR_CORRUPT, "bad block table");
+        if (H.nb > P->block_cap) return fail(P, LFC_ERR_INVALID_ARG, "container has more blocks than the plan holds");
+        if ((H.id & 0x80) && (!h_prev || !h_prev[i])) return fail(P, LFC_ERR_INVALID_ARG, "temporal container needs prev");
+        if ((uint64_t)nbytes > h_out_bytes[i]) return fail(P, LFC_ERR_CAPACITY, "output frame buffer too small");
+        H.sizes.resize(H.nb);
+        CK(cudaMemcpyAsync(H.sizes.data(), h_in[i] + 40, 4 * (size_t)H.nb, cudaMemcpyDeviceToHost, P->stream));
+        CK(cudaStreamSynchronize(P->stream));
+        uint64_t total = hdr;
+        for (uint32_t v : H.sizes) total += v;
+        if (total != h_in_sizes[i]) return fail(P, LFC_ERR_CORRUPT, "block sizes do not add up to the container");
+    }
+    int32_t *d_status = ws.mtfreclen;  // block_cap * kTilesPerBlock int32, free while decoding
+    int f0 = 0;
+    while (f0 < n) {
+        std::vector<DecBlockHost> blocks;
+        int f1 = f0;
+        while (f1 < n && (int)blocks.size() + hd[f1].nb <= P->block_cap) {
+            const Hdr &H = hd[f1];
+            const int64_t nbytes = 2LL * H.W * H.H;
+            uint64_t off = 40 + 4ull * H.nb;
+            for (int k = 0; k < H.nb; k++) {
+                DecBlockHost d;
+                d.src = h_in[f1] + off;
+                d.src_len = H.sizes[k];
+                d.dst = ws.stream + (size_t)(f1 - f0) * ws.stream_slot + (size_t)k * H.bb;
+                d.expect = (int32_t)std::min<int64_t>(H.bb, nbytes - (int64_t)k * H.bb);
+                d.pad = 0;
+                blocks.push_back(d);
+                off += H.sizes[k];
+            }
+            f1++;
+        }
+        if (f1 - f0 > P->cfg.max_frames) return fail(P, LFC_ERR_INVALID_ARG, "too many frames");
+        const int nb = (int)blocks.size();
+        CK(cudaMemcpyAsync(ws.chunk_desc, blocks.data(), sizeof(DecBlockHost) * nb, cudaMemcpyHostToDevice, P->stream));
+        CK(launch_bzip2_decode(P, ws.chunk_desc, nb, d_status));
+        std::vector<int32_t> st(nb);
+        CK(cudaMemcpyAsync(st.data(), d_status, 4 * (size_t)nb, cudaMemcpyDeviceToHost, P->stream));
+        CK(cudaStreamSynchronize(P->stream));
+        for (int k = 0; k < nb; k++)
+            if (st[k] != 0) return fail(P, LFC_ERR_CORRUPT, "bzip2 block failed to decode (code " + std::to_string(st[k]) + ")");
+        std::vector<const uint8_t *> outp;
+        std::vector<int64_t> outl;
+        for (int i = f0; i < f1; i++) {
+            const Hdr &H = hd[i];
+            const uint16_t *Z = reinterpret_cast<const uint16_t *>(ws.stream + (size_t)(i - f0) * ws.stream_slot);
+            const uint16_t *pv = (H.id & 0x80) ? h_prev[i] : nullptr;
+            CK(launch_inverse_predict(P, Z, pv, h_out[i], ws.rank, H.W, H.H, H.p, H.id));
+            outp.push_back(reinterpret_cast<const uint8_t *>(h_out[i]));
+            outl.push_back(2LL * H.W * H.H);
+        }
+        CK(launch_range_crc(P, outp.data(), outl.data(), f1 - f0, ws.frame_crc));
+        std::vector<uint32_t> crc(f1 - f0);
+        CK(cudaMemcpyAsync(crc.data(), ws.frame_crc, 4 * (size_t)(f1 - f0), cudaMemcpyDeviceToHost, P->stream));
+        CK(cudaStreamSynchronize(P->stream));
+        for (int i = f0; i < f1; i++)
+            if (crc[i - f0] != hd[i].crc) return fail(P, LFC_ERR_CORRUPT, "frame CRC mismatch");
+        f0 = f1;
+    }
+    return LFC_OK;
 }

@@ -1,0 +1,522 @@
+// decode.cu -- decompression (Fig. 2b: unpack the header, bzip2-decode every
+// block, then the inverse predictor chosen by the header's id).
+//
+// One CTA per bzip2 stream. Every read of the coded stream is checked
+// against its length and every write against its buffer, so corrupt input
+// ends in an error flag, never an out-of-bounds access.
+//  1. thread 0: headers, tables, Huffman decoding, inverse RUNA/RUNB and MTF
+//     (sequential by nature) -> the BWT last column L;
+//  2. the CTA: LF mapping T[j] = C[L[j]] + rank of j among equal bytes (a
+//     stable counting sort of L with per-warp counters);
+//  3. 1024 walkers invert the BWT: each starts at its own row (walker 0 at
+//     origPtr), follows T until it meets another walker's start row, the
+//     pieces are chained from walker 0, and every walker re-walks its piece
+//     writing bytes from the end of the block backwards;
+//  4. thread 0: inverse RLE1; the CTA: CRC-32/BZIP2 of the output vs the
+//     stored block CRC.
+#include "lfc_common.cuh"
+
+namespace lfc {
+
+constexpr int kDecThreads = 1024;
+constexpr int kWalkers = kDecThreads;
+constexpr uint32_t kPolyD = 0x04C11DB7u;
+
+enum : int32_t {
+    DEC_OK = 0, DEC_BAD_MAGIC = 1, DEC_TRUNC = 2, DEC_BAD_TABLE = 3, DEC_BAD_DATA = 4,
+    DEC_OVERFLOW = 5, DEC_BAD_ORIG = 6, DEC_BAD_LEN = 7, DEC_BAD_CRC = 8, DEC_BAD_WALK = 9
+};
+
+struct DecBlock {
+    const uint8_t *src;   // one standalone bzip2 stream
+    int64_t src_len;
+    uint8_t *dst;         // decoded bytes go here
+    int32_t expect;       // decoded length the container promises
+    int32_t pad;
+};
+
+struct BitReader {
+    const uint8_t *p;
+    int64_t nbits, pos;
+    bool err;
+    __device__ uint32_t get(int k) {
+        if (pos + k > nbits) { err = true; pos = nbits; return 0; }
+        uint32_t v = 0;
+        for (int i = 0; i < k; i++) {
+            const int64_t q = pos + i;
+            v = (v << 1) | ((p[q >> 3] >> (7 - (q & 7))) & 1u);
+        }
+        pos += k;
+        return v;
+    }
+};
+
+__device__ __forceinline__ uint32_t gf_mul(uint32_t a, uint32_t b) {
+    uint32_t r = 0;
+    for (int i = 31; i >= 0; i--) {
+        r = (r & 0x80000000u) ? (r << 1) ^ kPolyD : (r << 1);
+        if ((b >> i) & 1u) r ^= a;
+    }
+    return r;
+}
+__device__ __forceinline__ uint32_t xpow8(uint64_t k) {
+    uint32_t r = 1u, b = 0x100u;
+    while (k) {
+        if (k & 1) r = gf_mul(r, b);
+        b = gf_mul(b, b);
+        k >>= 1;
+    }
+    return r;
+}
+
+struct DecShared {
+    uint32_t crc_tab[256];
+    uint32_t warp_cnt[kDecThreads / 32][256];
+    uint32_t C[256];
+    int32_t walk_next[kWalkers];
+    int32_t walk_len[kWalkers];
+    int64_t walk_pos[kWalkers];
+    uint8_t seq_to_unseq[256];
+    uint8_t mtf[256];
+    uint8_t sel_list[8];
+    uint8_t len[6][258];
+    int32_t first[6][22], count[6][22], pidx[6][22];
+    uint16_t perm[6][258];
+    uint32_t red[32];
+    int32_t status, nblock, orig, n_in_use, n_groups, n_sel, out_len;
+    uint32_t stored_crc;
+};
+
+// Workspace per block: sel (kMaxSelectors bytes), L (kBlockCap), T (int32
+// kBlockCap), rowmark (int32 kBlockCap, walker id or -1), blk (kBlockCap).
+__global__ void __launch_bounds__(kDecThreads) bzip2_decode_kernel(const DecBlock *__restrict__ blocks, int32_t *__restrict__ status,
+                                                                   uint8_t *__restrict__ sel_all, uint8_t *__restrict__ L_all,
+                                                                   int32_t *__restrict__ T_all, int32_t *__restrict__ mark_all,
+                                                                   uint8_t *__restrict__ blk_all) {
+    extern __shared__ __align__(16) uint8_t smraw[];
+    DecShared &S = *reinterpret_cast<DecShared *>(smraw);
+    const int b = blockIdx.x;
+    const DecBlock D = blocks[b];
+    uint8_t *sel = sel_all + (size_t)b * kMaxSelectors;
+    uint8_t *L = L_all + (size_t)b * kBlockCap;
+    int32_t *T = T_all + (size_t)b * kBlockCap;
+    int32_t *mark = mark_all + (size_t)b * kBlockCap;
+    uint8_t *blk = blk_all + (size_t)b * kBlockCap;
+    const int tid = threadIdx.x;
+    for (int i = tid; i < 256; i += blockDim.x) {
+        uint32_t v = (uint32_t)i << 24;
+        for (int k = 0; k < 8; k++) v = (v & 0x80000000u) ? (v << 1) ^ kPolyD : (v << 1);
+        S.crc_tab[i] = v;
+    }
+    if (tid == 0) {
+        S.status = DEC_OK;
+        BitReader br{D.src, D.src_len * 8, 0, false};
+        int st = DEC_OK;
+        int nblock = 0;
+        do {
+            if (br.get(8) != 'B' || br.get(8) != 'Z' || br.get(8) != 'h') { st = DEC_BAD_MAGIC; break; }
+            const uint32_t lvl = br.get(8);
+            if (lvl < '1' || lvl > '9') { st = DEC_BAD_MAGIC; break; }
+            const int block_max = 100000 * (int)(lvl - '0');
+            if (br.get(24) != 0x314159u || br.get(24) != 0x265359u) { st = DEC_BAD_MAGIC; break; }
+            S.stored_crc = br.get(32);
+            if (br.get(1) != 0) { st = DEC_BAD_DATA; break; }
+            const int orig = (int)br.get(24);
+            const uint32_t used16 = br.get(16);
+            int niu = 0;
+            for (int i = 0; i < 16; i++) {
+                if (!(used16 & (1u << (15 - i)))) continue;
+                const uint32_t bits = br.get(16);
+                for (int j = 0; j < 16; j++)
+                    if (bits & (1u << (15 - j))) S.seq_to_unseq[niu++] = (uint8_t)(i * 16 + j);
+            }
+            if (br.err) { st = DEC_TRUNC; break; }
+            if (niu == 0) { st = DEC_BAD_TABLE; break; }
+            const int alpha = niu + 2;
+            const int ng = (int)br.get(3);
+            const int nsel = (int)br.get(15);
+            if (br.err) { st = DEC_TRUNC; break; }
+            if (ng < 2 || ng > 6 || nsel < 1 || nsel > kMaxSelectors) { st = DEC_BAD_TABLE; break; }
+            for (int t = 0; t < ng; t++) S.sel_list[t] = (uint8_t)t;
+            for (int i = 0; i < nsel && st == DEC_OK; i++) {
+                int j = 0;
+                while (br.get(1)) {
+                    if (++j >= ng) { st = DEC_BAD_TABLE; break; }
+                }
+                if (br.err) st = DEC_TRUNC;
+                if (st != DEC_OK) break;
+                const uint8_t v = S.sel_list[j];
+                for (int q = j; q > 0; q--) S.sel_list[q] = S.sel_list[q - 1];
+                S.sel_list[0] = v;
+                sel[i] = v;
+            }
+            if (st != DEC_OK) break;
+            for (int t = 0; t < ng && st == DEC_OK; t++) {
+                int cur = (int)br.get(5);
+                for (int v = 0; v < alpha && st == DEC_OK; v++) {
+                    for (;;) {
+                        if (cur < 1 || cur > 20 || br.err) { st = br.err ? DEC_TRUNC : DEC_BAD_TABLE; break; }
+                        if (!br.get(1)) break;
+                        cur += br.get(1) ? -1 : 1;
+                    }
+                    S.len[t][v] = (uint8_t)cur;
+                }
+            }
+            if (st != DEC_OK) break;
+            // canonical tables: the codes of length l are first[l] ..
+            // first[l] + count[l] - 1, in increasing symbol order
+            for (int t = 0; t < ng; t++) {
+                int np = 0;
+                int32_t code = 0;
+                for (int l = 1; l <= 20; l++) {
+                    S.first[t][l] = code;
+                    S.pidx[t][l] = np;
+                    int cnt = 0;
+                    for (int v = 0; v < alpha; v++)
+                        if (S.len[t][v] == l) { S.perm[t][np++] = (uint16_t)v; cnt++; }
+                    S.count[t][l] = cnt;
+                    code = (code + cnt) << 1;
+                }
+            }
+            // Huffman decoding with inverse RUNA/RUNB and MTF
+            for (int k = 0; k < niu; k++) S.mtf[k] = (uint8_t)k;
+            int gi = 0, in_group = 0, t = 0;
+            int64_t run = 0, run_w = 1;
+            for (;;) {
+                if (in_group == 0) {
+                    if (gi >= nsel) { st = DEC_BAD_DATA; break; }
+                    t = sel[gi++];
+                    in_group = 50;
+                }
+                in_group--;
+                int32_t c = 0;
+                int s = -1;
+                for (int l = 1; l <= 20; l++) {
+                    c = (c << 1) | (int32_t)br.get(1);
+                    if (br.err) break;
+                    const uint32_t d = (uint32_t)(c - S.first[t][l]);
+                    if (d < (uint32_t)S.count[t][l]) { s = S.perm[t][S.pidx[t][l] + (int)d]; break; }
+                }
+                if (br.err) { st = DEC_TRUNC; break; }
+                if (s < 0) { st = DEC_BAD_DATA; break; }
+                if (s <= 1) {
+                    run += (int64_t)(s + 1) * run_w;
+                    run_w <<= 1;
+                    if (run > block_max) { st = DEC_OVERFLOW; break; }
+                    continue;
+                }
+                if (run > 0) {
+                    if (nblock + run > block_max || nblock + run > kBlockCap) { st = DEC_OVERFLOW; break; }
+                    const uint8_t v = S.seq_to_unseq[S.mtf[0]];
+                    for (int64_t q = 0; q < run; q++) L[nblock++] = v;
+                    run = 0;
+                    run_w = 1;
+                }
+                if (s == alpha - 1) break;  // EOB
+                const int j = s - 1;
+                if (j >= niu) { st = DEC_BAD_DATA; break; }
+                const uint8_t v = S.mtf[j];
+                for (int q = j; q > 0; q--) S.mtf[q] = S.mtf[q - 1];
+                S.mtf[0] = v;
+                if (nblock >= block_max || nblock >= kBlockCap) { st = DEC_OVERFLOW; break; }
+                L[nblock++] = S.seq_to_unseq[v];
+            }
+            if (st != DEC_OK) break;
+            if (orig >= nblock) { st = DEC_BAD_ORIG; break; }
+            S.orig = orig;
+        } while (0);
+        S.status = st;
+        S.nblock = nblock;
+    }
+    __syncthreads();
+    if (S.status != DEC_OK) {
+        if (tid == 0) status[b] = S.status;
+        return;
+    }
+    const int m = S.nblock;
+    // ---- 2. LF mapping: stable counting sort of L with per-warp counters
+    const int w = tid >> 5, lane = tid & 31, NW = kDecThreads / 32;
+    for (int i = lane; i < 256; i += 32) S.warp_cnt[w][i] = 0;
+    __syncwarp();
+    const int per_w = (m + NW - 1) / NW;
+    const int wa = min(m, w * per_w), we = min(m, wa + per_w);
+    for (int base = wa; base < we; base += 32) {
+        const int j = base + lane;
+        const bool ok = j < we;
+        const uint32_t c = ok ? L[j] : 0u;
+        const uint32_t mm = __match_any_sync(LFC_FULL, ok ? c : 256u + lane);
+        if (ok && (mm & lanemask_gt()) == 0) S.warp_cnt[w][c] += __popc(mm);
+        __syncwarp();
+    }
+    __syncthreads();
+    if (tid < 256) {
+        uint32_t acc = 0;
+        for (int ww = 0; ww < NW; ww++) acc += S.warp_cnt[ww][tid];
+        S.C[tid] = acc;
+    }
+    __syncthreads();
+    if (tid == 0) {
+        uint32_t acc = 0;
+        for (int c = 0; c < 256; c++) { const uint32_t v = S.C[c]; S.C[c] = acc; acc += v; }
+    }
+    __syncthreads();
+    if (tid < 256) {
+        uint32_t acc = S.C[tid];
+        for (int ww = 0; ww < NW; ww++) { const uint32_t v = S.warp_cnt[ww][tid]; S.warp_cnt[ww][tid] = acc; acc += v; }
+    }
+    __syncthreads();
+    for (int base = wa; base < we; base += 32) {
+        const int j = base + lane;
+        const bool ok = j < we;
+        const uint32_t c = ok ? L[j] : 0u;
+        const uint32_t mm = __match_any_sync(LFC_FULL, ok ? c : 256u + lane);
+        uint32_t before = ok ? S.warp_cnt[w][c] : 0u;
+        __syncwarp();
+        if (ok) {
+            T[j] = (int32_t)(before + __popc(mm & lanemask_lt()));
+            if ((mm & lanemask_gt()) == 0) S.warp_cnt[w][c] = before + __popc(mm);
+        }
+        __syncwarp();
+    }
+    for (int j = tid; j < m; j += blockDim.x) mark[j] = -1;
+    __syncthreads();
+    // ---- 3. walkers
+    const int nwk = min(kWalkers, m);
+    int start = -1;
+    if (tid < nwk) {
+        if (tid == 0) {
+            start = S.orig;
+        } else {
+            start = (int)((int64_t)tid * m / nwk);
+            if (start == S.orig) start = -1;  // orig is walker 0's row
+        }
+        if (start >= 0) mark[start] = tid;
+    }
+    __syncthreads();
+    if (start >= 0) {
+        int r = start, steps = 0;
+        do {
+            r = T[r];
+            steps++;
+        } while (mark[r] < 0 && steps <= m);
+        S.walk_len[tid] = steps;
+        S.walk_next[tid] = steps <= m ? mark[r] : -1;
+    } else if (tid < kWalkers) {
+        S.walk_len[tid] = 0;
+        S.walk_next[tid] = -1;
+    }
+    __syncthreads();
+    if (tid == 0) {
+        int k = 0;
+        int64_t pos = 0;
+        int visited = 0;
+        bool bad = false;
+        for (int i = 0; i < kWalkers; i++) S.walk_pos[i] = -1;
+        while (pos < m) {
+            if (k < 0 || k >= kWalkers || S.walk_pos[k] >= 0 || S.walk_len[k] <= 0) { bad = true; break; }
+            S.walk_pos[k] = pos;
+            pos += S.walk_len[k];
+            visited++;
+            k = S.walk_next[k];
+        }
+        if (bad || pos != m || k != 0) S.status = DEC_BAD_WALK;
+    }
+    __syncthreads();
+    if (S.status != DEC_OK) {
+        if (tid == 0) status[b] = S.status;
+        return;
+    }
+    if (start >= 0 && S.walk_pos[tid] >= 0) {
+        int r = start;
+        const int64_t p0 = S.walk_pos[tid];
+        for (int s = 0; s < S.walk_len[tid]; s++) {
+            blk[m - 1 - (p0 + s)] = L[r];
+            r = T[r];
+        }
+    }
+    __syncthreads();
+    // ---- 4. inverse RLE1 (thread 0), then CRC
+    if (tid == 0) {
+        int o = 0, same = 0, last = -1, st = DEC_OK;
+        for (int i = 0; i < m && st == DEC_OK; i++) {
+            const uint8_t v = blk[i];
+            if (o >= D.expect) { st = DEC_BAD_LEN; break; }
+            D.dst[o++] = v;
+            same = (v == last) ? same + 1 : 1;
+            last = v;
+            if (same == 4) {
+                if (i + 1 >= m) { st = DEC_BAD_DATA; break; }
+                const int extra = blk[++i];
+                if (o + extra > D.expect) { st = DEC_BAD_LEN; break; }
+                for (int q = 0; q < extra; q++) D.dst[o++] = v;
+                same = 0;
+                last = -1;
+            }
+        }
+        if (st == DEC_OK && o != D.expect) st = DEC_BAD_LEN;
+        S.status = st;
+        S.out_len = o;
+    }
+    __syncthreads();
+    if (S.status != DEC_OK) {
+        if (tid == 0) status[b] = S.status;
+        return;
+    }
+    const int n = S.out_len;
+    const int per = (n + blockDim.x - 1) / blockDim.x;
+    const int a = min(n, tid * per), e = min(n, a + per);
+    uint32_t r = 0;
+    for (int i = a; i < e; i++) r = (r << 8) ^ S.crc_tab[(r >> 24) ^ D.dst[i]];
+    if (e > a) r = gf_mul(r, xpow8((uint64_t)(n - e)));
+    for (int o = 16; o > 0; o >>= 1) r ^= __shfl_xor_sync(LFC_FULL, r, o);
+    if (lane == 0) S.red[w] = r;
+    __syncthreads();
+    if (tid == 0) {
+        uint32_t t = 0;
+        for (int i = 0; i < NW; i++) t ^= S.red[i];
+        t ^= gf_mul(0xFFFFFFFFu, xpow8((uint64_t)n));
+        status[b] = (~t == S.stored_crc) ? DEC_OK : DEC_BAD_CRC;
+    }
+}
+
+// ------------------------------------------------------ inverse predictor
+__device__ __forceinline__ int32_t as_s16(uint32_t v) { return (int32_t)(int16_t)(uint16_t)v; }
+__device__ __forceinline__ uint32_t unzig(uint32_t z) { return (uint32_t)(((z >> 1) ^ (0u - (z & 1u))) & 0xFFFFu); }
+
+__device__ __forceinline__ int32_t jp(int f, int32_t A, int32_t B, int32_t C) {
+    switch (f) {
+    case 1: return A;
+    case 2: return B;
+    case 3: return C;
+    case 4: return A + B - C;
+    case 5: return A + ((B - C) >> 1);
+    case 6: return B + ((A - C) >> 1);
+    case 7: return (A + B) >> 1;
+    default: return 0;
+    }
+}
+__device__ __forceinline__ int32_t gp(int f, int row, int col, int32_t A, int32_t B, int32_t C) {
+    if (row == 0) return col == 0 ? 0 : A;
+    if (col == 0) return B;
+    return jp(f, A, B, C);
+}
+
+struct InvFrame {
+    const uint16_t *Z;      // symbol stream (stream order)
+    const uint16_t *prev;   // previous raw frame or nullptr
+    uint16_t *X;            // output frame
+    int32_t *E;             // int32 scratch field (W*H)
+    int32_t W, H, p, id;
+};
+
+__device__ __forceinline__ size_t stream_index(const InvFrame &F, int y, int x) {
+    if (!((F.id >> 6) & 1)) return (size_t)y * F.W + x;
+    const int Nx = F.W / F.p, Ny = F.H / F.p;
+    const int t = y / F.p, v = y % F.p, s = x / F.p, u = x % F.p;
+    return (size_t)(v * Ny + t) * F.W + (size_t)u * Nx + s;
+}
+
+// Residual field e at every pixel (raw for f == 0 without temporal).
+__global__ void inv_residual_kernel(InvFrame F) {
+    const int64_t n = (int64_t)F.W * F.H;
+    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x) {
+        const int y = (int)(k / F.W), x = (int)(k % F.W);
+        const uint32_t z = F.Z[stream_index(F, y, x)];
+        const int f = F.id & 15;
+        const bool tmp = (F.id >> 7) & 1;
+        F.E[k] = (f == 0 && !tmp) ? (int32_t)z : as_s16(unzig(z));
+    }
+}
+
+// Inter-lenslet inverse over the view grid of every (u, v): one thread per
+// view walks its Ny x Nx grid in raster order. signed_out: keep the result
+// as signed 16-bit (phase stage / temporal fields).
+__global__ void inv_inter_kernel(InvFrame F, int signed_field) {
+    const int p = F.p, Nx = F.W / p, Ny = F.H / p;
+    const int view = blockIdx.x * blockDim.x + threadIdx.x;
+    if (view >= p * p) return;
+    const int v = view / p, u = view % p;
+    const int f = F.id & 15;
+    for (int t = 0; t < Ny; t++) {
+        for (int s = 0; s < Nx; s++) {
+            const size_t k = (size_t)(t * p + v) * F.W + s * p + u;
+            const int32_t A = s > 0 ? F.E[k - p] : 0;
+            const int32_t B = t > 0 ? F.E[k - (size_t)p * F.W] : 0;
+            const int32_t C = (s > 0 && t > 0) ? F.E[k - (size_t)p * F.W - p] : 0;
+            const uint32_t val = ((uint32_t)F.E[k] + (uint32_t)gp(f, t, s, A, B, C)) & 0xFFFFu;
+            F.E[k] = signed_field ? as_s16(val) : (int32_t)val;
+        }
+    }
+}
+
+// Intra-lenslet inverse: one thread per lenslet, raster order inside it.
+__global__ void inv_intra_kernel(InvFrame F, int signed_field) {
+    const int p = F.p, Nx = F.W / p, Ny = F.H / p;
+    const int lens = blockIdx.x * blockDim.x + threadIdx.x;
+    if (lens >= Nx * Ny) return;
+    const int t = lens / Nx, s = lens % Nx;
+    const int f = F.id & 15;
+    for (int v = 0; v < p; v++) {
+        for (int u = 0; u < p; u++) {
+            const size_t k = (size_t)(t * p + v) * F.W + s * p + u;
+            const int32_t A = u > 0 ? F.E[k - 1] : 0;
+            const int32_t B = v > 0 ? F.E[k - F.W] : 0;
+            const int32_t C = (u > 0 && v > 0) ? F.E[k - F.W - 1] : 0;
+            const uint32_t val = ((uint32_t)F.E[k] + (uint32_t)gp(f, v, u, A, B, C)) & 0xFFFFu;
+            F.E[k] = signed_field ? as_s16(val) : (int32_t)val;
+        }
+    }
+}
+
+// Base field -> raw counts (adds the previous frame for temporal ids).
+__global__ void inv_finish_kernel(InvFrame F) {
+    const int64_t n = (int64_t)F.W * F.H;
+    const bool tmp = (F.id >> 7) & 1;
+    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x) {
+        uint32_t v = (uint32_t)F.E[k];
+        if (tmp) v += F.prev[k];
+        F.X[k] = (uint16_t)(v & 0xFFFFu);
+    }
+}
+
+size_t decode_smem_bytes() { return sizeof(DecShared); }
+
+cudaError_t launch_bzip2_decode(lfc_plan P, const void *d_blocks, int nblocks, int32_t *d_status) {
+    Workspace &ws = P->ws;
+    const size_t smem = sizeof(DecShared);
+    cudaError_t e = cudaFuncSetAttribute(bzip2_decode_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    bzip2_decode_kernel<<<nblocks, kDecThreads, smem, P->stream>>>(reinterpret_cast<const DecBlock *>(d_blocks), d_status,
+                                                                  ws.sel, ws.bwt, ws.sa, ws.sa2, ws.rle);
+    count_launches(P, 1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_inverse_predict(lfc_plan P, const uint16_t *Z, const uint16_t *prev, uint16_t *X, int32_t *E,
+                                   int W, int H, int p, int id) {
+    InvFrame F{Z, prev, X, E, W, H, p, id};
+    cudaStream_t s = P->stream;
+    const int f = id & 15, dom = (id >> 4) & 3;
+    const bool tmp = (id >> 7) & 1;
+    inv_residual_kernel<<<1216, 256, 0, s>>>(F);
+    int launches = 2;
+    if (f != 0) {
+        const int nl = (W / p) * (H / p), nv = p * p;
+        if (dom == 0) {
+            inv_intra_kernel<<<(nl + 127) / 128, 128, 0, s>>>(F, tmp ? 1 : 0);
+            launches++;
+        } else if (dom == 1) {
+            inv_inter_kernel<<<(nv + 63) / 64, 64, 0, s>>>(F, tmp ? 1 : 0);
+            launches++;
+        } else {
+            inv_inter_kernel<<<(nv + 63) / 64, 64, 0, s>>>(F, 1);
+            inv_intra_kernel<<<(nl + 127) / 128, 128, 0, s>>>(F, tmp ? 1 : 0);
+            launches += 2;
+        }
+    }
+    inv_finish_kernel<<<1216, 256, 0, s>>>(F);
+    count_launches(P, launches);
+    return cudaGetLastError();
+}
+
+}  // namespace lfc

@@ -259,4 +259,16 @@ cudaError_t launch_container(lfc_plan P, int nframes, const int32_t *h_block0, c
                              const uint64_t *h_out_off, uint64_t *d_out_sizes, int block_bytes);
 cudaError_t launch_copy_streams(lfc_plan P, int nblocks, uint8_t *d_out, size_t stride, uint32_t *d_sizes);
 
+// decode.cu
+struct DecBlockHost {
+    const uint8_t *src;
+    int64_t src_len;
+    uint8_t *dst;
+    int32_t expect;
+    int32_t pad;
+};
+cudaError_t launch_bzip2_decode(lfc_plan P, const void *d_blocks, int nblocks, int32_t *d_status);
+cudaError_t launch_inverse_predict(lfc_plan P, const uint16_t *Z, const uint16_t *prev, uint16_t *X, int32_t *E,
+                                   int W, int H, int p, int id);
+
 }  // namespace lfc

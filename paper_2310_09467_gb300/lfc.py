@@ -74,7 +74,7 @@ def load():
         "lfc_max_stream_bytes": (sz, [ctypes.c_int32]),
         "lfc_plan_block_capacity": (i32, [P]),
         "lfc_decompress": (i32, [P, ctypes.POINTER(P), ctypes.POINTER(u64), i32, ctypes.POINTER(P),
-                                 ctypes.POINTER(P)]),
+                                 ctypes.POINTER(u64), ctypes.POINTER(P)]),
         "lfc_status_string": (ctypes.c_char_p, [i32]),
         "lfc_plan_set_timing": (i32, [P, i32]),
         "lfc_plan_timing": (i32, [P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int64), i32]),
@@ -266,10 +266,11 @@ class Plan:
         ins = (ctypes.c_void_p * n)(*[b.data_ptr() for b in blobs])
         szs = (ctypes.c_uint64 * n)(*[b.numel() for b in blobs])
         os_ = (ctypes.c_void_p * n)(*[o.data_ptr() for o in outs])
+        ob = (ctypes.c_uint64 * n)(*[o.numel() * o.element_size() for o in outs])
         pv = None
         if prevs is not None:
             pv = (ctypes.c_void_p * n)(*[(p.data_ptr() if p is not None else None) for p in prevs])
-        rc = self.lib.lfc_decompress(self.h, ins, szs, n, os_, pv)
+        rc = self.lib.lfc_decompress(self.h, ins, szs, n, os_, ob, pv)
         self._check(rc, "lfc_decompress")
         return outs
 

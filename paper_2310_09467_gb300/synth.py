@@ -156,10 +156,13 @@ def cell_photons(W: int, H: int, p: int, n_cells: int = 50, level: float = 500.0
         xr = X * np.cos(th) + Y * np.sin(th)
         yr = -X * np.sin(th) + Y * np.cos(th)
         r = np.sqrt((xr / a) ** 2 + (yr / b) ** 2)
-        ring = np.exp(-(((r - 1.0) * min(a, b)) ** 2) / (2 * ring_w ** 2))
-        inside = (r < 1.0) * 0.3
-        tex = 0.5 + 0.5 * noise((xr + ox) / 16.0 * 4, (yr + oy) / 16.0 * 4)
-        sub[:, :, ta:tb, sa:sb] += level * (ring + inside) * tex
+        d2 = ((r - 1.0) * min(a, b)) ** 2
+        env = np.where(d2 < 36 * ring_w ** 2, np.exp(-d2 / (2 * ring_w ** 2)), 0.0) + (r < 1.0) * 0.3
+        sel = env > 0
+        tex = 0.5 + 0.5 * noise((xr[sel] + ox) / 16.0 * 4, (yr[sel] + oy) / 16.0 * 4)
+        blk = np.zeros(env.shape)
+        blk[sel] = level * env[sel] * tex
+        sub[:, :, ta:tb, sa:sb] += blk
     sub *= aperture[:, :, None, None]
     return sub
 

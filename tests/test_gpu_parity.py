@@ -120,3 +120,65 @@ def test_compress_batch_temporal(lfc):
         best, _ = oracle.judge(frs[i], 15, prev=pv)
         assert blob == oracle.compress_id(frs[i], 15, best, prev=pv, block_bytes=30000)
         assert np.array_equal(oracle.decompress(blob, prev=pv), frs[i])
+
+
+def _dev_bytes(blob):
+    import torch
+    return torch.from_numpy(np.frombuffer(blob, dtype=np.uint8).copy()).cuda()
+
+
+@pytest.mark.parametrize("k", range(4))
+def test_decompress_round_trip(lfc, k):
+    import torch
+    fr, p = _frames()[k]
+    plan = lfc.Plan(fr.shape[1], fr.shape[0], p, block_bytes=20000)
+    blob = plan.compress_to_bytes([lfc.to_device_frame(fr)], p)[0]
+    out = torch.empty(fr.shape, dtype=torch.int16, device="cuda")
+    plan.decompress([_dev_bytes(blob)], [out])
+    assert np.array_equal(lfc.from_device_frame(out), fr)
+    # the GPU decoder also reads the oracle's containers of every id
+    for cid in (0, 0x44, 0x27, 0x66):
+        ref = oracle.compress_id(fr, p, cid, block_bytes=20000)
+        out2 = torch.empty(fr.shape, dtype=torch.int16, device="cuda")
+        plan.decompress([_dev_bytes(ref)], [out2])
+        assert np.array_equal(lfc.from_device_frame(out2), fr), cid
+
+
+def test_decompress_temporal_chain(lfc):
+    import torch
+    vs = synth.VesselSeries(180, 180, 15, seed=12)
+    frs = [vs.frame(k) for k in range(3)]
+    plan = lfc.Plan(180, 180, 15, max_frames=3, temporal=True, block_bytes=30000)
+    ds = [lfc.to_device_frame(x) for x in frs]
+    blobs = plan.compress_to_bytes(ds, 15, prevs=[None, ds[0], ds[1]])
+    outs = [torch.empty(frs[0].shape, dtype=torch.int16, device="cuda") for _ in range(3)]
+    plan.decompress([_dev_bytes(b) for b in blobs], outs, prevs=[None, outs[0], outs[1]])
+    for o, f in zip(outs, frs):
+        assert np.array_equal(lfc.from_device_frame(o), f)
+
+
+def test_decompress_rejects_corruption(lfc):
+    """Host-side fault injection: flipped and truncated bytes give CORRUPT
+    (or, for a flip in padding bits, the exact frame), never a fault."""
+    import torch
+    fr, p = _frames()[1]
+    plan = lfc.Plan(fr.shape[1], fr.shape[0], p, block_bytes=20000)
+    blob = plan.compress_to_bytes([lfc.to_device_frame(fr)], p)[0]
+    rng = np.random.default_rng(3)
+    for pos in list(rng.integers(0, len(blob), 40)) + [0, 8, 12, 20, 24, 28, 32, 36, 40, 44]:
+        t = bytearray(blob)
+        t[pos] ^= 1 << int(rng.integers(0, 8))
+        out = torch.zeros(fr.shape, dtype=torch.int16, device="cuda")
+        try:
+            plan.decompress([_dev_bytes(bytes(t))], [out])
+        except lfc.LfcError as e:
+            assert e.status in (1, 2, 3), e
+            continue
+        assert np.array_equal(lfc.from_device_frame(out), fr), pos
+    out = torch.zeros(fr.shape, dtype=torch.int16, device="cuda")
+    with pytest.raises(lfc.LfcError):
+        plan.decompress([_dev_bytes(blob[:-7])], [out])
+    small = torch.zeros(10, dtype=torch.int16, device="cuda")
+    with pytest.raises(lfc.LfcError) as ei:
+        plan.decompress([_dev_bytes(blob)], [small])
+    assert ei.value.status == 2
