@@ -214,6 +214,34 @@ int lfc_plan_timing(lfc_plan plan, double *ms, int64_t *spans, int n_stages);
 /* Kernel launches this plan has issued since creation (host counter). */
 int64_t lfc_plan_launch_count(lfc_plan plan);
 
+/* Allocation-free judge of one frame. The paper has no counterpart: this
+ * entry point exists for callers that may not allocate device memory, such
+ * as an acquisition loop that reserves its whole device-memory budget at
+ * start-up, or a plug-in running inside another framework whose allocator
+ * owns the device, where cudaMalloc/cudaFree (which can also synchronise
+ * the device) are not allowed on the processing path. It needs no plan and
+ * calls no allocating routine: its scratch (one 65536-bin histogram, chain
+ * summaries, the log2 table, descriptors and scores; about 0.8 MB) is one
+ * file-scope device array that every GPU loading the library holds until
+ * the process exits. Same results as lfc_judge for one frame:
+ *   h_frame    host pointer to one frame (device data); at most 4096 rows,
+ *              width at most 2656, 2 * width * height <= 2^26;
+ *   h_ids      host array of n_ids (1..256) valid candidate ids; temporal
+ *              ids need h_frame->prev;
+ *   d_choice   device, 1 byte: the best id;
+ *   d_scores   device, 256 uint64 or NULL: score of id c at [c] for the
+ *              judged ids, other entries untouched;
+ *   cuda_stream the stream to run on (NULL = legacy default stream).
+ * The first call on a device sets up that device's scratch (looks up its
+ * address and fills the log2 table, synchronising cuda_stream); make that
+ * first call before any stream capture. All calls share the one array and
+ * leave their contents in it; each call clears what must start at zero, and
+ * calls whose work overlaps on the GPU (other streams, other host threads)
+ * race on it. Asynchronous after set-up. Errors: INVALID_ARG (sizes beyond
+ * the limits above, bad ids), CUDA. */
+int lfc_judge_noalloc(const lfc_frame *h_frame, const uint8_t *h_ids, int n_ids, uint8_t *d_choice,
+                      uint64_t *d_scores, void *cuda_stream);
+
 /* Text of a status code. */
 const char *lfc_status_string(int status);
 

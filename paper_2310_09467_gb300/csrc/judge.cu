@@ -18,6 +18,8 @@
 // chains across warps, CTAs and buckets in a small fixup kernel.
 #include "lfc_common.cuh"
 
+#include <mutex>
+
 namespace lfc {
 
 // ------------------------------------------------------------ prediction
@@ -426,3 +428,128 @@ cudaError_t launch_symbols_one(const FrameDev &F, int id, uint16_t *dst, cudaStr
 }
 
 }  // namespace lfc
+
+// ============================================================ no allocation
+// lfc_judge_noalloc: the judge of one frame for callers that may not allocate
+// device memory. It launches the kernels above one candidate at a time with
+// all of their scratch in one file-scope device array, so no call allocates.
+// (The paper has no counterpart; see include/lfc.h.)
+namespace lfc {
+
+constexpr int kNoAllocRowsPerSeg = 128;
+constexpr int kNoAllocMaxSegs = 32;  // frames up to 32 * 128 = 4096 rows
+constexpr int kNoAllocMaxDevices = 64;
+
+struct NoAllocScratch {
+    uint32_t hist[kHistBins];                 // one candidate's pair histogram
+    uint64_t l2tab[kHistBins];                // fixed-point log2 table, filled at set-up
+    uint16_t summ[kNoAllocMaxSegs * 512];     // per-segment first/last tables
+    uint64_t scores[256];                     // score by id
+    JudgeFrame jf_one[256];                   // candidate i: K = 1, cand_off = i
+    JudgeFrame jf_all;                        // all candidates, for the argmax
+    int32_t zero[4];                          // frame_index / hist_frame tables = {0}
+    uint8_t cand[256];
+};
+
+static __device__ __align__(256) NoAllocScratch g_noalloc_scratch;
+
+struct IdList {
+    uint8_t id[256];
+    int32_t n;
+};
+
+__global__ void noalloc_describe_kernel(NoAllocScratch *s, FrameDev F, IdList ids, int segs) {
+    const int i = threadIdx.x;
+    if (i < ids.n) {
+        s->cand[i] = ids.id[i];
+        JudgeFrame &J = s->jf_one[i];
+        J.F = F;
+        J.K = 1;
+        J.cand_off = i;
+        J.segs = segs;
+        J.rows_per_seg = kNoAllocRowsPerSeg;
+        J.cta_base = 0;
+        J.hist_off = 0;
+        J.summ_off = 0;
+    }
+    if (i == 0) {
+        s->jf_all = s->jf_one[0];
+        s->jf_all.K = ids.n;
+        s->jf_all.cand_off = 0;
+        for (int k = 0; k < 4; k++) s->zero[k] = 0;
+    }
+}
+
+__global__ void noalloc_copy_scores_kernel(const NoAllocScratch *s, IdList ids, uint64_t *out) {
+    const int i = threadIdx.x;
+    if (i < ids.n) out[ids.id[i]] = s->scores[ids.id[i]];
+}
+
+static std::mutex g_noalloc_mu;
+static NoAllocScratch *g_noalloc_ptr[kNoAllocMaxDevices];
+
+// Per-device set-up on the first call: the array's device address (host code
+// may not use the symbol itself) and the log2 table, filled synchronously.
+static int noalloc_setup(cudaStream_t st, NoAllocScratch **out) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return LFC_ERR_CUDA;
+    if (dev < 0 || dev >= kNoAllocMaxDevices) return LFC_ERR_INVALID_ARG;
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    if (!g_noalloc_ptr[dev]) {
+        void *p = nullptr;
+        if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) return LFC_ERR_CUDA;
+        NoAllocScratch *s = reinterpret_cast<NoAllocScratch *>(p);
+        l2_table_kernel<<<kHistBins / 256, 256, 0, st>>>(s->l2tab);
+        if (cudaGetLastError() != cudaSuccess || cudaStreamSynchronize(st) != cudaSuccess) return LFC_ERR_CUDA;
+        g_noalloc_ptr[dev] = s;
+    }
+    *out = g_noalloc_ptr[dev];
+    return LFC_OK;
+}
+
+}  // namespace lfc
+
+extern "C" int lfc_judge_noalloc(const lfc_frame *frame, const uint8_t *h_ids, int n_ids, uint8_t *d_choice,
+                                 uint64_t *d_scores, void *cuda_stream) {
+    using namespace lfc;
+    if (!frame || !frame->data || !d_choice || !h_ids || n_ids < 1 || n_ids > 256 || frame->reserved != 0)
+        return LFC_ERR_INVALID_ARG;
+    const int W = frame->width, H = frame->height, p = frame->pitch;
+    if (W <= 0 || H <= 0 || p <= 0 || W % p || H % p || (int64_t)W * H * 2 > ((int64_t)1 << 26))
+        return LFC_ERR_INVALID_ARG;
+    if (judge_smem_bytes(W) > 232448 || H > kNoAllocMaxSegs * kNoAllocRowsPerSeg) return LFC_ERR_INVALID_ARG;
+    IdList ids;
+    ids.n = n_ids;
+    for (int i = 0; i < n_ids; i++) {
+        const int id = h_ids[i], f = id & 15, dom = (id >> 4) & 3;
+        if (f > 7 || dom > 2 || (f == 0 && dom != 0)) return LFC_ERR_INVALID_ARG;
+        if ((id & 0x80) && !frame->prev) return LFC_ERR_INVALID_ARG;
+        ids.id[i] = (uint8_t)id;
+    }
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(cuda_stream);
+    NoAllocScratch *s = nullptr;
+    int rc = noalloc_setup(st, &s);
+    if (rc != LFC_OK) return rc;
+    FrameDev F;
+    F.X = frame->data;
+    F.prev = frame->prev;
+    F.W = W;
+    F.H = H;
+    F.p = p;
+    F.Nx = W / p;
+    F.Ny = H / p;
+    const int segs = (H + kNoAllocRowsPerSeg - 1) / kNoAllocRowsPerSeg;
+    const size_t smem = judge_smem_bytes(W);
+    if (cudaFuncSetAttribute(judge_hist_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+        return LFC_ERR_CUDA;
+    noalloc_describe_kernel<<<1, 256, 0, st>>>(s, F, ids, segs);
+    for (int i = 0; i < n_ids; i++) {
+        if (cudaMemsetAsync(s->hist, 0, sizeof(s->hist), st) != cudaSuccess) return LFC_ERR_CUDA;
+        judge_hist_kernel<<<segs, kJudgeWarps * 32, smem, st>>>(&s->jf_one[i], 1, s->cand, s->hist, s->summ, W);
+        judge_fixup_kernel<<<1, 256, 0, st>>>(&s->jf_one[i], s->zero, s->hist, s->summ);
+        entropy_kernel<<<1, 1024, 0, st>>>(s->hist, s->l2tab, &s->jf_one[i], s->zero, s->cand, s->scores, s->zero);
+    }
+    argmax_kernel<<<1, 32, 0, st>>>(&s->jf_all, 1, s->cand, s->scores, d_choice, s->zero);
+    if (d_scores) noalloc_copy_scores_kernel<<<1, 256, 0, st>>>(s, ids, d_scores);
+    return cudaGetLastError() == cudaSuccess ? LFC_OK : LFC_ERR_CUDA;
+}

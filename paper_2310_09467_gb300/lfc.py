@@ -26,7 +26,7 @@ STATUS = {0: "LFC_OK", 1: "LFC_ERR_INVALID_ARG", 2: "LFC_ERR_CAPACITY", 3: "LFC_
 EXPORTS = ["lfc_plan_create", "lfc_plan_destroy", "lfc_plan_last_error", "lfc_judge", "lfc_symbols",
            "lfc_max_compressed_bytes", "lfc_compress", "lfc_bzip2_encode", "lfc_max_stream_bytes",
            "lfc_plan_block_capacity", "lfc_decompress", "lfc_status_string", "lfc_plan_set_timing",
-           "lfc_plan_timing", "lfc_plan_launch_count"]
+           "lfc_plan_timing", "lfc_plan_launch_count", "lfc_judge_noalloc"]
 
 STAGES = ["judge_hist", "judge_score", "emit", "crc", "rle1", "bwt_sort8", "bwt_refine", "bwt_out", "mtf",
           "huffman", "pack", "container"]
@@ -79,6 +79,7 @@ def load():
         "lfc_plan_set_timing": (i32, [P, i32]),
         "lfc_plan_timing": (i32, [P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int64), i32]),
         "lfc_plan_launch_count": (ctypes.c_int64, [P]),
+        "lfc_judge_noalloc": (i32, [ctypes.POINTER(Frame), ctypes.POINTER(ctypes.c_uint8), i32, P, P, P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
