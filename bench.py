@@ -212,16 +212,20 @@ def main():
     sz = sizes.cpu().numpy()
     comp_bytes = int(sz.sum())
 
-    # roofline of the dominant kernel: the judge histogram kernel, whose
-    # algorithmic traffic is (K + 1) n per frame (frame read once, one n-byte
-    # candidate stream consumed per candidate)
+    # roofline of the dominant kernel (largest stage time with a byte model).
+    # judge_hist: chain_hist_kernel reads every candidate stream once, K n per
+    # frame; judge_emit: emit_all_kernel reads the frame and writes the K
+    # candidate streams, (K + 1) n per frame (n = 2 W H bytes).
     K = 26
-    judge_ms, judge_spans = stages["judge_hist"]
-    judge_bytes = (K + 1) * raw_bytes * args.steps
+    models = {"judge_hist": ("chain_hist_kernel", K * raw_bytes * args.steps, "K*n per frame, K=26, n=2*W*H"),
+              "judge_emit": ("emit_all_kernel", (K + 1) * raw_bytes * args.steps, "(K+1)*n per frame, K=26, n=2*W*H")}
+    dom = max(models, key=lambda k: stages[k][0])
+    kname, kbytes, kmodel = models[dom]
+    kms, kspans = stages[dom]
     peak, peak_kind = peaks()
-    achieved = judge_bytes / 1e9 / (judge_ms / 1e3) if judge_ms > 0 else 0.0
+    achieved = kbytes / 1e9 / (kms / 1e3) if kms > 0 else 0.0
     traffic = None
-    tr_path = os.path.join(ROOT, "profiles", "judge_hist_traffic.json")
+    tr_path = os.path.join(ROOT, "profiles", kname + "_traffic.json")
     if os.path.exists(tr_path):
         traffic = json.load(open(tr_path)).get("bytes_per_launch")
 
@@ -264,11 +268,10 @@ def main():
                        "candidates": K, "block_bytes": 720000, "l2": "flushed between steps (512 MB write); batch > L2",
                        "parallelism": "replicas" if world > 1 else "1 GPU"},
             "ratio": raw_bytes / comp_bytes, "bits_per_dim": 8.0 * comp_bytes / (raw_bytes / 2),
-            "roofline": {"bound": "hbm", "kernel": "judge_hist_kernel", "achieved": achieved, "peak": peak,
+            "roofline": {"bound": "hbm", "kernel": kname, "achieved": achieved, "peak": peak,
                          "unit": "GB/s", "frac": achieved / peak, "traffic": traffic,
-                         "peak_source": peak_kind + " (hbm_gbs)",
-                         "bytes_model": "(K+1)*n per frame, K=26, n=2*W*H",
-                         "avg_launch_ms": judge_ms / max(1, judge_spans)},
+                         "peak_source": peak_kind + " (hbm_gbs)", "bytes_model": kmodel,
+                         "avg_launch_ms": kms / max(1, kspans), "launches_timed": kspans},
             "stages_ms_per_step": {k: v[0] / args.steps for k, v in stages.items()},
             "clocks": clk, "gpu_launches": launches,
             "e2e": {"value": e2e_value, "unit": "MB/s", "h2d_bytes_per_step": raw_bytes, "d2h_bytes_per_step": d2h},

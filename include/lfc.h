@@ -206,6 +206,7 @@ enum {
     LFC_STAGE_HUFFMAN,
     LFC_STAGE_PACK,
     LFC_STAGE_CONTAINER,
+    LFC_STAGE_JUDGE_EMIT,     /* every candidate stream of the judged frames */
     LFC_NUM_STAGES
 };
 int lfc_plan_set_timing(lfc_plan plan, int enable);

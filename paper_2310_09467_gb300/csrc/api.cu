@@ -11,8 +11,7 @@ using namespace lfc;
 
 namespace {
 
-constexpr int kRowsPerSeg = 128;   // judge: stream rows per CTA
-constexpr int kJudgeFramesCap = 16;
+constexpr int kJudgeFramesCap = 8;
 
 int fail(lfc_plan P, int code, const std::string &what, cudaError_t e = cudaSuccess) {
     if (P) {
@@ -182,7 +181,7 @@ extern "C" int lfc_plan_block_capacity(lfc_plan P) { return P ? P->block_cap : 0
 static void free_ws(Workspace &w) {
     void *ptrs[] = {w.hist, w.summ, w.scores, w.choice, w.jframes, w.cand, w.l2tab, w.stream, w.blocks, w.bstate,
                     w.rle, w.sa, w.sa2, w.rank, w.act, w.act2, w.val, w.val2, w.tilecnt, w.tileaux, w.bwt,
-                    w.mtfidx, w.mtflists, w.mtfrec, w.mtfreclen, w.sym, w.freq, w.sel, w.lens, w.codes, w.packed,
+                    w.mtfidx, w.mtflists, w.mtfrec, w.mtfreclen, w.sym, w.freq, w.sel, w.lens, w.codes, w.packed, w.cstream,
                     w.act_total, w.block_dst, w.frame_crc, w.crc_part, w.chunk_desc, w.dec_tt};
     for (void *p : ptrs)
         if (p) cudaFree(p);
@@ -195,7 +194,7 @@ extern "C" int lfc_plan_create(const lfc_config *cfg, void *cuda_stream, lfc_pla
     *out = nullptr;
     if (!geometry_ok(cfg->width, cfg->height, cfg->pitch) || cfg->max_frames < 1) return LFC_ERR_INVALID_ARG;
     if (cfg->block_bytes < 0 || cfg->block_bytes > kMaxBlockBytes) return LFC_ERR_INVALID_ARG;
-    if (judge_smem_bytes(cfg->width) > 232448) return LFC_ERR_INVALID_ARG;
+    if (cfg->pitch > 64) return LFC_ERR_INVALID_ARG;
     lfc_plan P = new (std::nothrow) lfc_plan_s();
     if (!P) return LFC_ERR_NOMEM;
     P->cfg = *cfg;
@@ -237,8 +236,10 @@ extern "C" int lfc_plan_create(const lfc_config *cfg, void *cuda_stream, lfc_pla
     P->judge_frames_cap = std::min(F, kJudgeFramesCap);
     P->block_cap = (int)std::max<int64_t>(bpf, std::min<int64_t>((int64_t)F * bpf, 192));
     const int JF = P->judge_frames_cap, BC = P->block_cap;
-    const int64_t segs_max = (cfg->height + kRowsPerSeg - 1) / kRowsPerSeg;
+    const int64_t segs_max = (n_max + chain_seg_bytes() - 1) / chain_seg_bytes();
     ws.summ_cap = (int64_t)JF * kMaxCand * segs_max;
+    ws.cstream_kmax = K;
+    ws.cstream_slot = (n_max + 255) & ~(int64_t)255;
     ws.stream_slot = (n_max + 255) & ~(int64_t)255;
     ws.stream_words = (stream_bound(bb) + 3) / 4 + 4;
     ws.crc_part_cap = 262144;
@@ -254,6 +255,7 @@ extern "C" int lfc_plan_create(const lfc_config *cfg, void *cuda_stream, lfc_pla
     AL(cand, (size_t)1 << 20);
     AL(l2tab, (size_t)kHistBins);
     AL(stream, (size_t)F * ws.stream_slot);
+    AL(cstream, (size_t)JF * K * ws.cstream_slot);
     AL(blocks, (size_t)BC);
     AL(bstate, (size_t)BC);
     AL(rle, (size_t)BC * kBlockCap);
@@ -311,6 +313,7 @@ extern "C" void lfc_plan_destroy(lfc_plan P) {
 // ------------------------------------------------------------------ judge
 static int judge_impl(lfc_plan P, const lfc_frame *frames, int n, uint8_t *d_choice, uint64_t *d_scores) {
     Workspace &ws = P->ws;
+    const int64_t seg_bytes = chain_seg_bytes();
     for (int f0 = 0; f0 < n; f0 += P->judge_frames_cap) {
         const int f1 = std::min(n, f0 + P->judge_frames_cap);
         const int nf = f1 - f0;
@@ -318,19 +321,28 @@ static int judge_impl(lfc_plan P, const lfc_frame *frames, int n, uint8_t *d_cho
         std::vector<int32_t> frame_index(nf), hist_frame;
         std::vector<uint8_t> cand;
         int64_t cta = 0, hist = 0, summ = 0;
-        int max_w = 0;
+        JudgeLaunch L{0, 16, 0, 0, 0};
         for (int i = 0; i < nf; i++) {
             const lfc_frame &fr = frames[f0 + i];
             const bool tmp = fr.prev != nullptr && !P->ids_temporal.empty();
             JudgeFrame &J = jf[i];
             J.F = to_dev(fr, tmp);
             J.cand_off = (int32_t)cand.size();
+            uint32_t fset[2] = {0, 0};
             for (uint8_t id : P->ids_spatial) cand.push_back(id);
             if (tmp)
                 for (uint8_t id : P->ids_temporal) cand.push_back(id);
+            for (size_t k = J.cand_off; k < cand.size(); k++) {
+                const int id = cand[k], f = id & 15, dom = (id >> 4) & 3;
+                if (f && dom != 1) fset[(id >> 7) & 1] |= 1u << f;
+            }
+            L.nslots_max = std::max(L.nslots_max, std::max(__builtin_popcount(fset[0]), __builtin_popcount(fset[1])));
+            L.any_temporal |= tmp ? 1 : 0;
+            L.max_p = std::max(L.max_p, fr.pitch);
             J.K = (int32_t)(cand.size() - J.cand_off);
-            J.rows_per_seg = kRowsPerSeg;
-            J.segs = (fr.height + kRowsPerSeg - 1) / kRowsPerSeg;
+            const int64_t nbytes = 2LL * fr.width * fr.height;
+            J.rows_per_seg = 0;
+            J.segs = (int32_t)((nbytes + seg_bytes - 1) / seg_bytes);
             J.cta_base = cta;
             J.hist_off = hist;
             J.summ_off = summ;
@@ -339,7 +351,15 @@ static int judge_impl(lfc_plan P, const lfc_frame *frames, int n, uint8_t *d_cho
             for (int k = 0; k < J.K; k++) hist_frame.push_back(i);
             hist += J.K;
             frame_index[i] = f0 + i;
-            max_w = std::max(max_w, fr.width);
+        }
+        // lenslets per emission tile: as many as shared memory allows (<= 16)
+        L.TS = 16;
+        while (L.TS > 1 && emit_all_smem_bytes(L.max_p, L.TS, L.nslots_max) > 200 * 1024) L.TS /= 2;
+        if (emit_all_smem_bytes(L.max_p, L.TS, L.nslots_max) > 200 * 1024)
+            return fail(P, LFC_ERR_INVALID_ARG, "pitch too large for the emission tile");
+        for (int i = 0; i < nf; i++) {
+            const FrameDev &F = jf[i].F;
+            L.max_tiles = std::max(L.max_tiles, F.Ny * ((F.Nx + L.TS - 1) / L.TS));
         }
         if (summ > ws.summ_cap) return fail(P, LFC_ERR_INVALID_ARG, "judge summary capacity exceeded");
         // one staging blob: frames | frame_index | hist_frame | cand
@@ -347,16 +367,15 @@ static int judge_impl(lfc_plan P, const lfc_frame *frames, int n, uint8_t *d_cho
         const size_t o2 = o1 + 4 * nf;
         const size_t o3 = o2 + 4 * hist_frame.size();
         const size_t total = o3 + cand.size();
+        if (total > ((size_t)1 << 20)) return fail(P, LFC_ERR_INVALID_ARG, "judge table too large");
         std::vector<uint8_t> blob(total);
         memcpy(blob.data(), jf.data(), o1);
         memcpy(blob.data() + o1, frame_index.data(), 4 * nf);
         memcpy(blob.data() + o2, hist_frame.data(), 4 * hist_frame.size());
         memcpy(blob.data() + o3, cand.data(), cand.size());
-        if (total > ((size_t)1 << 20)) return fail(P, LFC_ERR_INVALID_ARG, "judge table too large");
         uint8_t *d = reinterpret_cast<uint8_t *>(ws.cand);
         CK(cudaMemcpyAsync(d, blob.data(), total, cudaMemcpyHostToDevice, P->stream));
-        CK(launch_judge(P, reinterpret_cast<const JudgeFrame *>(d), nf, cta, max_w, d + o3, (int)cand.size(), hist,
-                        d_scores, d_choice, frame_index.data()));
+        CK(launch_judge(P, reinterpret_cast<const JudgeFrame *>(d), nf, cta, L, d + o3, hist, d_scores, d_choice));
     }
     return LFC_OK;
 }

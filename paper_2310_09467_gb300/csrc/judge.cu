@@ -346,33 +346,31 @@ size_t judge_smem_bytes(int maxW) {
     return (size_t)32768 * 4 + (size_t)kJudgeWarps * 256 * 2 * 2 + (size_t)kJudgeWarps * maxW * 2;
 }
 
-cudaError_t launch_judge(lfc_plan P, const JudgeFrame *d_frames, int nframes, int64_t total_ctas, int max_w,
-                         const uint8_t *d_cand, int total_cand, int64_t nhist, uint64_t *d_scores,
-                         uint8_t *d_choice, const int32_t *h_frame_index) {
-    (void)h_frame_index;
+cudaError_t launch_judge(lfc_plan P, const JudgeFrame *d_frames, int nframes, int64_t total_ctas,
+                         const JudgeLaunch &L, const uint8_t *d_cand, int64_t nhist, uint64_t *d_scores,
+                         uint8_t *d_choice) {
     cudaStream_t s = P->stream;
     Workspace &ws = P->ws;
-    cudaError_t e;
-    const size_t smem = judge_smem_bytes(max_w);
-    e = cudaFuncSetAttribute(judge_hist_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    e = cudaMemsetAsync(ws.hist, 0, (size_t)nhist * kHistBins * 4, s);
+    cudaError_t e = cudaMemsetAsync(ws.hist, 0, (size_t)nhist * kHistBins * 4, s);
     if (e != cudaSuccess) return e;
     // frame index table and hist->frame table ride behind the frame table
     const int32_t *d_frame_index = reinterpret_cast<const int32_t *>(d_frames + nframes);
     const int32_t *d_hist_frame = d_frame_index + nframes;
+    stage_begin(P, LFC_STAGE_JUDGE_EMIT);
+    e = launch_emit_all(P, d_frames, nframes, d_cand, L.max_tiles, L.TS, L.nslots_max, L.any_temporal, L.max_p);
+    stage_end(P, LFC_STAGE_JUDGE_EMIT);
+    if (e != cudaSuccess) return e;
     stage_begin(P, LFC_STAGE_JUDGE_HIST);
-    judge_hist_kernel<<<(unsigned)total_ctas, kJudgeWarps * 32, smem, s>>>(d_frames, nframes, d_cand, ws.hist,
-                                                                            ws.summ, max_w);
+    e = launch_chain_hist(P, d_frames, nframes, d_cand, total_ctas);
     stage_end(P, LFC_STAGE_JUDGE_HIST);
+    if (e != cudaSuccess) return e;
     stage_begin(P, LFC_STAGE_JUDGE_SCORE);
     judge_fixup_kernel<<<(unsigned)nhist, 256, 0, s>>>(d_frames, d_hist_frame, ws.hist, ws.summ);
     entropy_kernel<<<(unsigned)nhist, 1024, 0, s>>>(ws.hist, ws.l2tab, d_frames, d_hist_frame, d_cand, d_scores,
                                                    d_frame_index);
     argmax_kernel<<<nframes, 32, 0, s>>>(d_frames, nframes, d_cand, d_scores, d_choice, d_frame_index);
     stage_end(P, LFC_STAGE_JUDGE_SCORE);
-    count_launches(P, 4);
-    (void)total_cand;
+    count_launches(P, 3);
     return cudaGetLastError();
 }
 

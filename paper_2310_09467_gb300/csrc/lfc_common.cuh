@@ -157,6 +157,9 @@ struct Workspace {
     uint8_t *cand = nullptr;       // judge_frames_cap * kMaxCand
     uint64_t *l2tab = nullptr;     // 65536
     int64_t summ_cap = 0;
+    uint8_t *cstream = nullptr;    // candidate streams: judge_frames_cap * cstream_kmax slots
+    int64_t cstream_slot = 0;
+    int cstream_kmax = 0;
     // symbol streams of the frames being compressed
     uint8_t *stream = nullptr;     // max_frames * stream_slot
     int64_t stream_slot = 0;
@@ -232,9 +235,19 @@ inline void count_launches(lfc_plan P, int n) { P->launches += n; }
 // judge.cu
 cudaError_t init_l2_table(uint64_t *tab, cudaStream_t s);
 size_t judge_smem_bytes(int maxW);
+// judge_stream.cu
+size_t emit_all_smem_bytes(int p, int ts, int nslots);
+size_t chain_smem_bytes();
+int64_t chain_seg_bytes();
+cudaError_t launch_emit_all(lfc_plan P, const JudgeFrame *d_frames, int nframes, const uint8_t *d_cand, int max_tiles,
+                            int TS, int nslots_max, int any_temporal, int max_p);
+cudaError_t launch_chain_hist(lfc_plan P, const JudgeFrame *d_frames, int nframes, const uint8_t *d_cand, int64_t total_ctas);
+struct JudgeLaunch {
+    int max_tiles, TS, nslots_max, any_temporal, max_p;
+};
 cudaError_t launch_judge(lfc_plan P, const JudgeFrame *d_frames, int nframes, int64_t total_ctas,
-                         int max_w, const uint8_t *d_cand, int total_cand, int64_t nhist,
-                         uint64_t *d_scores, uint8_t *d_choice, const int32_t *h_frame_index);
+                         const JudgeLaunch &L, const uint8_t *d_cand, int64_t nhist,
+                         uint64_t *d_scores, uint8_t *d_choice);
 cudaError_t launch_emit(const FrameDev *h_frames, const uint8_t *d_choice, int nframes,
                         uint8_t *const *h_dst, cudaStream_t s);
 cudaError_t launch_symbols_one(const FrameDev &F, int id, uint16_t *dst, cudaStream_t s);

@@ -29,7 +29,7 @@ EXPORTS = ["lfc_plan_create", "lfc_plan_destroy", "lfc_plan_last_error", "lfc_ju
            "lfc_plan_timing", "lfc_plan_launch_count", "lfc_judge_noalloc"]
 
 STAGES = ["judge_hist", "judge_score", "emit", "crc", "rle1", "bwt_sort8", "bwt_refine", "bwt_out", "mtf",
-          "huffman", "pack", "container"]
+          "huffman", "pack", "container", "judge_emit"]
 
 
 class LfcError(RuntimeError):
