@@ -181,7 +181,7 @@ extern "C" int lfc_plan_block_capacity(lfc_plan P) { return P ? P->block_cap : 0
 static void free_ws(Workspace &w) {
     void *ptrs[] = {w.hist, w.summ, w.scores, w.choice, w.jframes, w.cand, w.l2tab, w.stream, w.blocks, w.bstate,
                     w.rle, w.sa, w.sa2, w.rank, w.act, w.act2, w.val, w.val2, w.tilecnt, w.tileaux, w.bwt,
-                    w.mtfidx, w.mtflists, w.mtfrec, w.mtfreclen, w.sym, w.freq, w.sel, w.lens, w.codes, w.packed, w.cstream,
+                    w.mtfidx, w.mtflists, w.mtfrec, w.mtfreclen, w.sym, w.freq, w.sel, w.lens, w.codes, w.packed, w.cstream, w.chain_first,
                     w.act_total, w.block_dst, w.frame_crc, w.crc_part, w.chunk_desc, w.dec_tt};
     for (void *p : ptrs)
         if (p) cudaFree(p);
@@ -256,6 +256,7 @@ extern "C" int lfc_plan_create(const lfc_config *cfg, void *cuda_stream, lfc_pla
     AL(l2tab, (size_t)kHistBins);
     AL(stream, (size_t)F * ws.stream_slot);
     AL(cstream, (size_t)JF * K * ws.cstream_slot);
+    AL(chain_first, (size_t)ws.summ_cap * chain_first_bytes_per_cta());
     AL(blocks, (size_t)BC);
     AL(bstate, (size_t)BC);
     AL(rle, (size_t)BC * kBlockCap);

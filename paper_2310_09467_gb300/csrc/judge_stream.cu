@@ -10,13 +10,9 @@
 //    are formed once in shared memory; then every pixel's symbol is produced
 //    for every candidate of the kind and stored in the candidate's ordering
 //    (raw order: 480-byte row runs; view-major order: 32-byte runs).
-// 2. chain_hist_kernel: one CTA per 512 KB segment of a candidate stream.
-//    Each warp walks its contiguous bytes in 32-byte windows staged through
-//    shared memory; __match_any_sync finds equal bytes, the predecessor of
-//    the previous occurrence comes by shuffle or from a per-warp pending
-//    table, and pairs are counted in a shared-memory histogram of half the
-//    65536 bins per pass with warp-aggregated atomics. Per-warp first/last
-//    predecessor tables are stitched per CTA and across CTAs by the fixup.
+// 2. chain_hist_kernel: one CTA per 768 KB segment of a candidate stream,
+//    one thread per 2 KB range walking it byte by byte (see below); the
+//    ranges are stitched per CTA and the CTAs by the fixup kernel.
 #include "lfc_common.cuh"
 
 namespace lfc {
@@ -46,13 +42,9 @@ __device__ __forceinline__ uint16_t zz16(int32_t e) {
     return (uint16_t)(((s << 1) ^ (s >> 31)) & 0xFFFF);
 }
 
-struct CandInfo {
-    uint8_t ci, f, dom, ord, slot;  // slot: e1 field index of f
-};
-
 size_t emit_all_smem_bytes(int p, int ts, int nslots) {
     const size_t cells = (size_t)(2 * p) * (size_t)((ts + 1) * p);
-    return cells * 2 * (size_t)(1 + nslots) + 64 * sizeof(CandInfo) + 64;
+    return cells * 2 * (size_t)(1 + nslots) + 256;
 }
 
 // grid (tiles, frames, kind); kind 0 = raw base field, 1 = temporal difference
@@ -60,6 +52,9 @@ __global__ void __launch_bounds__(kEmitThreads) emit_all_kernel(const JudgeFrame
                                                                 const uint8_t *__restrict__ cand, uint8_t *__restrict__ cstream,
                                                                 int64_t cslot, int kmax, int TS) {
     extern __shared__ __align__(16) uint8_t esm[];
+    __shared__ int16_t slot_of[8][3][2];  // candidate index for (f, domain, ordering), -1 if absent
+    __shared__ int8_t eslot_of[8];        // intra residual field of f
+    __shared__ uint32_t fmask_ord[2];     // f values with any candidate in that ordering
     const int fi = blockIdx.y, kind = blockIdx.z;
     const JudgeFrame &J = frames[fi];
     const FrameDev F = J.F;
@@ -72,7 +67,6 @@ __global__ void __launch_bounds__(kEmitThreads) emit_all_kernel(const JudgeFrame
     const int cells = TR * TC;
     uint16_t *Fb = reinterpret_cast<uint16_t *>(esm);
     int16_t *E = reinterpret_cast<int16_t *>(esm) + cells;
-    // candidate list of this kind, f-set of the intra residual fields
     uint32_t fset = 0;
     int nc = 0;
     for (int k = 0; k < J.K; k++) {
@@ -83,20 +77,16 @@ __global__ void __launch_bounds__(kEmitThreads) emit_all_kernel(const JudgeFrame
         if (f && dom != 1) fset |= 1u << f;
     }
     if (nc == 0) return;
-    const int nslots = __popc(fset);
-    CandInfo *ci_list = reinterpret_cast<CandInfo *>(E + (size_t)nslots * cells);
     if (threadIdx.x == 0) {
-        int j = 0;
+        for (int i = 0; i < 48; i++) (&slot_of[0][0][0])[i] = -1;
+        fmask_ord[0] = fmask_ord[1] = 0;
+        for (int f = 0; f < 8; f++) eslot_of[f] = (int8_t)__popc(fset & ((1u << f) - 1u));
         for (int k = 0; k < J.K; k++) {
             const int id = cand[J.cand_off + k];
             if (((id >> 7) & 1) != kind) continue;
-            CandInfo c;
-            c.ci = (uint8_t)k;
-            c.f = (uint8_t)(id & 15);
-            c.dom = (uint8_t)((id >> 4) & 3);
-            c.ord = (uint8_t)((id >> 6) & 1);
-            c.slot = (uint8_t)__popc(fset & ((1u << c.f) - 1u));
-            ci_list[j++] = c;
+            const int f = id & 15, dom = (id >> 4) & 3, ord = (id >> 6) & 1;
+            slot_of[f][dom][ord] = (int16_t)k;
+            fmask_ord[ord] |= 1u << f;
         }
     }
     const int y0 = (t - 1) * p, x0 = (s0 - 1) * p;
@@ -112,8 +102,8 @@ __global__ void __launch_bounds__(kEmitThreads) emit_all_kernel(const JudgeFrame
         Fb[ly * TC + lx] = (uint16_t)v;
     }
     __syncthreads();
-    // intra residual fields (signed 16-bit) for every f in use
 #define FVAL(idx) (kind ? (int32_t)(int16_t)Fb[idx] : (int32_t)Fb[idx])
+    // intra residual fields (signed 16-bit) for every f in use
     for (int q = threadIdx.x; q < TR * ncols; q += blockDim.x) {
         const int ly = q / ncols, lx = q - ly * ncols;
         const int v = ly % p, u = lx % p;
@@ -122,59 +112,59 @@ __global__ void __launch_bounds__(kEmitThreads) emit_all_kernel(const JudgeFrame
         const int32_t A = u > 0 ? FVAL(idx - 1) : 0;
         const int32_t B = v > 0 ? FVAL(idx - TC) : 0;
         const int32_t C = (u > 0 && v > 0) ? FVAL(idx - TC - 1) : 0;
-        uint32_t fs = fset;
-        int slot = 0;
-        while (fs) {
-            const int f = __ffs(fs) - 1;
-            fs &= fs - 1;
-            E[(size_t)slot * cells + idx] = (int16_t)(Xv - g_pred(f, v, u, A, B, C));
-            slot++;
-        }
+#pragma unroll
+        for (int f = 1; f < 8; f++)
+            if (fset & (1u << f)) E[(size_t)eslot_of[f] * cells + idx] = (int16_t)(Xv - g_pred(f, v, u, A, B, C));
     }
     __syncthreads();
-    const int npx = p * ns * p;
-    const int64_t n_sym = (int64_t)W * F.H;
+    const int n_cols_out = ns * p;
+    uint16_t *base = reinterpret_cast<uint16_t *>(cstream + (size_t)fi * kmax * (size_t)cslot);
+    const size_t cslot16 = (size_t)cslot / 2;
     for (int ord = 0; ord < 2; ord++) {
-        for (int q = threadIdx.x; q < npx; q += blockDim.x) {
-            int ly, lx;
-            int64_t pos;
-            if (ord == 0) {
-                const int lr = q / (ns * p), lc = q - lr * (ns * p);
-                ly = p + lr;
-                lx = p + lc;
-                pos = (int64_t)(t * p + lr) * W + (int64_t)s0 * p + lc;
-            } else {
-                const int v = q / (p * ns), rem = q - v * (p * ns), u = rem / ns, si = rem - u * ns;
-                ly = p + v;
-                lx = p + si * p + u;
-                pos = (int64_t)(v * Ny + t) * W + (int64_t)u * Nx + s0 + si;
+        const uint32_t fm = fmask_ord[ord];
+        if (!fm || (int)threadIdx.x >= n_cols_out) continue;
+        int lx, s;
+        int64_t pos0, pstep;
+        if (ord == 0) {  // thread = raw column; rows r -> raw rows t*p + r
+            const int lc = threadIdx.x;
+            lx = p + lc;
+            s = s0 + lc / p;
+            pos0 = (int64_t)(t * p) * W + (int64_t)s0 * p + lc;
+            pstep = W;
+        } else {         // thread = (u, lenslet); rows r -> view rows (v = r) * Ny + t
+            const int u = threadIdx.x / ns, si = threadIdx.x - u * ns;
+            lx = p + si * p + u;
+            s = s0 + si;
+            pos0 = (int64_t)t * W + (int64_t)u * Nx + s0 + si;
+            pstep = (int64_t)Ny * W;
+        }
+        for (int r = 0; r < p; r++) {
+            const int idx = (p + r) * TC + lx;
+            const int64_t pos = pos0 + r * pstep;
+            const int32_t Xv = FVAL(idx);
+            if (fm & 1u) {
+                const int k = slot_of[0][0][ord];
+                base[(size_t)k * cslot16 + pos] = kind ? zz16(Xv) : (uint16_t)Xv;
             }
-            const int s = s0 + (lx - p) / p;
-            const int idx = ly * TC + lx;
-            for (int k = 0; k < nc; k++) {
-                const CandInfo c = ci_list[k];
-                if (c.ord != ord) continue;
-                uint16_t z;
-                if (c.f == 0) {
-                    z = kind ? zz16(FVAL(idx)) : Fb[idx];
-                } else if (c.dom == 0) {
-                    z = zz16(E[(size_t)c.slot * cells + idx]);
-                } else if (c.dom == 1) {
-                    const int32_t Xv = FVAL(idx);
-                    const int32_t A = s > 0 ? FVAL(idx - p) : 0;
-                    const int32_t B = t > 0 ? FVAL(idx - p * TC) : 0;
-                    const int32_t C = (s > 0 && t > 0) ? FVAL(idx - p * TC - p) : 0;
-                    z = zz16(Xv - g_pred(c.f, t, s, A, B, C));
-                } else {
-                    const int16_t *Ef = E + (size_t)c.slot * cells;
-                    const int32_t Xv = Ef[idx];
-                    const int32_t A = s > 0 ? Ef[idx - p] : 0;
-                    const int32_t B = t > 0 ? Ef[idx - p * TC] : 0;
-                    const int32_t C = (s > 0 && t > 0) ? Ef[idx - p * TC - p] : 0;
-                    z = zz16(Xv - g_pred(c.f, t, s, A, B, C));
+            const int32_t XA = s > 0 ? FVAL(idx - p) : 0;
+            const int32_t XB = t > 0 ? FVAL(idx - p * TC) : 0;
+            const int32_t XC = (s > 0 && t > 0) ? FVAL(idx - p * TC - p) : 0;
+#pragma unroll
+            for (int f = 1; f < 8; f++) {
+                if (!(fm & (1u << f))) continue;
+                const int k0 = slot_of[f][0][ord], k1 = slot_of[f][1][ord], k2 = slot_of[f][2][ord];
+                if (k1 >= 0) base[(size_t)k1 * cslot16 + pos] = zz16(Xv - g_pred(f, t, s, XA, XB, XC));
+                if (k0 >= 0 || k2 >= 0) {
+                    const int16_t *Ef = E + (size_t)eslot_of[f] * cells;
+                    const int32_t e = Ef[idx];
+                    if (k0 >= 0) base[(size_t)k0 * cslot16 + pos] = zz16(e);
+                    if (k2 >= 0) {
+                        const int32_t eA = s > 0 ? Ef[idx - p] : 0;
+                        const int32_t eB = t > 0 ? Ef[idx - p * TC] : 0;
+                        const int32_t eC = (s > 0 && t > 0) ? Ef[idx - p * TC - p] : 0;
+                        base[(size_t)k2 * cslot16 + pos] = zz16(e - g_pred(f, t, s, eA, eB, eC));
+                    }
                 }
-                uint16_t *out = reinterpret_cast<uint16_t *>(cstream + ((size_t)fi * kmax + c.ci) * (size_t)cslot);
-                if (pos < n_sym) out[pos] = z;
             }
         }
     }
@@ -182,13 +172,24 @@ __global__ void __launch_bounds__(kEmitThreads) emit_all_kernel(const JudgeFrame
 }
 
 // ------------------------------------------------------ pair-chain histogram
-constexpr int kChainWarps = 32;
-constexpr int kChunk = 512;
-constexpr int64_t kSegBytes = 512 * 1024;
+// One thread walks a contiguous byte range of a candidate stream in one
+// pass. Its pending table (predecessor of the last occurrence of each byte
+// value, 0xFFFF before the first) holds 16-bit entries in shared memory, entry
+// b of thread t in half (b % 2) of word (b / 2) * T + t, so each lane always
+// hits its own bank. The first occurrence of every value in the range goes
+// to a global scratch table, so the CTA can stitch the ranges in order
+// afterwards. Pairs (x, y) with x, y < 64 (the hot corner for small residuals)
+// are counted in shared memory, the very common pair (0, 0) in a register,
+// all others with fire-and-forget atomics into the L2-resident histogram.
+constexpr int kChainThreads = 384;
+constexpr int kRangeBytes = 2048;                                   // per thread
+constexpr int64_t kSegBytes = (int64_t)kChainThreads * kRangeBytes;  // per CTA
+constexpr int kHot = 64;                                            // hot corner side
 constexpr uint16_t kNoPred = 0xFFFF;
 
-size_t chain_smem_bytes() { return 131072 + (size_t)kChainWarps * 256 * 2 * 2 + (size_t)kChainWarps * kChunk; }
+size_t chain_smem_bytes() { return (size_t)kHot * kHot * 4 + (size_t)128 * kChainThreads * 4; }
 int64_t chain_seg_bytes() { return kSegBytes; }
+int64_t chain_first_bytes_per_cta() { return (int64_t)kChainThreads * 256; }
 
 __device__ __forceinline__ int find_frame_s(const JudgeFrame *fr, int n, int64_t cta) {
     int lo = 0, hi = n - 1;
@@ -199,14 +200,34 @@ __device__ __forceinline__ int find_frame_s(const JudgeFrame *fr, int n, int64_t
     return lo;
 }
 
-__global__ void __launch_bounds__(kChainWarps * 32, 1)
+__device__ __forceinline__ void chain_byte(uint32_t b, uint32_t &prev, uint32_t *tblt, uint32_t *hot, uint32_t *ghist,
+                                           uint8_t *first, uint32_t &c0) {
+    const uint32_t a = prev;
+    prev = b;
+    uint32_t *wp = tblt + (b >> 1) * kChainThreads;
+    const uint32_t word = *wp;
+    const uint32_t sh = (b & 1u) << 4;
+    const uint32_t pend = (word >> sh) & 0xFFFFu;
+    if (pend != kNoPred) {
+        if ((pend | a) == 0) {
+            c0++;
+        } else if ((pend | a) < (uint32_t)kHot) {
+            atomicAdd(&hot[pend * kHot + a], 1u);
+        } else {
+            atomicAdd(&ghist[(pend << 8) | a], 1u);
+        }
+    } else {
+        first[b] = (uint8_t)a;
+    }
+    *wp = (word & ~(0xFFFFu << sh)) | (a << sh);
+}
+
+__global__ void __launch_bounds__(kChainThreads)
 chain_hist_kernel(const JudgeFrame *__restrict__ frames, int nframes, const uint8_t *__restrict__ cstream, int64_t cslot,
-                  int kmax, uint32_t *__restrict__ hist, uint16_t *__restrict__ summ) {
+                  int kmax, uint32_t *__restrict__ hist, uint16_t *__restrict__ summ, uint8_t *__restrict__ first_all) {
     extern __shared__ __align__(16) uint8_t smem[];
-    uint32_t *sh_hist = reinterpret_cast<uint32_t *>(smem);
-    uint16_t *sh_first = reinterpret_cast<uint16_t *>(smem + 131072);
-    uint16_t *sh_last = sh_first + kChainWarps * 256;
-    uint8_t *sh_buf = reinterpret_cast<uint8_t *>(sh_last + kChainWarps * 256);
+    uint32_t *hot = reinterpret_cast<uint32_t *>(smem);   // [kHot][kHot]
+    uint32_t *tbl = hot + kHot * kHot;                    // [128][T]
     const int fi = find_frame_s(frames, nframes, blockIdx.x);
     const JudgeFrame &J = frames[fi];
     const int64_t local = (int64_t)blockIdx.x - J.cta_base;
@@ -214,77 +235,46 @@ chain_hist_kernel(const JudgeFrame *__restrict__ frames, int nframes, const uint
     const uint8_t *S = cstream + ((size_t)fi * kmax + ci) * (size_t)cslot;
     uint32_t *ghist = hist + (size_t)(J.hist_off + ci) * kHistBins;
     const int64_t n = 2LL * J.F.W * J.F.H;
-    const int64_t a = (int64_t)seg * kSegBytes, b = min(n, a + kSegBytes);
-    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int64_t per = (((b - a) + kChainWarps - 1) / kChainWarps + kChunk - 1) / kChunk * kChunk;
-    const int64_t wa = min(b, a + w * per), we = min(b, wa + per);
-    uint16_t *my_first = sh_first + w * 256, *my_last = sh_last + w * 256;
-    uint8_t *buf = sh_buf + w * kChunk;
-    const uint32_t carry0 = wa < we ? (uint32_t)S[wa == 0 ? n - 1 : wa - 1] : 0u;
-
-    for (int pass = 0; pass < 2; pass++) {
-        for (int i = threadIdx.x; i < 32768; i += blockDim.x) sh_hist[i] = 0;
-        for (int i = lane; i < 256; i += 32) { my_first[i] = kNoPred; my_last[i] = kNoPred; }
-        __syncthreads();
-        uint32_t prev = carry0;
-        for (int64_t c0 = wa; c0 < we; c0 += kChunk) {
-            const int cnt = (int)min((int64_t)kChunk, we - c0);
-            const int64_t o = c0 + 16 * lane;
-            if (o + 16 <= we) {
-                *reinterpret_cast<uint4 *>(buf + 16 * lane) = __ldg(reinterpret_cast<const uint4 *>(S + o));
-            } else {
-                for (int k = 0; k < 16; k++) buf[16 * lane + k] = (o + k < we) ? S[o + k] : 0;
-            }
-            __syncwarp();
-            for (int w0 = 0; w0 < cnt; w0 += 32) {
-                const int q = w0 + lane;
-                const bool valid = q < cnt;
-                const uint32_t bb = buf[q];
-                uint32_t aa = __shfl_up_sync(LFC_FULL, bb, 1);
-                if (lane == 0) aa = prev;
-                prev = __shfl_sync(LFC_FULL, bb, 31);
-                const uint32_t m = __match_any_sync(LFC_FULL, valid ? bb : 256u + lane);
-                const uint32_t lower = m & lanemask_lt();
-                const int pl = lower ? 31 - __clz(lower) : lane;
-                const uint32_t a_prev = __shfl_sync(LFC_FULL, aa, pl);
-                int bin = -1;
-                if (valid) {
-                    if (lower) {
-                        bin = (int)((a_prev << 8) | aa);
-                    } else {
-                        const uint16_t pend = my_last[bb];
-                        if (pend != kNoPred) bin = (int)(((uint32_t)pend << 8) | aa);
-                        else my_first[bb] = (uint16_t)aa;
-                    }
-                }
-                __syncwarp();
-                if (valid && (m & lanemask_gt()) == 0) my_last[bb] = (uint16_t)aa;
-                __syncwarp();
-                const bool contrib = bin >= 0 && (bin >> 15) == pass;
-                const uint32_t hm = __match_any_sync(LFC_FULL, contrib ? (uint32_t)bin : 0x10000u + lane);
-                if (contrib && (hm & lanemask_lt()) == 0) atomicAdd(&sh_hist[bin & 0x7FFF], (uint32_t)__popc(hm));
-            }
-            __syncwarp();
-        }
-        __syncthreads();
-        for (int i = threadIdx.x; i < 32768; i += blockDim.x) {
-            const uint32_t c = sh_hist[i];
-            if (c) atomicAdd(&ghist[pass * 32768 + i], c);
-        }
-        __syncthreads();
+    const int t = threadIdx.x;
+    const int64_t ra64 = min(n, (int64_t)seg * kSegBytes + (int64_t)t * kRangeBytes);
+    const int len = (int)(min(n, ra64 + kRangeBytes) - ra64);
+    const uint8_t *R = S + ra64;
+    uint8_t *first = first_all + ((size_t)blockIdx.x * kChainThreads + t) * 256;
+    uint32_t *tblt = tbl + t;
+    for (int i = t; i < kHot * kHot; i += kChainThreads) hot[i] = 0;
+    for (int k = 0; k < 128; k++) tblt[k * kChainThreads] = 0xFFFFFFFFu;
+    __syncthreads();
+    uint32_t prev = len > 0 ? (uint32_t)S[ra64 == 0 ? n - 1 : ra64 - 1] : 0u;
+    uint32_t c0 = 0;
+    const int full = len & ~15;
+    for (int i0 = 0; i0 < full; i0 += 16) {
+        const uint4 v = __ldg(reinterpret_cast<const uint4 *>(R + i0));
+        const uint32_t wv[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+        for (int k = 0; k < 16; k++) chain_byte((wv[k >> 2] >> (8 * (k & 3))) & 0xFFu, prev, tblt, hot, ghist, first, c0);
     }
-    if (threadIdx.x < 256) {
-        const int bv = threadIdx.x;
-        uint16_t first = kNoPred, cur = kNoPred;
-        for (int ww = 0; ww < kChainWarps; ww++) {
-            const uint16_t f = sh_first[ww * 256 + bv];
-            if (f == kNoPred) continue;
+    for (int i = full; i < len; i++) chain_byte(R[i], prev, tblt, hot, ghist, first, c0);
+    if (c0) atomicAdd(&hot[0], c0);
+    __syncthreads();
+    for (int i = t; i < kHot * kHot; i += kChainThreads) {
+        const uint32_t c = hot[i];
+        if (c) atomicAdd(&ghist[((uint32_t)(i / kHot) << 8) | (uint32_t)(i % kHot)], c);
+    }
+    // stitch the threads' ranges in order (thread b handles byte value b)
+    if (t < 256) {
+        const int bv = t;
+        const uint8_t *first_cta = first_all + (size_t)blockIdx.x * kChainThreads * 256;
+        uint16_t f0 = kNoPred, cur = kNoPred;
+        for (int tt = 0; tt < kChainThreads; tt++) {
+            const uint16_t last = (uint16_t)((tbl[(bv >> 1) * kChainThreads + tt] >> ((bv & 1) * 16)) & 0xFFFFu);
+            if (last == kNoPred) continue;
+            const uint16_t f = first_cta[(size_t)tt * 256 + bv];
             if (cur != kNoPred) atomicAdd(&ghist[((uint32_t)cur << 8) | f], 1u);
-            else first = f;
-            cur = sh_last[ww * 256 + bv];
+            else f0 = f;
+            cur = last;
         }
         uint16_t *out = summ + (size_t)(J.summ_off + (int64_t)ci * J.segs + seg) * 512;
-        out[bv] = first;
+        out[bv] = f0;
         out[256 + bv] = cur;
     }
 }
@@ -306,8 +296,9 @@ cudaError_t launch_chain_hist(lfc_plan P, const JudgeFrame *d_frames, int nframe
     const size_t smem = chain_smem_bytes();
     cudaError_t e = cudaFuncSetAttribute(chain_hist_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    chain_hist_kernel<<<(unsigned)total_ctas, kChainWarps * 32, smem, P->stream>>>(
-        d_frames, nframes, P->ws.cstream, P->ws.cstream_slot, P->ws.cstream_kmax, P->ws.hist, P->ws.summ);
+    chain_hist_kernel<<<(unsigned)total_ctas, kChainThreads, smem, P->stream>>>(
+        d_frames, nframes, P->ws.cstream, P->ws.cstream_slot, P->ws.cstream_kmax, P->ws.hist, P->ws.summ,
+        P->ws.chain_first);
     count_launches(P, 1);
     return cudaGetLastError();
 }

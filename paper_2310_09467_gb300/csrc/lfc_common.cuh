@@ -158,6 +158,7 @@ struct Workspace {
     uint64_t *l2tab = nullptr;     // 65536
     int64_t summ_cap = 0;
     uint8_t *cstream = nullptr;    // candidate streams: judge_frames_cap * cstream_kmax slots
+    uint8_t *chain_first = nullptr;// first-occurrence predecessors, per chain CTA x thread x 256
     int64_t cstream_slot = 0;
     int cstream_kmax = 0;
     // symbol streams of the frames being compressed
@@ -239,6 +240,7 @@ size_t judge_smem_bytes(int maxW);
 size_t emit_all_smem_bytes(int p, int ts, int nslots);
 size_t chain_smem_bytes();
 int64_t chain_seg_bytes();
+int64_t chain_first_bytes_per_cta();
 cudaError_t launch_emit_all(lfc_plan P, const JudgeFrame *d_frames, int nframes, const uint8_t *d_cand, int max_tiles,
                             int TS, int nslots_max, int any_temporal, int max_p);
 cudaError_t launch_chain_hist(lfc_plan P, const JudgeFrame *d_frames, int nframes, const uint8_t *d_cand, int64_t total_ctas);
