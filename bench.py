@@ -186,6 +186,7 @@ def main():
     clocks = Clocks(local)
     plan.set_timing(True)
     l0 = plan.launch_count()
+    bc0 = plan.bwt_counters()
     barrier()
     clocks.start()
     step_ms = []
@@ -201,6 +202,11 @@ def main():
     clk = clocks.stop()
     stages = plan.timing()
     launches = plan.launch_count() - l0
+    bc1 = plan.bwt_counters()
+    bwt_info = {"rounds_per_call": (bc1["rounds"] - bc0["rounds"]) / max(1, bc1["calls"] - bc0["calls"]),
+                "tied_per_round_per_call": [(b - a) / max(1, bc1["calls"] - bc0["calls"]) for a, b in
+                                            zip(bc0["tied_per_round"] + [0] * 32, bc1["tied_per_round"])],
+                "elements_per_call": (bc1["input_bytes"] - bc0["input_bytes"]) / max(1, bc1["calls"] - bc0["calls"])}
     plan.set_timing(False)
     total_ms = sum(step_ms)
     if world > 1:
@@ -273,7 +279,7 @@ def main():
                          "peak_source": peak_kind + " (hbm_gbs)", "bytes_model": kmodel,
                          "avg_launch_ms": kms / max(1, kspans), "launches_timed": kspans},
             "stages_ms_per_step": {k: v[0] / args.steps for k, v in stages.items()},
-            "clocks": clk, "gpu_launches": launches,
+            "clocks": clk, "gpu_launches": launches, "bwt": bwt_info,
             "e2e": {"value": e2e_value, "unit": "MB/s", "h2d_bytes_per_step": raw_bytes, "d2h_bytes_per_step": d2h},
             "cpu_baseline": cpu,
         }

@@ -157,6 +157,22 @@ size_t lfc_max_compressed_bytes(int32_t width, int32_t height, int32_t block_byt
 int lfc_compress(lfc_plan plan, const lfc_frame *h_frames, int n, const uint8_t *d_choice,
                  uint8_t *d_out, size_t out_cap, uint64_t *d_out_sizes);
 
+/* A batch is one lfc_compress call captured once as a CUDA graph (with the
+ * suffix-sort rounds as a device-driven WHILE node), so that a stream of
+ * batches with the same frame buffers and geometry costs one cudaGraphLaunch
+ * each. lfc_batch_create takes the same arguments as lfc_compress, records
+ * every descriptor table in a device buffer it owns (allocated here, not on
+ * launch), captures the work on the plan's stream and instantiates it; it is
+ * synchronous. lfc_batch_launch replays it on the plan's stream with the data
+ * the frame buffers hold at that time; outputs land as for lfc_compress.
+ * Batches share the plan's workspace: launches on one plan are serialised by
+ * its stream. Errors: as lfc_compress, plus NOMEM, CUDA. */
+typedef struct lfc_batch_s *lfc_batch;
+int lfc_batch_create(lfc_plan plan, const lfc_frame *h_frames, int n, const uint8_t *d_choice, uint8_t *d_out,
+                     size_t out_cap, uint64_t *d_out_sizes, lfc_batch *out);
+int lfc_batch_launch(lfc_batch batch);
+void lfc_batch_destroy(lfc_batch batch);
+
 /* Standalone bzip2 streams of arbitrary byte blocks (the coder stage of
  * lfc_compress on its own). Block b is d_in[h_offsets[b] .. + h_sizes[b]),
  * 1 <= size <= 720000 and n_blocks <= the plan's block capacity
@@ -214,6 +230,14 @@ int lfc_plan_timing(lfc_plan plan, double *ms, int64_t *spans, int n_stages);
 
 /* Kernel launches this plan has issued since creation (host counter). */
 int64_t lfc_plan_launch_count(lfc_plan plan);
+
+/* Suffix-sort counters since creation (host values, read without a sync):
+ * out[0] BWT calls, out[1] prefix-doubling rounds, out[2] elements sorted
+ * (sum of RLE1 block lengths; exact after the stream is synchronised),
+ * out[3] tied elements entering rounds (sum over rounds), out[4 + r] tied
+ * elements entering round r (r < n - 4, summed over calls). Returns the
+ * number of values written. */
+int lfc_plan_bwt_counters(lfc_plan plan, int64_t *out, int n);
 
 /* Allocation-free judge of one frame. The paper has no counterpart: this
  * entry point exists for callers that may not allocate device memory, such

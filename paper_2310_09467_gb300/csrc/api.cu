@@ -99,6 +99,8 @@ static cudaEvent_t take_event(lfc_plan P) {
 
 void stage_begin(lfc_plan P, int stage) {
     if (!P->timing) return;
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(P->stream, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone) return;
     cudaEvent_t e = take_event(P);
     cudaEventRecord(e, P->stream);
     P->open_ev[stage] = e;
@@ -148,6 +150,18 @@ extern "C" int lfc_plan_timing(lfc_plan P, double *ms, int64_t *spans, int n_sta
 }
 
 extern "C" int64_t lfc_plan_launch_count(lfc_plan P) { return P ? P->launches : 0; }
+
+extern "C" int lfc_plan_bwt_counters(lfc_plan P, int64_t *out, int n) {
+    if (!P || !out || n < 0) return 0;
+    int k = 0;
+    const int64_t head[3] = {P->bwt_calls, P->bwt_rounds, P->bwt_tied_total};
+    if (k < n) out[k++] = head[0];
+    if (k < n) out[k++] = head[1];
+    if (k < n) out[k++] = P->bwt_elements_in;
+    if (k < n) out[k++] = head[2];
+    for (int r = 0; r < 32 && k < n; r++) out[k++] = P->bwt_round_tied[r];
+    return k;
+}
 
 extern "C" const char *lfc_status_string(int s) {
     switch (s) {
@@ -287,6 +301,8 @@ extern "C" int lfc_plan_create(const lfc_config *cfg, void *cuda_stream, lfc_pla
 #undef AL
     if (e == cudaSuccess) e = cudaMalloc(&ws.chunk_desc, ws.chunk_desc_bytes);
     if (e == cudaSuccess) e = cudaMallocHost(reinterpret_cast<void **>(&ws.h_act_total), 4 * sizeof(int32_t));
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&P->aux_stream, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&P->cap_stream, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = init_l2_table(ws.l2tab, P->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(P->stream);
     if (e != cudaSuccess) {
@@ -308,11 +324,62 @@ extern "C" void lfc_plan_destroy(lfc_plan P) {
     for (cudaEvent_t e : P->open_ev)
         if (e) cudaEventDestroy(e);
     free_ws(P->ws);
+    if (P->aux_stream) cudaStreamDestroy(P->aux_stream);
+    if (P->cap_stream) cudaStreamDestroy(P->cap_stream);
     delete P;
 }
 
-// ------------------------------------------------------------------ judge
-static int judge_impl(lfc_plan P, const lfc_frame *frames, int n, uint8_t *d_choice, uint64_t *d_scores) {
+// ------------------------------------------------------- descriptor arena
+// Every call first lays out all of its descriptor tables on the host, copies
+// them to the device once, then only launches kernels. A batch keeps its
+// arena and replays the launches as a CUDA graph.
+namespace {
+
+struct Arena {
+    std::vector<uint8_t> host;
+    size_t reserve(size_t n) {
+        const size_t o = (host.size() + 15) & ~(size_t)15;
+        host.resize(o + n);
+        return o;
+    }
+    size_t put(const void *p, size_t n) {
+        const size_t o = reserve(n);
+        if (n) memcpy(host.data() + o, p, n);
+        return o;
+    }
+};
+
+struct JudgeChunk {
+    size_t off_tables = 0, off_cand = 0;
+    int nf = 0;
+    int64_t ctas = 0, nhist = 0;
+    JudgeLaunch L{};
+};
+
+struct CoderPass {
+    size_t off_blocks = 0, off_crc = 0, off_fo = 0;
+    int nblocks = 0, max_m = 0, f0 = 0, f1 = 0;
+    CrcRun crc;
+    std::vector<BlockDesc> blocks;
+};
+
+struct CompressDesc {
+    Arena arena;
+    std::vector<JudgeChunk> judge;
+    CrcRun frame_crc;
+    size_t off_frame_crc = 0;
+    std::vector<CoderPass> passes;
+    std::vector<FrameDev> fd;
+    std::vector<uint8_t *> dst;
+    int n = 0, bb = 0;
+};
+
+bool capturing(lfc_plan P) {
+    cudaStreamCaptureStatus st = cudaStreamCaptureStatusNone;
+    return cudaStreamIsCapturing(P->stream, &st) == cudaSuccess && st != cudaStreamCaptureStatusNone;
+}
+
+int build_judge(lfc_plan P, const lfc_frame *frames, int n, Arena &A, std::vector<JudgeChunk> &out) {
     Workspace &ws = P->ws;
     const int64_t seg_bytes = chain_seg_bytes();
     for (int f0 = 0; f0 < n; f0 += P->judge_frames_cap) {
@@ -322,7 +389,8 @@ static int judge_impl(lfc_plan P, const lfc_frame *frames, int n, uint8_t *d_cho
         std::vector<int32_t> frame_index(nf), hist_frame;
         std::vector<uint8_t> cand;
         int64_t cta = 0, hist = 0, summ = 0;
-        JudgeLaunch L{0, 16, 0, 0, 0};
+        JudgeChunk C;
+        C.L = JudgeLaunch{0, 16, 0, 0, 0};
         for (int i = 0; i < nf; i++) {
             const lfc_frame &fr = frames[f0 + i];
             const bool tmp = fr.prev != nullptr && !P->ids_temporal.empty();
@@ -337,9 +405,9 @@ static int judge_impl(lfc_plan P, const lfc_frame *frames, int n, uint8_t *d_cho
                 const int id = cand[k], f = id & 15, dom = (id >> 4) & 3;
                 if (f && dom != 1) fset[(id >> 7) & 1] |= 1u << f;
             }
-            L.nslots_max = std::max(L.nslots_max, std::max(__builtin_popcount(fset[0]), __builtin_popcount(fset[1])));
-            L.any_temporal |= tmp ? 1 : 0;
-            L.max_p = std::max(L.max_p, fr.pitch);
+            C.L.nslots_max = std::max(C.L.nslots_max, std::max(__builtin_popcount(fset[0]), __builtin_popcount(fset[1])));
+            C.L.any_temporal |= tmp ? 1 : 0;
+            C.L.max_p = std::max(C.L.max_p, fr.pitch);
             J.K = (int32_t)(cand.size() - J.cand_off);
             const int64_t nbytes = 2LL * fr.width * fr.height;
             J.rows_per_seg = 0;
@@ -354,41 +422,209 @@ static int judge_impl(lfc_plan P, const lfc_frame *frames, int n, uint8_t *d_cho
             frame_index[i] = f0 + i;
         }
         // lenslets per emission tile: as many as shared memory allows (<= 16)
-        L.TS = 16;
-        while (L.TS > 1 && emit_all_smem_bytes(L.max_p, L.TS, L.nslots_max) > 200 * 1024) L.TS /= 2;
-        if (emit_all_smem_bytes(L.max_p, L.TS, L.nslots_max) > 200 * 1024)
+        C.L.TS = 16;
+        while (C.L.TS > 1 && emit_all_smem_bytes(C.L.max_p, C.L.TS, C.L.nslots_max) > 200 * 1024) C.L.TS /= 2;
+        if (emit_all_smem_bytes(C.L.max_p, C.L.TS, C.L.nslots_max) > 200 * 1024)
             return fail(P, LFC_ERR_INVALID_ARG, "pitch too large for the emission tile");
         for (int i = 0; i < nf; i++) {
             const FrameDev &F = jf[i].F;
-            L.max_tiles = std::max(L.max_tiles, F.Ny * ((F.Nx + L.TS - 1) / L.TS));
+            C.L.max_tiles = std::max(C.L.max_tiles, F.Ny * ((F.Nx + C.L.TS - 1) / C.L.TS));
         }
         if (summ > ws.summ_cap) return fail(P, LFC_ERR_INVALID_ARG, "judge summary capacity exceeded");
-        // one staging blob: frames | frame_index | hist_frame | cand
-        const size_t o1 = sizeof(JudgeFrame) * nf;
-        const size_t o2 = o1 + 4 * nf;
-        const size_t o3 = o2 + 4 * hist_frame.size();
-        const size_t total = o3 + cand.size();
-        if (total > ((size_t)1 << 20)) return fail(P, LFC_ERR_INVALID_ARG, "judge table too large");
-        std::vector<uint8_t> blob(total);
-        memcpy(blob.data(), jf.data(), o1);
-        memcpy(blob.data() + o1, frame_index.data(), 4 * nf);
-        memcpy(blob.data() + o2, hist_frame.data(), 4 * hist_frame.size());
-        memcpy(blob.data() + o3, cand.data(), cand.size());
-        uint8_t *d = reinterpret_cast<uint8_t *>(ws.cand);
-        CK(cudaMemcpyAsync(d, blob.data(), total, cudaMemcpyHostToDevice, P->stream));
-        CK(launch_judge(P, reinterpret_cast<const JudgeFrame *>(d), nf, cta, L, d + o3, hist, d_scores, d_choice));
+        // frames | frame_index | hist_frame (the kernels find the tables behind the frames)
+        std::vector<uint8_t> t(sizeof(JudgeFrame) * nf + 4 * nf + 4 * hist_frame.size());
+        memcpy(t.data(), jf.data(), sizeof(JudgeFrame) * nf);
+        memcpy(t.data() + sizeof(JudgeFrame) * nf, frame_index.data(), 4 * nf);
+        memcpy(t.data() + sizeof(JudgeFrame) * nf + 4 * nf, hist_frame.data(), 4 * hist_frame.size());
+        C.off_tables = A.put(t.data(), t.size());
+        C.off_cand = A.put(cand.data(), cand.size());
+        C.nf = nf;
+        C.ctas = cta;
+        C.nhist = hist;
+        out.push_back(C);
     }
     return LFC_OK;
 }
 
-extern "C" int lfc_judge(lfc_plan P, const lfc_frame *frames, int n, uint8_t *d_choice, uint64_t *d_scores) {
-    if (!P || !frames || n < 1 || !d_choice) return fail(P, LFC_ERR_INVALID_ARG, "lfc_judge: bad arguments");
-    if (n > P->cfg.max_frames) return fail(P, LFC_ERR_INVALID_ARG, "lfc_judge: n > max_frames");
+int run_judge(lfc_plan P, const std::vector<JudgeChunk> &chunks, const uint8_t *d_arena, uint8_t *d_choice,
+              uint64_t *d_scores) {
+    int f0 = 0;
+    for (const JudgeChunk &C : chunks) {
+        CK(launch_judge(P, reinterpret_cast<const JudgeFrame *>(d_arena + C.off_tables), C.nf, C.ctas, C.L,
+                        d_arena + C.off_cand, C.nhist, d_scores, d_choice));
+        f0 += C.nf;
+    }
+    return LFC_OK;
+}
+
+// Coder descriptors for one pass over the given blocks.
+void build_pass(Arena &A, CoderPass &cp) {
+    int max_len = 0;
+    std::vector<const uint8_t *> ptr(cp.blocks.size());
+    std::vector<int64_t> len(cp.blocks.size());
+    for (size_t b = 0; b < cp.blocks.size(); b++) {
+        max_len = std::max(max_len, cp.blocks[b].len);
+        ptr[b] = cp.blocks[b].src;
+        len[b] = cp.blocks[b].len;
+    }
+    cp.nblocks = (int)cp.blocks.size();
+    cp.max_m = std::min(kRleCap, max_len + max_len / 4 + 4);
+    cp.off_blocks = A.put(cp.blocks.data(), sizeof(BlockDesc) * cp.blocks.size());
+    const int nchunks = crc_count_chunks(len.data(), cp.nblocks);
+    cp.off_crc = A.reserve(crc_table_bytes(nchunks, cp.nblocks));
+    crc_build_tables(ptr.data(), len.data(), cp.nblocks, A.host.data() + cp.off_crc, &cp.crc);
+}
+
+int run_pass(lfc_plan P, const CoderPass &cp, const uint8_t *d_arena) {
+    Workspace &ws = P->ws;
+    const int nb = cp.nblocks;
+    for (const BlockDesc &b : cp.blocks) P->bwt_elements_in += b.len;
+    CK(cudaMemsetAsync(ws.bstate, 0, sizeof(BlockState) * nb, P->stream));
+    stage_begin(P, LFC_STAGE_CRC);
+    CK(launch_crc(P, d_arena + cp.off_crc, cp.crc, &ws.bstate[0].crc, (int)(sizeof(BlockState) / 4)));
+    stage_end(P, LFC_STAGE_CRC);
+    stage_begin(P, LFC_STAGE_RLE1);
+    CK(launch_rle1(P, nb, reinterpret_cast<const BlockDesc *>(d_arena + cp.off_blocks)));
+    stage_end(P, LFC_STAGE_RLE1);
+    CK(launch_bwt(P, nb, cp.max_m));
+    stage_begin(P, LFC_STAGE_MTF);
+    CK(launch_mtf_rle2(P, nb));
+    stage_end(P, LFC_STAGE_MTF);
+    stage_begin(P, LFC_STAGE_HUFFMAN);
+    CK(launch_huffman(P, nb));
+    stage_end(P, LFC_STAGE_HUFFMAN);
+    stage_begin(P, LFC_STAGE_PACK);
+    CK(launch_pack(P, nb));
+    stage_end(P, LFC_STAGE_PACK);
+    return LFC_OK;
+}
+
+int check_frames(lfc_plan P, const lfc_frame *frames, int n) {
+    if (!P || !frames || n < 1) return fail(P, LFC_ERR_INVALID_ARG, "bad frame list");
+    if (n > P->cfg.max_frames) return fail(P, LFC_ERR_INVALID_ARG, "n > max_frames");
     for (int i = 0; i < n; i++) {
-        int r = check_frame(P, frames[i]);
+        const int r = check_frame(P, frames[i]);
         if (r) return r;
     }
-    return judge_impl(P, frames, n, d_choice, d_scores ? d_scores : P->ws.scores);
+    return LFC_OK;
+}
+
+int build_compress(lfc_plan P, const lfc_frame *frames, int n, bool judge, size_t out_cap, CompressDesc &D,
+                   std::vector<uint64_t> &out_off) {
+    Workspace &ws = P->ws;
+    const int bb = block_bytes_of(P);
+    D.n = n;
+    D.bb = bb;
+    out_off.resize(n);
+    uint64_t need = 0;
+    for (int i = 0; i < n; i++) {
+        out_off[i] = need;
+        need += container_bound(frames[i].width, frames[i].height, bb);
+    }
+    if (need > out_cap) return fail(P, LFC_ERR_CAPACITY, "lfc_compress: out_cap below the sum of container bounds");
+    if (judge) {
+        const int r = build_judge(P, frames, n, D.arena, D.judge);
+        if (r) return r;
+    }
+    D.fd.resize(n);
+    D.dst.resize(n);
+    std::vector<const uint8_t *> raw(n);
+    std::vector<int64_t> rawlen(n);
+    for (int i = 0; i < n; i++) {
+        D.fd[i] = to_dev(frames[i], frames[i].prev != nullptr);
+        D.dst[i] = ws.stream + (size_t)i * ws.stream_slot;
+        raw[i] = reinterpret_cast<const uint8_t *>(frames[i].data);
+        rawlen[i] = 2LL * frames[i].width * frames[i].height;
+    }
+    const int nck = crc_count_chunks(rawlen.data(), n);
+    D.off_frame_crc = D.arena.reserve(crc_table_bytes(nck, n));
+    crc_build_tables(raw.data(), rawlen.data(), n, D.arena.host.data() + D.off_frame_crc, &D.frame_crc);
+    int f0 = 0;
+    while (f0 < n) {
+        CoderPass cp;
+        std::vector<FrameOut> fo;
+        int f1 = f0;
+        while (f1 < n) {
+            const int64_t nbytes = rawlen[f1];
+            const int64_t nbf = (nbytes + bb - 1) / bb;
+            if ((int64_t)cp.blocks.size() + nbf > P->block_cap) break;
+            FrameOut F;
+            F.out_off = out_off[f1];
+            F.block0 = (int32_t)cp.blocks.size();
+            F.nblocks = (int32_t)nbf;
+            F.W = frames[f1].width;
+            F.H = frames[f1].height;
+            F.p = frames[f1].pitch;
+            F.pad = 0;
+            fo.push_back(F);
+            for (int64_t k = 0; k < nbf; k++) {
+                BlockDesc d;
+                d.src = D.dst[f1] + k * bb;
+                d.len = (int32_t)std::min<int64_t>(bb, nbytes - k * bb);
+                d.frame = f1;
+                cp.blocks.push_back(d);
+            }
+            f1++;
+        }
+        if (f1 == f0) return fail(P, LFC_ERR_INVALID_ARG, "lfc_compress: frame needs more blocks than the plan holds");
+        cp.f0 = f0;
+        cp.f1 = f1;
+        build_pass(D.arena, cp);
+        cp.off_fo = D.arena.put(fo.data(), sizeof(FrameOut) * fo.size());
+        D.passes.push_back(std::move(cp));
+        f0 = f1;
+    }
+    return LFC_OK;
+}
+
+int run_compress(lfc_plan P, const CompressDesc &D, const uint8_t *d_arena, const uint8_t *d_choice, uint8_t *d_out,
+                 uint64_t *d_out_sizes) {
+    Workspace &ws = P->ws;
+    const uint8_t *choice = d_choice;
+    if (!D.judge.empty()) {
+        const int r = run_judge(P, D.judge, d_arena, ws.choice, ws.scores);
+        if (r) return r;
+        choice = ws.choice;
+    }
+    stage_begin(P, LFC_STAGE_EMIT);
+    CK(launch_emit(D.fd.data(), choice, D.n, D.dst.data(), P->stream));
+    count_launches(P, (D.n + 7) / 8);
+    stage_end(P, LFC_STAGE_EMIT);
+    stage_begin(P, LFC_STAGE_CRC);
+    CK(launch_crc(P, d_arena + D.off_frame_crc, D.frame_crc, ws.frame_crc, 1));
+    stage_end(P, LFC_STAGE_CRC);
+    for (const CoderPass &cp : D.passes) {
+        const int r = run_pass(P, cp, d_arena);
+        if (r) return r;
+        stage_begin(P, LFC_STAGE_CONTAINER);
+        CK(launch_container(P, cp.f1 - cp.f0, cp.nblocks, reinterpret_cast<const FrameOut *>(d_arena + cp.off_fo),
+                            choice + cp.f0, ws.frame_crc + cp.f0, d_out, d_out_sizes + cp.f0, D.bb));
+        stage_end(P, LFC_STAGE_CONTAINER);
+    }
+    return LFC_OK;
+}
+
+int stage_arena(lfc_plan P, const Arena &A) {
+    if (A.host.size() > P->ws.chunk_desc_bytes) return fail(P, LFC_ERR_INVALID_ARG, "descriptor tables exceed the plan's staging buffer");
+    if (!A.host.empty())
+        CK(cudaMemcpyAsync(P->ws.chunk_desc, A.host.data(), A.host.size(), cudaMemcpyHostToDevice, P->stream));
+    return LFC_OK;
+}
+
+}  // namespace
+
+extern "C" int lfc_judge(lfc_plan P, const lfc_frame *frames, int n, uint8_t *d_choice, uint64_t *d_scores) {
+    if (!P || !d_choice) return fail(P, LFC_ERR_INVALID_ARG, "lfc_judge: bad arguments");
+    int r = check_frames(P, frames, n);
+    if (r) return r;
+    Arena A;
+    std::vector<JudgeChunk> chunks;
+    r = build_judge(P, frames, n, A, chunks);
+    if (r) return r;
+    r = stage_arena(P, A);
+    if (r) return r;
+    return run_judge(P, chunks, reinterpret_cast<const uint8_t *>(P->ws.chunk_desc), d_choice,
+                     d_scores ? d_scores : P->ws.scores);
 }
 
 extern "C" int lfc_symbols(lfc_plan P, const lfc_frame *frame, int id, uint16_t *d_out) {
@@ -402,52 +638,29 @@ extern "C" int lfc_symbols(lfc_plan P, const lfc_frame *frame, int id, uint16_t 
     return LFC_OK;
 }
 
-// ------------------------------------------------------------------ coder
-// Runs the coder on blocks[0..nb) of the plan's block table (already staged).
-static int code_blocks(lfc_plan P, const std::vector<BlockDesc> &blocks) {
-    Workspace &ws = P->ws;
-    const int nb = (int)blocks.size();
-    int max_len = 0;
-    for (const BlockDesc &b : blocks) max_len = std::max(max_len, b.len);
-    CK(cudaMemcpyAsync(ws.blocks, blocks.data(), sizeof(BlockDesc) * nb, cudaMemcpyHostToDevice, P->stream));
-    CK(cudaMemsetAsync(ws.bstate, 0, sizeof(BlockState) * nb, P->stream));
-    stage_begin(P, LFC_STAGE_CRC);
-    CK(launch_block_crc(P, blocks.data(), nb, ws.bstate));
-    stage_end(P, LFC_STAGE_CRC);
-    stage_begin(P, LFC_STAGE_RLE1);
-    CK(launch_rle1(P, nb));
-    stage_end(P, LFC_STAGE_RLE1);
-    const int max_m = std::min(kRleCap, max_len + max_len / 4 + 4);
-    CK(launch_bwt(P, nb, max_m));
-    stage_begin(P, LFC_STAGE_MTF);
-    CK(launch_mtf_rle2(P, nb));
-    stage_end(P, LFC_STAGE_MTF);
-    stage_begin(P, LFC_STAGE_HUFFMAN);
-    CK(launch_huffman(P, nb));
-    stage_end(P, LFC_STAGE_HUFFMAN);
-    stage_begin(P, LFC_STAGE_PACK);
-    CK(launch_pack(P, nb));
-    stage_end(P, LFC_STAGE_PACK);
-    return LFC_OK;
-}
-
 extern "C" int lfc_bzip2_encode(lfc_plan P, const uint8_t *d_in, const uint64_t *h_offsets, const uint32_t *h_sizes,
                                 int n_blocks, uint8_t *d_out, size_t out_stride, uint32_t *d_stream_sizes) {
     if (!P || !d_in || !h_offsets || !h_sizes || !d_out || !d_stream_sizes || n_blocks < 1)
         return fail(P, LFC_ERR_INVALID_ARG, "lfc_bzip2_encode: bad arguments");
     if (n_blocks > P->block_cap) return fail(P, LFC_ERR_INVALID_ARG, "lfc_bzip2_encode: too many blocks");
-    std::vector<BlockDesc> blocks(n_blocks);
+    CoderPass cp;
     uint32_t max_size = 0;
     for (int b = 0; b < n_blocks; b++) {
         if (h_sizes[b] < 1 || h_sizes[b] > (uint32_t)kMaxBlockBytes)
             return fail(P, LFC_ERR_INVALID_ARG, "lfc_bzip2_encode: block size outside 1..720000");
-        blocks[b].src = d_in + h_offsets[b];
-        blocks[b].len = (int32_t)h_sizes[b];
-        blocks[b].frame = -1;
+        BlockDesc d;
+        d.src = d_in + h_offsets[b];
+        d.len = (int32_t)h_sizes[b];
+        d.frame = -1;
+        cp.blocks.push_back(d);
         max_size = std::max(max_size, h_sizes[b]);
     }
     if (out_stride < (size_t)stream_bound(max_size)) return fail(P, LFC_ERR_CAPACITY, "lfc_bzip2_encode: out_stride too small");
-    int r = code_blocks(P, blocks);
+    Arena A;
+    build_pass(A, cp);
+    int r = stage_arena(P, A);
+    if (r) return r;
+    r = run_pass(P, cp, reinterpret_cast<const uint8_t *>(P->ws.chunk_desc));
     if (r) return r;
     stage_begin(P, LFC_STAGE_CONTAINER);
     CK(launch_copy_streams(P, n_blocks, d_out, out_stride, d_stream_sizes));
@@ -457,73 +670,96 @@ extern "C" int lfc_bzip2_encode(lfc_plan P, const uint8_t *d_in, const uint64_t 
 
 extern "C" int lfc_compress(lfc_plan P, const lfc_frame *frames, int n, const uint8_t *d_choice, uint8_t *d_out,
                             size_t out_cap, uint64_t *d_out_sizes) {
-    if (!P || !frames || n < 1 || !d_out || !d_out_sizes) return fail(P, LFC_ERR_INVALID_ARG, "lfc_compress: bad arguments");
-    if (n > P->cfg.max_frames) return fail(P, LFC_ERR_INVALID_ARG, "lfc_compress: n > max_frames");
-    Workspace &ws = P->ws;
-    const int bb = block_bytes_of(P);
-    std::vector<uint64_t> out_off(n);
-    uint64_t need = 0;
-    for (int i = 0; i < n; i++) {
-        int r = check_frame(P, frames[i]);
-        if (r) return r;
-        out_off[i] = need;
-        need += container_bound(frames[i].width, frames[i].height, bb);
+    if (!P || !d_out || !d_out_sizes) return fail(P, LFC_ERR_INVALID_ARG, "lfc_compress: bad arguments");
+    int r = check_frames(P, frames, n);
+    if (r) return r;
+    CompressDesc D;
+    std::vector<uint64_t> out_off;
+    r = build_compress(P, frames, n, d_choice == nullptr, out_cap, D, out_off);
+    if (r) return r;
+    r = stage_arena(P, D.arena);
+    if (r) return r;
+    return run_compress(P, D, reinterpret_cast<const uint8_t *>(P->ws.chunk_desc), d_choice, d_out, d_out_sizes);
+}
+
+// ------------------------------------------------------------------ batches
+struct lfc_batch_s {
+    lfc_plan P = nullptr;
+    uint8_t *d_arena = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    int64_t nodes = 0;
+};
+
+extern "C" int lfc_batch_create(lfc_plan P, const lfc_frame *frames, int n, const uint8_t *d_choice, uint8_t *d_out,
+                                size_t out_cap, uint64_t *d_out_sizes, lfc_batch *out) {
+    if (!P || !d_out || !d_out_sizes || !out) return fail(P, LFC_ERR_INVALID_ARG, "lfc_batch_create: bad arguments");
+    *out = nullptr;
+    int r = check_frames(P, frames, n);
+    if (r) return r;
+    CompressDesc D;
+    std::vector<uint64_t> out_off;
+    r = build_compress(P, frames, n, d_choice == nullptr, out_cap, D, out_off);
+    if (r) return r;
+    lfc_batch B = new (std::nothrow) lfc_batch_s();
+    if (!B) return fail(P, LFC_ERR_NOMEM, "lfc_batch_create: host allocation");
+    B->P = P;
+    cudaError_t e = cudaMalloc(reinterpret_cast<void **>(&B->d_arena), std::max<size_t>(D.arena.host.size(), 16));
+    if (e == cudaSuccess && !D.arena.host.empty())
+        e = cudaMemcpy(B->d_arena, D.arena.host.data(), D.arena.host.size(), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(P->stream);
+    if (e != cudaSuccess) {
+        if (B->d_arena) cudaFree(B->d_arena);
+        delete B;
+        return fail(P, e == cudaErrorMemoryAllocation ? LFC_ERR_NOMEM : LFC_ERR_CUDA, "lfc_batch_create: arena", e);
     }
-    if (need > out_cap) return fail(P, LFC_ERR_CAPACITY, "lfc_compress: out_cap below the sum of container bounds");
-    const uint8_t *choice = d_choice;
-    if (!choice) {
-        int r = judge_impl(P, frames, n, ws.choice, ws.scores);
-        if (r) return r;
-        choice = ws.choice;
+    // record on the plan's capture stream (the plan's own stream may be the
+    // legacy default stream, which cannot be captured); replay on the plan's
+    // stream
+    const bool was_timing = P->timing;
+    P->timing = false;
+    const int64_t l0 = P->launches;
+    cudaStream_t home = P->stream;
+    P->stream = P->cap_stream;
+    e = cudaStreamBeginCapture(P->stream, cudaStreamCaptureModeThreadLocal);
+    int rr = e == cudaSuccess ? run_compress(P, D, B->d_arena, d_choice, d_out, d_out_sizes)
+                              : fail(P, LFC_ERR_CUDA, "lfc_batch_create: begin capture", e);
+    cudaGraph_t g = nullptr;
+    cudaError_t e2 = cudaStreamEndCapture(P->stream, &g);
+    P->stream = home;
+    P->timing = was_timing;
+    B->nodes = P->launches - l0;
+    P->launches = l0;
+    if (e == cudaSuccess) e = e2;
+    if (e == cudaSuccess && rr == LFC_OK) e = cudaGraphInstantiate(&B->exec, g, 0);
+    B->graph = g;
+    if (e != cudaSuccess || rr != LFC_OK) {
+        if (B->exec) cudaGraphExecDestroy(B->exec);
+        if (g) cudaGraphDestroy(g);
+        cudaFree(B->d_arena);
+        delete B;
+        cudaGetLastError();
+        return rr != LFC_OK ? rr : fail(P, LFC_ERR_CUDA, "lfc_batch_create: graph capture", e);
     }
-    std::vector<FrameDev> fd(n);
-    std::vector<uint8_t *> dst(n);
-    std::vector<const uint8_t *> raw(n);
-    std::vector<int64_t> rawlen(n);
-    for (int i = 0; i < n; i++) {
-        fd[i] = to_dev(frames[i], frames[i].prev != nullptr);
-        dst[i] = ws.stream + (size_t)i * ws.stream_slot;
-        raw[i] = reinterpret_cast<const uint8_t *>(frames[i].data);
-        rawlen[i] = 2LL * frames[i].width * frames[i].height;
-    }
-    stage_begin(P, LFC_STAGE_EMIT);
-    CK(launch_emit(fd.data(), choice, n, dst.data(), P->stream));
-    count_launches(P, (n + 7) / 8);
-    stage_end(P, LFC_STAGE_EMIT);
-    stage_begin(P, LFC_STAGE_CRC);
-    CK(launch_range_crc(P, raw.data(), rawlen.data(), n, ws.frame_crc));
-    stage_end(P, LFC_STAGE_CRC);
-    // passes of whole frames
-    int f0 = 0;
-    while (f0 < n) {
-        std::vector<BlockDesc> blocks;
-        std::vector<int32_t> block0;
-        int f1 = f0;
-        while (f1 < n) {
-            const int64_t nbytes = rawlen[f1];
-            const int64_t nbf = (nbytes + bb - 1) / bb;
-            if ((int64_t)blocks.size() + nbf > P->block_cap) break;
-            block0.push_back((int32_t)blocks.size());
-            for (int64_t k = 0; k < nbf; k++) {
-                BlockDesc d;
-                d.src = dst[f1] + k * bb;
-                d.len = (int32_t)std::min<int64_t>(bb, nbytes - k * bb);
-                d.frame = f1;
-                blocks.push_back(d);
-            }
-            f1++;
-        }
-        if (f1 == f0) return fail(P, LFC_ERR_INVALID_ARG, "lfc_compress: frame needs more blocks than the plan holds");
-        block0.push_back((int32_t)blocks.size());
-        int r = code_blocks(P, blocks);
-        if (r) return r;
-        stage_begin(P, LFC_STAGE_CONTAINER);
-        CK(launch_container(P, f1 - f0, block0.data(), fd.data() + f0, choice + f0, ws.frame_crc + f0, d_out,
-                            out_off.data() + f0, d_out_sizes + f0, bb));
-        stage_end(P, LFC_STAGE_CONTAINER);
-        f0 = f1;
-    }
+    *out = B;
     return LFC_OK;
+}
+
+extern "C" int lfc_batch_launch(lfc_batch B) {
+    if (!B) return LFC_ERR_INVALID_ARG;
+    lfc_plan P = B->P;
+    CK(cudaGraphLaunch(B->exec, P->stream));
+    P->launches += B->nodes;
+    return LFC_OK;
+}
+
+extern "C" void lfc_batch_destroy(lfc_batch B) {
+    if (!B) return;
+    cudaStreamSynchronize(B->P->stream);
+    if (B->exec) cudaGraphExecDestroy(B->exec);
+    if (B->graph) cudaGraphDestroy(B->graph);
+    if (B->d_arena) cudaFree(B->d_arena);
+    delete B;
 }
 
 static uint32_t rd32h(const uint8_t *p) {

@@ -75,9 +75,9 @@ __global__ void __launch_bounds__(1024) rle1_kernel(const BlockDesc *__restrict_
     if (threadIdx.x == 0) st[b].m = total_out;
 }
 
-cudaError_t launch_rle1(lfc_plan P, int nblocks) {
+cudaError_t launch_rle1(lfc_plan P, int nblocks, const BlockDesc *d_blocks) {
     Workspace &ws = P->ws;
-    rle1_kernel<<<nblocks, 1024, 0, P->stream>>>(ws.blocks, ws.bstate, ws.rle, ws.sa2);
+    rle1_kernel<<<nblocks, 1024, 0, P->stream>>>(d_blocks, ws.bstate, ws.rle, ws.sa2);
     count_launches(P, 1);
     return cudaGetLastError();
 }
@@ -107,12 +107,18 @@ __device__ __forceinline__ int sort_count(const BlockState &s, int h) {
 }
 
 // Per-tile digit histogram, stored digit-major: cnt[b][digit][tile].
+// Round state in device memory: rs[0] tied elements after the round, rs[1]
+// their per-block maximum, rs[2] the shift h, rs[3] the round number.
 template <int MODE>
-__global__ void __launch_bounds__(kSortThreads) radix_hist_kernel(int pass, int h, const BlockState *__restrict__ st,
+__device__ __forceinline__ int round_h(const int32_t *rs) { return MODE == 0 ? 0 : rs[2]; }
+
+template <int MODE>
+__global__ void __launch_bounds__(kSortThreads) radix_hist_kernel(int pass, const int32_t *__restrict__ rs, const BlockState *__restrict__ st,
                                                                   const int32_t *__restrict__ in_all, const uint8_t *__restrict__ rle_all,
                                                                   const int32_t *__restrict__ rank_all, uint32_t *__restrict__ cnt_all) {
     __shared__ uint32_t hst[256];
     const int b = blockIdx.y, tile = blockIdx.x;
+    const int h = round_h<MODE>(rs);
     const BlockState s = st[b];
     const int n = sort_count<MODE>(s, h);
     if (tile * kTile >= n) return;
@@ -138,9 +144,10 @@ __global__ void __launch_bounds__(kSortThreads) radix_hist_kernel(int pass, int 
 
 // Exclusive scan of a block's counts in (digit, tile) order, in place.
 template <int MODE>
-__global__ void __launch_bounds__(1024) radix_scan_kernel(int h, const BlockState *__restrict__ st, uint32_t *__restrict__ cnt_all) {
+__global__ void __launch_bounds__(1024) radix_scan_kernel(const int32_t *__restrict__ rs, const BlockState *__restrict__ st, uint32_t *__restrict__ cnt_all) {
     __shared__ uint32_t sh[33];
     const int b = blockIdx.x;
+    const int h = round_h<MODE>(rs);
     const int n = sort_count<MODE>(st[b], h);
     if (n == 0) return;
     const int nt = (n + kTile - 1) / kTile;
@@ -163,7 +170,7 @@ __global__ void __launch_bounds__(1024) radix_scan_kernel(int h, const BlockStat
 // 32 at a time in order; equal digits are ranked with __match_any_sync and a
 // per-warp running count, then offset by earlier warps' counts.
 template <int MODE>
-__global__ void __launch_bounds__(kSortThreads) radix_scatter_kernel(int pass, int h, const BlockState *__restrict__ st,
+__global__ void __launch_bounds__(kSortThreads) radix_scatter_kernel(int pass, const int32_t *__restrict__ rs, const BlockState *__restrict__ st,
                                                                      const int32_t *__restrict__ in_all, int32_t *__restrict__ out_all,
                                                                      const uint8_t *__restrict__ rle_all, const int32_t *__restrict__ rank_all,
                                                                      const uint32_t *__restrict__ cnt_all) {
@@ -171,6 +178,7 @@ __global__ void __launch_bounds__(kSortThreads) radix_scatter_kernel(int pass, i
     __shared__ uint32_t wcnt[NW][256];
     __shared__ uint32_t base[256];
     const int b = blockIdx.y, tile = blockIdx.x;
+    const int h = round_h<MODE>(rs);
     const BlockState s = st[b];
     const int n = sort_count<MODE>(s, h);
     if (tile * kTile >= n) return;
@@ -249,16 +257,18 @@ __device__ __forceinline__ uint64_t elem_key(int k, const int32_t *sorted, const
 // Pass A: per tile, the largest head position and the number of elements
 // that stay tied. Head flags go to flags[] for pass B.
 template <int MODE>
-__global__ void __launch_bounds__(kSortThreads) heads_tile_kernel(int h, const BlockState *__restrict__ st,
-                                                                  const int32_t *__restrict__ sorted_all, const int32_t *__restrict__ act_all,
+__global__ void __launch_bounds__(kSortThreads) heads_tile_kernel(const int32_t *__restrict__ rs, const BlockState *__restrict__ st,
+                                                                  const int32_t *__restrict__ sorted_all, const int32_t *__restrict__ actA,
+                                                                  const int32_t *__restrict__ actB,
                                                                   const uint8_t *__restrict__ rle_all, const int32_t *__restrict__ rank_all,
                                                                   uint8_t *__restrict__ flags_all, int32_t *__restrict__ aux_all) {
     const int b = blockIdx.y, tile = blockIdx.x;
+    const int h = round_h<MODE>(rs);
     const BlockState s = st[b];
     const int n = sort_count<MODE>(s, h);
     if (tile * kTile >= n) return;
     const int32_t *sorted = sorted_all + (size_t)b * kBlockCap;
-    const int32_t *act = act_all + (size_t)b * kBlockCap;
+    const int32_t *act = ((MODE == 1 && (rs[3] & 1)) ? actB : actA) + (size_t)b * kBlockCap;
     const uint8_t *rle = rle_all + (size_t)b * kBlockCap;
     const int32_t *rank = rank_all + (size_t)b * kBlockCap;
     uint8_t *flags = flags_all + (size_t)b * kBlockCap;
@@ -301,11 +311,12 @@ __global__ void __launch_bounds__(kSortThreads) heads_tile_kernel(int h, const B
 // Pass across tiles of a block: exclusive max of head positions, exclusive
 // sum of tied counts, total tied count of the block.
 template <int MODE>
-__global__ void __launch_bounds__(256) heads_scan_kernel(int h, BlockState *__restrict__ st, int32_t *__restrict__ aux_all,
-                                                         int32_t *__restrict__ counters) {
+__global__ void __launch_bounds__(256) heads_scan_kernel(int32_t *__restrict__ rs, BlockState *__restrict__ st, int32_t *__restrict__ aux_all) {
     __shared__ int32_t shm[33];
     __shared__ int32_t shs[33];
     const int b = blockIdx.x;
+    const int h = round_h<MODE>(rs);
+    int32_t *counters = rs;
     const int n = sort_count<MODE>(st[b], h);
     int32_t *aux = aux_all + (size_t)b * kTilesPerBlock * 4;
     const int nt = (n + kTile - 1) / kTile;
@@ -327,14 +338,21 @@ __global__ void __launch_bounds__(256) heads_scan_kernel(int h, BlockState *__re
 // sorted tied elements (MODE 1); elements still tied are compacted into the
 // next round's lists.
 template <int MODE>
-__global__ void __launch_bounds__(kSortThreads) heads_apply_kernel(int h, const BlockState *__restrict__ st,
-                                                                   const int32_t *__restrict__ sorted_all, const int32_t *__restrict__ act_all,
+__global__ void __launch_bounds__(kSortThreads) heads_apply_kernel(const int32_t *__restrict__ rs, const BlockState *__restrict__ st,
+                                                                   const int32_t *__restrict__ sorted_all, int32_t *__restrict__ actA,
+                                                                   int32_t *__restrict__ actB,
                                                                    const uint8_t *__restrict__ flags_all, const int32_t *__restrict__ aux_all,
                                                                    int32_t *__restrict__ rank_all, int32_t *__restrict__ sa_all,
-                                                                   int32_t *__restrict__ act_out_all, int32_t *__restrict__ val_out_all) {
+                                                                   int32_t *__restrict__ val_out_all) {
     __shared__ int32_t shm[33];
     __shared__ int32_t shs[33];
     const int b = blockIdx.y, tile = blockIdx.x;
+    const int h = round_h<MODE>(rs);
+    // round r reads list A (r even) or B (r odd) and writes the other; the
+    // initial pass (MODE 0) writes A, which round 0 reads
+    const bool odd = MODE == 1 && (rs[3] & 1);
+    const int32_t *act_all = odd ? actB : actA;
+    int32_t *act_out_all = MODE == 0 ? actA : (odd ? actA : actB);
     const BlockState s = st[b];
     const int n = sort_count<MODE>(s, h);
     if (tile * kTile >= n) return;
@@ -380,6 +398,20 @@ __global__ void commit_round_kernel(BlockState *st, int nblocks) {
     if (b < nblocks) { st[b].n_act = st[b].n_act_next; st[b].n_act_next = 0; }
 }
 
+__global__ void round_start_kernel(int32_t *rs, int first) {
+    rs[0] = 0;
+    rs[1] = 0;
+    if (first) { rs[2] = 8; rs[3] = 0; }
+}
+
+// End of a doubling round: double h; inside a graph, continue the WHILE node
+// while tied elements remain and h is below the largest block length.
+__global__ void round_end_kernel(int32_t *rs, int max_m, cudaGraphConditionalHandle cond, int set_cond) {
+    rs[2] *= 2;
+    rs[3] += 1;
+    if (set_cond) cudaGraphSetConditional(cond, (rs[0] > 0 && rs[2] < max_m) ? 1u : 0u);
+}
+
 // L[j] = block[(SA[j] - 1) mod m]; origPtr = j with SA[j] = 0; bytes in use.
 __global__ void __launch_bounds__(kSortThreads) bwt_output_kernel(BlockState *__restrict__ st, const int32_t *__restrict__ sa_all,
                                                                   const uint8_t *__restrict__ rle_all, uint8_t *__restrict__ L_all) {
@@ -405,13 +437,36 @@ __global__ void __launch_bounds__(kSortThreads) bwt_output_kernel(BlockState *__
 }
 
 template <int MODE>
-static void radix_pass(lfc_plan P, int nblocks, int tiles, int pass, int h, const int32_t *in, int32_t *out) {
+static void radix_pass(lfc_plan P, cudaStream_t st, int nblocks, int tiles, int pass, const int32_t *in, int32_t *out) {
     Workspace &ws = P->ws;
     dim3 grid(tiles, nblocks);
-    radix_hist_kernel<MODE><<<grid, kSortThreads, 0, P->stream>>>(pass, h, ws.bstate, in, ws.rle, ws.rank, ws.tilecnt);
-    radix_scan_kernel<MODE><<<nblocks, 1024, 0, P->stream>>>(h, ws.bstate, ws.tilecnt);
-    radix_scatter_kernel<MODE><<<grid, kSortThreads, 0, P->stream>>>(pass, h, ws.bstate, in, out, ws.rle, ws.rank, ws.tilecnt);
+    radix_hist_kernel<MODE><<<grid, kSortThreads, 0, st>>>(pass, ws.act_total, ws.bstate, in, ws.rle, ws.rank, ws.tilecnt);
+    radix_scan_kernel<MODE><<<nblocks, 1024, 0, st>>>(ws.act_total, ws.bstate, ws.tilecnt);
+    radix_scatter_kernel<MODE><<<grid, kSortThreads, 0, st>>>(pass, ws.act_total, ws.bstate, in, out, ws.rle, ws.rank, ws.tilecnt);
     count_launches(P, 3);
+}
+
+// One prefix-doubling round over the tied elements (h and the parity of the
+// active lists come from the round state in device memory).
+static void bwt_round(lfc_plan P, cudaStream_t st, int nblocks, int tiles, int max_m, cudaGraphConditionalHandle cond,
+                      int set_cond) {
+    Workspace &ws = P->ws;
+    round_start_kernel<<<1, 1, 0, st>>>(ws.act_total, 0);
+    // 5 LSD passes over the 40-bit key: val -> val2 -> val -> val2 -> val -> val2
+    for (int pass = 0; pass < 5; pass++) {
+        const int32_t *in = (pass & 1) ? ws.val2 : ws.val;
+        int32_t *out = (pass & 1) ? ws.val : ws.val2;
+        radix_pass<1>(P, st, nblocks, tiles, pass, in, out);
+    }
+    dim3 g1(tiles, nblocks);
+    heads_tile_kernel<1><<<g1, kSortThreads, 0, st>>>(ws.act_total, ws.bstate, ws.val2, ws.act, ws.act2, ws.rle, ws.rank,
+                                                      ws.bwt, ws.tileaux);
+    heads_scan_kernel<1><<<nblocks, 256, 0, st>>>(ws.act_total, ws.bstate, ws.tileaux);
+    heads_apply_kernel<1><<<g1, kSortThreads, 0, st>>>(ws.act_total, ws.bstate, ws.val2, ws.act, ws.act2, ws.bwt,
+                                                       ws.tileaux, ws.rank, ws.sa, ws.val);
+    commit_round_kernel<<<(nblocks + 255) / 256, 256, 0, st>>>(ws.bstate, nblocks);
+    round_end_kernel<<<1, 1, 0, st>>>(ws.act_total, max_m, cond, set_cond);
+    count_launches(P, 6);
 }
 
 cudaError_t launch_bwt(lfc_plan P, int nblocks, int max_m) {
@@ -420,51 +475,75 @@ cudaError_t launch_bwt(lfc_plan P, int nblocks, int max_m) {
     cudaError_t e;
     const int tiles = (max_m + kTile - 1) / kTile;
     if (tiles == 0) return cudaSuccess;
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    e = cudaStreamIsCapturing(s, &cap);
+    if (e != cudaSuccess) return e;
+    const bool graph = cap == cudaStreamCaptureStatusActive;
     // phase 1: 8 LSD passes, identity -> sa2 -> sa -> ... -> sa
     stage_begin(P, LFC_STAGE_BWT_SORT8);
     for (int pass = 0; pass < 8; pass++) {
         const int32_t *in = (pass & 1) ? ws.sa2 : ws.sa;
         int32_t *out = (pass & 1) ? ws.sa : ws.sa2;
-        radix_pass<0>(P, nblocks, tiles, pass, 0, in, out);
+        radix_pass<0>(P, s, nblocks, tiles, pass, in, out);
     }
     stage_end(P, LFC_STAGE_BWT_SORT8);
     stage_begin(P, LFC_STAGE_BWT_REFINE);
-    e = cudaMemsetAsync(ws.act_total, 0, 2 * sizeof(int32_t), s);
-    if (e != cudaSuccess) return e;
+    round_start_kernel<<<1, 1, 0, s>>>(ws.act_total, 1);
     dim3 grid(tiles, nblocks);
-    heads_tile_kernel<0><<<grid, kSortThreads, 0, s>>>(0, ws.bstate, ws.sa, ws.sa, ws.rle, ws.rank, ws.bwt, ws.tileaux);
-    heads_scan_kernel<0><<<nblocks, 256, 0, s>>>(0, ws.bstate, ws.tileaux, ws.act_total);
-    heads_apply_kernel<0><<<grid, kSortThreads, 0, s>>>(0, ws.bstate, ws.sa, ws.sa, ws.bwt, ws.tileaux, ws.rank, ws.sa,
-                                                        ws.act, ws.val);
+    heads_tile_kernel<0><<<grid, kSortThreads, 0, s>>>(ws.act_total, ws.bstate, ws.sa, ws.sa, ws.sa, ws.rle, ws.rank, ws.bwt,
+                                                       ws.tileaux);
+    heads_scan_kernel<0><<<nblocks, 256, 0, s>>>(ws.act_total, ws.bstate, ws.tileaux);
+    heads_apply_kernel<0><<<grid, kSortThreads, 0, s>>>(ws.act_total, ws.bstate, ws.sa, ws.act, ws.act2, ws.bwt,
+                                                        ws.tileaux, ws.rank, ws.sa, ws.val);
     commit_round_kernel<<<(nblocks + 255) / 256, 256, 0, s>>>(ws.bstate, nblocks);
-    count_launches(P, 4);
-    e = cudaMemcpyAsync(ws.h_act_total, ws.act_total, 2 * sizeof(int32_t), cudaMemcpyDeviceToHost, s);
-    if (e != cudaSuccess) return e;
-    e = cudaStreamSynchronize(s);
-    if (e != cudaSuccess) return e;
-    int32_t *act = ws.act, *act2 = ws.act2;
-    for (int h = 8; ws.h_act_total[0] > 0 && h < max_m; h *= 2) {
-        const int t1 = (ws.h_act_total[1] + kTile - 1) / kTile;
-        // 5 LSD passes over the 40-bit key: val -> val2 -> val -> val2 -> val -> val2
-        for (int pass = 0; pass < 5; pass++) {
-            const int32_t *in = (pass & 1) ? ws.val2 : ws.val;
-            int32_t *out = (pass & 1) ? ws.val : ws.val2;
-            radix_pass<1>(P, nblocks, t1, pass, h, in, out);
-        }
-        e = cudaMemsetAsync(ws.act_total, 0, 2 * sizeof(int32_t), s);
+    count_launches(P, 5);
+    P->bwt_calls++;
+    if (graph) {
+        // rounds as a WHILE node: the body is one round, its last kernel
+        // decides whether another round runs
+        const cudaGraphNode_t *deps = nullptr;
+        const cudaGraphEdgeData *edata = nullptr;
+        size_t ndeps = 0;
+        cudaGraph_t cg = nullptr;
+        unsigned long long cid = 0;
+        e = cudaStreamGetCaptureInfo(s, &cap, &cid, &cg, &deps, &edata, &ndeps);
         if (e != cudaSuccess) return e;
-        dim3 g1(t1, nblocks);
-        heads_tile_kernel<1><<<g1, kSortThreads, 0, s>>>(h, ws.bstate, ws.val2, act, ws.rle, ws.rank, ws.bwt, ws.tileaux);
-        heads_scan_kernel<1><<<nblocks, 256, 0, s>>>(h, ws.bstate, ws.tileaux, ws.act_total);
-        heads_apply_kernel<1><<<g1, kSortThreads, 0, s>>>(h, ws.bstate, ws.val2, act, ws.bwt, ws.tileaux, ws.rank, ws.sa,
-                                                          act2, ws.val);
-        commit_round_kernel<<<(nblocks + 255) / 256, 256, 0, s>>>(ws.bstate, nblocks);
-        count_launches(P, 4);
-        int32_t *tmp = act; act = act2; act2 = tmp;
-        e = cudaMemcpyAsync(ws.h_act_total, ws.act_total, 2 * sizeof(int32_t), cudaMemcpyDeviceToHost, s);
+        cudaGraphConditionalHandle cond;
+        e = cudaGraphConditionalHandleCreate(&cond, cg, 1, cudaGraphCondAssignDefault);
+        if (e != cudaSuccess) return e;
+        cudaGraphNodeParams np = {};
+        np.type = cudaGraphNodeTypeConditional;
+        np.conditional.handle = cond;
+        np.conditional.type = cudaGraphCondTypeWhile;
+        np.conditional.size = 1;
+        cudaGraphNode_t node;
+        e = cudaGraphAddNode(&node, cg, deps, edata, ndeps, &np);
+        if (e != cudaSuccess) return e;
+        cudaGraph_t body = np.conditional.phGraph_out[0];
+        e = cudaStreamBeginCaptureToGraph(P->aux_stream, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed);
+        if (e != cudaSuccess) return e;
+        bwt_round(P, P->aux_stream, nblocks, kTilesPerBlock, max_m, cond, 1);
+        e = cudaStreamEndCapture(P->aux_stream, &body);
+        if (e != cudaSuccess) return e;
+        e = cudaStreamUpdateCaptureDependencies(s, &node, nullptr, 1, cudaStreamSetCaptureDependencies);
+        if (e != cudaSuccess) return e;
+    } else {
+        e = cudaMemcpyAsync(ws.h_act_total, ws.act_total, 4 * sizeof(int32_t), cudaMemcpyDeviceToHost, s);
         if (e != cudaSuccess) return e;
         e = cudaStreamSynchronize(s);
         if (e != cudaSuccess) return e;
+        int round = 0;
+        for (int h = 8; ws.h_act_total[0] > 0 && h < max_m; h *= 2, round++) {
+            P->bwt_rounds++;
+            P->bwt_tied_total += ws.h_act_total[0];
+            if (round < 32) P->bwt_round_tied[round] += ws.h_act_total[0];
+            const int t1 = (ws.h_act_total[1] + kTile - 1) / kTile;
+            bwt_round(P, s, nblocks, t1, max_m, cudaGraphConditionalHandle{}, 0);
+            e = cudaMemcpyAsync(ws.h_act_total, ws.act_total, 4 * sizeof(int32_t), cudaMemcpyDeviceToHost, s);
+            if (e != cudaSuccess) return e;
+            e = cudaStreamSynchronize(s);
+            if (e != cudaSuccess) return e;
+        }
     }
     stage_end(P, LFC_STAGE_BWT_REFINE);
     stage_begin(P, LFC_STAGE_BWT_OUT);

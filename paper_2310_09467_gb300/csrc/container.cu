@@ -13,12 +13,6 @@ __device__ __forceinline__ void st32(uint8_t *p, uint32_t v) {
     p[0] = (uint8_t)v; p[1] = (uint8_t)(v >> 8); p[2] = (uint8_t)(v >> 16); p[3] = (uint8_t)(v >> 24);
 }
 
-struct FrameOut {
-    uint64_t out_off;    // container offset in d_out
-    int32_t block0, nblocks;
-    int32_t W, H, p, pad;
-};
-
 // One warp per frame: header, block table, destination of every stream.
 __global__ void container_header_kernel(const FrameOut *__restrict__ fo, int nframes, const BlockState *__restrict__ st,
                                         const uint8_t *__restrict__ choice, const uint32_t *__restrict__ frame_crc,
@@ -65,26 +59,11 @@ __global__ void copy_streams_kernel(const BlockState *__restrict__ st, const uin
     for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < nbytes; i += gridDim.x * blockDim.x) dst[i] = src[i];
 }
 
-cudaError_t launch_container(lfc_plan P, int nframes, const int32_t *h_block0, const FrameDev *h_frames,
-                             const uint8_t *d_choice, const uint32_t *d_frame_crc, uint8_t *d_out,
-                             const uint64_t *h_out_off, uint64_t *d_out_sizes, int block_bytes) {
-    std::vector<FrameOut> fo(nframes);
-    for (int f = 0; f < nframes; f++) {
-        fo[f].out_off = h_out_off[f];
-        fo[f].block0 = h_block0[f];
-        fo[f].nblocks = h_block0[f + 1] - h_block0[f];
-        fo[f].W = h_frames[f].W;
-        fo[f].H = h_frames[f].H;
-        fo[f].p = h_frames[f].p;
-        fo[f].pad = 0;
-    }
+cudaError_t launch_container(lfc_plan P, int nframes, int nblocks, const FrameOut *d_fo, const uint8_t *d_choice,
+                             const uint32_t *d_frame_crc, uint8_t *d_out, uint64_t *d_out_sizes, int block_bytes) {
     Workspace &ws = P->ws;
-    FrameOut *d_fo = reinterpret_cast<FrameOut *>(ws.chunk_desc);
-    cudaError_t e = cudaMemcpyAsync(d_fo, fo.data(), sizeof(FrameOut) * nframes, cudaMemcpyHostToDevice, P->stream);
-    if (e != cudaSuccess) return e;
     container_header_kernel<<<nframes, 32, 0, P->stream>>>(d_fo, nframes, ws.bstate, d_choice, d_frame_crc, d_out,
                                                            d_out_sizes, ws.block_dst, block_bytes);
-    const int nblocks = h_block0[nframes];
     dim3 grid(64, nblocks);
     copy_streams_kernel<<<grid, 256, 0, P->stream>>>(ws.bstate, ws.packed, ws.stream_words, ws.block_dst, d_out, 0, nullptr);
     count_launches(P, 2);

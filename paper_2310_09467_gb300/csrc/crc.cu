@@ -87,43 +87,71 @@ __global__ void crc_finish_kernel(const uint32_t *__restrict__ part, const int32
     out[(size_t)rg * out_stride_words] = ~r;
 }
 
-// Chunk tables live in the plan's chunk_desc buffer: [CrcChunk x nchunks]
-// [int32 first_chunk x (n+1)] [int64 range_len x n], one stream-ordered copy.
-static cudaError_t run_ranges(lfc_plan P, const uint8_t *const *ptr, const int64_t *len, int n, uint32_t *out,
-                              int out_stride_words) {
-    std::vector<CrcChunk> ch;
+// Descriptor tables of one CRC run, laid out in a caller-provided host
+// buffer: [CrcChunk x nchunks] [int32 first_chunk x (n+1)] (pad 8)
+// [int64 range_len x n].
+int crc_count_chunks(const int64_t *len, int n) {
+    int c = 0;
+    for (int r = 0; r < n; r++) c += (int)((len[r] + kCrcChunk - 1) / kCrcChunk);
+    return c;
+}
+
+size_t crc_table_bytes(int nchunks, int n) {
+    size_t o = (size_t)nchunks * sizeof(CrcChunk) + (size_t)(n + 1) * 4;
+    o = (o + 7) & ~(size_t)7;
+    return o + (size_t)n * 8;
+}
+
+void crc_build_tables(const uint8_t *const *ptr, const int64_t *len, int n, uint8_t *out, CrcRun *run) {
+    CrcChunk *ch = reinterpret_cast<CrcChunk *>(out);
+    int k = 0;
     std::vector<int32_t> first(n + 1);
     for (int r = 0; r < n; r++) {
-        first[r] = (int32_t)ch.size();
+        first[r] = k;
         for (int64_t o = 0; o < len[r]; o += kCrcChunk) {
             CrcChunk c;
             c.src = ptr[r] + o;
             c.len = (int32_t)(len[r] - o < kCrcChunk ? len[r] - o : kCrcChunk);
             c.range = r;
             c.after = len[r] - o - c.len;
-            ch.push_back(c);
+            memcpy(&ch[k++], &c, sizeof(c));
         }
     }
-    first[n] = (int32_t)ch.size();
-    const size_t nchunks = ch.size();
-    if ((int64_t)nchunks > P->ws.crc_part_cap) return cudaErrorInvalidValue;
-    std::vector<uint8_t> blob(nchunks * sizeof(CrcChunk) + (n + 1) * 4 + 8 + n * 8);
-    size_t o = 0;
-    memcpy(blob.data(), ch.data(), nchunks * sizeof(CrcChunk));
-    o += nchunks * sizeof(CrcChunk);
-    memcpy(blob.data() + o, first.data(), (n + 1) * 4);
-    o += (n + 1) * 4;
+    first[n] = k;
+    size_t o = (size_t)k * sizeof(CrcChunk);
+    memcpy(out + o, first.data(), (size_t)(n + 1) * 4);
+    run->off_first = o;
+    o += (size_t)(n + 1) * 4;
     o = (o + 7) & ~(size_t)7;
-    memcpy(blob.data() + o, len, n * 8);
-    uint8_t *d = reinterpret_cast<uint8_t *>(P->ws.chunk_desc);
-    cudaError_t e = cudaMemcpyAsync(d, blob.data(), o + n * 8, cudaMemcpyHostToDevice, P->stream);
-    if (e != cudaSuccess) return e;  // pageable source: staged before the call returns
-    if (nchunks) crc_chunk_kernel<<<(unsigned)nchunks, 256, 0, P->stream>>>(reinterpret_cast<const CrcChunk *>(d), P->ws.crc_part);
-    crc_finish_kernel<<<(n + 127) / 128, 128, 0, P->stream>>>(
-        P->ws.crc_part, reinterpret_cast<const int32_t *>(d + nchunks * sizeof(CrcChunk)),
-        reinterpret_cast<const int64_t *>(d + o), n, out, out_stride_words);
-    count_launches(P, nchunks ? 2 : 1);
+    memcpy(out + o, len, (size_t)n * 8);
+    run->off_len = o;
+    run->nchunks = k;
+    run->nranges = n;
+}
+
+// Launches a CRC run whose tables sit at d_tables (device).
+cudaError_t launch_crc(lfc_plan P, const uint8_t *d_tables, const CrcRun &run, uint32_t *out, int out_stride_words) {
+    if (run.nchunks > P->ws.crc_part_cap) return cudaErrorInvalidValue;
+    if (run.nchunks) crc_chunk_kernel<<<(unsigned)run.nchunks, 256, 0, P->stream>>>(reinterpret_cast<const CrcChunk *>(d_tables), P->ws.crc_part);
+    crc_finish_kernel<<<(run.nranges + 127) / 128, 128, 0, P->stream>>>(
+        P->ws.crc_part, reinterpret_cast<const int32_t *>(d_tables + run.off_first),
+        reinterpret_cast<const int64_t *>(d_tables + run.off_len), run.nranges, out, out_stride_words);
+    count_launches(P, run.nchunks ? 2 : 1);
     return cudaGetLastError();
+}
+
+// Immediate form: stage the tables in the plan's descriptor buffer first.
+static cudaError_t run_ranges(lfc_plan P, const uint8_t *const *ptr, const int64_t *len, int n, uint32_t *out,
+                              int out_stride_words) {
+    const int nchunks = crc_count_chunks(len, n);
+    std::vector<uint8_t> blob(crc_table_bytes(nchunks, n));
+    CrcRun run;
+    crc_build_tables(ptr, len, n, blob.data(), &run);
+    if (blob.size() > P->ws.chunk_desc_bytes) return cudaErrorInvalidValue;
+    uint8_t *d = reinterpret_cast<uint8_t *>(P->ws.chunk_desc);
+    cudaError_t e = cudaMemcpyAsync(d, blob.data(), blob.size(), cudaMemcpyHostToDevice, P->stream);
+    if (e != cudaSuccess) return e;  // pageable source: staged before the call returns
+    return launch_crc(P, d, run, out, out_stride_words);
 }
 
 cudaError_t launch_block_crc(lfc_plan P, const BlockDesc *h_blocks, int nblocks, BlockState *d_state) {

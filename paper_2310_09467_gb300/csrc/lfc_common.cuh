@@ -207,6 +207,8 @@ struct Workspace {
 struct lfc_plan_s {
     lfc_config cfg;
     cudaStream_t stream = nullptr;
+    cudaStream_t aux_stream = nullptr;  // capture of conditional-node bodies
+    cudaStream_t cap_stream = nullptr;  // capture of batches
     int device = 0;
     std::string err;
     std::vector<uint8_t> ids_spatial;   // judged for every frame
@@ -222,6 +224,8 @@ struct lfc_plan_s {
     std::vector<cudaEvent_t> event_pool;
     cudaEvent_t open_ev[LFC_NUM_STAGES] = {};
     double stage_ms[LFC_NUM_STAGES] = {};
+    int64_t bwt_calls = 0, bwt_rounds = 0, bwt_tied_total = 0, bwt_elements = 0, bwt_elements_in = 0;
+    int64_t bwt_round_tied[32] = {};
     int64_t stage_spans[LFC_NUM_STAGES] = {};
 };
 
@@ -255,12 +259,20 @@ cudaError_t launch_emit(const FrameDev *h_frames, const uint8_t *d_choice, int n
 cudaError_t launch_symbols_one(const FrameDev &F, int id, uint16_t *dst, cudaStream_t s);
 
 // crc.cu
+struct CrcRun {
+    int nchunks = 0, nranges = 0;
+    size_t off_first = 0, off_len = 0;
+};
+int crc_count_chunks(const int64_t *len, int n);
+size_t crc_table_bytes(int nchunks, int n);
+void crc_build_tables(const uint8_t *const *ptr, const int64_t *len, int n, uint8_t *out, CrcRun *run);
+cudaError_t launch_crc(lfc_plan P, const uint8_t *d_tables, const CrcRun &run, uint32_t *out, int out_stride_words);
 cudaError_t launch_block_crc(lfc_plan P, const BlockDesc *h_blocks, int nblocks, BlockState *d_state);
 cudaError_t launch_range_crc(lfc_plan P, const uint8_t *const *h_ptr, const int64_t *h_len, int n,
                              uint32_t *d_out);
 
 // bwt.cu
-cudaError_t launch_rle1(lfc_plan P, int nblocks);
+cudaError_t launch_rle1(lfc_plan P, int nblocks, const BlockDesc *d_blocks);
 cudaError_t launch_bwt(lfc_plan P, int nblocks, int max_m);
 
 // mtf_huff.cu
@@ -269,9 +281,13 @@ cudaError_t launch_huffman(lfc_plan P, int nblocks);
 cudaError_t launch_pack(lfc_plan P, int nblocks);
 
 // container.cu
-cudaError_t launch_container(lfc_plan P, int nframes, const int32_t *h_block0, const FrameDev *h_frames,
-                             const uint8_t *d_choice, const uint32_t *d_frame_crc, uint8_t *d_out,
-                             const uint64_t *h_out_off, uint64_t *d_out_sizes, int block_bytes);
+struct FrameOut {
+    uint64_t out_off;    // container offset in d_out
+    int32_t block0, nblocks;
+    int32_t W, H, p, pad;
+};
+cudaError_t launch_container(lfc_plan P, int nframes, int nblocks, const FrameOut *d_fo, const uint8_t *d_choice,
+                             const uint32_t *d_frame_crc, uint8_t *d_out, uint64_t *d_out_sizes, int block_bytes);
 cudaError_t launch_copy_streams(lfc_plan P, int nblocks, uint8_t *d_out, size_t stride, uint32_t *d_sizes);
 
 // decode.cu

@@ -26,7 +26,8 @@ STATUS = {0: "LFC_OK", 1: "LFC_ERR_INVALID_ARG", 2: "LFC_ERR_CAPACITY", 3: "LFC_
 EXPORTS = ["lfc_plan_create", "lfc_plan_destroy", "lfc_plan_last_error", "lfc_judge", "lfc_symbols",
            "lfc_max_compressed_bytes", "lfc_compress", "lfc_bzip2_encode", "lfc_max_stream_bytes",
            "lfc_plan_block_capacity", "lfc_decompress", "lfc_status_string", "lfc_plan_set_timing",
-           "lfc_plan_timing", "lfc_plan_launch_count", "lfc_judge_noalloc"]
+           "lfc_plan_timing", "lfc_plan_launch_count", "lfc_judge_noalloc", "lfc_plan_bwt_counters",
+           "lfc_batch_create", "lfc_batch_launch", "lfc_batch_destroy"]
 
 STAGES = ["judge_hist", "judge_score", "emit", "crc", "rle1", "bwt_sort8", "bwt_refine", "bwt_out", "mtf",
           "huffman", "pack", "container", "judge_emit"]
@@ -79,6 +80,10 @@ def load():
         "lfc_plan_set_timing": (i32, [P, i32]),
         "lfc_plan_timing": (i32, [P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int64), i32]),
         "lfc_plan_launch_count": (ctypes.c_int64, [P]),
+        "lfc_plan_bwt_counters": (i32, [P, ctypes.POINTER(ctypes.c_int64), i32]),
+        "lfc_batch_create": (i32, [P, ctypes.POINTER(Frame), i32, P, P, sz, P, ctypes.POINTER(P)]),
+        "lfc_batch_launch": (i32, [P]),
+        "lfc_batch_destroy": (None, [P]),
         "lfc_judge_noalloc": (i32, [ctypes.POINTER(Frame), ctypes.POINTER(ctypes.c_uint8), i32, P, P, P]),
     }
     for name, (res, args) in sig.items():
@@ -168,6 +173,14 @@ class Plan:
     def launch_count(self):
         return int(self.lib.lfc_plan_launch_count(self.h))
 
+    def bwt_counters(self):
+        """(calls, rounds, input bytes coded, tied elements over rounds, tied per round)."""
+        buf = (ctypes.c_int64 * 36)()
+        k = self.lib.lfc_plan_bwt_counters(self.h, buf, 36)
+        v = list(buf[:k])
+        return {"calls": v[0], "rounds": v[1], "input_bytes": v[2], "tied_total": v[3],
+                "tied_per_round": [x for x in v[4:] if x]}
+
     @property
     def block_capacity(self):
         return int(self.lib.lfc_plan_block_capacity(self.h))
@@ -227,6 +240,10 @@ class Plan:
         self._check(rc, "lfc_compress")
         return out, sizes, offs
 
+    def batch(self, frames, pitch, prevs=None, choice=None, out=None, sizes=None):
+        """Capture lfc_compress on these frame buffers as a CUDA graph."""
+        return Batch(self, frames, pitch, prevs, choice, out, sizes)
+
     def compress_to_bytes(self, frames, pitch, prevs=None, choice=None):
         out, sizes, offs = self.compress(frames, pitch, prevs, choice)
         sz = sizes.cpu().numpy()
@@ -274,6 +291,44 @@ class Plan:
         rc = self.lib.lfc_decompress(self.h, ins, szs, n, os_, ob, pv)
         self._check(rc, "lfc_decompress")
         return outs
+
+
+class Batch:
+    """One captured compress call (lfc_batch_*): launch() replays it."""
+
+    def __init__(self, plan, frames, pitch, prevs=None, choice=None, out=None, sizes=None):
+        torch = _torch()
+        self.plan = plan
+        self.frames = frames
+        n = len(frames)
+        self.arr = plan._frames(frames, pitch, prevs)
+        self.offs, total = plan.slots(frames)
+        self.out = out if out is not None else torch.empty(total, dtype=torch.uint8, device=frames[0].device)
+        self.sizes = sizes if sizes is not None else torch.empty(n, dtype=torch.int64, device=frames[0].device)
+        h = ctypes.c_void_p()
+        rc = plan.lib.lfc_batch_create(plan.h, self.arr, n, _ptr(choice), _ptr(self.out), self.out.numel(),
+                                       _ptr(self.sizes), ctypes.byref(h))
+        plan._check(rc, "lfc_batch_create")
+        self.h = h
+
+    def launch(self):
+        self.plan._check(self.plan.lib.lfc_batch_launch(self.h), "lfc_batch_launch")
+
+    def to_bytes(self):
+        sz = self.sizes.cpu().numpy()
+        host = self.out.cpu().numpy()
+        return [host[o:o + int(s)].tobytes() for o, s in zip(self.offs, sz)]
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.plan.lib.lfc_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def to_device_frame(arr: np.ndarray, device="cuda"):

@@ -1,0 +1,48 @@
+"""Uneven frame batches captured once as a CUDA graph (lfc_batch_*): every
+replay must produce exactly the containers lfc_compress produces for the
+data the frame buffers hold at launch time, including a temporal frame and
+the device-driven suffix-sort rounds."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2310_09467_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+
+def _batch_frames(seed):
+    vs = synth.VesselSeries(180, 165, 15, seed=seed)
+    return [
+        (synth.beads(195, 195, 13, peak=2000.0, seed=seed), 13, None),
+        (synth.cells(255, 240, 15, seed=seed + 1), 15, None),
+        (vs.frame(0), 15, None),
+        (vs.frame(1), 15, 2),      # temporal: previous = frame index 2
+        (synth.beads(130, 260, 13, peak=20.0, seed=seed + 2), 13, None),
+    ]
+
+
+def test_batch_graph_matches_compress_twice():
+    import torch
+    from paper_2310_09467_gb300 import build, lfc
+    build.build()
+    fr0 = _batch_frames(31)
+    plan = lfc.Plan(260, 260, 13, max_frames=len(fr0), temporal=True, block_bytes=25000)
+    dev = [torch.empty(f.shape, dtype=torch.int16, device="cuda") for f, _, _ in fr0]
+    pitches = [p for _, p, _ in fr0]
+    prevs = [dev[j] if j is not None else None for _, _, j in fr0]
+    for d, (f, _, _) in zip(dev, fr0):
+        d.copy_(lfc.to_device_frame(f))
+    batch = plan.batch(dev, pitches, prevs=prevs)
+    for rnd, frames in enumerate([fr0, _batch_frames(57)]):
+        for d, (f, _, _) in zip(dev, frames):
+            d.copy_(lfc.to_device_frame(f))
+        batch.launch()
+        torch.cuda.synchronize()
+        got = batch.to_bytes()
+        ref = plan.compress_to_bytes(dev, pitches, prevs=prevs)
+        assert got == ref, rnd
+        for blob, (f, p, j) in zip(got, frames):
+            pv = frames[j][0] if j is not None else None
+            assert np.array_equal(oracle.decompress(blob, prev=pv), f)
+    batch.close()
