@@ -138,6 +138,61 @@ def run_reference(args):
     return 0
 
 
+def run_uneven(args):
+    """Uneven batch: 256 frames mixing 1300x1300 (p 13), 2040x2040 (p 15) and
+    2550x2160 (p 15) from the bead, cell and vessel generators, compressed by
+    one CUDA-graph launch per batch with autotuned judge knobs; then the same
+    frames streamed at 100 frames/s in micro-batches of 3 (one graph launch
+    each) for per-frame p50/p99 latency."""
+    import numpy as np
+    import torch
+
+    from paper_2310_09467_gb300 import autotune, build, lfc, stream, synth
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    build.build()
+    batch_np = synth.uneven_batch_fast(args.uneven_frames)
+    frames_np = [f for f, _ in batch_np]
+    pitches = [p for _, p in batch_np]
+    n = len(frames_np)
+    raw_bytes = sum(f.nbytes for f in frames_np)
+    frames = [lfc.to_device_frame(f) for f in frames_np]
+    plan = lfc.Plan(2550, 2160, 15, max_frames=n)
+    tuned, _ = autotune.autotune(plan, frames[:24], pitches[:24], path=os.path.join(ROOT, "_build_tune.json"))
+    batch = plan.batch(frames, pitches)
+    stream_ = plan.stream
+    for _ in range(args.warmup):
+        batch.launch()
+    torch.cuda.synchronize()
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device="cuda")
+    clocks = Clocks(int(os.environ.get("LOCAL_RANK", "0")))
+    clocks.start()
+    ms = []
+    for _ in range(args.steps):
+        flush.fill_(1)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream_)
+        batch.launch()
+        b.record(stream_)
+        b.synchronize()
+        ms.append(a.elapsed_time(b))
+    clk = clocks.stop()
+    comp = int(batch.sizes.cpu().numpy().sum())
+    batch.close()
+    lat = stream.run_stream(plan, frames_np, pitches, micro=3, fps=100.0)
+    total_ms = sum(ms)
+    line = {"metric": METRIC, "value": raw_bytes * args.steps / 1e6 / (total_ms / 1e3), "unit": "MB/s",
+            "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u16/u8 integer",
+            "data": "synthetic", "config": {"workload": "uneven batch: %d frames, 1300^2/p13 + 2040^2/p15 + "
+                                                        "2550x2160/p15, beads/cells/vessel" % n,
+                                            "raw_bytes_per_step": raw_bytes, "graph_launches_per_step": 1,
+                                            "tuning": tuned},
+            "ratio": raw_bytes / comp, "latency_stream": lat, "clocks": clk}
+    print(json.dumps(line))
+    plan.close()
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -146,9 +201,13 @@ def main():
     ap.add_argument("--impl", default="lfc", choices=["lfc", "reference"])
     ap.add_argument("--per-kind", type=int, default=4)
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--workload", default="single2040", choices=["single2040", "uneven"])
+    ap.add_argument("--uneven-frames", type=int, default=256)
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "uneven":
+        return run_uneven(args)
 
     import numpy as np
     import torch

@@ -203,6 +203,26 @@ int lfc_plan_block_capacity(lfc_plan plan);
 int lfc_decompress(lfc_plan plan, const uint8_t *const *h_in, const uint64_t *h_in_sizes, int n,
                    uint16_t *const *h_out, const uint64_t *h_out_bytes, const uint16_t *const *h_prev);
 
+/* Tuning knobs of the judge (an autotuner picks them per frame geometry and
+ * candidate count; 0 keeps a field's default). They change only speed,
+ * never results.
+ *   emit_tile_lenslets      lenslets per row tile of the candidate emission
+ *                           kernel: 4, 8 or 16 (default 16);
+ *   chain_range_bytes       bytes of a candidate stream one thread of the
+ *                           pair-chain kernel walks: 2048, 4096 or 8192
+ *                           (default 2048);
+ *   judge_frames_per_launch frames per judge launch, 1 .. the plan's
+ *                           min(max_frames, 8) (default: that maximum).
+ * Errors: INVALID_ARG for values outside these sets. */
+typedef struct {
+    int32_t emit_tile_lenslets;
+    int32_t chain_range_bytes;
+    int32_t judge_frames_per_launch;
+    int32_t reserved;
+} lfc_tuning;
+int lfc_plan_set_tuning(lfc_plan plan, const lfc_tuning *tuning);
+int lfc_plan_get_tuning(lfc_plan plan, lfc_tuning *tuning);
+
 /* Stage timing (tracing). With timing enabled the plan records CUDA events on
  * its stream around each stage below and accumulates their device time; the
  * counters only change while enabled. lfc_plan_set_timing also zeroes them.

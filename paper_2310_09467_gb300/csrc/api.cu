@@ -151,6 +151,35 @@ extern "C" int lfc_plan_timing(lfc_plan P, double *ms, int64_t *spans, int n_sta
 
 extern "C" int64_t lfc_plan_launch_count(lfc_plan P) { return P ? P->launches : 0; }
 
+extern "C" int lfc_plan_set_tuning(lfc_plan P, const lfc_tuning *t) {
+    if (!P || !t) return LFC_ERR_INVALID_ARG;
+    lfc_tuning v = P->tune;
+    if (t->emit_tile_lenslets) {
+        if (t->emit_tile_lenslets != 4 && t->emit_tile_lenslets != 8 && t->emit_tile_lenslets != 16)
+            return fail(P, LFC_ERR_INVALID_ARG, "emit_tile_lenslets must be 4, 8 or 16");
+        v.emit_tile_lenslets = t->emit_tile_lenslets;
+    }
+    if (t->chain_range_bytes) {
+        if (t->chain_range_bytes != 2048 && t->chain_range_bytes != 4096 && t->chain_range_bytes != 8192)
+            return fail(P, LFC_ERR_INVALID_ARG, "chain_range_bytes must be 2048, 4096 or 8192");
+        v.chain_range_bytes = t->chain_range_bytes;
+    }
+    if (t->judge_frames_per_launch) {
+        if (t->judge_frames_per_launch < 1 || t->judge_frames_per_launch > P->judge_frames_cap)
+            return fail(P, LFC_ERR_INVALID_ARG, "judge_frames_per_launch outside 1..min(max_frames, 8)");
+        v.judge_frames_per_launch = t->judge_frames_per_launch;
+    }
+    P->tune = v;
+    return LFC_OK;
+}
+
+extern "C" int lfc_plan_get_tuning(lfc_plan P, lfc_tuning *t) {
+    if (!P || !t) return LFC_ERR_INVALID_ARG;
+    *t = P->tune;
+    if (t->judge_frames_per_launch == 0) t->judge_frames_per_launch = P->judge_frames_cap;
+    return LFC_OK;
+}
+
 extern "C" int lfc_plan_bwt_counters(lfc_plan P, int64_t *out, int n) {
     if (!P || !out || n < 0) return 0;
     int k = 0;
@@ -250,7 +279,8 @@ extern "C" int lfc_plan_create(const lfc_config *cfg, void *cuda_stream, lfc_pla
     P->judge_frames_cap = std::min(F, kJudgeFramesCap);
     P->block_cap = (int)std::max<int64_t>(bpf, std::min<int64_t>((int64_t)F * bpf, 192));
     const int JF = P->judge_frames_cap, BC = P->block_cap;
-    const int64_t segs_max = (n_max + chain_seg_bytes() - 1) / chain_seg_bytes();
+    const int64_t seg_min = (int64_t)chain_threads() * 2048;  // smallest tunable segment
+    const int64_t segs_max = (n_max + seg_min - 1) / seg_min;
     ws.summ_cap = (int64_t)JF * kMaxCand * segs_max;
     ws.cstream_kmax = K;
     ws.cstream_slot = (n_max + 255) & ~(int64_t)255;
@@ -381,16 +411,18 @@ bool capturing(lfc_plan P) {
 
 int build_judge(lfc_plan P, const lfc_frame *frames, int n, Arena &A, std::vector<JudgeChunk> &out) {
     Workspace &ws = P->ws;
-    const int64_t seg_bytes = chain_seg_bytes();
-    for (int f0 = 0; f0 < n; f0 += P->judge_frames_cap) {
-        const int f1 = std::min(n, f0 + P->judge_frames_cap);
+    const int range = P->tune.chain_range_bytes;
+    const int64_t seg_bytes = (int64_t)chain_threads() * range;
+    const int per_launch = P->tune.judge_frames_per_launch > 0 ? P->tune.judge_frames_per_launch : P->judge_frames_cap;
+    for (int f0 = 0; f0 < n; f0 += per_launch) {
+        const int f1 = std::min(n, f0 + per_launch);
         const int nf = f1 - f0;
         std::vector<JudgeFrame> jf(nf);
         std::vector<int32_t> frame_index(nf), hist_frame;
         std::vector<uint8_t> cand;
         int64_t cta = 0, hist = 0, summ = 0;
         JudgeChunk C;
-        C.L = JudgeLaunch{0, 16, 0, 0, 0};
+        C.L = JudgeLaunch{0, 16, 0, 0, 0, range};
         for (int i = 0; i < nf; i++) {
             const lfc_frame &fr = frames[f0 + i];
             const bool tmp = fr.prev != nullptr && !P->ids_temporal.empty();
@@ -421,8 +453,8 @@ int build_judge(lfc_plan P, const lfc_frame *frames, int n, Arena &A, std::vecto
             hist += J.K;
             frame_index[i] = f0 + i;
         }
-        // lenslets per emission tile: as many as shared memory allows (<= 16)
-        C.L.TS = 16;
+        // lenslets per emission tile: the tuned width, narrowed until it fits
+        C.L.TS = P->tune.emit_tile_lenslets;
         while (C.L.TS > 1 && emit_all_smem_bytes(C.L.max_p, C.L.TS, C.L.nslots_max) > 200 * 1024) C.L.TS /= 2;
         if (emit_all_smem_bytes(C.L.max_p, C.L.TS, C.L.nslots_max) > 200 * 1024)
             return fail(P, LFC_ERR_INVALID_ARG, "pitch too large for the emission tile");

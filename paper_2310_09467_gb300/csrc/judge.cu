@@ -361,7 +361,7 @@ cudaError_t launch_judge(lfc_plan P, const JudgeFrame *d_frames, int nframes, in
     stage_end(P, LFC_STAGE_JUDGE_EMIT);
     if (e != cudaSuccess) return e;
     stage_begin(P, LFC_STAGE_JUDGE_HIST);
-    e = launch_chain_hist(P, d_frames, nframes, d_cand, total_ctas);
+    e = launch_chain_hist(P, d_frames, nframes, d_cand, total_ctas, L.range_bytes);
     stage_end(P, LFC_STAGE_JUDGE_HIST);
     if (e != cudaSuccess) return e;
     stage_begin(P, LFC_STAGE_JUDGE_SCORE);

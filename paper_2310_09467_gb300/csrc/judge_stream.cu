@@ -10,8 +10,8 @@
 //    are formed once in shared memory; then every pixel's symbol is produced
 //    for every candidate of the kind and stored in the candidate's ordering
 //    (raw order: 480-byte row runs; view-major order: 32-byte runs).
-// 2. chain_hist_kernel: one CTA per 768 KB segment of a candidate stream,
-//    one thread per 2 KB range walking it byte by byte (see below); the
+// 2. chain_hist_kernel: one CTA per segment of a candidate stream, one
+//    thread per range (2-8 KB, tuned) walking it byte by byte (see below); the
 //    ranges are stitched per CTA and the CTAs by the fixup kernel.
 #include "lfc_common.cuh"
 
@@ -182,13 +182,11 @@ __global__ void __launch_bounds__(kEmitThreads) emit_all_kernel(const JudgeFrame
 // are counted in shared memory, the very common pair (0, 0) in a register,
 // all others with fire-and-forget atomics into the L2-resident histogram.
 constexpr int kChainThreads = 384;
-constexpr int kRangeBytes = 2048;                                   // per thread
-constexpr int64_t kSegBytes = (int64_t)kChainThreads * kRangeBytes;  // per CTA
 constexpr int kHot = 64;                                            // hot corner side
 constexpr uint16_t kNoPred = 0xFFFF;
 
 size_t chain_smem_bytes() { return (size_t)kHot * kHot * 4 + (size_t)128 * kChainThreads * 4; }
-int64_t chain_seg_bytes() { return kSegBytes; }
+int chain_threads() { return kChainThreads; }
 int64_t chain_first_bytes_per_cta() { return (int64_t)kChainThreads * 256; }
 
 __device__ __forceinline__ int find_frame_s(const JudgeFrame *fr, int n, int64_t cta) {
@@ -224,7 +222,8 @@ __device__ __forceinline__ void chain_byte(uint32_t b, uint32_t &prev, uint32_t 
 
 __global__ void __launch_bounds__(kChainThreads)
 chain_hist_kernel(const JudgeFrame *__restrict__ frames, int nframes, const uint8_t *__restrict__ cstream, int64_t cslot,
-                  int kmax, uint32_t *__restrict__ hist, uint16_t *__restrict__ summ, uint8_t *__restrict__ first_all) {
+                  int kmax, uint32_t *__restrict__ hist, uint16_t *__restrict__ summ, uint8_t *__restrict__ first_all,
+                  int range_bytes) {
     extern __shared__ __align__(16) uint8_t smem[];
     uint32_t *hot = reinterpret_cast<uint32_t *>(smem);   // [kHot][kHot]
     uint32_t *tbl = hot + kHot * kHot;                    // [128][T]
@@ -236,8 +235,9 @@ chain_hist_kernel(const JudgeFrame *__restrict__ frames, int nframes, const uint
     uint32_t *ghist = hist + (size_t)(J.hist_off + ci) * kHistBins;
     const int64_t n = 2LL * J.F.W * J.F.H;
     const int t = threadIdx.x;
-    const int64_t ra64 = min(n, (int64_t)seg * kSegBytes + (int64_t)t * kRangeBytes);
-    const int len = (int)(min(n, ra64 + kRangeBytes) - ra64);
+    const int64_t seg_bytes = (int64_t)kChainThreads * range_bytes;
+    const int64_t ra64 = min(n, (int64_t)seg * seg_bytes + (int64_t)t * range_bytes);
+    const int len = (int)(min(n, ra64 + range_bytes) - ra64);
     const uint8_t *R = S + ra64;
     uint8_t *first = first_all + ((size_t)blockIdx.x * kChainThreads + t) * 256;
     uint32_t *tblt = tbl + t;
@@ -291,14 +291,15 @@ cudaError_t launch_emit_all(lfc_plan P, const JudgeFrame *d_frames, int nframes,
     return cudaGetLastError();
 }
 
-cudaError_t launch_chain_hist(lfc_plan P, const JudgeFrame *d_frames, int nframes, const uint8_t *d_cand, int64_t total_ctas) {
+cudaError_t launch_chain_hist(lfc_plan P, const JudgeFrame *d_frames, int nframes, const uint8_t *d_cand, int64_t total_ctas,
+                              int range_bytes) {
     (void)d_cand;
     const size_t smem = chain_smem_bytes();
     cudaError_t e = cudaFuncSetAttribute(chain_hist_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     chain_hist_kernel<<<(unsigned)total_ctas, kChainThreads, smem, P->stream>>>(
         d_frames, nframes, P->ws.cstream, P->ws.cstream_slot, P->ws.cstream_kmax, P->ws.hist, P->ws.summ,
-        P->ws.chain_first);
+        P->ws.chain_first, range_bytes);
     count_launches(P, 1);
     return cudaGetLastError();
 }

@@ -213,7 +213,8 @@ struct lfc_plan_s {
     std::string err;
     std::vector<uint8_t> ids_spatial;   // judged for every frame
     std::vector<uint8_t> ids_temporal;  // judged for frames with prev
-    int judge_frames_cap = 0;           // frames per judge launch
+    int judge_frames_cap = 0;           // frames per judge launch (allocated)
+    lfc_tuning tune{16, 2048, 0, 0};    // autotuned judge knobs
     int block_cap = 0;                  // blocks per coder pass
     lfc::Workspace ws;
     // tracing: CUDA events around stages, harvested by lfc_plan_timing
@@ -243,13 +244,14 @@ size_t judge_smem_bytes(int maxW);
 // judge_stream.cu
 size_t emit_all_smem_bytes(int p, int ts, int nslots);
 size_t chain_smem_bytes();
-int64_t chain_seg_bytes();
+int chain_threads();
 int64_t chain_first_bytes_per_cta();
 cudaError_t launch_emit_all(lfc_plan P, const JudgeFrame *d_frames, int nframes, const uint8_t *d_cand, int max_tiles,
                             int TS, int nslots_max, int any_temporal, int max_p);
-cudaError_t launch_chain_hist(lfc_plan P, const JudgeFrame *d_frames, int nframes, const uint8_t *d_cand, int64_t total_ctas);
+cudaError_t launch_chain_hist(lfc_plan P, const JudgeFrame *d_frames, int nframes, const uint8_t *d_cand, int64_t total_ctas,
+                              int range_bytes);
 struct JudgeLaunch {
-    int max_tiles, TS, nslots_max, any_temporal, max_p;
+    int max_tiles, TS, nslots_max, any_temporal, max_p, range_bytes;
 };
 cudaError_t launch_judge(lfc_plan P, const JudgeFrame *d_frames, int nframes, int64_t total_ctas,
                          const JudgeLaunch &L, const uint8_t *d_cand, int64_t nhist,

@@ -27,7 +27,8 @@ EXPORTS = ["lfc_plan_create", "lfc_plan_destroy", "lfc_plan_last_error", "lfc_ju
            "lfc_max_compressed_bytes", "lfc_compress", "lfc_bzip2_encode", "lfc_max_stream_bytes",
            "lfc_plan_block_capacity", "lfc_decompress", "lfc_status_string", "lfc_plan_set_timing",
            "lfc_plan_timing", "lfc_plan_launch_count", "lfc_judge_noalloc", "lfc_plan_bwt_counters",
-           "lfc_batch_create", "lfc_batch_launch", "lfc_batch_destroy"]
+           "lfc_batch_create", "lfc_batch_launch", "lfc_batch_destroy",
+           "lfc_plan_set_tuning", "lfc_plan_get_tuning"]
 
 STAGES = ["judge_hist", "judge_score", "emit", "crc", "rle1", "bwt_sort8", "bwt_refine", "bwt_out", "mtf",
           "huffman", "pack", "container", "judge_emit"]
@@ -44,6 +45,11 @@ class Config(ctypes.Structure):
                 ("max_frames", ctypes.c_int32), ("candidate_mask", ctypes.c_uint64 * 4),
                 ("temporal", ctypes.c_int32), ("keyframe_interval", ctypes.c_int32),
                 ("block_bytes", ctypes.c_int32), ("topk", ctypes.c_int32), ("tau", ctypes.c_float)]
+
+
+class Tuning(ctypes.Structure):
+    _fields_ = [("emit_tile_lenslets", ctypes.c_int32), ("chain_range_bytes", ctypes.c_int32),
+                ("judge_frames_per_launch", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
 class Frame(ctypes.Structure):
@@ -83,6 +89,8 @@ def load():
         "lfc_plan_bwt_counters": (i32, [P, ctypes.POINTER(ctypes.c_int64), i32]),
         "lfc_batch_create": (i32, [P, ctypes.POINTER(Frame), i32, P, P, sz, P, ctypes.POINTER(P)]),
         "lfc_batch_launch": (i32, [P]),
+        "lfc_plan_set_tuning": (i32, [P, ctypes.POINTER(Tuning)]),
+        "lfc_plan_get_tuning": (i32, [P, ctypes.POINTER(Tuning)]),
         "lfc_batch_destroy": (None, [P]),
         "lfc_judge_noalloc": (i32, [ctypes.POINTER(Frame), ctypes.POINTER(ctypes.c_uint8), i32, P, P, P]),
     }
@@ -169,6 +177,16 @@ class Plan:
         sp = (ctypes.c_int64 * n)()
         self._check(self.lib.lfc_plan_timing(self.h, ms, sp, n), "lfc_plan_timing")
         return {k: (ms[i], sp[i]) for i, k in enumerate(STAGES)}
+
+    def set_tuning(self, emit_tile_lenslets=0, chain_range_bytes=0, judge_frames_per_launch=0):
+        t = Tuning(emit_tile_lenslets, chain_range_bytes, judge_frames_per_launch, 0)
+        self._check(self.lib.lfc_plan_set_tuning(self.h, ctypes.byref(t)), "lfc_plan_set_tuning")
+
+    def get_tuning(self):
+        t = Tuning()
+        self._check(self.lib.lfc_plan_get_tuning(self.h, ctypes.byref(t)), "lfc_plan_get_tuning")
+        return {"emit_tile_lenslets": t.emit_tile_lenslets, "chain_range_bytes": t.chain_range_bytes,
+                "judge_frames_per_launch": t.judge_frames_per_launch}
 
     def launch_count(self):
         return int(self.lib.lfc_plan_launch_count(self.h))

@@ -298,3 +298,25 @@ def uneven_batch(n: int = 256, base_seed: int = 1000):
             fr = VesselSeries(W, H, p, seed=s).frame(0)
         out.append((fr, p))
     return out
+
+
+def uneven_batch_fast(n: int = 256, base_seed: int = 1000):
+    """Frame i: size class i mod 3, generator (i // 3) mod 3 (beads 2000,
+    cells 500, vessel 300). The expected-photon field of each (size,
+    generator) pair is rendered once; every frame draws its own Poisson and
+    read noise with seed base + i. Returns a list of (frame, pitch)."""
+    fields = {}
+    out = []
+    for i in range(n):
+        c, g = i % 3, (i // 3) % 3
+        W, H, p = SIZE_CLASSES[c]
+        if (c, g) not in fields:
+            s = base_seed + 10 * c + g
+            if g == 0:
+                fields[(c, g)] = bead_photons(W, H, p, peak=2000.0, seed=s)
+            elif g == 1:
+                fields[(c, g)] = cell_photons(W, H, p, level=500.0, seed=s)
+            else:
+                fields[(c, g)] = VesselSeries(W, H, p, seed=s).photons(0)
+        out.append((_to_raw(fields[(c, g)], np.random.default_rng(base_seed + i)), p))
+    return out
