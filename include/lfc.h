@@ -287,6 +287,54 @@ int lfc_plan_bwt_counters(lfc_plan plan, int64_t *out, int n);
 int lfc_judge_noalloc(const lfc_frame *h_frame, const uint8_t *h_ids, int n_ids, uint8_t *d_choice,
                       uint64_t *d_scores, void *cuda_stream);
 
+/* Learned candidate proposal (a small network trained to predict the
+ * criterion's choice; the paper motivates cutting the criterion's time,
+ * Sec. 4). Input: a 2 x 256 x 256 thumbnail (channel 0 raw layout, channel 1
+ * view-major mosaic; bs x bs block means with bs = ceil(max(W, H) / 256),
+ * edge blocks over their valid pixels; log1p(max(mean - 100, 0)) / 8;
+ * zero padding). Network: 4 x [3x3 convolution (2 -> 32, then 32 -> 32
+ * channels), zero padding 1, bias, ReLU], mean pool, linear 32 -> K, softmax.
+ * BF16 weights and activations, FP32 accumulation (tensor cores), FP32 master
+ * parameters and Adam state. Parameters (FP32, this order): for l = 0..3
+ * w_l[3][3][cin_l][32] (cin = 2, 32, 32, 32) then b_l[32]; wl[32][K]; bl[K].
+ * All calls run on the stream given at creation; d_* are device pointers. */
+typedef struct lfc_cnn_s *lfc_cnn;
+/* Allocates the network for n_classes outputs (2..64) and batches up to
+ * max_batch, initialised He-normal from seed. Synchronous. */
+int lfc_cnn_create(int n_classes, int max_batch, uint64_t seed, void *cuda_stream, lfc_cnn *out);
+void lfc_cnn_destroy(lfc_cnn cnn);
+const char *lfc_cnn_last_error(lfc_cnn cnn);
+size_t lfc_cnn_param_count(lfc_cnn cnn);
+/* Host FP32 parameters in / out (checkpoints); get also returns the last
+ * gradients when h_grads is not NULL. Synchronous. */
+int lfc_cnn_set_params(lfc_cnn cnn, const float *h_params, size_t n);
+int lfc_cnn_get_params(lfc_cnn cnn, float *h_params, float *h_grads, size_t n);
+/* Thumbnails of n frames (prev ignored) into the network's input;
+ * d_thumbs (n x 2 x 256 x 256 FP32) receives a copy when not NULL. */
+int lfc_cnn_thumbnails(lfc_cnn cnn, const lfc_frame *h_frames, int n, float *d_thumbs);
+/* Input from caller FP32 thumbnails (n x 2 x 256 x 256), rounded to BF16. */
+int lfc_cnn_set_thumbnails(lfc_cnn cnn, const float *d_thumbs, int n);
+/* Softmax probabilities (n x K FP32) of the current input. */
+int lfc_cnn_forward(lfc_cnn cnn, int n, float *d_probs);
+/* Forward, mean cross-entropy with d_labels (n int32 class indices) and the
+ * gradients of every parameter; per-frame losses to d_loss if not NULL. */
+int lfc_cnn_backward(lfc_cnn cnn, int n, const int32_t *d_labels, float *d_loss);
+/* One Adam update with the last gradients (bias-corrected). */
+int lfc_cnn_adam_step(lfc_cnn cnn, float lr, float beta1, float beta2, float eps);
+
+/* Attaches a trained network to a plan: class k of the network is candidate
+ * id h_class_ids[k] (n_classes must equal the network's). With topk > 0 the
+ * judge of every frame without a previous frame runs only on the network's
+ * topk most probable ids, or on all candidates when the top probability is
+ * below tau; temporal frames are always judged exhaustively. The network
+ * must run on the plan's stream. cnn = NULL detaches. */
+int lfc_plan_set_proposal(lfc_plan plan, lfc_cnn cnn, const uint8_t *h_class_ids, int n_classes, int topk, float tau);
+
+/* Candidate masks the proposal gives n frames (n x 4 uint64, bit id % 64 of
+ * word id / 64), as used by lfc_judge/lfc_compress. Errors: INVALID_ARG when
+ * no network is attached. */
+int lfc_propose(lfc_plan plan, const lfc_frame *h_frames, int n, uint64_t *d_masks);
+
 /* Text of a status code. */
 const char *lfc_status_string(int status);
 

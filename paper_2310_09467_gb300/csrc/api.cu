@@ -224,7 +224,7 @@ extern "C" int lfc_plan_block_capacity(lfc_plan P) { return P ? P->block_cap : 0
 static void free_ws(Workspace &w) {
     void *ptrs[] = {w.hist, w.summ, w.scores, w.choice, w.jframes, w.cand, w.l2tab, w.stream, w.blocks, w.bstate,
                     w.rle, w.sa, w.sa2, w.rank, w.act, w.act2, w.val, w.val2, w.tilecnt, w.tileaux, w.bwt,
-                    w.mtfidx, w.mtflists, w.mtfrec, w.mtfreclen, w.sym, w.freq, w.sel, w.lens, w.codes, w.packed, w.cstream, w.chain_first,
+                    w.mtfidx, w.mtflists, w.mtfrec, w.mtfreclen, w.sym, w.freq, w.sel, w.lens, w.codes, w.packed, w.cstream, w.chain_first, w.masks, w.class_ids,
                     w.act_total, w.block_dst, w.frame_crc, w.crc_part, w.chunk_desc, w.dec_tt};
     for (void *p : ptrs)
         if (p) cudaFree(p);
@@ -301,6 +301,8 @@ extern "C" int lfc_plan_create(const lfc_config *cfg, void *cuda_stream, lfc_pla
     AL(stream, (size_t)F * ws.stream_slot);
     AL(cstream, (size_t)JF * K * ws.cstream_slot);
     AL(chain_first, (size_t)ws.summ_cap * chain_first_bytes_per_cta());
+    AL(masks, (size_t)F * 4);
+    AL(class_ids, (size_t)64);
     AL(blocks, (size_t)BC);
     AL(bstate, (size_t)BC);
     AL(rle, (size_t)BC * kBlockCap);
@@ -394,6 +396,7 @@ struct CoderPass {
 };
 
 struct CompressDesc {
+    std::vector<lfc_frame> frames;
     Arena arena;
     std::vector<JudgeChunk> judge;
     CrcRun frame_crc;
@@ -447,6 +450,7 @@ int build_judge(lfc_plan P, const lfc_frame *frames, int n, Arena &A, std::vecto
             J.cta_base = cta;
             J.hist_off = hist;
             J.summ_off = summ;
+            J.mask = (P->cnn && P->topk > 0 && !tmp) ? ws.masks + (size_t)4 * (f0 + i) : nullptr;
             cta += (int64_t)J.K * J.segs;
             summ += (int64_t)J.K * J.segs;
             for (int k = 0; k < J.K; k++) hist_frame.push_back(i);
@@ -478,8 +482,13 @@ int build_judge(lfc_plan P, const lfc_frame *frames, int n, Arena &A, std::vecto
     return LFC_OK;
 }
 
-int run_judge(lfc_plan P, const std::vector<JudgeChunk> &chunks, const uint8_t *d_arena, uint8_t *d_choice,
-              uint64_t *d_scores) {
+int run_judge(lfc_plan P, const std::vector<lfc_frame> &frames, const std::vector<JudgeChunk> &chunks,
+              const uint8_t *d_arena, uint8_t *d_choice, uint64_t *d_scores) {
+    if (P->cnn && P->topk > 0) {
+        const int r = cnn_propose(P->cnn, frames.data(), (int)frames.size(), P->ws.class_ids, P->topk, P->tau, P->ws.masks,
+                                  P->stream);
+        if (r) return fail(P, r, "proposal network failed");
+    }
     int f0 = 0;
     for (const JudgeChunk &C : chunks) {
         CK(launch_judge(P, reinterpret_cast<const JudgeFrame *>(d_arena + C.off_tables), C.nf, C.ctas, C.L,
@@ -547,6 +556,7 @@ int build_compress(lfc_plan P, const lfc_frame *frames, int n, bool judge, size_
     const int bb = block_bytes_of(P);
     D.n = n;
     D.bb = bb;
+    D.frames.assign(frames, frames + n);
     out_off.resize(n);
     uint64_t need = 0;
     for (int i = 0; i < n; i++) {
@@ -614,7 +624,7 @@ int run_compress(lfc_plan P, const CompressDesc &D, const uint8_t *d_arena, cons
     Workspace &ws = P->ws;
     const uint8_t *choice = d_choice;
     if (!D.judge.empty()) {
-        const int r = run_judge(P, D.judge, d_arena, ws.choice, ws.scores);
+        const int r = run_judge(P, D.frames, D.judge, d_arena, ws.choice, ws.scores);
         if (r) return r;
         choice = ws.choice;
     }
@@ -655,8 +665,8 @@ extern "C" int lfc_judge(lfc_plan P, const lfc_frame *frames, int n, uint8_t *d_
     if (r) return r;
     r = stage_arena(P, A);
     if (r) return r;
-    return run_judge(P, chunks, reinterpret_cast<const uint8_t *>(P->ws.chunk_desc), d_choice,
-                     d_scores ? d_scores : P->ws.scores);
+    return run_judge(P, std::vector<lfc_frame>(frames, frames + n), chunks, reinterpret_cast<const uint8_t *>(P->ws.chunk_desc),
+                     d_choice, d_scores ? d_scores : P->ws.scores);
 }
 
 extern "C" int lfc_symbols(lfc_plan P, const lfc_frame *frame, int id, uint16_t *d_out) {
@@ -893,3 +903,33 @@ extern "C" int lfc_decompress(lfc_plan P, const uint8_t *const *h_in, const uint
     }
     return LFC_OK;
 }
+
+// ------------------------------------------------------- learned proposal
+extern "C" int lfc_plan_set_proposal(lfc_plan P, lfc_cnn cnn, const uint8_t *h_class_ids, int n_classes, int topk,
+                                     float tau) {
+    if (!P) return LFC_ERR_INVALID_ARG;
+    if (!cnn) {
+        P->cnn = nullptr;
+        P->topk = 0;
+        return LFC_OK;
+    }
+    if (!h_class_ids || n_classes != cnn_classes(cnn) || n_classes > 64 || topk < 1 || topk > n_classes)
+        return fail(P, LFC_ERR_INVALID_ARG, "lfc_plan_set_proposal: classes or topk");
+    for (int k = 0; k < n_classes; k++)
+        if (!id_valid(h_class_ids[k]) || (h_class_ids[k] & 0x80)) return fail(P, LFC_ERR_INVALID_ARG, "lfc_plan_set_proposal: class id");
+    CK(cudaMemcpy(P->ws.class_ids, h_class_ids, (size_t)n_classes, cudaMemcpyHostToDevice));
+    P->cnn = cnn;
+    P->topk = topk;
+    P->tau = tau;
+    return LFC_OK;
+}
+
+extern "C" int lfc_propose(lfc_plan P, const lfc_frame *frames, int n, uint64_t *d_masks) {
+    if (!P || !d_masks) return fail(P, LFC_ERR_INVALID_ARG, "lfc_propose: bad arguments");
+    if (!P->cnn) return fail(P, LFC_ERR_INVALID_ARG, "lfc_propose: no network attached");
+    const int r = check_frames(P, frames, n);
+    if (r) return r;
+    const int rr = cnn_propose(P->cnn, frames, n, P->ws.class_ids, P->topk, P->tau, d_masks, P->stream);
+    return rr ? fail(P, rr, "proposal network failed") : LFC_OK;
+}
+

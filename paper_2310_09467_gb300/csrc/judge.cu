@@ -232,11 +232,13 @@ judge_hist_kernel(const JudgeFrame *__restrict__ frames, int nframes, const uint
 // One CTA (256 threads) per (frame, candidate): links segments and adds the
 // bucket-boundary pairs.
 __global__ void judge_fixup_kernel(const JudgeFrame *__restrict__ frames, const int32_t *__restrict__ hist_frame,
-                                   uint32_t *__restrict__ hist, const uint16_t *__restrict__ summ) {
+                                   const uint8_t *__restrict__ cand, uint32_t *__restrict__ hist,
+                                   const uint16_t *__restrict__ summ) {
     __shared__ uint16_t gfirst[256], glast[256];
     const int hidx = blockIdx.x;  // global histogram index
     const JudgeFrame &J = frames[hist_frame[hidx]];
     const int ci = (int)(hidx - J.hist_off);
+    if (J.mask && !cand_on(J, cand[J.cand_off + ci])) return;
     uint32_t *ghist = hist + (size_t)hidx * kHistBins;
     const int b = threadIdx.x;
     uint16_t first = kNone, cur = kNone;
@@ -290,6 +292,10 @@ __global__ void __launch_bounds__(1024) entropy_kernel(const uint32_t *__restric
                                                        const int32_t *__restrict__ frame_index) {
     __shared__ uint64_t part[32];
     const int hidx = blockIdx.x;
+    {
+        const JudgeFrame &J = frames[hist_frame[hidx]];
+        if (J.mask && !cand_on(J, cand[J.cand_off + (hidx - J.hist_off)])) return;
+    }
     const uint4 *h4 = reinterpret_cast<const uint4 *>(hist + (size_t)hidx * kHistBins);
     uint64_t s = 0;
     for (int i = threadIdx.x; i < kHistBins / 4; i += blockDim.x) {
@@ -326,6 +332,7 @@ __global__ void argmax_kernel(const JudgeFrame *__restrict__ frames, int nframes
     int best_id = 256;
     for (int k = threadIdx.x; k < J.K; k += 32) {
         const int id = cand[J.cand_off + k];
+        if (!cand_on(J, id)) continue;
         const uint64_t v = sc[id];
         if (best_id == 256 || v > best || (v == best && id < best_id)) { best = v; best_id = id; }
     }
@@ -365,7 +372,7 @@ cudaError_t launch_judge(lfc_plan P, const JudgeFrame *d_frames, int nframes, in
     stage_end(P, LFC_STAGE_JUDGE_HIST);
     if (e != cudaSuccess) return e;
     stage_begin(P, LFC_STAGE_JUDGE_SCORE);
-    judge_fixup_kernel<<<(unsigned)nhist, 256, 0, s>>>(d_frames, d_hist_frame, ws.hist, ws.summ);
+    judge_fixup_kernel<<<(unsigned)nhist, 256, 0, s>>>(d_frames, d_hist_frame, d_cand, ws.hist, ws.summ);
     entropy_kernel<<<(unsigned)nhist, 1024, 0, s>>>(ws.hist, ws.l2tab, d_frames, d_hist_frame, d_cand, d_scores,
                                                    d_frame_index);
     argmax_kernel<<<nframes, 32, 0, s>>>(d_frames, nframes, d_cand, d_scores, d_choice, d_frame_index);
@@ -469,6 +476,7 @@ __global__ void noalloc_describe_kernel(NoAllocScratch *s, FrameDev F, IdList id
         J.cta_base = 0;
         J.hist_off = 0;
         J.summ_off = 0;
+        J.mask = nullptr;
     }
     if (i == 0) {
         s->jf_all = s->jf_one[0];
@@ -544,7 +552,7 @@ extern "C" int lfc_judge_noalloc(const lfc_frame *frame, const uint8_t *h_ids, i
     for (int i = 0; i < n_ids; i++) {
         if (cudaMemsetAsync(s->hist, 0, sizeof(s->hist), st) != cudaSuccess) return LFC_ERR_CUDA;
         judge_hist_kernel<<<segs, kJudgeWarps * 32, smem, st>>>(&s->jf_one[i], 1, s->cand, s->hist, s->summ, W);
-        judge_fixup_kernel<<<1, 256, 0, st>>>(&s->jf_one[i], s->zero, s->hist, s->summ);
+        judge_fixup_kernel<<<1, 256, 0, st>>>(&s->jf_one[i], s->zero, s->cand, s->hist, s->summ);
         entropy_kernel<<<1, 1024, 0, st>>>(s->hist, s->l2tab, &s->jf_one[i], s->zero, s->cand, s->scores, s->zero);
     }
     argmax_kernel<<<1, 32, 0, st>>>(&s->jf_all, 1, s->cand, s->scores, d_choice, s->zero);

@@ -71,7 +71,7 @@ __global__ void __launch_bounds__(kEmitThreads) emit_all_kernel(const JudgeFrame
     int nc = 0;
     for (int k = 0; k < J.K; k++) {
         const int id = cand[J.cand_off + k];
-        if (((id >> 7) & 1) != kind) continue;
+        if (((id >> 7) & 1) != kind || !cand_on(J, id)) continue;
         nc++;
         const int f = id & 15, dom = (id >> 4) & 3;
         if (f && dom != 1) fset |= 1u << f;
@@ -83,7 +83,7 @@ __global__ void __launch_bounds__(kEmitThreads) emit_all_kernel(const JudgeFrame
         for (int f = 0; f < 8; f++) eslot_of[f] = (int8_t)__popc(fset & ((1u << f) - 1u));
         for (int k = 0; k < J.K; k++) {
             const int id = cand[J.cand_off + k];
-            if (((id >> 7) & 1) != kind) continue;
+            if (((id >> 7) & 1) != kind || !cand_on(J, id)) continue;
             const int f = id & 15, dom = (id >> 4) & 3, ord = (id >> 6) & 1;
             slot_of[f][dom][ord] = (int16_t)k;
             fmask_ord[ord] |= 1u << f;
@@ -221,9 +221,9 @@ __device__ __forceinline__ void chain_byte(uint32_t b, uint32_t &prev, uint32_t 
 }
 
 __global__ void __launch_bounds__(kChainThreads)
-chain_hist_kernel(const JudgeFrame *__restrict__ frames, int nframes, const uint8_t *__restrict__ cstream, int64_t cslot,
-                  int kmax, uint32_t *__restrict__ hist, uint16_t *__restrict__ summ, uint8_t *__restrict__ first_all,
-                  int range_bytes) {
+chain_hist_kernel(const JudgeFrame *__restrict__ frames, int nframes, const uint8_t *__restrict__ cand,
+                  const uint8_t *__restrict__ cstream, int64_t cslot, int kmax, uint32_t *__restrict__ hist,
+                  uint16_t *__restrict__ summ, uint8_t *__restrict__ first_all, int range_bytes) {
     extern __shared__ __align__(16) uint8_t smem[];
     uint32_t *hot = reinterpret_cast<uint32_t *>(smem);   // [kHot][kHot]
     uint32_t *tbl = hot + kHot * kHot;                    // [128][T]
@@ -235,6 +235,7 @@ chain_hist_kernel(const JudgeFrame *__restrict__ frames, int nframes, const uint
     uint32_t *ghist = hist + (size_t)(J.hist_off + ci) * kHistBins;
     const int64_t n = 2LL * J.F.W * J.F.H;
     const int t = threadIdx.x;
+    if (!cand_on(J, cand[J.cand_off + ci])) return;  // not proposed: no stream, no histogram
     const int64_t seg_bytes = (int64_t)kChainThreads * range_bytes;
     const int64_t ra64 = min(n, (int64_t)seg * seg_bytes + (int64_t)t * range_bytes);
     const int len = (int)(min(n, ra64 + range_bytes) - ra64);
@@ -293,12 +294,11 @@ cudaError_t launch_emit_all(lfc_plan P, const JudgeFrame *d_frames, int nframes,
 
 cudaError_t launch_chain_hist(lfc_plan P, const JudgeFrame *d_frames, int nframes, const uint8_t *d_cand, int64_t total_ctas,
                               int range_bytes) {
-    (void)d_cand;
     const size_t smem = chain_smem_bytes();
     cudaError_t e = cudaFuncSetAttribute(chain_hist_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     chain_hist_kernel<<<(unsigned)total_ctas, kChainThreads, smem, P->stream>>>(
-        d_frames, nframes, P->ws.cstream, P->ws.cstream_slot, P->ws.cstream_kmax, P->ws.hist, P->ws.summ,
+        d_frames, nframes, d_cand, P->ws.cstream, P->ws.cstream_slot, P->ws.cstream_kmax, P->ws.hist, P->ws.summ,
         P->ws.chain_first, range_bytes);
     count_launches(P, 1);
     return cudaGetLastError();

@@ -119,7 +119,12 @@ struct JudgeFrame {
     int64_t cta_base;      // first CTA index of this frame
     int64_t hist_off;      // first histogram (in units of 65536 bins)
     int64_t summ_off;      // first segment summary
+    const uint64_t *mask;  // candidate mask (4 words) from the proposal, or nullptr = all
 };
+
+__device__ __forceinline__ bool cand_on(const JudgeFrame &J, int id) {
+    return J.mask == nullptr || ((J.mask[id >> 6] >> (id & 63)) & 1ull);
+}
 
 // One bzip2 block: input bytes at src[0 .. len).
 struct BlockDesc {
@@ -159,6 +164,8 @@ struct Workspace {
     int64_t summ_cap = 0;
     uint8_t *cstream = nullptr;    // candidate streams: judge_frames_cap * cstream_kmax slots
     uint8_t *chain_first = nullptr;// first-occurrence predecessors, per chain CTA x thread x 256
+    uint64_t *masks = nullptr;     // proposal candidate masks, max_frames x 4
+    uint8_t *class_ids = nullptr;  // proposal class -> candidate id (64)
     int64_t cstream_slot = 0;
     int cstream_kmax = 0;
     // symbol streams of the frames being compressed
@@ -215,6 +222,9 @@ struct lfc_plan_s {
     std::vector<uint8_t> ids_temporal;  // judged for frames with prev
     int judge_frames_cap = 0;           // frames per judge launch (allocated)
     lfc_tuning tune{16, 2048, 0, 0};    // autotuned judge knobs
+    lfc_cnn cnn = nullptr;              // learned proposal (optional)
+    int topk = 0;
+    float tau = 0.f;
     int block_cap = 0;                  // blocks per coder pass
     lfc::Workspace ws;
     // tracing: CUDA events around stages, harvested by lfc_plan_timing
@@ -231,6 +241,12 @@ struct lfc_plan_s {
 };
 
 namespace lfc {
+
+// cnn.cu
+int cnn_propose(lfc_cnn C, const lfc_frame *frames, int n, const uint8_t *d_class_ids, int topk, float tau,
+                uint64_t *d_masks, cudaStream_t s);
+int cnn_classes(lfc_cnn C);
+int cnn_max_batch(lfc_cnn C);
 
 // ---------------------------------------------------------------- tracing
 void stage_begin(lfc_plan P, int stage);

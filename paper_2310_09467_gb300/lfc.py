@@ -28,7 +28,10 @@ EXPORTS = ["lfc_plan_create", "lfc_plan_destroy", "lfc_plan_last_error", "lfc_ju
            "lfc_plan_block_capacity", "lfc_decompress", "lfc_status_string", "lfc_plan_set_timing",
            "lfc_plan_timing", "lfc_plan_launch_count", "lfc_judge_noalloc", "lfc_plan_bwt_counters",
            "lfc_batch_create", "lfc_batch_launch", "lfc_batch_destroy",
-           "lfc_plan_set_tuning", "lfc_plan_get_tuning"]
+           "lfc_plan_set_tuning", "lfc_plan_get_tuning",
+           "lfc_cnn_create", "lfc_cnn_destroy", "lfc_cnn_last_error", "lfc_cnn_param_count", "lfc_cnn_set_params",
+           "lfc_cnn_get_params", "lfc_cnn_thumbnails", "lfc_cnn_set_thumbnails", "lfc_cnn_forward", "lfc_cnn_backward",
+           "lfc_cnn_adam_step", "lfc_plan_set_proposal", "lfc_propose"]
 
 STAGES = ["judge_hist", "judge_score", "emit", "crc", "rle1", "bwt_sort8", "bwt_refine", "bwt_out", "mtf",
           "huffman", "pack", "container", "judge_emit"]
@@ -91,6 +94,19 @@ def load():
         "lfc_batch_launch": (i32, [P]),
         "lfc_plan_set_tuning": (i32, [P, ctypes.POINTER(Tuning)]),
         "lfc_plan_get_tuning": (i32, [P, ctypes.POINTER(Tuning)]),
+        "lfc_cnn_create": (i32, [i32, i32, ctypes.c_uint64, P, ctypes.POINTER(P)]),
+        "lfc_cnn_destroy": (None, [P]),
+        "lfc_cnn_last_error": (ctypes.c_char_p, [P]),
+        "lfc_cnn_param_count": (sz, [P]),
+        "lfc_cnn_set_params": (i32, [P, P, sz]),
+        "lfc_cnn_get_params": (i32, [P, P, P, sz]),
+        "lfc_cnn_thumbnails": (i32, [P, ctypes.POINTER(Frame), i32, P]),
+        "lfc_cnn_set_thumbnails": (i32, [P, P, i32]),
+        "lfc_cnn_forward": (i32, [P, i32, P]),
+        "lfc_cnn_backward": (i32, [P, i32, P, P]),
+        "lfc_cnn_adam_step": (i32, [P, ctypes.c_float, ctypes.c_float, ctypes.c_float, ctypes.c_float]),
+        "lfc_plan_set_proposal": (i32, [P, P, ctypes.POINTER(ctypes.c_uint8), i32, i32, ctypes.c_float]),
+        "lfc_propose": (i32, [P, ctypes.POINTER(Frame), i32, P]),
         "lfc_batch_destroy": (None, [P]),
         "lfc_judge_noalloc": (i32, [ctypes.POINTER(Frame), ctypes.POINTER(ctypes.c_uint8), i32, P, P, P]),
     }
@@ -258,6 +274,18 @@ class Plan:
         self._check(rc, "lfc_compress")
         return out, sizes, offs
 
+    def set_proposal(self, cnn, class_ids, topk, tau):
+        ids = (ctypes.c_uint8 * len(class_ids))(*class_ids)
+        self._check(self.lib.lfc_plan_set_proposal(self.h, cnn.h if cnn else None, ids, len(class_ids), topk, tau),
+                    "lfc_plan_set_proposal")
+
+    def propose(self, frames, pitch):
+        torch = _torch()
+        arr = self._frames(frames, pitch)
+        masks = torch.zeros((len(frames), 4), dtype=torch.int64, device=frames[0].device)
+        self._check(self.lib.lfc_propose(self.h, arr, len(frames), _ptr(masks)), "lfc_propose")
+        return masks
+
     def batch(self, frames, pitch, prevs=None, choice=None, out=None, sizes=None):
         """Capture lfc_compress on these frame buffers as a CUDA graph."""
         return Batch(self, frames, pitch, prevs, choice, out, sizes)
@@ -309,6 +337,93 @@ class Plan:
         rc = self.lib.lfc_decompress(self.h, ins, szs, n, os_, ob, pv)
         self._check(rc, "lfc_decompress")
         return outs
+
+
+class Cnn:
+    """The proposal network (lfc_cnn_*): thumbnails, forward, backward, Adam."""
+
+    def __init__(self, n_classes, max_batch, seed=0, stream=None):
+        torch = _torch()
+        self.lib = load()
+        self.K = n_classes
+        self.max_batch = max_batch
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        h = ctypes.c_void_p()
+        rc = self.lib.lfc_cnn_create(n_classes, max_batch, seed, ctypes.c_void_p(self.stream.cuda_stream), ctypes.byref(h))
+        if rc != LFC_OK:
+            raise LfcError(rc, "lfc_cnn_create")
+        self.h = h
+        self.n_params = int(self.lib.lfc_cnn_param_count(h))
+
+    def _check(self, rc, what):
+        if rc != LFC_OK:
+            msg = self.lib.lfc_cnn_last_error(self.h)
+            raise LfcError(rc, "%s: %s" % (what, msg.decode() if msg else ""))
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.lfc_cnn_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_params(self, flat):
+        a = np.ascontiguousarray(flat, dtype=np.float32)
+        assert a.size == self.n_params
+        self._check(self.lib.lfc_cnn_set_params(self.h, a.ctypes.data_as(ctypes.c_void_p), a.size), "set_params")
+
+    def get_params(self, grads=False):
+        p = np.empty(self.n_params, dtype=np.float32)
+        g = np.empty(self.n_params, dtype=np.float32) if grads else None
+        self._check(self.lib.lfc_cnn_get_params(self.h, p.ctypes.data_as(ctypes.c_void_p),
+                                                None if g is None else g.ctypes.data_as(ctypes.c_void_p),
+                                                self.n_params), "get_params")
+        return (p, g) if grads else p
+
+    def thumbnails(self, frames, pitch, want=False):
+        torch = _torch()
+        arr = Plan._frames(frames, pitch)
+        out = torch.empty((len(frames), 2, 256, 256), dtype=torch.float32, device=frames[0].device) if want else None
+        self._check(self.lib.lfc_cnn_thumbnails(self.h, arr, len(frames), _ptr(out)), "thumbnails")
+        return out
+
+    def set_thumbnails(self, thumbs):
+        self._check(self.lib.lfc_cnn_set_thumbnails(self.h, _ptr(thumbs.contiguous()), thumbs.shape[0]), "set_thumbnails")
+
+    def forward(self, n):
+        torch = _torch()
+        probs = torch.empty((n, self.K), dtype=torch.float32, device="cuda")
+        self._check(self.lib.lfc_cnn_forward(self.h, n, _ptr(probs)), "forward")
+        return probs
+
+    def backward(self, labels):
+        torch = _torch()
+        n = labels.numel()
+        loss = torch.empty(n, dtype=torch.float32, device="cuda")
+        self._check(self.lib.lfc_cnn_backward(self.h, n, _ptr(labels), _ptr(loss)), "backward")
+        return loss
+
+    def adam_step(self, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8):
+        self._check(self.lib.lfc_cnn_adam_step(self.h, lr, beta1, beta2, eps), "adam_step")
+
+    def flat_from_dict(self, P):
+        keys = ["w0", "b0", "w1", "b1", "w2", "b2", "w3", "b3", "wl", "bl"]
+        return np.concatenate([np.asarray(P[k], dtype=np.float64).reshape(-1) for k in keys]).astype(np.float32)
+
+    def dict_from_flat(self, flat):
+        shapes = [("w0", (3, 3, 2, 32)), ("b0", (32,)), ("w1", (3, 3, 32, 32)), ("b1", (32,)),
+                  ("w2", (3, 3, 32, 32)), ("b2", (32,)), ("w3", (3, 3, 32, 32)), ("b3", (32,)),
+                  ("wl", (32, self.K)), ("bl", (self.K,))]
+        out, o = {}, 0
+        for k, shp in shapes:
+            n = int(np.prod(shp))
+            out[k] = np.asarray(flat[o:o + n], dtype=np.float64).reshape(shp)
+            o += n
+        return out
 
 
 class Batch:
