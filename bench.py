@@ -193,6 +193,50 @@ def run_uneven(args):
     return 0
 
 
+def run_learned(args):
+    """Learned proposal vs exhaustive judge on 2040x2040 frames: train the
+    network (own kernels) on frames labelled by the exhaustive judge, then
+    compress held-out frames with and without the proposal."""
+    import numpy as np
+    import torch
+
+    from paper_2310_09467_gb300 import build, learn, lfc, synth
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    build.build()
+    t0 = time.time()
+    tr_fields = synth.training_fields(args.train_beads, args.train_cells, args.train_vessels, seed0=10000)
+    te_fields = synth.training_fields(4, 2, 2, seed0=20000)
+    train_frames = learn.make_frames(tr_fields, draws=args.draws, seed0=0)
+    test_frames = learn.make_frames(te_fields, draws=1, seed0=500000)
+    gen_s = time.time() - t0
+    plan = lfc.Plan(W, H, PITCH, max_frames=8)
+    class_ids = sorted([0x00, 0x40] + [f | (d << 4) | (o << 6) for o in (0, 1) for d in (0, 1, 2) for f in (4, 5, 6, 7)])
+    labels = learn.labels_for(plan, train_frames, PITCH, class_ids)
+    test_labels = learn.labels_for(plan, test_frames, PITCH, class_ids)
+    net = lfc.Cnn(len(class_ids), 32, seed=1)
+    t1 = time.time()
+    hist = learn.train(net, train_frames, labels, PITCH, epochs=args.epochs, batch=32, lr=2e-3)
+    torch.cuda.synchronize()
+    train_s = time.time() - t1
+    acc1 = learn.accuracy(net, test_frames, test_labels, PITCH, 1)
+    acc3 = learn.accuracy(net, test_frames, test_labels, PITCH, 3)
+    res = learn.evaluate(plan, net, class_ids, test_frames, PITCH)
+    raw = 2 * W * H
+    best = res["top3_tau0.0"]
+    line = {"metric": METRIC, "value": best["fps"] * raw / 1e6, "unit": "MB/s", "n_gpus": 1,
+            "higher_is_better": True, "dtype": "u16/u8 integer; CNN bf16/fp32", "data": "synthetic",
+            "config": {"workload": "learned proposal vs exhaustive judge, 2040x2040 p15",
+                       "train_frames": len(train_frames), "test_frames": len(test_frames), "epochs": args.epochs},
+            "exhaustive_MBps": res["exhaustive"]["fps"] * raw / 1e6,
+            "settings": {k: {kk: (round(vv, 4) if isinstance(vv, float) else vv) for kk, vv in v.items()}
+                         for k, v in res.items()},
+            "test_accuracy": {"top1": acc1, "top3": acc3}, "train_loss": [round(x, 4) for x in hist],
+            "label_hist": np.bincount(labels.cpu().numpy(), minlength=len(class_ids)).tolist(),
+            "seconds": {"generate": gen_s, "train": train_s}}
+    print(json.dumps(line))
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -201,13 +245,20 @@ def main():
     ap.add_argument("--impl", default="lfc", choices=["lfc", "reference"])
     ap.add_argument("--per-kind", type=int, default=4)
     ap.add_argument("--no-cpu", action="store_true")
-    ap.add_argument("--workload", default="single2040", choices=["single2040", "uneven"])
+    ap.add_argument("--workload", default="single2040", choices=["single2040", "uneven", "learned"])
+    ap.add_argument("--train-beads", type=int, default=16)
+    ap.add_argument("--train-cells", type=int, default=4)
+    ap.add_argument("--train-vessels", type=int, default=8)
+    ap.add_argument("--draws", type=int, default=4)
+    ap.add_argument("--epochs", type=int, default=30)
     ap.add_argument("--uneven-frames", type=int, default=256)
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
     if args.workload == "uneven":
         return run_uneven(args)
+    if args.workload == "learned":
+        return run_learned(args)
 
     import numpy as np
     import torch

@@ -320,3 +320,38 @@ def uneven_batch_fast(n: int = 256, base_seed: int = 1000):
                 fields[(c, g)] = VesselSeries(W, H, p, seed=s).photons(0)
         out.append((_to_raw(fields[(c, g)], np.random.default_rng(base_seed + i)), p))
     return out
+
+
+def photons_to_frame_torch(sub, scale: float, seed: int, device="cuda"):
+    """Expected photons sub[v, u, t, s] (numpy, unit level) times ``scale``
+    -> raw frame as an int16 CUDA tensor holding the uint16 bits, with
+    Poisson and read noise drawn by torch on the device (fixed seed). Used
+    to make large training sets quickly; same forward model as _to_raw."""
+    import torch
+    g = torch.Generator(device=device)
+    g.manual_seed(int(seed))
+    lam = torch.as_tensor(sub, dtype=torch.float32, device=device) * float(scale)
+    ph = torch.poisson(lam.clamp_min(0), generator=g)
+    dn = ph + torch.randn(lam.shape, generator=g, device=device) * READ_SIGMA_DN + OFFSET_DN
+    dn = torch.clamp(torch.round(dn), 0, 65535).to(torch.int32)
+    p, _, Ny, Nx = sub.shape
+    raw = dn.permute(2, 0, 3, 1).reshape(Ny * p, Nx * p).contiguous()
+    return torch.where(raw >= 32768, raw - 65536, raw).to(torch.int16)
+
+
+def training_fields(n_beads: int, n_cells: int, n_vessels: int, W: int = 2040, H: int = 2040, p: int = 15,
+                    seed0: int = 10000):
+    """Unit-level expected-photon fields of the three generators (beads: peak
+    1, cells: level 1, vessels: peak 1), seeds seed0 + k."""
+    out = []
+    k = 0
+    for _ in range(n_beads):
+        out.append(("beads", bead_photons(W, H, p, peak=1.0, seed=seed0 + k)))
+        k += 1
+    for _ in range(n_cells):
+        out.append(("cells", cell_photons(W, H, p, level=1.0, seed=seed0 + k)))
+        k += 1
+    for _ in range(n_vessels):
+        out.append(("vessel", VesselSeries(W, H, p, peak=1.0, seed=seed0 + k).photons(k % 50)))
+        k += 1
+    return out
