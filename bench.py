@@ -193,6 +193,59 @@ def run_uneven(args):
     return 0
 
 
+def run_series(args):
+    """Time series: 100 frames of a 2040x2040 vessel series (spots flowing
+    2-10 px/frame, 300 photons); temporal candidates (K = 52) on every frame
+    but the keyframes (every 16th); all frames in one CUDA-graph launch;
+    compared with the same frames compressed without temporal candidates."""
+    import numpy as np
+    import torch
+
+    from paper_2310_09467_gb300 import build, lfc, synth
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    build.build()
+    n, G = args.series_frames, 16
+    vs = synth.VesselSeries(W, H, PITCH, peak=1.0, seed=4)
+    frames = [synth.photons_to_frame_torch(vs.photons(k), 300.0, 70000 + k) for k in range(n)]
+    prevs = [None if k % G == 0 else frames[k - 1] for k in range(n)]
+    raw_bytes = n * 2 * W * H
+    out = {}
+    for temporal in (True, False):
+        plan = lfc.Plan(W, H, PITCH, max_frames=n, temporal=temporal)
+        batch = plan.batch(frames, PITCH, prevs=prevs if temporal else None)
+        for _ in range(args.warmup):
+            batch.launch()
+        torch.cuda.synchronize()
+        ms = []
+        st = plan.stream
+        for _ in range(args.steps):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(st)
+            batch.launch()
+            b.record(st)
+            b.synchronize()
+            ms.append(a.elapsed_time(b))
+        comp = int(batch.sizes.cpu().numpy().sum())
+        if temporal:
+            ids = []
+            host = batch.out.cpu().numpy()
+            for o in batch.offs:
+                ids.append(int(host[o + 20]))
+            out["temporal_ids"] = int(sum(1 for i in ids if i & 0x80))
+        out["temporal" if temporal else "spatial"] = {"MBps": raw_bytes * args.steps / 1e6 / (sum(ms) / 1e3),
+                                                     "ratio": raw_bytes / comp, "bytes": comp}
+        batch.close()
+        plan.close()
+    line = {"metric": METRIC, "value": out["temporal"]["MBps"], "unit": "MB/s", "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "higher_is_better": True, "dtype": "u16/u8 integer", "data": "synthetic",
+            "config": {"workload": "time series: %d frames 2040x2040 p15 vessel, keyframe every %d, one graph launch" % (n, G),
+                       "candidates": "52 (26 spatial + 26 temporal) on non-keyframes"},
+            "ratio": out["temporal"]["ratio"], "ratio_without_temporal": out["spatial"]["ratio"],
+            "MBps_without_temporal": out["spatial"]["MBps"], "frames_choosing_temporal": out["temporal_ids"]}
+    print(json.dumps(line))
+    return 0
+
+
 def run_learned(args):
     """Learned proposal vs exhaustive judge on 2040x2040 frames: train the
     network (own kernels) on frames labelled by the exhaustive judge, then
@@ -245,7 +298,8 @@ def main():
     ap.add_argument("--impl", default="lfc", choices=["lfc", "reference"])
     ap.add_argument("--per-kind", type=int, default=4)
     ap.add_argument("--no-cpu", action="store_true")
-    ap.add_argument("--workload", default="single2040", choices=["single2040", "uneven", "learned"])
+    ap.add_argument("--workload", default="single2040", choices=["single2040", "uneven", "learned", "series"])
+    ap.add_argument("--series-frames", type=int, default=100)
     ap.add_argument("--train-beads", type=int, default=16)
     ap.add_argument("--train-cells", type=int, default=4)
     ap.add_argument("--train-vessels", type=int, default=8)
@@ -259,6 +313,8 @@ def main():
         return run_uneven(args)
     if args.workload == "learned":
         return run_learned(args)
+    if args.workload == "series":
+        return run_series(args)
 
     import numpy as np
     import torch
