@@ -14,6 +14,8 @@
 //     key (m < 2^20), splits groups, and doubles h. Groups left when h >= m
 //     hold identical rotations, already in start-index order (every pass is
 //     stable and the first starts from the identity).
+#include <climits>
+
 #include "lfc_common.cuh"
 
 namespace lfc {
@@ -22,63 +24,201 @@ constexpr int kSortThreads = 256;
 constexpr int kPerThread = kTile / kSortThreads;  // 16
 
 // ------------------------------------------------------------------ RLE1
-// One CTA (1024 threads) per block: run starts are compacted, every run's
-// coded length (a run of L bytes is cut into 255-byte runs; a run of 4..255
-// becomes 4 bytes + count, shorter ones stay literal) is prefix-summed, and
-// the runs are written.
-__global__ void __launch_bounds__(1024) rle1_kernel(const BlockDesc *__restrict__ blocks, BlockState *__restrict__ st,
-                                                    uint8_t *__restrict__ rle_all, int32_t *__restrict__ scratch_all) {
-    __shared__ int32_t sh[33];
-    const int b = blockIdx.x;
-    const BlockDesc B = blocks[b];
-    const uint8_t *src = B.src;
-    const int n = B.len;
-    uint8_t *out = rle_all + (size_t)b * kBlockCap;
-    int32_t *runs = scratch_all + (size_t)b * kBlockCap;
-    const int T = blockDim.x;
-    const int per = (n + T - 1) / T;
-    const int a = min(n, (int)threadIdx.x * per), e = min(n, a + per);
-    int cnt = 0;
-    for (int i = a; i < e; i++) cnt += (i == 0 || src[i] != src[i - 1]);
-    int total_runs;
-    int off = block_excl_sum<int>(cnt, sh, &total_runs);
-    for (int i = a; i < e; i++)
-        if (i == 0 || src[i] != src[i - 1]) runs[off++] = i;
+// A run of L equal bytes is cut into 255-byte pieces; a piece of 4 or more
+// bytes becomes its first 4 bytes and a count byte (length - 4), a shorter
+// one stays literal. So the byte at offset k of its run adds w(k mod 255)
+// output bytes, w = 1, 1, 1, 2, 0, 0, ... (the fourth byte carries the count
+// byte), and a run of L bytes codes to G(L) = sum_{k<L} w(k mod 255) bytes.
+// That makes RLE1 a scan over 4096-byte tiles of every block, in three
+// kernels: per tile the first / last run start and the output of the
+// positions whose run starts inside the tile (1); per block, in tile order,
+// the run start carried into each tile and the tile's output offset (2); per
+// tile, every position's output offset and its bytes, staged in shared
+// memory and stored coalesced (3).
+constexpr int kRleTile = 4096;
+constexpr int kRleThreads = 256;                  // 16 bytes per thread
+constexpr int kRleMaxTiles = (LFC_MAX_BLOCK_BYTES + kRleTile - 1) / kRleTile;
+constexpr int kRleOutCap = kRleTile / 4 * 5 + 16; // at most 5 output bytes per 4 inputs, + edge
+static_assert(kRleMaxTiles <= kTilesPerBlock, "RLE1 tile records live in the per-block tile scratch");
+
+__device__ __forceinline__ int rle_w(int k) {
+    const int j = k % 255;
+    return j < 3 ? 1 : (j == 3 ? 2 : 0);
+}
+__device__ __forceinline__ int rle_G(int L) {
+    const int r = L % 255;
+    return 5 * (L / 255) + (r < 4 ? r : 5);
+}
+
+// Stage tile bytes [ts, te) of block B in s and find the run starts of this
+// thread's 16 positions (bit q of the mask: position 16 * tid + q starts a
+// run). Returns the mask; first / last are tile offsets (kRleTile / -1 when
+// the thread has no start).
+__device__ __forceinline__ uint32_t rle_tile_starts(const uint8_t *src, int ts, int te, uint8_t *s, int &first,
+                                                    int &last) {
+    const int len = te - ts;
+    if (len == kRleTile && (((uintptr_t)(src + ts)) & 15) == 0) {
+        reinterpret_cast<uint4 *>(s)[threadIdx.x] = __ldg(reinterpret_cast<const uint4 *>(src + ts) + threadIdx.x);
+    } else {
+        for (int k = threadIdx.x; k < len; k += kRleThreads) s[k] = src[ts + k];
+    }
     __syncthreads();
-    // coded length per run
-    const int perR = (total_runs + T - 1) / T;
-    const int ra = min(total_runs, (int)threadIdx.x * perR), re = min(total_runs, ra + perR);
-    int bytes = 0;
-    for (int r = ra; r < re; r++) {
-        const int L = (r + 1 < total_runs ? runs[r + 1] : n) - runs[r];
-        const int q = L / 255, rem = L % 255;
-        bytes += rem >= 4 ? 5 * (q + 1) : 5 * q + rem;
-    }
-    int total_out;
-    int o = block_excl_sum<int>(bytes, sh, &total_out);
-    for (int r = ra; r < re; r++) {
-        const int s0 = runs[r];
-        const int L = (r + 1 < total_runs ? runs[r + 1] : n) - s0;
-        const uint8_t v = src[s0];
-        const int q = L / 255, rem = L % 255;
-        for (int c = 0; c < q; c++) {
-            out[o] = v; out[o + 1] = v; out[o + 2] = v; out[o + 3] = v; out[o + 4] = 251;
-            o += 5;
-        }
-        if (rem >= 4) {
-            out[o] = v; out[o + 1] = v; out[o + 2] = v; out[o + 3] = v; out[o + 4] = (uint8_t)(rem - 4);
-            o += 5;
-        } else {
-            for (int c = 0; c < rem; c++) out[o++] = v;
+    const int a = 16 * threadIdx.x;
+    uint32_t mask = 0;
+    first = kRleTile;
+    last = -1;
+    if (a < len) {
+        int c = a > 0 ? (int)s[a - 1] : (ts > 0 ? (int)src[ts - 1] : -1);
+        uint8_t v[16];
+        *reinterpret_cast<uint4 *>(v) = reinterpret_cast<const uint4 *>(s)[threadIdx.x];
+#pragma unroll
+        for (int q = 0; q < 16; q++) {
+            if (a + q < len && (int)v[q] != c) {
+                mask |= 1u << q;
+                first = min(first, a + q);
+                last = a + q;
+            }
+            c = v[q];
         }
     }
-    if (threadIdx.x == 0) st[b].m = total_out;
+    return mask;
+}
+
+// (1) aux[tile] = {first start (absolute; tile end if none), last start
+//     (absolute; -1 if none), output of the positions after the first start}.
+__global__ void __launch_bounds__(kRleThreads) rle1_tile_kernel(const BlockDesc *__restrict__ blocks,
+                                                                int32_t *__restrict__ aux_all) {
+    __shared__ __align__(16) uint8_t s[kRleTile];
+    __shared__ int sh[33];
+    __shared__ int sfirst, slast;
+    const int b = blockIdx.y, tile = blockIdx.x;
+    const BlockDesc B = blocks[b];
+    const int ts = tile * kRleTile;
+    if (ts >= B.len) return;
+    const int te = min(B.len, ts + kRleTile);
+    if (threadIdx.x == 0) { sfirst = kRleTile; slast = -1; }
+    int first, last;
+    const uint32_t mask = rle_tile_starts(B.src, ts, te, s, first, last);
+    const int carry = block_excl_max(last, sh);
+    int rs = carry, out = 0;
+    const int a = 16 * threadIdx.x;
+#pragma unroll
+    for (int q = 0; q < 16; q++) {
+        if (mask & (1u << q)) rs = a + q;
+        if (rs >= 0 && a + q < te - ts) out += rle_w(a + q - rs);
+    }
+    int total;
+    block_excl_sum<int>(out, sh, &total);
+    if (first < kRleTile) atomicMin(&sfirst, first);
+    if (last >= 0) atomicMax(&slast, last);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int32_t *aux = aux_all + ((size_t)b * kTilesPerBlock + tile) * 4;
+        aux[0] = sfirst < kRleTile ? ts + sfirst : te;
+        aux[1] = slast >= 0 ? ts + slast : -1;
+        aux[2] = total;
+    }
+}
+
+// (2) one warp per block: aux[tile][1] = run start carried into the tile,
+//     aux[tile][2] = the tile's output offset; st.m = RLE1 length.
+__global__ void __launch_bounds__(32) rle1_scan_kernel(const BlockDesc *__restrict__ blocks,
+                                                       BlockState *__restrict__ st, int32_t *__restrict__ aux_all) {
+    const int b = blockIdx.x;
+    const int n = blocks[b].len;
+    const int ntile = (n + kRleTile - 1) / kRleTile;
+    int32_t *aux = aux_all + (size_t)b * kTilesPerBlock * 4;
+    const int lane = (int)lane_id();
+    int carryR = -1, carryO = 0;
+    for (int base = 0; base < ntile; base += 32) {
+        const int t = base + lane;
+        const bool valid = t < ntile;
+        const int fs = valid ? aux[t * 4 + 0] : n;
+        const int ls = valid ? aux[t * 4 + 1] : -1;
+        const int lo = valid ? aux[t * 4 + 2] : 0;
+        const int imax = warp_incl_max(ls);
+        int ex = __shfl_up_sync(LFC_FULL, imax, 1);
+        if (lane == 0) ex = -1;
+        const int R = max(carryR, ex);
+        const int ts = t * kRleTile;
+        const int pre = (valid && R >= 0) ? rle_G(fs - R) - rle_G(ts - R) : 0;
+        const int out = valid ? pre + lo : 0;
+        const int incl = warp_incl_sum(out);
+        if (valid) {
+            aux[t * 4 + 1] = R;
+            aux[t * 4 + 2] = carryO + incl - out;
+        }
+        carryR = max(carryR, __shfl_sync(LFC_FULL, imax, 31));
+        carryO += __shfl_sync(LFC_FULL, incl, 31);
+    }
+    if (lane == 0) st[b].m = carryO;
+}
+
+// (3) every position's output offset and bytes; the count byte of a piece
+//     needs its run's end, found among the next <= 252 positions.
+__global__ void __launch_bounds__(kRleThreads) rle1_write_kernel(const BlockDesc *__restrict__ blocks,
+                                                                 const int32_t *__restrict__ aux_all,
+                                                                 uint8_t *__restrict__ rle_all) {
+    __shared__ __align__(16) uint8_t s[kRleTile];
+    __shared__ uint8_t ob[kRleOutCap];
+    __shared__ int sh[33];
+    __shared__ int tfirst[kRleThreads];
+    const int b = blockIdx.y, tile = blockIdx.x;
+    const BlockDesc B = blocks[b];
+    const int n = B.len, ts = tile * kRleTile;
+    if (ts >= n) return;
+    const int te = min(n, ts + kRleTile), len = te - ts;
+    const int ntile = (n + kRleTile - 1) / kRleTile;
+    const int32_t *aux = aux_all + ((size_t)b * kTilesPerBlock + tile) * 4;
+    const int R = aux[1], off = aux[2];
+    const int next_fs = tile + 1 < ntile ? aux[4] : n;
+    int first, last;
+    const uint32_t mask = rle_tile_starts(B.src, ts, te, s, first, last);
+    tfirst[threadIdx.x] = first < kRleTile ? ts + first : INT_MAX;
+    const int carry = block_excl_max(last >= 0 ? ts + last : -1, sh);  // also orders tfirst
+    const int a = 16 * threadIdx.x;
+    int rs = max(carry, R), cnt = 0;
+    uint8_t w[16];
+#pragma unroll
+    for (int q = 0; q < 16; q++) {
+        if (mask & (1u << q)) rs = ts + a + q;
+        w[q] = (a + q < len) ? (uint8_t)rle_w(ts + a + q - rs) : 0;
+        cnt += w[q];
+    }
+    int total;
+    int o = block_excl_sum<int>(cnt, sh, &total);
+    rs = max(carry, R);
+    for (int q = 0; q < 16; q++) {
+        if (mask & (1u << q)) rs = ts + a + q;
+        if (!w[q]) continue;
+        const uint8_t v = s[a + q];
+        ob[o++] = v;
+        if (w[q] == 2) {
+            const int i = ts + a + q, cap = i - 3 + 255;
+            int end;
+            const uint32_t later = q < 15 ? (mask >> (q + 1)) : 0u;
+            if (later) {
+                end = i + 1 + __ffs(later) - 1;
+            } else {
+                end = next_fs;
+                for (int tt = threadIdx.x + 1; tt < kRleThreads && ts + 16 * tt < cap; tt++)
+                    if (tfirst[tt] != INT_MAX) { end = tfirst[tt]; break; }
+            }
+            ob[o++] = (uint8_t)(min(end, cap) - (i - 3) - 4);
+        }
+    }
+    __syncthreads();
+    uint8_t *out = rle_all + (size_t)b * kBlockCap + off;
+    for (int k = threadIdx.x; k < total; k += kRleThreads) out[k] = ob[k];
 }
 
 cudaError_t launch_rle1(lfc_plan P, int nblocks, const BlockDesc *d_blocks) {
     Workspace &ws = P->ws;
-    rle1_kernel<<<nblocks, 1024, 0, P->stream>>>(d_blocks, ws.bstate, ws.rle, ws.sa2);
-    count_launches(P, 1);
+    const dim3 grid(kRleMaxTiles, nblocks);
+    rle1_tile_kernel<<<grid, kRleThreads, 0, P->stream>>>(d_blocks, ws.tileaux);
+    rle1_scan_kernel<<<nblocks, 32, 0, P->stream>>>(d_blocks, ws.bstate, ws.tileaux);
+    rle1_write_kernel<<<grid, kRleThreads, 0, P->stream>>>(d_blocks, ws.tileaux, ws.rle);
+    count_launches(P, 3);
     return cudaGetLastError();
 }
 

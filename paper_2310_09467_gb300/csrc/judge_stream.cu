@@ -198,18 +198,20 @@ __device__ __forceinline__ int find_frame_s(const JudgeFrame *fr, int n, int64_t
     return lo;
 }
 
-__device__ __forceinline__ void chain_byte(uint32_t b, uint32_t &prev, uint32_t *tblt, uint32_t *hot, uint32_t *ghist,
-                                           uint8_t *first, uint32_t &c0) {
+// tbl is indexed as word (b / 2) * T + t: callers pass the thread's column t.
+__device__ __forceinline__ void chain_byte(uint32_t b, uint32_t &prev, uint32_t *tbl, int t, uint32_t *hot,
+                                           uint32_t *ghist, uint8_t *first, uint32_t &c0) {
     const uint32_t a = prev;
     prev = b;
-    uint32_t *wp = tblt + (b >> 1) * kChainThreads;
-    const uint32_t word = *wp;
+    const uint32_t wi = (b >> 1) * kChainThreads + (uint32_t)t;
+    const uint32_t word = tbl[wi];
     const uint32_t sh = (b & 1u) << 4;
     const uint32_t pend = (word >> sh) & 0xFFFFu;
     if (pend != kNoPred) {
-        if ((pend | a) == 0) {
+        const uint32_t both = pend | a;
+        if (both == 0) {
             c0++;
-        } else if ((pend | a) < (uint32_t)kHot) {
+        } else if (both < (uint32_t)kHot) {
             atomicAdd(&hot[pend * kHot + a], 1u);
         } else {
             atomicAdd(&ghist[(pend << 8) | a], 1u);
@@ -217,7 +219,13 @@ __device__ __forceinline__ void chain_byte(uint32_t b, uint32_t &prev, uint32_t 
     } else {
         first[b] = (uint8_t)a;
     }
-    *wp = (word & ~(0xFFFFu << sh)) | (a << sh);
+    tbl[wi] = (word & ~(0xFFFFu << sh)) | (a << sh);
+}
+
+__device__ __forceinline__ void chain_word(uint32_t w, uint32_t &prev, uint32_t *tbl, int t, uint32_t *hot,
+                                           uint32_t *ghist, uint8_t *first, uint32_t &c0) {
+#pragma unroll
+    for (int q = 0; q < 4; q++) chain_byte((w >> (8 * q)) & 0xFFu, prev, tbl, t, hot, ghist, first, c0);
 }
 
 __global__ void __launch_bounds__(kChainThreads)
@@ -241,20 +249,26 @@ chain_hist_kernel(const JudgeFrame *__restrict__ frames, int nframes, const uint
     const int len = (int)(min(n, ra64 + range_bytes) - ra64);
     const uint8_t *R = S + ra64;
     uint8_t *first = first_all + ((size_t)blockIdx.x * kChainThreads + t) * 256;
-    uint32_t *tblt = tbl + t;
     for (int i = t; i < kHot * kHot; i += kChainThreads) hot[i] = 0;
-    for (int k = 0; k < 128; k++) tblt[k * kChainThreads] = 0xFFFFFFFFu;
+    for (int k = 0; k < 128; k++) tbl[k * kChainThreads + t] = 0xFFFFFFFFu;
     __syncthreads();
     uint32_t prev = len > 0 ? (uint32_t)S[ra64 == 0 ? n - 1 : ra64 - 1] : 0u;
     uint32_t c0 = 0;
     const int full = len & ~15;
+    const uint4 *R4 = reinterpret_cast<const uint4 *>(R);
+    // two 16-byte loads in flight ahead of the bytes being walked
+    uint4 v0 = full > 0 ? __ldg(R4) : make_uint4(0, 0, 0, 0);
+    uint4 v1 = full > 16 ? __ldg(R4 + 1) : make_uint4(0, 0, 0, 0);
     for (int i0 = 0; i0 < full; i0 += 16) {
-        const uint4 v = __ldg(reinterpret_cast<const uint4 *>(R + i0));
-        const uint32_t wv[4] = {v.x, v.y, v.z, v.w};
-#pragma unroll
-        for (int k = 0; k < 16; k++) chain_byte((wv[k >> 2] >> (8 * (k & 3))) & 0xFFu, prev, tblt, hot, ghist, first, c0);
+        const uint4 v2 = (i0 + 32 < full) ? __ldg(R4 + (i0 >> 4) + 2) : make_uint4(0, 0, 0, 0);
+        chain_word(v0.x, prev, tbl, t, hot, ghist, first, c0);
+        chain_word(v0.y, prev, tbl, t, hot, ghist, first, c0);
+        chain_word(v0.z, prev, tbl, t, hot, ghist, first, c0);
+        chain_word(v0.w, prev, tbl, t, hot, ghist, first, c0);
+        v0 = v1;
+        v1 = v2;
     }
-    for (int i = full; i < len; i++) chain_byte(R[i], prev, tblt, hot, ghist, first, c0);
+    for (int i = full; i < len; i++) chain_byte(R[i], prev, tbl, t, hot, ghist, first, c0);
     if (c0) atomicAdd(&hot[0], c0);
     __syncthreads();
     for (int i = t; i < kHot * kHot; i += kChainThreads) {
