@@ -14,7 +14,7 @@ import os
 
 SPACE = {
     "emit_tile_lenslets": (4, 8, 16),
-    "chain_range_bytes": (2048, 4096, 8192),
+    "chain_range_bytes": (8192, 16384, 32768),
 }
 
 

@@ -160,8 +160,8 @@ extern "C" int lfc_plan_set_tuning(lfc_plan P, const lfc_tuning *t) {
         v.emit_tile_lenslets = t->emit_tile_lenslets;
     }
     if (t->chain_range_bytes) {
-        if (t->chain_range_bytes != 2048 && t->chain_range_bytes != 4096 && t->chain_range_bytes != 8192)
-            return fail(P, LFC_ERR_INVALID_ARG, "chain_range_bytes must be 2048, 4096 or 8192");
+        if (t->chain_range_bytes != 8192 && t->chain_range_bytes != 16384 && t->chain_range_bytes != 32768)
+            return fail(P, LFC_ERR_INVALID_ARG, "chain_range_bytes must be 8192, 16384 or 32768");
         v.chain_range_bytes = t->chain_range_bytes;
     }
     if (t->judge_frames_per_launch) {
@@ -224,7 +224,7 @@ extern "C" int lfc_plan_block_capacity(lfc_plan P) { return P ? P->block_cap : 0
 static void free_ws(Workspace &w) {
     void *ptrs[] = {w.hist, w.summ, w.scores, w.choice, w.jframes, w.cand, w.l2tab, w.stream, w.blocks, w.bstate,
                     w.rle, w.sa, w.sa2, w.rank, w.act, w.act2, w.val, w.val2, w.tilecnt, w.tileaux, w.bwt,
-                    w.mtfidx, w.mtflists, w.mtfrec, w.mtfreclen, w.sym, w.freq, w.sel, w.lens, w.codes, w.packed, w.cstream, w.chain_first, w.masks, w.class_ids,
+                    w.mtfidx, w.mtflists, w.mtfrec, w.mtfreclen, w.sym, w.freq, w.sel, w.lens, w.codes, w.packed, w.cstream, w.masks, w.class_ids,
                     w.act_total, w.block_dst, w.frame_crc, w.crc_part, w.chunk_desc, w.dec_tt};
     for (void *p : ptrs)
         if (p) cudaFree(p);
@@ -279,7 +279,7 @@ extern "C" int lfc_plan_create(const lfc_config *cfg, void *cuda_stream, lfc_pla
     P->judge_frames_cap = std::min(F, kJudgeFramesCap);
     P->block_cap = (int)std::max<int64_t>(bpf, std::min<int64_t>((int64_t)F * bpf, 192));
     const int JF = P->judge_frames_cap, BC = P->block_cap;
-    const int64_t seg_min = (int64_t)chain_threads() * 2048;  // smallest tunable segment
+    const int64_t seg_min = chain_seg_bytes(8192);  // smallest tunable segment
     const int64_t segs_max = (n_max + seg_min - 1) / seg_min;
     ws.summ_cap = (int64_t)JF * kMaxCand * segs_max;
     ws.cstream_kmax = K;
@@ -300,7 +300,6 @@ extern "C" int lfc_plan_create(const lfc_config *cfg, void *cuda_stream, lfc_pla
     AL(l2tab, (size_t)kHistBins);
     AL(stream, (size_t)F * ws.stream_slot);
     AL(cstream, (size_t)JF * K * ws.cstream_slot);
-    AL(chain_first, (size_t)ws.summ_cap * chain_first_bytes_per_cta());
     AL(masks, (size_t)F * 4);
     AL(class_ids, (size_t)64);
     AL(blocks, (size_t)BC);
@@ -415,7 +414,7 @@ bool capturing(lfc_plan P) {
 int build_judge(lfc_plan P, const lfc_frame *frames, int n, Arena &A, std::vector<JudgeChunk> &out) {
     Workspace &ws = P->ws;
     const int range = P->tune.chain_range_bytes;
-    const int64_t seg_bytes = (int64_t)chain_threads() * range;
+    const int64_t seg_bytes = chain_seg_bytes(range);
     const int per_launch = P->tune.judge_frames_per_launch > 0 ? P->tune.judge_frames_per_launch : P->judge_frames_cap;
     for (int f0 = 0; f0 < n; f0 += per_launch) {
         const int f1 = std::min(n, f0 + per_launch);

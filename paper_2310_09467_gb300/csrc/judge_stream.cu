@@ -11,8 +11,8 @@
 //    for every candidate of the kind and stored in the candidate's ordering
 //    (raw order: 480-byte row runs; view-major order: 32-byte runs).
 // 2. chain_hist_kernel: one CTA per segment of a candidate stream, one
-//    thread per range (2-8 KB, tuned) walking it byte by byte (see below); the
-//    ranges are stitched per CTA and the CTAs by the fixup kernel.
+//    warp per range (8-32 KB, tuned) walking it 32 bytes a step (see below);
+//    the ranges are stitched per CTA and the CTAs by the fixup kernel.
 #include "lfc_common.cuh"
 
 namespace lfc {
@@ -172,22 +172,33 @@ __global__ void __launch_bounds__(kEmitThreads) emit_all_kernel(const JudgeFrame
 }
 
 // ------------------------------------------------------ pair-chain histogram
-// One thread walks a contiguous byte range of a candidate stream in one
-// pass. Its pending table (predecessor of the last occurrence of each byte
-// value, 0xFFFF before the first) holds 16-bit entries in shared memory, entry
-// b of thread t in half (b % 2) of word (b / 2) * T + t, so each lane always
-// hits its own bank. The first occurrence of every value in the range goes
-// to a global scratch table, so the CTA can stitch the ranges in order
-// afterwards. Pairs (x, y) with x, y < 64 (the hot corner for small residuals)
-// are counted in shared memory, the very common pair (0, 0) in a register,
-// all others with fire-and-forget atomics into the L2-resident histogram.
-constexpr int kChainThreads = 384;
-constexpr int kHot = 64;                                            // hot corner side
-constexpr uint16_t kNoPred = 0xFFFF;
+// The judge-BWT's last column lists, bucket by bucket (first byte b), the
+// predecessors of b's occurrences in stream order, so its bigram histogram
+// counts the pairs (pred of one occurrence of b, pred of the next one), plus
+// the pairs across bucket boundaries (fixup kernel).
+//
+// One warp walks a contiguous range of a candidate stream 32 bytes per step,
+// lane j on position 32 q + j. __match_any_sync groups the lanes holding the
+// same byte value; a lane's pending predecessor is that of the previous lane
+// of its group, or, for the group's first lane, the warp's table entry
+// (predecessor of the last occurrence so far, 0xFFFF before the first), which
+// the group's last lane then overwrites. The first occurrence of every value
+// in the range keeps its predecessor, so the CTA stitches its warps' ranges
+// in order afterwards. Pairs (x, y) with x, y < kHot are counted in shared
+// memory, the pair (0, 0) by a warp ballot into a register, all others with
+// fire-and-forget atomics into the L2-resident histogram. Bytes come in as
+// 512-byte chunks (one 16-byte load per lane, the next chunk in flight)
+// through a per-warp staging buffer.
+constexpr int kChainWarps = 16;
+constexpr int kChainThreads = kChainWarps * 32;
+constexpr int kChainChunk = 512;
+constexpr int kHot = 128;                                            // hot corner side
+constexpr uint32_t kNoPred = 0xFFFF;
 
-size_t chain_smem_bytes() { return (size_t)kHot * kHot * 4 + (size_t)128 * kChainThreads * 4; }
-int chain_threads() { return kChainThreads; }
-int64_t chain_first_bytes_per_cta() { return (int64_t)kChainThreads * 256; }
+size_t chain_smem_bytes() {
+    return (size_t)kHot * kHot * 4 + (size_t)kChainWarps * (256 * 2 + 256 + kChainChunk);
+}
+int64_t chain_seg_bytes(int range_bytes) { return (int64_t)kChainWarps * range_bytes; }
 
 __device__ __forceinline__ int find_frame_s(const JudgeFrame *fr, int n, int64_t cta) {
     int lo = 0, hi = n - 1;
@@ -198,99 +209,103 @@ __device__ __forceinline__ int find_frame_s(const JudgeFrame *fr, int n, int64_t
     return lo;
 }
 
-// tbl is indexed as word (b / 2) * T + t: callers pass the thread's column t.
-__device__ __forceinline__ void chain_byte(uint32_t b, uint32_t &prev, uint32_t *tbl, int t, uint32_t *hot,
-                                           uint32_t *ghist, uint8_t *first, uint32_t &c0) {
-    const uint32_t a = prev;
-    prev = b;
-    const uint32_t wi = (b >> 1) * kChainThreads + (uint32_t)t;
-    const uint32_t word = tbl[wi];
-    const uint32_t sh = (b & 1u) << 4;
-    const uint32_t pend = (word >> sh) & 0xFFFFu;
-    if (pend != kNoPred) {
-        const uint32_t both = pend | a;
-        if (both == 0) {
-            c0++;
-        } else if (both < (uint32_t)kHot) {
-            atomicAdd(&hot[pend * kHot + a], 1u);
-        } else {
-            atomicAdd(&ghist[(pend << 8) | a], 1u);
-        }
-    } else {
-        first[b] = (uint8_t)a;
+// One 32-byte step; FULL: all 32 positions exist.
+template <bool FULL>
+__device__ __forceinline__ void chain_step(const uint8_t *stage, int pos, int lim, uint32_t &carry, uint16_t *pend,
+                                           uint8_t *first, uint32_t *hot, uint32_t *ghist, uint32_t &c0,
+                                           uint32_t lt, uint32_t gt) {
+    const int lane = threadIdx.x & 31;
+    const bool valid = FULL || pos < lim;
+    const uint32_t b = valid ? stage[pos] : 0u;
+    uint32_t a = __shfl_up_sync(LFC_FULL, b, 1);
+    if (lane == 0) a = carry;
+    carry = __shfl_sync(LFC_FULL, b, 31);
+    const uint32_t grp = __match_any_sync(LFC_FULL, valid ? b : 256u + lane);
+    const uint32_t lower = grp & lt;
+    uint32_t p = __shfl_sync(LFC_FULL, a, lower ? 31 - __clz(lower) : lane);
+    if (valid && !lower) p = pend[b];
+    __syncwarp();
+    if (valid && !(grp & gt)) pend[b] = (uint16_t)a;
+    const bool pair = valid && p != kNoPred;
+    if (valid && !pair) first[b] = (uint8_t)a;
+    const uint32_t both = p | a;
+    const uint32_t zb = __ballot_sync(LFC_FULL, pair && both == 0);
+    c0 += __popc(zb);
+    if (pair && both != 0) {
+        if (both < (uint32_t)kHot) atomicAdd(&hot[p * kHot + a], 1u);
+        else atomicAdd(&ghist[(p << 8) | a], 1u);
     }
-    tbl[wi] = (word & ~(0xFFFFu << sh)) | (a << sh);
-}
-
-__device__ __forceinline__ void chain_word(uint32_t w, uint32_t &prev, uint32_t *tbl, int t, uint32_t *hot,
-                                           uint32_t *ghist, uint8_t *first, uint32_t &c0) {
-#pragma unroll
-    for (int q = 0; q < 4; q++) chain_byte((w >> (8 * q)) & 0xFFu, prev, tbl, t, hot, ghist, first, c0);
+    __syncwarp();
 }
 
 __global__ void __launch_bounds__(kChainThreads)
 chain_hist_kernel(const JudgeFrame *__restrict__ frames, int nframes, const uint8_t *__restrict__ cand,
                   const uint8_t *__restrict__ cstream, int64_t cslot, int kmax, uint32_t *__restrict__ hist,
-                  uint16_t *__restrict__ summ, uint8_t *__restrict__ first_all, int range_bytes) {
+                  uint16_t *__restrict__ summ, int range_bytes) {
     extern __shared__ __align__(16) uint8_t smem[];
-    uint32_t *hot = reinterpret_cast<uint32_t *>(smem);   // [kHot][kHot]
-    uint32_t *tbl = hot + kHot * kHot;                    // [128][T]
+    uint32_t *hot = reinterpret_cast<uint32_t *>(smem);                      // [kHot][kHot]
+    uint16_t *pend_all = reinterpret_cast<uint16_t *>(hot + kHot * kHot);    // [warps][256]
+    uint8_t *first_all = reinterpret_cast<uint8_t *>(pend_all + kChainWarps * 256);  // [warps][256]
+    uint8_t *stage_all = first_all + kChainWarps * 256;                       // [warps][512]
     const int fi = find_frame_s(frames, nframes, blockIdx.x);
     const JudgeFrame &J = frames[fi];
     const int64_t local = (int64_t)blockIdx.x - J.cta_base;
     const int ci = (int)(local / J.segs), seg = (int)(local % J.segs);
+    if (!cand_on(J, cand[J.cand_off + ci])) return;  // not proposed: no stream, no histogram
     const uint8_t *S = cstream + ((size_t)fi * kmax + ci) * (size_t)cslot;
     uint32_t *ghist = hist + (size_t)(J.hist_off + ci) * kHistBins;
     const int64_t n = 2LL * J.F.W * J.F.H;
-    const int t = threadIdx.x;
-    if (!cand_on(J, cand[J.cand_off + ci])) return;  // not proposed: no stream, no histogram
-    const int64_t seg_bytes = (int64_t)kChainThreads * range_bytes;
-    const int64_t ra64 = min(n, (int64_t)seg * seg_bytes + (int64_t)t * range_bytes);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t ra64 = min(n, ((int64_t)seg * kChainWarps + warp) * range_bytes);
     const int len = (int)(min(n, ra64 + range_bytes) - ra64);
-    const uint8_t *R = S + ra64;
-    uint8_t *first = first_all + ((size_t)blockIdx.x * kChainThreads + t) * 256;
-    for (int i = t; i < kHot * kHot; i += kChainThreads) hot[i] = 0;
-    for (int k = 0; k < 128; k++) tbl[k * kChainThreads + t] = 0xFFFFFFFFu;
+    uint16_t *pend = pend_all + warp * 256;
+    uint8_t *first = first_all + warp * 256;
+    uint8_t *stage = stage_all + warp * kChainChunk;
+    for (int i = threadIdx.x; i < kHot * kHot; i += kChainThreads) hot[i] = 0;
+    for (int k = lane; k < 256; k += 32) pend[k] = (uint16_t)kNoPred;
     __syncthreads();
-    uint32_t prev = len > 0 ? (uint32_t)S[ra64 == 0 ? n - 1 : ra64 - 1] : 0u;
+    uint32_t carry = len > 0 ? (uint32_t)S[ra64 == 0 ? n - 1 : ra64 - 1] : 0u;
     uint32_t c0 = 0;
-    const int full = len & ~15;
-    const uint4 *R4 = reinterpret_cast<const uint4 *>(R);
-    // two 16-byte loads in flight ahead of the bytes being walked
-    uint4 v0 = full > 0 ? __ldg(R4) : make_uint4(0, 0, 0, 0);
-    uint4 v1 = full > 16 ? __ldg(R4 + 1) : make_uint4(0, 0, 0, 0);
-    for (int i0 = 0; i0 < full; i0 += 16) {
-        const uint4 v2 = (i0 + 32 < full) ? __ldg(R4 + (i0 >> 4) + 2) : make_uint4(0, 0, 0, 0);
-        chain_word(v0.x, prev, tbl, t, hot, ghist, first, c0);
-        chain_word(v0.y, prev, tbl, t, hot, ghist, first, c0);
-        chain_word(v0.z, prev, tbl, t, hot, ghist, first, c0);
-        chain_word(v0.w, prev, tbl, t, hot, ghist, first, c0);
-        v0 = v1;
-        v1 = v2;
+    const uint32_t lt = lanemask_lt(), gt = lanemask_gt();
+    const uint8_t *R = S + ra64;
+    const int full = len / kChainChunk;
+    uint4 nxt = full > 0 ? __ldg(reinterpret_cast<const uint4 *>(R) + lane) : make_uint4(0, 0, 0, 0);
+    for (int c = 0; c < full; c++) {
+        reinterpret_cast<uint4 *>(stage)[lane] = nxt;
+        if (c + 1 < full) nxt = __ldg(reinterpret_cast<const uint4 *>(R + (size_t)(c + 1) * kChainChunk) + lane);
+        __syncwarp();
+#pragma unroll 1
+        for (int q = 0; q < kChainChunk / 32; q++)
+            chain_step<true>(stage, q * 32 + lane, kChainChunk, carry, pend, first, hot, ghist, c0, lt, gt);
     }
-    for (int i = full; i < len; i++) chain_byte(R[i], prev, tbl, t, hot, ghist, first, c0);
-    if (c0) atomicAdd(&hot[0], c0);
+    const int rem = len - full * kChainChunk;
+    if (rem > 0) {
+        for (int k = lane; k < rem; k += 32) stage[k] = R[(size_t)full * kChainChunk + k];
+        __syncwarp();
+        for (int q = 0; q * 32 < rem; q++)
+            chain_step<false>(stage, q * 32 + lane, rem, carry, pend, first, hot, ghist, c0, lt, gt);
+    }
+    if (lane == 0 && c0) atomicAdd(&hot[0], c0);
     __syncthreads();
-    for (int i = t; i < kHot * kHot; i += kChainThreads) {
+    for (int i = threadIdx.x; i < kHot * kHot; i += kChainThreads) {
         const uint32_t c = hot[i];
         if (c) atomicAdd(&ghist[((uint32_t)(i / kHot) << 8) | (uint32_t)(i % kHot)], c);
     }
-    // stitch the threads' ranges in order (thread b handles byte value b)
-    if (t < 256) {
-        const int bv = t;
-        const uint8_t *first_cta = first_all + (size_t)blockIdx.x * kChainThreads * 256;
-        uint16_t f0 = kNoPred, cur = kNoPred;
-        for (int tt = 0; tt < kChainThreads; tt++) {
-            const uint16_t last = (uint16_t)((tbl[(bv >> 1) * kChainThreads + tt] >> ((bv & 1) * 16)) & 0xFFFFu);
+    // stitch the warps' ranges in order (thread b handles byte value b)
+    if (threadIdx.x < 256) {
+        const int bv = threadIdx.x;
+        uint32_t f0 = kNoPred, cur = kNoPred;
+        for (int w = 0; w < kChainWarps; w++) {
+            const uint32_t last = pend_all[w * 256 + bv];
             if (last == kNoPred) continue;
-            const uint16_t f = first_cta[(size_t)tt * 256 + bv];
-            if (cur != kNoPred) atomicAdd(&ghist[((uint32_t)cur << 8) | f], 1u);
+            const uint32_t f = first_all[w * 256 + bv];
+            if (cur != kNoPred) atomicAdd(&ghist[(cur << 8) | f], 1u);
             else f0 = f;
             cur = last;
         }
         uint16_t *out = summ + (size_t)(J.summ_off + (int64_t)ci * J.segs + seg) * 512;
-        out[bv] = f0;
-        out[256 + bv] = cur;
+        out[bv] = (uint16_t)f0;
+        out[256 + bv] = (uint16_t)cur;
     }
 }
 
@@ -313,7 +328,7 @@ cudaError_t launch_chain_hist(lfc_plan P, const JudgeFrame *d_frames, int nframe
     if (e != cudaSuccess) return e;
     chain_hist_kernel<<<(unsigned)total_ctas, kChainThreads, smem, P->stream>>>(
         d_frames, nframes, d_cand, P->ws.cstream, P->ws.cstream_slot, P->ws.cstream_kmax, P->ws.hist, P->ws.summ,
-        P->ws.chain_first, range_bytes);
+        range_bytes);
     count_launches(P, 1);
     return cudaGetLastError();
 }

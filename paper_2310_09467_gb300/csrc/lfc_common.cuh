@@ -163,7 +163,6 @@ struct Workspace {
     uint64_t *l2tab = nullptr;     // 65536
     int64_t summ_cap = 0;
     uint8_t *cstream = nullptr;    // candidate streams: judge_frames_cap * cstream_kmax slots
-    uint8_t *chain_first = nullptr;// first-occurrence predecessors, per chain CTA x thread x 256
     uint64_t *masks = nullptr;     // proposal candidate masks, max_frames x 4
     uint8_t *class_ids = nullptr;  // proposal class -> candidate id (64)
     int64_t cstream_slot = 0;
@@ -221,7 +220,7 @@ struct lfc_plan_s {
     std::vector<uint8_t> ids_spatial;   // judged for every frame
     std::vector<uint8_t> ids_temporal;  // judged for frames with prev
     int judge_frames_cap = 0;           // frames per judge launch (allocated)
-    lfc_tuning tune{16, 2048, 0, 0};    // autotuned judge knobs
+    lfc_tuning tune{16, 16384, 0, 0};    // autotuned judge knobs
     lfc_cnn cnn = nullptr;              // learned proposal (optional)
     int topk = 0;
     float tau = 0.f;
@@ -260,8 +259,7 @@ size_t judge_smem_bytes(int maxW);
 // judge_stream.cu
 size_t emit_all_smem_bytes(int p, int ts, int nslots);
 size_t chain_smem_bytes();
-int chain_threads();
-int64_t chain_first_bytes_per_cta();
+int64_t chain_seg_bytes(int range_bytes);  // stream bytes one chain CTA covers
 cudaError_t launch_emit_all(lfc_plan P, const JudgeFrame *d_frames, int nframes, const uint8_t *d_cand, int max_tiles,
                             int TS, int nslots_max, int any_temporal, int max_p);
 cudaError_t launch_chain_hist(lfc_plan P, const JudgeFrame *d_frames, int nframes, const uint8_t *d_cand, int64_t total_ctas,

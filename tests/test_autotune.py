@@ -14,8 +14,8 @@ def test_batch_key_and_cache_round_trip(tmp_path):
     assert k1 == k2 == "1300x1300p13*1,2040x2040p15*2|K26|T0"
     path = str(tmp_path / "t.json")
     assert autotune.load_cache(path) == {}
-    autotune.save_cache({k1: {"emit_tile_lenslets": 8, "chain_range_bytes": 4096, "judge_frames_per_launch": 2}}, path)
-    assert autotune.load_cache(path)[k1]["chain_range_bytes"] == 4096
+    autotune.save_cache({k1: {"emit_tile_lenslets": 8, "chain_range_bytes": 16384, "judge_frames_per_launch": 2}}, path)
+    assert autotune.load_cache(path)[k1]["chain_range_bytes"] == 16384
     open(path, "w").write("not json")
     assert autotune.load_cache(path) == {}
     c = list(autotune.candidates(8))
