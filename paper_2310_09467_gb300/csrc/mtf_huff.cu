@@ -127,36 +127,41 @@ __global__ void __launch_bounds__(32) mtf_encode_kernel(const BlockState *__rest
     for (int q = 0; q < 8; q++) v |= (uint64_t)lst[lane * 8 + q] << (8 * q);
     const uint8_t *L = L_all + (size_t)b * kBlockCap;
     uint8_t *out = idx_all + (size_t)b * kBlockCap;
+    __shared__ uint8_t idxbuf[32];
+    uint32_t front = (uint32_t)v & 0xFFu;
     for (int w0 = s0; w0 < s1; w0 += 32) {
         const int i = w0 + lane;
         const int cnt = min(32, s1 - w0);
         const uint32_t mys = i < s1 ? seq[L[i]] : 0u;
-        uint32_t myidx = 0;
-        for (int k = 0; k < cnt; k++) {
+        // a byte equal to its predecessor has index 0 and leaves the list as is
+        uint32_t prv = __shfl_up_sync(LFC_FULL, mys, 1);
+        if (lane == 0) prv = front;
+        const uint32_t live = cnt == 32 ? LFC_FULL : ((1u << cnt) - 1u);
+        const uint32_t rep = __ballot_sync(LFC_FULL, mys == prv) & live;
+        uint32_t todo = live & ~rep;
+        while (todo) {
+            const int k = __ffs(todo) - 1;
+            todo &= todo - 1u;
             const uint32_t s = __shfl_sync(LFC_FULL, mys, k);
-            const uint32_t front = __shfl_sync(LFC_FULL, (uint32_t)v & 0xFFu, 0);
-            if (front == s) {               // index 0: list unchanged
-                if (lane == k) myidx = 0;
-                continue;
-            }
-            const uint32_t pat = s * 0x01010101u;
-            const uint32_t eql = __vcmpeq4((uint32_t)v, pat), eqh = __vcmpeq4((uint32_t)(v >> 32), pat);
-            const uint32_t bal = __ballot_sync(LFC_FULL, (eql | eqh) != 0);
-            const int owner = __ffs(bal) - 1;
-            int byte = eql ? (__ffs(eql) - 1) >> 3 : 4 + ((__ffs(eqh) - 1) >> 3);
-            byte = __shfl_sync(LFC_FULL, byte, owner);
-            const uint64_t carry_up = __shfl_up_sync(LFC_FULL, v >> 56, 1);
-            const uint64_t carry = lane == 0 ? (uint64_t)s : carry_up;
-            const uint64_t shifted = (v << 8) | carry;
+            // the list holds every symbol once: exactly one lane has a zero byte
+            const uint64_t x = v ^ ((uint64_t)s * 0x0101010101010101ull);
+            const uint64_t z = (x - 0x0101010101010101ull) & ~x & 0x8080808080808080ull;
+            const int owner = __ffs(__ballot_sync(LFC_FULL, z != 0)) - 1;
+            const uint32_t up = __shfl_up_sync(LFC_FULL, (uint32_t)(v >> 56), 1);
+            const uint64_t shifted = (v << 8) | (lane == 0 ? (uint64_t)s : (uint64_t)up);
             if (lane < owner) {
                 v = shifted;
             } else if (lane == owner) {
+                const int byte = (__ffsll((long long)z) - 1) >> 3;  // lowest flag is the true zero
                 const uint64_t mask = byte == 7 ? ~0ull : ((1ull << (8 * (byte + 1))) - 1ull);
                 v = (shifted & mask) | (v & ~mask);
+                idxbuf[k] = (uint8_t)(owner * 8 + byte);
             }
-            if (lane == k) myidx = (uint32_t)(owner * 8 + byte);
         }
-        if (i < s1) out[i] = (uint8_t)myidx;
+        front = __shfl_sync(LFC_FULL, mys, cnt - 1);
+        __syncwarp();
+        if (i < s1) out[i] = ((rep >> lane) & 1u) ? (uint8_t)0 : idxbuf[lane];
+        __syncwarp();
     }
 }
 
