@@ -4,16 +4,18 @@
 //
 // BWT = sort of all cyclic rotations, ties between identical rotations by
 // start index. Two phases over all blocks of a pass at once, one CTA per
-// (4096-element tile, block), block-major so a block's bytes and suffix
-// array stay in L2 while its tiles run:
-//  1. LSD radix sort of the start positions by their first 8 bytes: 8 stable
-//     passes, 8-bit digits gathered from the block (no keys are stored).
+// (4096-element tile, block), block-major so a block's data stays in L2
+// while its tiles run. Every element carries its sort key: a radix pass
+// reads (key, element) pairs coalesced, ranks each tile by digit in shared
+// memory and writes each digit's run of the tile contiguously.
+//  1. Keys = the first 8 bytes of each rotation (big-endian), built from
+//     sequential reads; 8 stable LSD passes of 8-bit digits.
 //  2. Prefix doubling on the groups still tied: rank[i] = head position of
-//     i's group in the suffix array; each round sorts the tied elements by
-//     (rank[i], rank[i + h]) with 5 stable 8-bit LSD passes over the 40-bit
-//     key (m < 2^20), splits groups, and doubles h. Groups left when h >= m
-//     hold identical rotations, already in start-index order (every pass is
-//     stable and the first starts from the identity).
+//     i's group in the suffix array; each round keys the tied elements by
+//     (rank[i] << 20 | rank[i + h]) (m < 2^20), sorts them with 5 stable LSD
+//     passes, splits groups, and doubles h. Groups left when h >= m hold
+//     identical rotations, already in start-index order (every pass is stable
+//     and the first starts from the identity).
 #include <climits>
 
 #include "lfc_common.cuh"
@@ -223,63 +225,93 @@ cudaError_t launch_rle1(lfc_plan P, int nblocks, const BlockDesc *d_blocks) {
 }
 
 // ------------------------------------------------------------ sort keys
-// MODE 0: element = start position, digit = byte (7 - pass) of its 8-byte
-//         prefix. MODE 1: element = start position of a tied element, digit
-//         = byte `pass` of (rank[v] << 20 | rank[(v + h) mod m]).
-template <int MODE>
-__device__ __forceinline__ uint32_t sort_digit(int32_t v, int pass, const uint8_t *rle, const int32_t *rank, int m, int h) {
-    if (MODE == 0) {
-        int i = v + (7 - pass);
-        while (i >= m) i -= m;
-        return rle[i];
-    } else {
-        int j = v + h;
-        if (j >= m) j -= m;
-        const uint64_t key = ((uint64_t)(uint32_t)rank[v] << 20) | (uint32_t)rank[j];
-        return (uint32_t)(key >> (8 * pass)) & 255u;
-    }
-}
-
 template <int MODE>
 __device__ __forceinline__ int sort_count(const BlockState &s, int h) {
     if (MODE == 0) return s.m;
     return h < s.m ? s.n_act : 0;
 }
 
-// Per-tile digit histogram, stored digit-major: cnt[b][digit][tile].
-// Round state in device memory: rs[0] tied elements after the round, rs[1]
-// their per-block maximum, rs[2] the shift h, rs[3] the round number.
 template <int MODE>
 __device__ __forceinline__ int round_h(const int32_t *rs) { return MODE == 0 ? 0 : rs[2]; }
 
+// Phase 1 keys: K[v] = bytes v .. v + 7 (cyclic) big-endian, element v.
+__global__ void __launch_bounds__(kSortThreads) key8_kernel(const BlockState *__restrict__ st,
+                                                            const uint8_t *__restrict__ rle_all,
+                                                            uint64_t *__restrict__ K_all, int32_t *__restrict__ V_all) {
+    __shared__ uint8_t sb[kTile + 8];
+    const int b = blockIdx.y, tile = blockIdx.x;
+    const int m = st[b].m;
+    const int t0 = tile * kTile;
+    if (t0 >= m) return;
+    const int cnt = min(kTile, m - t0);
+    const uint8_t *rle = rle_all + (size_t)b * kBlockCap;
+    for (int i = threadIdx.x; i < cnt + 7; i += kSortThreads) sb[i] = rle[(t0 + i) % m];
+    __syncthreads();
+    uint64_t *K = K_all + (size_t)b * kBlockCap;
+    int32_t *V = V_all + (size_t)b * kBlockCap;
+    for (int r = 0; r < kPerThread; r++) {
+        const int kl = r * kSortThreads + threadIdx.x;
+        if (kl >= cnt) break;
+        uint64_t key = 0;
+#pragma unroll
+        for (int q = 0; q < 8; q++) key = (key << 8) | sb[kl + q];
+        K[t0 + kl] = key;
+        V[t0 + kl] = t0 + kl;
+    }
+}
+
+// Round keys of the tied elements: rank[v] << 20 | rank[(v + h) mod m].
+__global__ void __launch_bounds__(kSortThreads) key40_kernel(const int32_t *__restrict__ rs, const BlockState *__restrict__ st,
+                                                             const int32_t *__restrict__ V_all, const int32_t *__restrict__ rank_all,
+                                                             uint64_t *__restrict__ K_all) {
+    const int b = blockIdx.y, tile = blockIdx.x;
+    const int h = rs[2];
+    const BlockState s = st[b];
+    const int n = sort_count<1>(s, h);
+    const size_t bo = (size_t)b * kBlockCap;
+    for (int r = 0; r < kPerThread; r++) {
+        const int k = tile * kTile + r * kSortThreads + threadIdx.x;
+        if (k >= n) break;
+        const int v = V_all[bo + k];
+        int j = v + h;
+        if (j >= s.m) j -= s.m;
+        K_all[bo + k] = ((uint64_t)(uint32_t)rank_all[bo + v] << 20) | (uint32_t)rank_all[bo + j];
+    }
+}
+
+// Per-tile digit histogram, stored digit-major: cnt[b][digit][tile]. A warp
+// whose 32 digits agree adds them with one atomic (long equal runs are the
+// norm in these streams).
+// Round state in device memory: rs[0] tied elements after the round, rs[1]
+// their per-block maximum, rs[2] the shift h, rs[3] the round number.
 template <int MODE>
 __global__ void __launch_bounds__(kSortThreads) radix_hist_kernel(int pass, const int32_t *__restrict__ rs, const BlockState *__restrict__ st,
-                                                                  const int32_t *__restrict__ in_all, const uint8_t *__restrict__ rle_all,
-                                                                  const int32_t *__restrict__ rank_all, uint32_t *__restrict__ cnt_all) {
-    __shared__ uint32_t hst[256];
+                                                                  const uint64_t *__restrict__ K_all, uint32_t *__restrict__ cnt_all) {
+    constexpr int NW = kSortThreads / 32;
+    __shared__ uint32_t hst[NW][256];
     const int b = blockIdx.y, tile = blockIdx.x;
     const int h = round_h<MODE>(rs);
-    const BlockState s = st[b];
-    const int n = sort_count<MODE>(s, h);
+    const int n = sort_count<MODE>(st[b], h);
     if (tile * kTile >= n) return;
-    hst[threadIdx.x] = 0;
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (int i = threadIdx.x; i < NW * 256; i += kSortThreads) (&hst[0][0])[i] = 0;
     __syncthreads();
-    const int32_t *in = in_all + (size_t)b * kBlockCap;
-    const uint8_t *rle = rle_all + (size_t)b * kBlockCap;
-    const int32_t *rank = rank_all + (size_t)b * kBlockCap;
-    for (int i = 0; i < kPerThread; i++) {
-        const int k = tile * kTile + i * kSortThreads + threadIdx.x;
-        const bool ok = k < n;
-        uint32_t d = 0;
-        if (ok) {
-            const int32_t v = (MODE == 0 && pass == 0) ? k : in[k];
-            d = sort_digit<MODE>(v, pass, rle, rank, s.m, h);
+    const uint64_t *K = K_all + (size_t)b * kBlockCap;
+    const int shift = 8 * pass;
+    for (int r = 0; r < kPerThread; r++) {
+        const int k = tile * kTile + w * 512 + r * 32 + lane;
+        const uint32_t d = k < n ? (uint32_t)(K[k] >> shift) & 255u : 0xFFFFFFFFu;
+        const uint32_t d0 = __shfl_sync(LFC_FULL, d, 0);
+        if (__all_sync(LFC_FULL, d == d0)) {
+            if (lane == 0 && d0 != 0xFFFFFFFFu) atomicAdd(&hst[w][d0], 32u);
+        } else if (d != 0xFFFFFFFFu) {
+            atomicAdd(&hst[w][d], 1u);
         }
-        const uint32_t mm = __match_any_sync(LFC_FULL, ok ? d : 256u + lane_id());
-        if (ok && (mm & lanemask_lt()) == 0) atomicAdd(&hst[d], (uint32_t)__popc(mm));
     }
     __syncthreads();
-    cnt_all[((size_t)b * 256 + threadIdx.x) * kTilesPerBlock + tile] = hst[threadIdx.x];
+    uint32_t c = 0;
+    for (int i = 0; i < NW; i++) c += hst[i][threadIdx.x];
+    cnt_all[((size_t)b * 256 + threadIdx.x) * kTilesPerBlock + tile] = c;
 }
 
 // Exclusive scan of a block's counts in (digit, tile) order, in place.
@@ -306,124 +338,120 @@ __global__ void __launch_bounds__(1024) radix_scan_kernel(const int32_t *__restr
     }
 }
 
-// Stable scatter: warp w owns elements [w*512, (w+1)*512) of the tile, taken
-// 32 at a time in order; equal digits are ranked with __match_any_sync and a
-// per-warp running count, then offset by earlier warps' counts.
+// Stable scatter of (key, element) pairs: warp w owns elements
+// [w*512, (w+1)*512) of the tile, taken 32 at a time in order; equal digits
+// are ranked with __match_any_sync and a per-warp running count. The tile is
+// placed in shared memory in digit order, then each digit's run is written
+// to its global offset with consecutive threads on consecutive addresses.
+constexpr size_t kScatterSmem = (size_t)kTile * 12 + (size_t)(kSortThreads / 32) * 256 * 4 + 2 * 256 * 4;
+
 template <int MODE>
 __global__ void __launch_bounds__(kSortThreads) radix_scatter_kernel(int pass, const int32_t *__restrict__ rs, const BlockState *__restrict__ st,
-                                                                     const int32_t *__restrict__ in_all, int32_t *__restrict__ out_all,
-                                                                     const uint8_t *__restrict__ rle_all, const int32_t *__restrict__ rank_all,
+                                                                     const uint64_t *__restrict__ Kin_all, const int32_t *__restrict__ Vin_all,
+                                                                     uint64_t *__restrict__ Kout_all, int32_t *__restrict__ Vout_all,
                                                                      const uint32_t *__restrict__ cnt_all) {
     constexpr int NW = kSortThreads / 32;
-    __shared__ uint32_t wcnt[NW][256];
-    __shared__ uint32_t base[256];
+    extern __shared__ __align__(16) uint8_t smem[];
+    uint64_t *sK = reinterpret_cast<uint64_t *>(smem);           // [kTile]
+    int32_t *sV = reinterpret_cast<int32_t *>(sK + kTile);        // [kTile]
+    uint32_t *wcnt = reinterpret_cast<uint32_t *>(sV + kTile);    // [NW][256]
+    uint32_t *loff = wcnt + NW * 256;                             // [256] tile-local start of a digit
+    uint32_t *gbase = loff + 256;                                 // [256] global start of the tile's run
+    __shared__ uint32_t sh[33];
     const int b = blockIdx.y, tile = blockIdx.x;
     const int h = round_h<MODE>(rs);
-    const BlockState s = st[b];
-    const int n = sort_count<MODE>(s, h);
+    const int n = sort_count<MODE>(st[b], h);
     if (tile * kTile >= n) return;
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    for (int i = threadIdx.x; i < NW * 256; i += kSortThreads) (&wcnt[0][0])[i] = 0;
-    base[threadIdx.x] = cnt_all[((size_t)b * 256 + threadIdx.x) * kTilesPerBlock + tile];
+    const int shift = 8 * pass;
+    for (int i = threadIdx.x; i < NW * 256; i += kSortThreads) wcnt[i] = 0;
+    gbase[threadIdx.x] = cnt_all[((size_t)b * 256 + threadIdx.x) * kTilesPerBlock + tile];
     __syncthreads();
-    const int32_t *in = in_all + (size_t)b * kBlockCap;
-    int32_t *out = out_all + (size_t)b * kBlockCap;
-    const uint8_t *rle = rle_all + (size_t)b * kBlockCap;
-    const int32_t *rank = rank_all + (size_t)b * kBlockCap;
+    const size_t bo = (size_t)b * kBlockCap;
+    const uint64_t *Kin = Kin_all + bo;
+    const int32_t *Vin = Vin_all + bo;
+    uint64_t keys[kPerThread];
     int32_t vals[kPerThread];
-    uint32_t digs[kPerThread], rnk[kPerThread];
+    uint32_t rnk[kPerThread];
+    const uint32_t lt = lanemask_lt(), gt = lanemask_gt();
 #pragma unroll
     for (int r = 0; r < kPerThread; r++) {
         const int k = tile * kTile + w * 512 + r * 32 + lane;
         const bool ok = k < n;
-        int32_t v = 0;
-        uint32_t d = 0;
-        if (ok) {
-            v = (MODE == 0 && pass == 0) ? k : in[k];
-            d = sort_digit<MODE>(v, pass, rle, rank, s.m, h);
-        }
+        keys[r] = ok ? Kin[k] : 0;
+        vals[r] = ok ? Vin[k] : 0;
+        const uint32_t d = (uint32_t)(keys[r] >> shift) & 255u;
         const uint32_t mm = __match_any_sync(LFC_FULL, ok ? d : 256u + lane);
         uint32_t before = 0;
-        if (ok) before = wcnt[w][d];
+        if (ok) before = wcnt[w * 256 + d];
         __syncwarp();
-        if (ok && (mm & lanemask_gt()) == 0) wcnt[w][d] = before + __popc(mm);
+        if (ok && (mm & gt) == 0) wcnt[w * 256 + d] = before + __popc(mm);
         __syncwarp();
-        vals[r] = v;
-        digs[r] = ok ? d : 0xFFFFFFFFu;
-        rnk[r] = before + __popc(mm & lanemask_lt());
+        rnk[r] = ok ? before + __popc(mm & lt) : 0xFFFFFFFFu;
     }
     __syncthreads();
-    {   // per digit: exclusive prefix over warps, plus the tile's global offset
+    {   // per digit: exclusive prefix over warps, then over digits
         const int d = threadIdx.x;
-        uint32_t acc = base[d];
+        uint32_t acc = 0;
         for (int ww = 0; ww < NW; ww++) {
-            const uint32_t c = wcnt[ww][d];
-            wcnt[ww][d] = acc;
+            const uint32_t c = wcnt[ww * 256 + d];
+            wcnt[ww * 256 + d] = acc;
             acc += c;
         }
+        loff[d] = block_excl_sum<uint32_t>(acc, sh, nullptr);
     }
     __syncthreads();
 #pragma unroll
-    for (int r = 0; r < kPerThread; r++)
-        if (digs[r] != 0xFFFFFFFFu) out[wcnt[w][digs[r]] + rnk[r]] = vals[r];
+    for (int r = 0; r < kPerThread; r++) {
+        if (rnk[r] == 0xFFFFFFFFu) continue;
+        const uint32_t d = (uint32_t)(keys[r] >> shift) & 255u;
+        const uint32_t pos = loff[d] + wcnt[w * 256 + d] + rnk[r];
+        sK[pos] = keys[r];
+        sV[pos] = vals[r];
+    }
+    __syncthreads();
+    const int cnt = min(kTile, n - tile * kTile);
+    uint64_t *Kout = Kout_all + bo;
+    int32_t *Vout = Vout_all + bo;
+    for (int j = threadIdx.x; j < cnt; j += kSortThreads) {
+        const uint64_t key = sK[j];
+        const uint32_t d = (uint32_t)(key >> shift) & 255u;
+        const uint32_t g = gbase[d] + ((uint32_t)j - loff[d]);
+        Kout[g] = key;
+        Vout[g] = sV[j];
+    }
 }
 
 // ---------------------------------------------------------- group heads
-__device__ __forceinline__ uint64_t key8(const uint8_t *rle, int m, int v) {
-    uint64_t k = 0;
-    int i = v;
-#pragma unroll
-    for (int q = 0; q < 8; q++) {
-        k = (k << 8) | rle[i];
-        if (++i == m) i = 0;
-    }
-    return k;
-}
-
-__device__ __forceinline__ uint64_t key40(const int32_t *rank, int m, int v, int h) {
-    int j = v + h;
-    if (j >= m) j -= m;
-    return ((uint64_t)(uint32_t)rank[v] << 20) | (uint32_t)rank[j];
-}
-
-// Head flags of elements [k, k + 16) of a thread, MODE 0 over the suffix
-// array (m elements), MODE 1 over the sorted tied elements (n_act).
-template <int MODE>
-__device__ __forceinline__ uint64_t elem_key(int k, const int32_t *sorted, const uint8_t *rle, const int32_t *rank, int m, int h) {
-    const int32_t v = sorted[k];
-    return MODE == 0 ? key8(rle, m, v) : key40(rank, m, v, h);
-}
-
+// Head flags come from neighbouring keys of the sorted (key, element) list:
+// the 8-byte prefixes after phase 1, the 40-bit round keys after a round.
 // Pass A: per tile, the largest head position and the number of elements
 // that stay tied. Head flags go to flags[] for pass B.
 template <int MODE>
 __global__ void __launch_bounds__(kSortThreads) heads_tile_kernel(const int32_t *__restrict__ rs, const BlockState *__restrict__ st,
-                                                                  const int32_t *__restrict__ sorted_all, const int32_t *__restrict__ actA,
+                                                                  const uint64_t *__restrict__ keys_all, const int32_t *__restrict__ actA,
                                                                   const int32_t *__restrict__ actB,
-                                                                  const uint8_t *__restrict__ rle_all, const int32_t *__restrict__ rank_all,
                                                                   uint8_t *__restrict__ flags_all, int32_t *__restrict__ aux_all) {
     const int b = blockIdx.y, tile = blockIdx.x;
     const int h = round_h<MODE>(rs);
     const BlockState s = st[b];
     const int n = sort_count<MODE>(s, h);
     if (tile * kTile >= n) return;
-    const int32_t *sorted = sorted_all + (size_t)b * kBlockCap;
+    const uint64_t *K = keys_all + (size_t)b * kBlockCap;
     const int32_t *act = ((MODE == 1 && (rs[3] & 1)) ? actB : actA) + (size_t)b * kBlockCap;
-    const uint8_t *rle = rle_all + (size_t)b * kBlockCap;
-    const int32_t *rank = rank_all + (size_t)b * kBlockCap;
     uint8_t *flags = flags_all + (size_t)b * kBlockCap;
     const int k0 = tile * kTile + threadIdx.x * kPerThread;
     int hmax = -1, tied = 0;
     if (k0 < n) {
         const int k1 = min(n, k0 + kPerThread);
-        uint64_t prevk = k0 > 0 ? elem_key<MODE>(k0 - 1, sorted, rle, rank, s.m, h) : 0;
-        uint64_t cur = elem_key<MODE>(k0, sorted, rle, rank, s.m, h);
+        uint64_t prevk = k0 > 0 ? K[k0 - 1] : 0;
+        uint64_t cur = K[k0];
         bool curhead = (k0 == 0) || cur != prevk;
         for (int k = k0; k < k1; k++) {
             bool nexthead = true;
             uint64_t nk = 0;
             if (k + 1 < n) {
-                nk = elem_key<MODE>(k + 1, sorted, rle, rank, s.m, h);
+                nk = K[k + 1];
                 nexthead = nk != cur;
             }
             flags[k] = (uint8_t)curhead;
@@ -577,12 +605,14 @@ __global__ void __launch_bounds__(kSortThreads) bwt_output_kernel(BlockState *__
 }
 
 template <int MODE>
-static void radix_pass(lfc_plan P, cudaStream_t st, int nblocks, int tiles, int pass, const int32_t *in, int32_t *out) {
+static void radix_pass(lfc_plan P, cudaStream_t st, int nblocks, int tiles, int pass, const uint64_t *kin, const int32_t *vin,
+                       uint64_t *kout, int32_t *vout) {
     Workspace &ws = P->ws;
     dim3 grid(tiles, nblocks);
-    radix_hist_kernel<MODE><<<grid, kSortThreads, 0, st>>>(pass, ws.act_total, ws.bstate, in, ws.rle, ws.rank, ws.tilecnt);
+    radix_hist_kernel<MODE><<<grid, kSortThreads, 0, st>>>(pass, ws.act_total, ws.bstate, kin, ws.tilecnt);
     radix_scan_kernel<MODE><<<nblocks, 1024, 0, st>>>(ws.act_total, ws.bstate, ws.tilecnt);
-    radix_scatter_kernel<MODE><<<grid, kSortThreads, 0, st>>>(pass, ws.act_total, ws.bstate, in, out, ws.rle, ws.rank, ws.tilecnt);
+    radix_scatter_kernel<MODE><<<grid, kSortThreads, kScatterSmem, st>>>(pass, ws.act_total, ws.bstate, kin, vin, kout, vout,
+                                                                         ws.tilecnt);
     count_launches(P, 3);
 }
 
@@ -592,21 +622,21 @@ static void bwt_round(lfc_plan P, cudaStream_t st, int nblocks, int tiles, int m
                       int set_cond) {
     Workspace &ws = P->ws;
     round_start_kernel<<<1, 1, 0, st>>>(ws.act_total, 0);
-    // 5 LSD passes over the 40-bit key: val -> val2 -> val -> val2 -> val -> val2
-    for (int pass = 0; pass < 5; pass++) {
-        const int32_t *in = (pass & 1) ? ws.val2 : ws.val;
-        int32_t *out = (pass & 1) ? ws.val : ws.val2;
-        radix_pass<1>(P, st, nblocks, tiles, pass, in, out);
-    }
     dim3 g1(tiles, nblocks);
-    heads_tile_kernel<1><<<g1, kSortThreads, 0, st>>>(ws.act_total, ws.bstate, ws.val2, ws.act, ws.act2, ws.rle, ws.rank,
-                                                      ws.bwt, ws.tileaux);
+    key40_kernel<<<g1, kSortThreads, 0, st>>>(ws.act_total, ws.bstate, ws.val, ws.rank, ws.keys);
+    // 5 LSD passes over the 40-bit key: (keys, val) -> (keys2, val2) -> ... -> (keys2, val2)
+    for (int pass = 0; pass < 5; pass++) {
+        if (pass & 1) radix_pass<1>(P, st, nblocks, tiles, pass, ws.keys2, ws.val2, ws.keys, ws.val);
+        else radix_pass<1>(P, st, nblocks, tiles, pass, ws.keys, ws.val, ws.keys2, ws.val2);
+    }
+    heads_tile_kernel<1><<<g1, kSortThreads, 0, st>>>(ws.act_total, ws.bstate, ws.keys2, ws.act, ws.act2, ws.bwt,
+                                                      ws.tileaux);
     heads_scan_kernel<1><<<nblocks, 256, 0, st>>>(ws.act_total, ws.bstate, ws.tileaux);
     heads_apply_kernel<1><<<g1, kSortThreads, 0, st>>>(ws.act_total, ws.bstate, ws.val2, ws.act, ws.act2, ws.bwt,
                                                        ws.tileaux, ws.rank, ws.sa, ws.val);
     commit_round_kernel<<<(nblocks + 255) / 256, 256, 0, st>>>(ws.bstate, nblocks);
     round_end_kernel<<<1, 1, 0, st>>>(ws.act_total, max_m, cond, set_cond);
-    count_launches(P, 6);
+    count_launches(P, 7);
 }
 
 cudaError_t launch_bwt(lfc_plan P, int nblocks, int max_m) {
@@ -619,19 +649,23 @@ cudaError_t launch_bwt(lfc_plan P, int nblocks, int max_m) {
     e = cudaStreamIsCapturing(s, &cap);
     if (e != cudaSuccess) return e;
     const bool graph = cap == cudaStreamCaptureStatusActive;
-    // phase 1: 8 LSD passes, identity -> sa2 -> sa -> ... -> sa
+    e = cudaFuncSetAttribute(radix_scatter_kernel<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kScatterSmem);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(radix_scatter_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kScatterSmem);
+    if (e != cudaSuccess) return e;
+    // phase 1: prefix keys, then 8 LSD passes (keys, sa) -> (keys2, sa2) -> ... -> (keys, sa)
     stage_begin(P, LFC_STAGE_BWT_SORT8);
+    dim3 grid(tiles, nblocks);
+    key8_kernel<<<grid, kSortThreads, 0, s>>>(ws.bstate, ws.rle, ws.keys, ws.sa);
+    count_launches(P, 1);
     for (int pass = 0; pass < 8; pass++) {
-        const int32_t *in = (pass & 1) ? ws.sa2 : ws.sa;
-        int32_t *out = (pass & 1) ? ws.sa : ws.sa2;
-        radix_pass<0>(P, s, nblocks, tiles, pass, in, out);
+        if (pass & 1) radix_pass<0>(P, s, nblocks, tiles, pass, ws.keys2, ws.sa2, ws.keys, ws.sa);
+        else radix_pass<0>(P, s, nblocks, tiles, pass, ws.keys, ws.sa, ws.keys2, ws.sa2);
     }
     stage_end(P, LFC_STAGE_BWT_SORT8);
     stage_begin(P, LFC_STAGE_BWT_REFINE);
     round_start_kernel<<<1, 1, 0, s>>>(ws.act_total, 1);
-    dim3 grid(tiles, nblocks);
-    heads_tile_kernel<0><<<grid, kSortThreads, 0, s>>>(ws.act_total, ws.bstate, ws.sa, ws.sa, ws.sa, ws.rle, ws.rank, ws.bwt,
-                                                       ws.tileaux);
+    heads_tile_kernel<0><<<grid, kSortThreads, 0, s>>>(ws.act_total, ws.bstate, ws.keys, ws.sa, ws.sa, ws.bwt, ws.tileaux);
     heads_scan_kernel<0><<<nblocks, 256, 0, s>>>(ws.act_total, ws.bstate, ws.tileaux);
     heads_apply_kernel<0><<<grid, kSortThreads, 0, s>>>(ws.act_total, ws.bstate, ws.sa, ws.act, ws.act2, ws.bwt,
                                                         ws.tileaux, ws.rank, ws.sa, ws.val);

@@ -181,6 +181,8 @@ struct Workspace {
     int32_t *act2 = nullptr;
     int32_t *val = nullptr;        // SA values of the active elements
     int32_t *val2 = nullptr;
+    uint64_t *keys = nullptr;      // sort keys riding with sa / val, block_cap * kBlockCap
+    uint64_t *keys2 = nullptr;
     uint32_t *tilecnt = nullptr;   // block_cap * 256 * kTilesPerBlock
     int32_t *tileaux = nullptr;    // block_cap * kTilesPerBlock * 4
     uint8_t *bwt = nullptr;        // L column
