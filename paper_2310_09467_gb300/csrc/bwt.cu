@@ -298,9 +298,15 @@ __global__ void __launch_bounds__(kSortThreads) radix_hist_kernel(int pass, cons
     __syncthreads();
     const uint64_t *K = K_all + (size_t)b * kBlockCap;
     const int shift = 8 * pass;
-    for (int r = 0; r < kPerThread; r++) {
+    uint32_t dg[kPerThread];
+#pragma unroll
+    for (int r = 0; r < kPerThread; r++) {  // all loads in flight first
         const int k = tile * kTile + w * 512 + r * 32 + lane;
-        const uint32_t d = k < n ? (uint32_t)(K[k] >> shift) & 255u : 0xFFFFFFFFu;
+        dg[r] = k < n ? (uint32_t)(K[k] >> shift) & 255u : 0xFFFFFFFFu;
+    }
+#pragma unroll
+    for (int r = 0; r < kPerThread; r++) {
+        const uint32_t d = dg[r];
         const uint32_t d0 = __shfl_sync(LFC_FULL, d, 0);
         if (__all_sync(LFC_FULL, d == d0)) {
             if (lane == 0 && d0 != 0xFFFFFFFFu) atomicAdd(&hst[w][d0], 32u);
@@ -413,12 +419,16 @@ __global__ void __launch_bounds__(kSortThreads) radix_scatter_kernel(int pass, c
     const int cnt = min(kTile, n - tile * kTile);
     uint64_t *Kout = Kout_all + bo;
     int32_t *Vout = Vout_all + bo;
-    for (int j = threadIdx.x; j < cnt; j += kSortThreads) {
-        const uint64_t key = sK[j];
-        const uint32_t d = (uint32_t)(key >> shift) & 255u;
-        const uint32_t g = gbase[d] + ((uint32_t)j - loff[d]);
-        Kout[g] = key;
-        Vout[g] = sV[j];
+#pragma unroll 4
+    for (int r = 0; r < kPerThread; r++) {
+        const int j = r * kSortThreads + threadIdx.x;
+        if (j < cnt) {
+            const uint64_t key = sK[j];
+            const uint32_t d = (uint32_t)(key >> shift) & 255u;
+            const uint32_t g = gbase[d] + ((uint32_t)j - loff[d]);
+            Kout[g] = key;
+            Vout[g] = sV[j];
+        }
     }
 }
 
