@@ -42,35 +42,73 @@ struct CrcChunk {
     int64_t after;     // bytes of the range after this chunk
 };
 
-__device__ __forceinline__ void build_table(uint32_t *tab) {
+// T[k][i] = i * x^(32 + 8k) mod P: the effect of byte i followed by k zero
+// bytes on a zero register, so four bytes fold in one step.
+__device__ __forceinline__ void build_tables(uint32_t (*T)[256]) {
     for (int i = threadIdx.x; i < 256; i += blockDim.x) {
         uint32_t v = (uint32_t)i << 24;
         for (int k = 0; k < 8; k++) v = (v & 0x80000000u) ? (v << 1) ^ kPoly : (v << 1);
-        tab[i] = v;
+        T[0][i] = v;
+    }
+    __syncthreads();
+    for (int k = 1; k < 4; k++) {
+        for (int i = threadIdx.x; i < 256; i += blockDim.x) {
+            const uint32_t v = T[k - 1][i];
+            T[k][i] = (v << 8) ^ T[0][v >> 24];
+        }
+        __syncthreads();
     }
 }
 
-// One CTA per chunk: each thread reduces a contiguous piece, then the pieces
-// are shifted into place and xor-reduced; the chunk's remainder is shifted
-// by the bytes of its range that follow it.
+// One CTA per chunk, seen as front-padded with zeros to kCrcChunk bytes
+// (leading zeros leave a zero register unchanged): thread t reduces the
+// 256-byte piece t four bytes at a time, then the warps merge their pieces
+// in a shuffle tree (level j shifts the left half by x^(8 * 256 * 2^j)), the
+// warps are merged in order, and the chunk remainder is shifted by the bytes
+// of its range that follow it.
+constexpr int kCrcPiece = kCrcChunk / 256;
+
 __global__ void __launch_bounds__(256) crc_chunk_kernel(const CrcChunk *__restrict__ chunks, uint32_t *__restrict__ part) {
-    __shared__ uint32_t tab[256];
+    __shared__ uint32_t T[4][256];
     __shared__ uint32_t red[8];
-    build_table(tab);
+    __shared__ uint32_t cpow[6];
+    build_tables(T);
+    if (threadIdx.x < 6) cpow[threadIdx.x] = x_pow_8k((uint64_t)kCrcPiece << threadIdx.x);
     __syncthreads();
     const CrcChunk c = chunks[blockIdx.x];
-    const int per = (c.len + blockDim.x - 1) / blockDim.x;
-    const int a = min(c.len, (int)threadIdx.x * per), e = min(c.len, a + per);
+    const int pad = kCrcChunk - c.len;
+    const int start = (int)threadIdx.x * kCrcPiece - pad;  // real offset of the piece
     uint32_t r = 0;
-    for (int i = a; i < e; i++) r = (r << 8) ^ tab[(r >> 24) ^ c.src[i]];
-    if (e > a) r = gf_mulmod(r, x_pow_8k((uint64_t)(c.len - e) + (uint64_t)c.after));
-    for (int o = 16; o > 0; o >>= 1) r ^= __shfl_xor_sync(LFC_FULL, r, o);
-    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = r;
+    if (start + kCrcPiece > 0) {
+        const bool fast = start >= 0 && (((uintptr_t)(c.src + start)) & 3) == 0;
+        for (int i = 0; i < kCrcPiece; i += 4) {
+            uint32_t w;
+            if (fast) {
+                w = __byte_perm(__ldg(reinterpret_cast<const uint32_t *>(c.src + start + i)), 0u, 0x0123);
+            } else {
+                w = 0;
+                for (int q = 0; q < 4; q++) {
+                    const int o = start + i + q;
+                    w = (w << 8) | (o >= 0 ? (uint32_t)c.src[o] : 0u);
+                }
+            }
+            r ^= w;
+            r = T[3][r >> 24] ^ T[2][(r >> 16) & 255u] ^ T[1][(r >> 8) & 255u] ^ T[0][r & 255u];
+        }
+    }
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int j = 0; j < 5; j++) {
+        const uint32_t rp = __shfl_xor_sync(LFC_FULL, r, 1 << j);
+        const bool right = (lane >> j) & 1;
+        r = gf_mulmod(right ? rp : r, cpow[j]) ^ (right ? r : rp);
+    }
+    if (lane == 0) red[threadIdx.x >> 5] = r;
     __syncthreads();
     if (threadIdx.x == 0) {
-        uint32_t t = 0;
-        for (int i = 0; i < (int)(blockDim.x >> 5); i++) t ^= red[i];
-        part[blockIdx.x] = t;
+        uint32_t t = red[0];
+        for (int i = 1; i < (int)(blockDim.x >> 5); i++) t = gf_mulmod(t, cpow[5]) ^ red[i];
+        part[blockIdx.x] = c.after ? gf_mulmod(t, x_pow_8k((uint64_t)c.after)) : t;
     }
 }
 

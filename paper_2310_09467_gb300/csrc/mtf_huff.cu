@@ -7,6 +7,8 @@
 // without them"; one warp per block composes these summaries in order to get
 // every segment's starting list, then every segment replays MTF from its
 // list with the 256-entry list held in registers (8 entries per lane).
+#include <climits>
+
 #include "lfc_common.cuh"
 
 namespace lfc {
@@ -167,64 +169,174 @@ __global__ void __launch_bounds__(32) mtf_encode_kernel(const BlockState *__rest
 
 // ------------------------------------------------------------------ RLE2
 // Zero runs of length r -> bijective base-2 digits RUNA(0)/RUNB(1): digit k
-// is bit k of r + 1, floor(log2(r + 1)) digits. Index j > 0 -> j + 1.
-__global__ void __launch_bounds__(1024) rle2_kernel(BlockState *__restrict__ st, const uint8_t *__restrict__ idx_all,
-                                                    uint16_t *__restrict__ sym_all, uint32_t *__restrict__ freq_all) {
-    __shared__ int32_t sh[33];
-    __shared__ uint32_t fq[kMaxAlpha];
-    const int b = blockIdx.x;
-    const int m = st[b].m;
-    int n_in_use = 0;
-    for (int i = 0; i < 8; i++) n_in_use += __popc(st[b].in_use[i]);
-    const uint8_t *idx = idx_all + (size_t)b * kBlockCap;
-    uint16_t *sym = sym_all + (size_t)b * kSymStride;
-    for (int i = threadIdx.x; i < kMaxAlpha; i += blockDim.x) fq[i] = 0;
-    const int T = blockDim.x;
-    const int per = (m + T - 1) / T;
-    const int a = min(m, (int)threadIdx.x * per), e = min(m, a + per);
-    int lastnz = -1;
-    for (int i = a; i < e; i++) if (idx[i]) lastnz = i;
-    int carry = block_excl_max(lastnz, sh);
-    int cnt = 0;
-    {
-        int lz = carry;
-        for (int i = a; i < e; i++) {
-            if (idx[i]) { cnt++; lz = i; continue; }
-            if (i == m - 1 || idx[i + 1]) cnt += 31 - __clz(i - lz + 1);  // floor(log2(r + 1))
+// is bit k of r + 1, floor(log2(r + 1)) digits, emitted at the run's last
+// position. Index j > 0 -> j + 1. As for RLE1, a scan over 4096-position
+// tiles in three kernels: per tile the first / last nonzero index and the
+// symbols of the positions after the first nonzero (1); per block the last
+// nonzero before each tile, the symbols of each tile's leading zero run and
+// the tiles' symbol offsets (2); per tile the symbols and their frequencies (3).
+constexpr int kRle2Tile = 4096;
+constexpr int kRle2Threads = 256;
+
+__device__ __forceinline__ int run_digits(int r) { return 31 - __clz(r + 1); }
+
+// Nonzero mask of a thread's 16 positions [a, a + 16) of the tile, a run-end
+// mask (zero followed by a nonzero or by the end of the block) and the
+// thread's first / last nonzero position (absolute; INT_MAX / -1 if none).
+__device__ __forceinline__ void rle2_masks(const uint8_t *idx, int a, int te, int m, uint32_t &nz, uint32_t &end,
+                                           int &first, int &last, uint8_t (&v)[16]) {
+    *reinterpret_cast<uint4 *>(v) = *reinterpret_cast<const uint4 *>(idx + a);
+    const uint32_t nxt = a + 16 < m ? idx[a + 16] : 0u;
+    nz = 0; end = 0; first = INT_MAX; last = -1;
+#pragma unroll
+    for (int q = 0; q < 16; q++) {
+        if (a + q >= te) break;
+        if (v[q]) {
+            nz |= 1u << q;
+            first = min(first, a + q);
+            last = a + q;
+        } else {
+            const bool next_nz = q < 15 ? (a + q + 1 < m && v[q + 1] != 0) : (a + 16 < m && nxt != 0);
+            if (a + q == m - 1 || next_nz) end |= 1u << q;
         }
+    }
+}
+
+__global__ void __launch_bounds__(kRle2Threads) rle2_tile_kernel(const BlockState *__restrict__ st,
+                                                                 const uint8_t *__restrict__ idx_all,
+                                                                 int32_t *__restrict__ aux_all) {
+    __shared__ int sh[33];
+    __shared__ int sfirst, slast;
+    const int b = blockIdx.y, tile = blockIdx.x;
+    const int m = st[b].m;
+    const int ts = tile * kRle2Tile;
+    if (ts >= m) return;
+    const int te = min(m, ts + kRle2Tile);
+    if (threadIdx.x == 0) { sfirst = INT_MAX; slast = -1; }
+    const uint8_t *idx = idx_all + (size_t)b * kBlockCap;
+    const int a = ts + 16 * (int)threadIdx.x;
+    uint32_t nz = 0, end = 0;
+    int first = INT_MAX, last = -1;
+    uint8_t v[16];
+    if (a < te) rle2_masks(idx, a, te, m, nz, end, first, last, v);
+    int lz = block_excl_max(last, sh);   // last nonzero of the tile before this thread, or -1
+    int cnt = 0;
+#pragma unroll
+    for (int q = 0; q < 16; q++) {
+        if ((nz >> q) & 1u) { cnt++; lz = a + q; }
+        else if (((end >> q) & 1u) && lz >= ts) cnt += run_digits(a + q - lz);
     }
     int total;
-    int o = block_excl_sum<int>(cnt, sh, &total);
-    {
-        int lz = carry;
-        for (int i = a; i < e; i++) {
-            const uint32_t j = idx[i];
-            if (j) {
-                sym[o++] = (uint16_t)(j + 1);
-                atomicAdd(&fq[j + 1], 1u);
-                lz = i;
-                continue;
-            }
-            if (i == m - 1 || idx[i + 1]) {
-                const uint32_t r1 = (uint32_t)(i - lz) + 1u;
-                const int nd = 31 - __clz(r1);
-                for (int k = 0; k < nd; k++) {
-                    const uint32_t d = (r1 >> k) & 1u;
-                    sym[o++] = (uint16_t)d;
-                    atomicAdd(&fq[d], 1u);
-                }
+    block_excl_sum<int>(cnt, sh, &total);
+    if (first != INT_MAX) atomicMin(&sfirst, first);
+    if (last >= 0) atomicMax(&slast, last);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int32_t *aux = aux_all + ((size_t)b * kTilesPerBlock + tile) * 4;
+        aux[0] = sfirst != INT_MAX ? sfirst : te;
+        aux[1] = slast;
+        aux[2] = total;
+    }
+}
+
+// One warp per block: aux[tile][1] = last nonzero before the tile (-1 if
+// none), aux[tile][2] = the tile's symbol offset; symbol count, EOB and the
+// frequency table's start.
+__global__ void __launch_bounds__(32) rle2_scan_kernel(BlockState *__restrict__ st, int32_t *__restrict__ aux_all,
+                                                       uint16_t *__restrict__ sym_all, uint32_t *__restrict__ freq_all) {
+    const int b = blockIdx.x;
+    const int m = st[b].m;
+    const int ntile = (m + kRle2Tile - 1) / kRle2Tile;
+    int32_t *aux = aux_all + (size_t)b * kTilesPerBlock * 4;
+    const int lane = (int)lane_id();
+    int carryR = -1, carryO = 0;
+    for (int base = 0; base < ntile; base += 32) {
+        const int t = base + lane;
+        const bool valid = t < ntile;
+        const int ts = t * kRle2Tile, te = min(m, ts + kRle2Tile);
+        const int fs = valid ? aux[t * 4 + 0] : 0;
+        const int ls = valid ? aux[t * 4 + 1] : -1;
+        const int lo = valid ? aux[t * 4 + 2] : 0;
+        const int imax = warp_incl_max(ls);
+        int ex = __shfl_up_sync(LFC_FULL, imax, 1);
+        if (lane == 0) ex = -1;
+        const int R = max(carryR, ex);
+        int pre = 0;  // the zero run the tile starts with, if it ends in the tile
+        if (valid && fs > ts) {
+            if (fs < te) pre = run_digits(fs - 1 - R);
+            else if (te == m) pre = run_digits(m - 1 - R);
+        }
+        const int out = valid ? pre + lo : 0;
+        const int incl = warp_incl_sum(out);
+        if (valid) {
+            aux[t * 4 + 1] = R;
+            aux[t * 4 + 2] = carryO + incl - out;
+        }
+        carryR = max(carryR, __shfl_sync(LFC_FULL, imax, 31));
+        carryO += __shfl_sync(LFC_FULL, incl, 31);
+    }
+    int n_in_use = 0;
+    for (int i = 0; i < 8; i++) n_in_use += __popc(st[b].in_use[i]);
+    uint32_t *freq = freq_all + (size_t)b * kMaxAlpha;
+    for (int i = lane; i < kMaxAlpha; i += 32) freq[i] = i == n_in_use + 1 ? 1u : 0u;
+    if (lane == 0) {
+        sym_all[(size_t)b * kSymStride + carryO] = (uint16_t)(n_in_use + 1);
+        st[b].n_mtf = carryO + 1;
+        st[b].n_in_use = n_in_use;
+    }
+}
+
+__global__ void __launch_bounds__(kRle2Threads) rle2_write_kernel(const BlockState *__restrict__ st,
+                                                                  const uint8_t *__restrict__ idx_all,
+                                                                  const int32_t *__restrict__ aux_all,
+                                                                  uint16_t *__restrict__ sym_all, uint32_t *__restrict__ freq_all) {
+    __shared__ int sh[33];
+    __shared__ uint32_t fq[kMaxAlpha];
+    const int b = blockIdx.y, tile = blockIdx.x;
+    const int m = st[b].m;
+    const int ts = tile * kRle2Tile;
+    if (ts >= m) return;
+    const int te = min(m, ts + kRle2Tile);
+    for (int i = threadIdx.x; i < kMaxAlpha; i += kRle2Threads) fq[i] = 0;
+    const uint8_t *idx = idx_all + (size_t)b * kBlockCap;
+    const int32_t *aux = aux_all + ((size_t)b * kTilesPerBlock + tile) * 4;
+    const int R = aux[1], off = aux[2];
+    const int a = ts + 16 * (int)threadIdx.x;
+    uint32_t nz = 0, end = 0;
+    int first = INT_MAX, last = -1;
+    uint8_t v[16];
+    if (a < te) rle2_masks(idx, a, te, m, nz, end, first, last, v);
+    const int lz0 = max(block_excl_max(last, sh), R);
+    int lz = lz0, cnt = 0;
+#pragma unroll
+    for (int q = 0; q < 16; q++) {
+        if ((nz >> q) & 1u) { cnt++; lz = a + q; }
+        else if ((end >> q) & 1u) cnt += run_digits(a + q - lz);
+    }
+    int o = off + block_excl_sum<int>(cnt, sh, nullptr);
+    uint16_t *sym = sym_all + (size_t)b * kSymStride;
+    lz = lz0;
+#pragma unroll
+    for (int q = 0; q < 16; q++) {
+        if ((nz >> q) & 1u) {
+            const uint32_t s = (uint32_t)v[q] + 1u;
+            sym[o++] = (uint16_t)s;
+            atomicAdd(&fq[s], 1u);
+            lz = a + q;
+        } else if ((end >> q) & 1u) {
+            const uint32_t r1 = (uint32_t)(a + q - lz);  // run length r, digits of r + 1
+            const int nd = run_digits((int)r1);
+            for (int k = 0; k < nd; k++) {
+                const uint32_t d = ((r1 + 1u) >> k) & 1u;
+                sym[o++] = (uint16_t)d;
+                atomicAdd(&fq[d], 1u);
             }
         }
     }
     __syncthreads();
-    if (threadIdx.x == 0) {
-        sym[total] = (uint16_t)(n_in_use + 1);
-        fq[n_in_use + 1]++;
-        st[b].n_mtf = total + 1;
-        st[b].n_in_use = n_in_use;
-    }
-    __syncthreads();
-    for (int i = threadIdx.x; i < kMaxAlpha; i += blockDim.x) freq_all[(size_t)b * kMaxAlpha + i] = fq[i];
+    uint32_t *freq = freq_all + (size_t)b * kMaxAlpha;
+    for (int i = threadIdx.x; i < kMaxAlpha; i += kRle2Threads)
+        if (fq[i]) atomicAdd(&freq[i], fq[i]);
 }
 
 // --------------------------------------------------------------- Huffman
@@ -561,8 +673,11 @@ cudaError_t launch_mtf_rle2(lfc_plan P, int nblocks) {
     mtf_summary_kernel<<<grid, 32, 0, s>>>(ws.bstate, ws.bwt, ws.mtfrec, ws.mtfreclen);
     mtf_compose_kernel<<<nblocks, 32, 0, s>>>(ws.bstate, ws.mtfrec, ws.mtfreclen, ws.mtflists);
     mtf_encode_kernel<<<grid, 32, 0, s>>>(ws.bstate, ws.bwt, ws.mtflists, ws.mtfidx);
-    rle2_kernel<<<nblocks, 1024, 0, s>>>(ws.bstate, ws.mtfidx, ws.sym, ws.freq);
-    count_launches(P, 4);
+    const dim3 g2(kTilesPerBlock, nblocks);  // RLE1 output <= 900000 = 220 tiles
+    rle2_tile_kernel<<<g2, kRle2Threads, 0, s>>>(ws.bstate, ws.mtfidx, ws.tileaux);
+    rle2_scan_kernel<<<nblocks, 32, 0, s>>>(ws.bstate, ws.tileaux, ws.sym, ws.freq);
+    rle2_write_kernel<<<g2, kRle2Threads, 0, s>>>(ws.bstate, ws.mtfidx, ws.tileaux, ws.sym, ws.freq);
+    count_launches(P, 6);
     return cudaGetLastError();
 }
 
