@@ -14,9 +14,8 @@ namespace lfc {
 constexpr uint32_t kPoly = 0x04C11DB7u;
 constexpr int kCrcChunk = 65536;  // bytes per partial remainder
 
-__device__ __forceinline__ uint32_t gf_mulmod(uint32_t a, uint32_t b) {
+__host__ __device__ constexpr uint32_t gf_mulmod(uint32_t a, uint32_t b) {
     uint32_t r = 0;
-#pragma unroll 8
     for (int i = 31; i >= 0; i--) {
         r = (r & 0x80000000u) ? (r << 1) ^ kPoly : (r << 1);
         if ((b >> i) & 1u) r ^= a;
@@ -25,7 +24,7 @@ __device__ __forceinline__ uint32_t gf_mulmod(uint32_t a, uint32_t b) {
 }
 
 // x^(8k) mod P by square-and-multiply from x^8.
-__device__ __forceinline__ uint32_t x_pow_8k(uint64_t k) {
+__host__ __device__ constexpr uint32_t x_pow_8k(uint64_t k) {
     uint32_t result = 1u, base = 0x100u;
     while (k) {
         if (k & 1) result = gf_mulmod(result, base);
@@ -38,8 +37,7 @@ __device__ __forceinline__ uint32_t x_pow_8k(uint64_t k) {
 struct CrcChunk {
     const uint8_t *src;
     int32_t len;
-    int32_t range;     // which range this chunk belongs to
-    int64_t after;     // bytes of the range after this chunk
+    uint32_t shift;    // x^(8 * bytes of the range after this chunk) mod P
 };
 
 // T[k][i] = i * x^(32 + 8k) mod P: the effect of byte i followed by k zero
@@ -67,14 +65,14 @@ __device__ __forceinline__ void build_tables(uint32_t (*T)[256]) {
 // warps are merged in order, and the chunk remainder is shifted by the bytes
 // of its range that follow it.
 constexpr int kCrcPiece = kCrcChunk / 256;
+// shuffle-tree level j merges halves of 2^j pieces; level 5 merges warps
+__constant__ uint32_t c_crc_pow[6] = {x_pow_8k(kCrcPiece),      x_pow_8k(kCrcPiece * 2),  x_pow_8k(kCrcPiece * 4),
+                                      x_pow_8k(kCrcPiece * 8),  x_pow_8k(kCrcPiece * 16), x_pow_8k(kCrcPiece * 32)};
 
 __global__ void __launch_bounds__(256) crc_chunk_kernel(const CrcChunk *__restrict__ chunks, uint32_t *__restrict__ part) {
     __shared__ uint32_t T[4][256];
     __shared__ uint32_t red[8];
-    __shared__ uint32_t cpow[6];
     build_tables(T);
-    if (threadIdx.x < 6) cpow[threadIdx.x] = x_pow_8k((uint64_t)kCrcPiece << threadIdx.x);
-    __syncthreads();
     const CrcChunk c = chunks[blockIdx.x];
     const int pad = kCrcChunk - c.len;
     const int start = (int)threadIdx.x * kCrcPiece - pad;  // real offset of the piece
@@ -101,33 +99,33 @@ __global__ void __launch_bounds__(256) crc_chunk_kernel(const CrcChunk *__restri
     for (int j = 0; j < 5; j++) {
         const uint32_t rp = __shfl_xor_sync(LFC_FULL, r, 1 << j);
         const bool right = (lane >> j) & 1;
-        r = gf_mulmod(right ? rp : r, cpow[j]) ^ (right ? r : rp);
+        r = gf_mulmod(right ? rp : r, c_crc_pow[j]) ^ (right ? r : rp);
     }
     if (lane == 0) red[threadIdx.x >> 5] = r;
     __syncthreads();
     if (threadIdx.x == 0) {
         uint32_t t = red[0];
-        for (int i = 1; i < (int)(blockDim.x >> 5); i++) t = gf_mulmod(t, cpow[5]) ^ red[i];
-        part[blockIdx.x] = c.after ? gf_mulmod(t, x_pow_8k((uint64_t)c.after)) : t;
+        for (int i = 1; i < (int)(blockDim.x >> 5); i++) t = gf_mulmod(t, c_crc_pow[5]) ^ red[i];
+        part[blockIdx.x] = gf_mulmod(t, c.shift);
     }
 }
 
 // One thread per range: xor of its chunks' shifted remainders, plus the
-// shifted initial register, complemented.
+// initial register shifted over the whole range (I * x^(8|M|)), complemented.
 __global__ void crc_finish_kernel(const uint32_t *__restrict__ part, const int32_t *__restrict__ first_chunk,
-                                  const int64_t *__restrict__ range_len, int nranges, uint32_t *__restrict__ out,
+                                  const uint32_t *__restrict__ init_shifted, int nranges, uint32_t *__restrict__ out,
                                   int out_stride_words) {
     const int rg = blockIdx.x * blockDim.x + threadIdx.x;
     if (rg >= nranges) return;
-    uint32_t r = 0;
+    uint32_t r = init_shifted[rg];
     for (int c = first_chunk[rg]; c < first_chunk[rg + 1]; c++) r ^= part[c];
-    r ^= gf_mulmod(0xFFFFFFFFu, x_pow_8k((uint64_t)range_len[rg]));
     out[(size_t)rg * out_stride_words] = ~r;
 }
 
 // Descriptor tables of one CRC run, laid out in a caller-provided host
 // buffer: [CrcChunk x nchunks] [int32 first_chunk x (n+1)] (pad 8)
-// [int64 range_len x n].
+// [uint32 I * x^(8 len) mod P x n]. Shifts are accumulated from each range's
+// end, one GF(2) multiply per chunk.
 int crc_count_chunks(const int64_t *len, int n) {
     int c = 0;
     for (int r = 0; r < n; r++) c += (int)((len[r] + kCrcChunk - 1) / kCrcChunk);
@@ -141,19 +139,26 @@ size_t crc_table_bytes(int nchunks, int n) {
 }
 
 void crc_build_tables(const uint8_t *const *ptr, const int64_t *len, int n, uint8_t *out, CrcRun *run) {
+    constexpr uint32_t kFullShift = x_pow_8k(kCrcChunk);
     CrcChunk *ch = reinterpret_cast<CrcChunk *>(out);
     int k = 0;
     std::vector<int32_t> first(n + 1);
+    std::vector<uint32_t> init(n);
     for (int r = 0; r < n; r++) {
         first[r] = k;
-        for (int64_t o = 0; o < len[r]; o += kCrcChunk) {
+        const int nc = (int)((len[r] + kCrcChunk - 1) / kCrcChunk);
+        uint32_t acc = 1u;  // x^(8 * bytes after the chunk)
+        for (int i = nc - 1; i >= 0; i--) {
+            const int64_t o = (int64_t)i * kCrcChunk;
             CrcChunk c;
             c.src = ptr[r] + o;
             c.len = (int32_t)(len[r] - o < kCrcChunk ? len[r] - o : kCrcChunk);
-            c.range = r;
-            c.after = len[r] - o - c.len;
-            memcpy(&ch[k++], &c, sizeof(c));
+            c.shift = acc;
+            memcpy(&ch[k + i], &c, sizeof(c));
+            acc = gf_mulmod(acc, c.len == kCrcChunk ? kFullShift : x_pow_8k((uint64_t)c.len));
         }
+        init[r] = gf_mulmod(0xFFFFFFFFu, acc);
+        k += nc;
     }
     first[n] = k;
     size_t o = (size_t)k * sizeof(CrcChunk);
@@ -161,7 +166,7 @@ void crc_build_tables(const uint8_t *const *ptr, const int64_t *len, int n, uint
     run->off_first = o;
     o += (size_t)(n + 1) * 4;
     o = (o + 7) & ~(size_t)7;
-    memcpy(out + o, len, (size_t)n * 8);
+    memcpy(out + o, init.data(), (size_t)n * 4);
     run->off_len = o;
     run->nchunks = k;
     run->nranges = n;
@@ -173,7 +178,7 @@ cudaError_t launch_crc(lfc_plan P, const uint8_t *d_tables, const CrcRun &run, u
     if (run.nchunks) crc_chunk_kernel<<<(unsigned)run.nchunks, 256, 0, P->stream>>>(reinterpret_cast<const CrcChunk *>(d_tables), P->ws.crc_part);
     crc_finish_kernel<<<(run.nranges + 127) / 128, 128, 0, P->stream>>>(
         P->ws.crc_part, reinterpret_cast<const int32_t *>(d_tables + run.off_first),
-        reinterpret_cast<const int64_t *>(d_tables + run.off_len), run.nranges, out, out_stride_words);
+        reinterpret_cast<const uint32_t *>(d_tables + run.off_len), run.nranges, out, out_stride_words);
     count_launches(P, run.nchunks ? 2 : 1);
     return cudaGetLastError();
 }

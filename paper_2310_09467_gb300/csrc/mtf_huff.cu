@@ -109,11 +109,27 @@ __global__ void __launch_bounds__(32) mtf_compose_kernel(const BlockState *__res
     }
 }
 
-// One warp per segment: MTF indices from the segment's starting list.
+// One warp per segment: MTF indices from the segment's starting list, 32
+// positions per step. With the list (lst) and its inverse (posof) in shared
+// memory at the window start, lane k with symbol s:
+//  - s also at an earlier lane j of the window (the latest such j): s was at
+//    the front after j and each lane i in (j, k) pushed it back one place iff
+//    i's symbol was not moved to the front after j, i.e. prev(i) <= j, where
+//    prev(i) is the latest earlier lane with i's symbol (-1 if none);
+//  - otherwise: s is still in the old part of the list, behind the distinct
+//    symbols of lanes < k, so its index is P + #{first-occurrence lanes
+//    i < k with P_i > P}, P = posof[s].
+// Both counts compare one value per lane with every other lane's: done
+// bit-sliced over ballots of the values' bits. The list then becomes the
+// window's symbols by last use, then the old list without them; entries
+// behind the deepest window symbol keep their places.
 __global__ void __launch_bounds__(32) mtf_encode_kernel(const BlockState *__restrict__ st, const uint8_t *__restrict__ L_all,
                                                         const uint8_t *__restrict__ lists_all, uint8_t *__restrict__ idx_all) {
     __shared__ uint8_t seq[256];
     __shared__ uint32_t iush[8];
+    __shared__ uint8_t lst[256];
+    __shared__ uint8_t posof[256];
+    __shared__ uint32_t WP[8];
     const int b = blockIdx.y, g = blockIdx.x;
     const int m = st[b].m;
     const int s0 = g * kTile;
@@ -123,46 +139,89 @@ __global__ void __launch_bounds__(32) mtf_encode_kernel(const BlockState *__rest
     if (lane < 8) iush[lane] = st[b].in_use[lane];
     __syncwarp();
     build_seq_table(iush, seq);
+    int n_in_use = 0;
+    for (int i = 0; i < 8; i++) n_in_use += __popc(iush[i]);
+    const uint8_t *start = lists_all + ((size_t)b * kTilesPerBlock + g) * 256;
+    for (int q = lane; q < 256; q += 32) lst[q] = start[q];
     __syncwarp();
-    const uint8_t *lst = lists_all + ((size_t)b * kTilesPerBlock + g) * 256;
-    uint64_t v = 0;
-    for (int q = 0; q < 8; q++) v |= (uint64_t)lst[lane * 8 + q] << (8 * q);
+    for (int q = lane; q < n_in_use; q += 32) posof[lst[q]] = (uint8_t)q;
+    __syncwarp();
     const uint8_t *L = L_all + (size_t)b * kBlockCap;
     uint8_t *out = idx_all + (size_t)b * kBlockCap;
-    __shared__ uint8_t idxbuf[32];
-    uint32_t front = (uint32_t)v & 0xFFu;
+    const uint32_t lt = lanemask_lt(), gt = lanemask_gt();
     for (int w0 = s0; w0 < s1; w0 += 32) {
         const int i = w0 + lane;
-        const int cnt = min(32, s1 - w0);
-        const uint32_t mys = i < s1 ? seq[L[i]] : 0u;
-        // a byte equal to its predecessor has index 0 and leaves the list as is
-        uint32_t prv = __shfl_up_sync(LFC_FULL, mys, 1);
-        if (lane == 0) prv = front;
-        const uint32_t live = cnt == 32 ? LFC_FULL : ((1u << cnt) - 1u);
-        const uint32_t rep = __ballot_sync(LFC_FULL, mys == prv) & live;
-        uint32_t todo = live & ~rep;
-        while (todo) {
-            const int k = __ffs(todo) - 1;
-            todo &= todo - 1u;
-            const uint32_t s = __shfl_sync(LFC_FULL, mys, k);
-            // the list holds every symbol once: exactly one lane has a zero byte
-            const uint64_t x = v ^ ((uint64_t)s * 0x0101010101010101ull);
-            const uint64_t z = (x - 0x0101010101010101ull) & ~x & 0x8080808080808080ull;
-            const int owner = __ffs(__ballot_sync(LFC_FULL, z != 0)) - 1;
-            const uint32_t up = __shfl_up_sync(LFC_FULL, (uint32_t)(v >> 56), 1);
-            const uint64_t shifted = (v << 8) | (lane == 0 ? (uint64_t)s : (uint64_t)up);
-            if (lane < owner) {
-                v = shifted;
-            } else if (lane == owner) {
-                const int byte = (__ffsll((long long)z) - 1) >> 3;  // lowest flag is the true zero
-                const uint64_t mask = byte == 7 ? ~0ull : ((1ull << (8 * (byte + 1))) - 1ull);
-                v = (shifted & mask) | (v & ~mask);
-                idxbuf[k] = (uint8_t)(owner * 8 + byte);
+        const bool valid = i < s1;
+        const uint32_t s = valid ? (uint32_t)seq[L[i]] : 256u + lane;
+        const uint32_t grp = __match_any_sync(LFC_FULL, s);
+        const uint32_t lower = grp & lt;
+        const bool fo = valid && lower == 0;
+        const uint32_t FO = __ballot_sync(LFC_FULL, fo);
+        const uint32_t LAST = __ballot_sync(LFC_FULL, valid && (grp & gt) == 0);
+        const uint32_t P = fo ? (uint32_t)posof[s] : 0u;
+        uint32_t gtm = 0, eqm = LFC_FULL;  // lanes with P_i > P
+#pragma unroll
+        for (int bb = 7; bb >= 0; bb--) {
+            const uint32_t Bb = __ballot_sync(LFC_FULL, (P >> bb) & 1u);
+            if ((P >> bb) & 1u) {
+                eqm &= Bb;
+            } else {
+                gtm |= eqm & Bb;
+                eqm &= ~Bb;
             }
         }
-        front = __shfl_sync(LFC_FULL, mys, cnt - 1);
+        const int j = lower ? 31 - __clz(lower) : -1;
+        const uint32_t pp = lower ? (uint32_t)(j + 1) : 0u;  // prev + 1, in 0..32
+        const uint32_t T = (uint32_t)(j + 1);
+        uint32_t gt2 = 0, eq2 = LFC_FULL;  // lanes with prev_i + 1 > j + 1
+#pragma unroll
+        for (int bb = 5; bb >= 0; bb--) {
+            const uint32_t Bb = __ballot_sync(LFC_FULL, (pp >> bb) & 1u);
+            if ((T >> bb) & 1u) {
+                eq2 &= Bb;
+            } else {
+                gt2 |= eq2 & Bb;
+                eq2 &= ~Bb;
+            }
+        }
+        uint32_t idx;
+        if (lower == 0) idx = P + __popc(gtm & FO & lt);
+        else idx = __popc(lt & ~((2u << j) - 1u) & ~gt2);
+        if (valid) out[i] = (uint8_t)idx;
+        // list update
+        const uint32_t D = __popc(FO);
+        const uint32_t maxP = __reduce_max_sync(LFC_FULL, P);
+        if (lane < 8) WP[lane] = 0;
         __syncwarp();
-        if (i < s1) out[i] = ((rep >> lane) & 1u) ? (uint8_t)0 : idxbuf[lane];
+        if (fo) atomicOr(&WP[P >> 5], 1u << (P & 31));
+        __syncwarp();
+        uint32_t mv[8];  // (new position << 8 | symbol) of the moved old entries, 0xFFFFFFFF if none
+        uint32_t before = 0;  // window positions in earlier words
+#pragma unroll
+        for (int r = 0; r < 8; r++) {
+            mv[r] = 0xFFFFFFFFu;
+            const uint32_t q = (uint32_t)lane + 32u * r;
+            if (32u * r > maxP) continue;
+            const uint32_t wd = WP[r];
+            if (q <= maxP && ((wd >> lane) & 1u) == 0) {
+                const uint32_t rank = before + __popc(wd & lt);
+                mv[r] = ((D + q - rank) << 8) | lst[q];
+            }
+            before += __popc(wd);
+        }
+        __syncwarp();
+#pragma unroll
+        for (int r = 0; r < 8; r++) {
+            if (mv[r] == 0xFFFFFFFFu) continue;
+            const uint32_t np = mv[r] >> 8, x = mv[r] & 0xFFu;
+            lst[np] = (uint8_t)x;
+            posof[x] = (uint8_t)np;
+        }
+        if ((LAST >> lane) & 1u) {
+            const uint32_t np = __popc(LAST & gt);
+            lst[np] = (uint8_t)s;
+            posof[s] = (uint8_t)np;
+        }
         __syncwarp();
     }
 }
