@@ -397,7 +397,7 @@ def main():
     peak, peak_kind = peaks()
     achieved = kbytes / 1e9 / (kms / 1e3) if kms > 0 else 0.0
     traffic = None
-    tr_path = os.path.join(ROOT, "profiles", kname + "_traffic.json")
+    tr_path = os.path.join(ROOT, "profiles", kname + "_traffic.txt")  # JSON text: one ncu capture, scaled
     if os.path.exists(tr_path):
         traffic = json.load(open(tr_path)).get("bytes_per_launch")
 
