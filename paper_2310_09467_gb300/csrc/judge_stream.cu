@@ -44,18 +44,21 @@ __device__ __forceinline__ uint16_t zz16(int32_t e) {
 
 size_t emit_all_smem_bytes(int p, int ts, int nslots) {
     const size_t cells = (size_t)(2 * p) * (size_t)((ts + 1) * p);
-    return cells * 2 * (size_t)(1 + nslots) + 256;
+    const size_t outpx = (size_t)p * (size_t)(ts * p);
+    return cells * 2 * (size_t)(1 + nslots) + outpx * 2 * 3 + 256;
 }
 
-// grid (tiles, frames, kind); kind 0 = raw base field, 1 = temporal difference
-__global__ void __launch_bounds__(kEmitThreads) emit_all_kernel(const JudgeFrame *__restrict__ frames,
-                                                                const uint8_t *__restrict__ cand, uint8_t *__restrict__ cstream,
-                                                                int64_t cslot, int kmax, int TS) {
-    extern __shared__ __align__(16) uint8_t esm[];
-    __shared__ int16_t slot_of[8][3][2];  // candidate index for (f, domain, ordering), -1 if absent
-    __shared__ int8_t eslot_of[8];        // intra residual field of f
-    __shared__ uint32_t fmask_ord[2];     // f values with any candidate in that ordering
-    const int fi = blockIdx.y, kind = blockIdx.z;
+// grid (tiles, frames, kind); kind 0 = raw base field, 1 = temporal difference.
+// Symbols do not depend on the ordering, only their positions do: per
+// predictor function f, the intra / inter / phase-space symbols of the
+// tile's pixels are computed once into shared memory (thread = pixel column,
+// p rows each), then every candidate of that f is written from there in
+// its ordering, consecutive threads on consecutive output positions.
+template <int kind>
+__device__ __forceinline__ void emit_all_body(const JudgeFrame *__restrict__ frames, const uint8_t *__restrict__ cand,
+                                              uint8_t *__restrict__ cstream, int64_t cslot, int kmax, int TS,
+                                              uint8_t *esm, int16_t (*slot_of)[3][2], int8_t *eslot_of) {
+    const int fi = blockIdx.y;
     const JudgeFrame &J = frames[fi];
     const FrameDev F = J.F;
     if (kind == 1 && F.prev == nullptr) return;
@@ -65,110 +68,138 @@ __global__ void __launch_bounds__(kEmitThreads) emit_all_kernel(const JudgeFrame
     const int t = blockIdx.x / tiles_s, s0 = (blockIdx.x % tiles_s) * TS, ns = min(TS, Nx - s0);
     const int TR = 2 * p, TC = (TS + 1) * p, ncols = (ns + 1) * p;
     const int cells = TR * TC;
-    uint16_t *Fb = reinterpret_cast<uint16_t *>(esm);
-    int16_t *E = reinterpret_cast<int16_t *>(esm) + cells;
-    uint32_t fset = 0;
+    const int nco = ns * p, npx = p * nco;  // output columns and pixels of the tile
+    uint32_t fset = 0, fany = 0;
     int nc = 0;
     for (int k = 0; k < J.K; k++) {
         const int id = cand[J.cand_off + k];
         if (((id >> 7) & 1) != kind || !cand_on(J, id)) continue;
         nc++;
         const int f = id & 15, dom = (id >> 4) & 3;
+        fany |= 1u << f;
         if (f && dom != 1) fset |= 1u << f;
     }
     if (nc == 0) return;
+    const int nslots = __popc(fset);
+    uint16_t *Fb = reinterpret_cast<uint16_t *>(esm);
+    int16_t *E = reinterpret_cast<int16_t *>(esm) + cells;
+    uint16_t *Sy = reinterpret_cast<uint16_t *>(E + (size_t)nslots * cells);  // [3][npx]
     if (threadIdx.x == 0) {
         for (int i = 0; i < 48; i++) (&slot_of[0][0][0])[i] = -1;
-        fmask_ord[0] = fmask_ord[1] = 0;
         for (int f = 0; f < 8; f++) eslot_of[f] = (int8_t)__popc(fset & ((1u << f) - 1u));
         for (int k = 0; k < J.K; k++) {
             const int id = cand[J.cand_off + k];
             if (((id >> 7) & 1) != kind || !cand_on(J, id)) continue;
-            const int f = id & 15, dom = (id >> 4) & 3, ord = (id >> 6) & 1;
-            slot_of[f][dom][ord] = (int16_t)k;
-            fmask_ord[ord] |= 1u << f;
+            slot_of[id & 15][(id >> 4) & 3][(id >> 6) & 1] = (int16_t)k;
         }
     }
     const int y0 = (t - 1) * p, x0 = (s0 - 1) * p;
-    for (int q = threadIdx.x; q < TR * ncols; q += blockDim.x) {
-        const int ly = q / ncols, lx = q - ly * ncols;
-        const int y = y0 + ly, x = x0 + lx;
-        uint32_t v = 0;
-        if (y >= 0 && x >= 0) {
-            const size_t k = (size_t)y * W + x;
-            v = __ldg(F.X + k);
-            if (kind) v = (v - (uint32_t)__ldg(F.prev + k)) & 0xFFFFu;
+    for (int lx = threadIdx.x; lx < ncols; lx += blockDim.x) {  // column per thread, rows in a loop
+        const int x = x0 + lx;
+        for (int ly = 0; ly < TR; ly++) {
+            const int y = y0 + ly;
+            uint32_t v = 0;
+            if (y >= 0 && x >= 0) {
+                const size_t k = (size_t)y * W + x;
+                v = __ldg(F.X + k);
+                if (kind) v = (v - (uint32_t)__ldg(F.prev + k)) & 0xFFFFu;
+            }
+            Fb[ly * TC + lx] = (uint16_t)v;
         }
-        Fb[ly * TC + lx] = (uint16_t)v;
     }
     __syncthreads();
-#define FVAL(idx) (kind ? (int32_t)(int16_t)Fb[idx] : (int32_t)Fb[idx])
+#define FVAL(idx) (kind ? (int32_t)(int16_t)Fb[idx] : (int32_t)Fb[idx])  // kind is a template constant
     // intra residual fields (signed 16-bit) for every f in use
-    for (int q = threadIdx.x; q < TR * ncols; q += blockDim.x) {
-        const int ly = q / ncols, lx = q - ly * ncols;
-        const int v = ly % p, u = lx % p;
-        const int idx = ly * TC + lx;
-        const int32_t Xv = FVAL(idx);
-        const int32_t A = u > 0 ? FVAL(idx - 1) : 0;
-        const int32_t B = v > 0 ? FVAL(idx - TC) : 0;
-        const int32_t C = (u > 0 && v > 0) ? FVAL(idx - TC - 1) : 0;
+    for (int lx = threadIdx.x; lx < ncols; lx += blockDim.x) {
+        const int u = lx % p;
+        for (int ly = 0; ly < TR; ly++) {
+            const int v = ly < p ? ly : ly - p;  // TR = 2p rows
+            const int idx = ly * TC + lx;
+            const int32_t Xv = FVAL(idx);
+            const int32_t A = u > 0 ? FVAL(idx - 1) : 0;
+            const int32_t B = v > 0 ? FVAL(idx - TC) : 0;
+            const int32_t C = (u > 0 && v > 0) ? FVAL(idx - TC - 1) : 0;
 #pragma unroll
-        for (int f = 1; f < 8; f++)
-            if (fset & (1u << f)) E[(size_t)eslot_of[f] * cells + idx] = (int16_t)(Xv - g_pred(f, v, u, A, B, C));
+            for (int f = 1; f < 8; f++)
+                if (fset & (1u << f)) E[(size_t)eslot_of[f] * cells + idx] = (int16_t)(Xv - g_pred(f, v, u, A, B, C));
+        }
     }
     __syncthreads();
-    const int n_cols_out = ns * p;
     uint16_t *base = reinterpret_cast<uint16_t *>(cstream + (size_t)fi * kmax * (size_t)cslot);
     const size_t cslot16 = (size_t)cslot / 2;
-    for (int ord = 0; ord < 2; ord++) {
-        const uint32_t fm = fmask_ord[ord];
-        if (!fm || (int)threadIdx.x >= n_cols_out) continue;
-        int lx, s;
-        int64_t pos0, pstep;
-        if (ord == 0) {  // thread = raw column; rows r -> raw rows t*p + r
-            const int lc = threadIdx.x;
-            lx = p + lc;
-            s = s0 + lc / p;
-            pos0 = (int64_t)(t * p) * W + (int64_t)s0 * p + lc;
-            pstep = W;
-        } else {         // thread = (u, lenslet); rows r -> view rows (v = r) * Ny + t
-            const int u = threadIdx.x / ns, si = threadIdx.x - u * ns;
-            lx = p + si * p + u;
-            s = s0 + si;
-            pos0 = (int64_t)t * W + (int64_t)u * Nx + s0 + si;
-            pstep = (int64_t)Ny * W;
-        }
-        for (int r = 0; r < p; r++) {
-            const int idx = (p + r) * TC + lx;
-            const int64_t pos = pos0 + r * pstep;
-            const int32_t Xv = FVAL(idx);
-            if (fm & 1u) {
-                const int k = slot_of[0][0][ord];
-                base[(size_t)k * cslot16 + pos] = kind ? zz16(Xv) : (uint16_t)Xv;
-            }
-            const int32_t XA = s > 0 ? FVAL(idx - p) : 0;
-            const int32_t XB = t > 0 ? FVAL(idx - p * TC) : 0;
-            const int32_t XC = (s > 0 && t > 0) ? FVAL(idx - p * TC - p) : 0;
+    // view-major write-out: thread j -> (u, si) = (j / ns, j % ns), rows v
+    const int vm_j = threadIdx.x, vm_u = vm_j / ns, vm_si = vm_j - vm_u * ns;
 #pragma unroll
-            for (int f = 1; f < 8; f++) {
-                if (!(fm & (1u << f))) continue;
-                const int k0 = slot_of[f][0][ord], k1 = slot_of[f][1][ord], k2 = slot_of[f][2][ord];
-                if (k1 >= 0) base[(size_t)k1 * cslot16 + pos] = zz16(Xv - g_pred(f, t, s, XA, XB, XC));
-                if (k0 >= 0 || k2 >= 0) {
-                    const int16_t *Ef = E + (size_t)eslot_of[f] * cells;
+    for (int f = 0; f < 8; f++) {  // unrolled: the predictor of f is a constant
+        if (!((fany >> f) & 1u)) continue;
+        const bool n0 = slot_of[f][0][0] >= 0 || slot_of[f][0][1] >= 0;
+        const bool n1 = f && (slot_of[f][1][0] >= 0 || slot_of[f][1][1] >= 0);
+        const bool n2 = f && (slot_of[f][2][0] >= 0 || slot_of[f][2][1] >= 0);
+        const int16_t *Ef = E + (size_t)(f ? eslot_of[f] : 0) * cells;
+        for (int c = threadIdx.x, sc = c / p; c < nco; c += blockDim.x, sc = c / p) {
+            const int lx = p + c, s = s0 + sc;
+            for (int r = 0; r < p; r++) {
+                const int idx = (p + r) * TC + lx, q = r * nco + c;
+                const int32_t Xv = FVAL(idx);
+                if (f == 0) {
+                    Sy[q] = kind ? zz16(Xv) : (uint16_t)Xv;
+                    continue;
+                }
+                if (n1) {
+                    const int32_t XA = s > 0 ? FVAL(idx - p) : 0;
+                    const int32_t XB = t > 0 ? FVAL(idx - p * TC) : 0;
+                    const int32_t XC = (s > 0 && t > 0) ? FVAL(idx - p * TC - p) : 0;
+                    Sy[npx + q] = zz16(Xv - g_pred(f, t, s, XA, XB, XC));
+                }
+                if (n0 || n2) {
                     const int32_t e = Ef[idx];
-                    if (k0 >= 0) base[(size_t)k0 * cslot16 + pos] = zz16(e);
-                    if (k2 >= 0) {
+                    if (n0) Sy[q] = zz16(e);
+                    if (n2) {
                         const int32_t eA = s > 0 ? Ef[idx - p] : 0;
                         const int32_t eB = t > 0 ? Ef[idx - p * TC] : 0;
                         const int32_t eC = (s > 0 && t > 0) ? Ef[idx - p * TC - p] : 0;
-                        base[(size_t)k2 * cslot16 + pos] = zz16(e - g_pred(f, t, s, eA, eB, eC));
+                        Sy[2 * npx + q] = zz16(e - g_pred(f, t, s, eA, eB, eC));
                     }
                 }
             }
         }
+        __syncthreads();
+        for (int dom = 0; dom < 3; dom++) {
+            const uint16_t *src = Sy + (size_t)dom * npx;
+            const int k0 = slot_of[f][dom][0], k1 = slot_of[f][dom][1];
+            if (k0 >= 0) {  // raw order: rows of nco consecutive symbols
+                uint16_t *dst = base + (size_t)k0 * cslot16 + (size_t)(t * p) * W + (size_t)s0 * p;
+                for (int r = 0; r < p; r++)
+                    for (int c = threadIdx.x; c < nco; c += blockDim.x) dst[(size_t)r * W + c] = src[r * nco + c];
+            }
+            if (k1 >= 0) {  // view-major order: runs of ns symbols per (v, u)
+                uint16_t *dst = base + (size_t)k1 * cslot16 + (size_t)t * W + s0;
+                if (p * ns <= (int)blockDim.x) {
+                    if (vm_j < p * ns)
+                        for (int v = 0; v < p; v++)
+                            dst[(size_t)v * Ny * W + (size_t)vm_u * Nx + vm_si] = src[v * nco + vm_si * p + vm_u];
+                } else {
+                    for (int v = 0; v < p; v++)
+                        for (int j = threadIdx.x; j < p * ns; j += blockDim.x) {
+                            const int u = j / ns, si = j - u * ns;
+                            dst[(size_t)v * Ny * W + (size_t)u * Nx + si] = src[v * nco + si * p + u];
+                        }
+                }
+            }
+        }
+        __syncthreads();
     }
 #undef FVAL
+}
+
+__global__ void __launch_bounds__(kEmitThreads) emit_all_kernel(const JudgeFrame *__restrict__ frames,
+                                                                const uint8_t *__restrict__ cand, uint8_t *__restrict__ cstream,
+                                                                int64_t cslot, int kmax, int TS) {
+    extern __shared__ __align__(16) uint8_t esm[];
+    __shared__ int16_t slot_of[8][3][2];  // candidate index for (f, domain, ordering), -1 if absent
+    __shared__ int8_t eslot_of[8];        // intra residual field of f
+    if (blockIdx.z == 0) emit_all_body<0>(frames, cand, cstream, cslot, kmax, TS, esm, slot_of, eslot_of);
+    else emit_all_body<1>(frames, cand, cstream, cslot, kmax, TS, esm, slot_of, eslot_of);
 }
 
 // ------------------------------------------------------ pair-chain histogram
