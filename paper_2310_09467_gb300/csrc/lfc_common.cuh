@@ -146,7 +146,7 @@ struct BlockState {
     uint32_t crc;          // CRC-32/BZIP2 of the block input (word 8)
     uint32_t stream_bytes; // packed stream length
     uint32_t stream_bits;
-    uint32_t pad0;
+    uint32_t data_bit0;    // first bit of the Huffman-coded data in the stream
     uint32_t in_use[8];    // bytes present in the block
 };
 static_assert(sizeof(BlockState) == 80, "BlockState layout");

@@ -543,65 +543,142 @@ __global__ void __launch_bounds__(kHuffThreads) huffman_kernel(BlockState *__res
 
 // ------------------------------------------------------------ bit packing
 // Bits are numbered from the start of the stream; bit P lands in word P/32 at
-// bit 31 - P%32 (MSB first), and words are byte-swapped at the end.
+// bit 31 - P%32 (MSB first). Words are stored byte-swapped (so the bytes
+// come out in stream order); swapping commutes with OR, so partial words
+// from different writers are swapped first and OR-ed into zeroed memory.
+__device__ __forceinline__ uint32_t bswap32(uint32_t w) { return __byte_perm(w, 0u, 0x0123); }
+
 __device__ __forceinline__ void put_bits(uint32_t *words, uint64_t pos, uint32_t value, int nbits) {
     if (nbits == 0) return;
     const int sh = (int)(pos & 31);
     const uint64_t v = (uint64_t)value << (64 - nbits - sh);
     const uint32_t hi = (uint32_t)(v >> 32), lo = (uint32_t)v;
-    if (hi) atomicOr(&words[pos >> 5], hi);
-    if (lo) atomicOr(&words[(pos >> 5) + 1], lo);
+    if (hi) atomicOr(&words[pos >> 5], bswap32(hi));
+    if (lo) atomicOr(&words[(pos >> 5) + 1], bswap32(lo));
 }
 
-constexpr int kPackThreads = 1024;
+// MTF index of a selector of table s (tables listed 0..ng-1 initially),
+// given last[t] = position of the latest earlier selector of table t (-1 if
+// none): the number of tables used since s was last used, or, before its
+// first use, the tables used so far plus the unused tables below s.
+__device__ __forceinline__ int selector_mtf(int s, const int (&last)[kMaxGroups], int ng) {
+    int ls = -1;
+#pragma unroll
+    for (int t = 0; t < kMaxGroups; t++)
+        if (t == s) ls = last[t];
+    int j = 0;
+#pragma unroll
+    for (int t = 0; t < kMaxGroups; t++) {
+        if (t >= ng || t == s) continue;
+        j += ls >= 0 ? (last[t] > ls) : (last[t] >= 0 || t < s);
+    }
+    return j;
+}
 
-__global__ void __launch_bounds__(kPackThreads) pack_kernel(BlockState *__restrict__ st, const uint16_t *__restrict__ sym_all,
-                                                            const uint8_t *__restrict__ sel_all, const uint8_t *__restrict__ lens_all,
-                                                            const uint32_t *__restrict__ codes_all, uint32_t *__restrict__ packed_all,
-                                                            int64_t stream_words) {
+__device__ __forceinline__ void set_last(int (&last)[kMaxGroups], int s, int i) {
+#pragma unroll
+    for (int t = 0; t < kMaxGroups; t++)
+        if (t == s) last[t] = i;
+}
+
+// Data packing is a scan over tiles of 128 selector groups (50 symbols each):
+// group bit lengths and tile sums (1); per block the stream layout, the tile
+// offsets, the header, selector, code-length and trailer sections (2); each
+// group's codes from its bit offset, whole words stored, the two boundary
+// words OR-ed (3).
+constexpr int kPackGroups = 128;                                           // groups per tile = threads
+constexpr int kPackTiles = (kMaxSelectors + kPackGroups - 1) / kPackGroups;  // 141
+static_assert(kPackTiles <= kTilesPerBlock, "pack tile records live in the per-block tile scratch");
+constexpr int kLayoutThreads = 1024;
+
+__device__ __forceinline__ void load_tables(const uint8_t *lens_all, const uint32_t *codes_all, int b, int ng,
+                                            uint8_t (*len)[kMaxAlpha], uint32_t (*code)[kMaxAlpha]) {
+    for (int i = threadIdx.x; i < ng * kMaxAlpha; i += blockDim.x) {
+        const int t = i / kMaxAlpha, v = i - t * kMaxAlpha;
+        len[t][v] = lens_all[((size_t)b * kMaxGroups + t) * kMaxAlpha + v];
+        if (code) code[t][v] = codes_all[((size_t)b * kMaxGroups + t) * kMaxAlpha + v];
+    }
+}
+
+__global__ void __launch_bounds__(kPackGroups) pack_bits_kernel(const BlockState *__restrict__ st,
+                                                                const uint16_t *__restrict__ sym_all,
+                                                                const uint8_t *__restrict__ sel_all,
+                                                                const uint8_t *__restrict__ lens_all,
+                                                                uint16_t *__restrict__ gbits_all,
+                                                                int32_t *__restrict__ aux_all) {
     __shared__ uint8_t len[kMaxGroups][kMaxAlpha];
-    __shared__ uint32_t code[kMaxGroups][kMaxAlpha];
+    __shared__ int sh[33];
+    const int b = blockIdx.y, tile = blockIdx.x;
+    const BlockState S = st[b];
+    if (tile * kPackGroups >= S.n_sel) return;
+    load_tables(lens_all, nullptr, b, S.n_groups, len, nullptr);
+    __syncthreads();
+    const int gi = tile * kPackGroups + (int)threadIdx.x;
+    int bits = 0;
+    if (gi < S.n_sel) {
+        const uint16_t *sym = sym_all + (size_t)b * kSymStride;
+        const uint8_t *lt = len[sel_all[(size_t)b * kMaxSelectors + gi]];
+        const int a = gi * 50, e = min(S.n_mtf, a + 50);
+        for (int i = a; i < e; i++) bits += lt[sym[i]];
+        gbits_all[(size_t)b * (kBlockCap / 2) + gi] = (uint16_t)bits;
+    }
+    int total;
+    block_excl_sum<int>(bits, sh, &total);
+    if (threadIdx.x == 0) aux_all[((size_t)b * kTilesPerBlock + tile) * 4] = total;
+}
+
+__global__ void __launch_bounds__(kLayoutThreads) pack_layout_kernel(BlockState *__restrict__ st,
+                                                                     const uint8_t *__restrict__ sel_all,
+                                                                     const uint8_t *__restrict__ lens_all,
+                                                                     int32_t *__restrict__ aux_all,
+                                                                     uint32_t *__restrict__ packed_all, int64_t stream_words) {
+    __shared__ uint8_t len[kMaxGroups][kMaxAlpha];
     __shared__ uint64_t sh64[33];
+    __shared__ int shi[33];
     __shared__ uint32_t tbl_bits[kMaxGroups];
-    __shared__ uint64_t base_bits[8];
+    __shared__ uint64_t base_bits[4];
     const int b = blockIdx.x;
     const BlockState S = st[b];
-    const int ng = S.n_groups, nsel = S.n_sel, n_mtf = S.n_mtf, alpha = S.n_in_use + 2;
-    const uint16_t *sym = sym_all + (size_t)b * kSymStride;
+    const int ng = S.n_groups, nsel = S.n_sel, alpha = S.n_in_use + 2;
     const uint8_t *sel = sel_all + (size_t)b * kMaxSelectors;
     uint32_t *words = packed_all + (size_t)b * stream_words;
-    for (int i = threadIdx.x; i < ng * kMaxAlpha; i += blockDim.x) {
-        const int t = i / kMaxAlpha, v = i % kMaxAlpha;
-        len[t][v] = lens_all[((size_t)b * kMaxGroups + t) * kMaxAlpha + v];
-        code[t][v] = codes_all[((size_t)b * kMaxGroups + t) * kMaxAlpha + v];
-    }
+    int32_t *aux = aux_all + (size_t)b * kTilesPerBlock * 4;
+    load_tables(lens_all, nullptr, b, ng, len, nullptr);
     uint32_t used16 = 0;
     for (int i = 0; i < 16; i++) {
         const uint32_t half = (S.in_use[i >> 1] >> ((i & 1) * 16)) & 0xFFFFu;
         if (half) used16 |= 1u << (15 - i);
     }
     __syncthreads();
-    // --- selector MTF indices (list of ng tables, initially 0..ng-1)
+    // data tiles: exclusive offsets (one tile per thread, <= 141 tiles)
+    const int ntiles = (nsel + kPackGroups - 1) / kPackGroups;
+    const uint64_t tb = (int)threadIdx.x < ntiles ? (uint64_t)(uint32_t)aux[threadIdx.x * 4] : 0ull;
+    uint64_t data_total;
+    const uint64_t toff = block_excl_sum<uint64_t>(tb, sh64, &data_total);
+    if ((int)threadIdx.x < ntiles) aux[threadIdx.x * 4 + 1] = (int32_t)toff;
+    // selector MTF: each thread's span starts from the last use of every table
+    // before it (exclusive max-scans), then replays its span
     const int T = blockDim.x;
     const int sper = (nsel + T - 1) / T;
     const int sa = min(nsel, (int)threadIdx.x * sper), se = min(nsel, sa + sper);
+    int last0[kMaxGroups];
+#pragma unroll
+    for (int t = 0; t < kMaxGroups; t++) last0[t] = -1;
+    for (int i = sa; i < se; i++) set_last(last0, sel[i], i);
+#pragma unroll
+    for (int t = 0; t < kMaxGroups; t++) last0[t] = block_excl_max(last0[t], shi);
+    int last[kMaxGroups];
+#pragma unroll
+    for (int t = 0; t < kMaxGroups; t++) last[t] = last0[t];
     uint64_t sbits = 0;
     for (int i = sa; i < se; i++) {
-        const int s = sel[i];
-        uint32_t D = 0;
-        int j = -1;
-        for (int q = i - 1; q >= 0; q--) {
-            const int v = sel[q];
-            if (v == s) { j = __popc(D); break; }
-            D |= 1u << v;
-            if (__popc(D) == ng - 1) { j = ng - 1; break; }
-        }
-        if (j < 0) j = __popc(D) + __popc(((1u << s) - 1u) & ~D);
-        sbits += (uint64_t)j + 1;
+        const int sv = sel[i];
+        sbits += (uint64_t)selector_mtf(sv, last, ng) + 1;
+        set_last(last, sv, i);
     }
     uint64_t sel_total;
-    uint64_t sel_off = block_excl_sum<uint64_t>(sbits, sh64, &sel_total);
-    // --- code-length section bits per table (warp t)
+    const uint64_t sel_off = block_excl_sum<uint64_t>(sbits, sh64, &sel_total);
+    // code-length section bits per table (warp t)
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if (w < ng) {
         uint32_t bits = 0;
@@ -612,14 +689,7 @@ __global__ void __launch_bounds__(kPackThreads) pack_kernel(BlockState *__restri
         bits = warp_sum(bits);
         if (lane == 0) tbl_bits[w] = bits + 5u;
     }
-    // --- data bits
-    const int dper = (n_mtf + T - 1) / T;
-    const int da = min(n_mtf, (int)threadIdx.x * dper), de = min(n_mtf, da + dper);
-    uint64_t dbits = 0;
-    for (int i = da; i < de; i++) dbits += len[sel[i / 50]][sym[i]];
-    uint64_t data_total;
-    uint64_t data_off = block_excl_sum<uint64_t>(dbits, sh64, &data_total);
-    // layout
+    __syncthreads();
     if (threadIdx.x == 0) {
         uint64_t p = 32 + 48 + 32 + 1 + 24 + 16 + 16ull * __popc(used16) + 3 + 15;
         base_bits[0] = p;                       // selectors start
@@ -637,7 +707,6 @@ __global__ void __launch_bounds__(kPackThreads) pack_kernel(BlockState *__restri
     const int64_t nwords = (int64_t)((total_bits + 31) >> 5);
     for (int64_t i = threadIdx.x; i < nwords + 1 && i < stream_words; i += blockDim.x) words[i] = 0;
     __syncthreads();
-    // --- header (thread 0)
     if (threadIdx.x == 0) {
         uint64_t p = 0;
         put_bits(words, p, 0x425A6839u, 32); p += 32;  // "BZh9"
@@ -655,74 +724,84 @@ __global__ void __launch_bounds__(kPackThreads) pack_kernel(BlockState *__restri
         }
         put_bits(words, p, (uint32_t)ng, 3); p += 3;
         put_bits(words, p, (uint32_t)nsel, 15); p += 15;
-        // trailer
         uint64_t q = base_bits[2];
         put_bits(words, q, 0x177245u, 24); q += 24;
         put_bits(words, q, 0x385090u, 24); q += 24;
         put_bits(words, q, S.crc, 32);
+        st[b].stream_bits = (uint32_t)total_bits;
+        st[b].stream_bytes = (uint32_t)(total_bits >> 3);
+        st[b].data_bit0 = (uint32_t)base_bits[1];
     }
-    // --- selectors
-    {
+    {   // selectors: j ones then a zero
         uint64_t p = base_bits[0] + sel_off;
+        for (int t = 0; t < kMaxGroups; t++) last[t] = last0[t];
         for (int i = sa; i < se; i++) {
-            const int s = sel[i];
-            uint32_t D = 0;
-            int j = -1;
-            for (int q = i - 1; q >= 0; q--) {
-                const int v = sel[q];
-                if (v == s) { j = __popc(D); break; }
-                D |= 1u << v;
-                if (__popc(D) == ng - 1) { j = ng - 1; break; }
-            }
-            if (j < 0) j = __popc(D) + __popc(((1u << s) - 1u) & ~D);
+            const int sv = sel[i];
+            const int j = selector_mtf(sv, last, ng);
+            set_last(last, sv, i);
             put_bits(words, p, ((1u << j) - 1u) << 1, j + 1);
             p += (uint64_t)j + 1;
         }
     }
-    // --- code lengths (warp t, lane 0: sequential deltas)
-    if (w < ng && lane == 0) {
+    if (w < ng) {  // code lengths: 5-bit start, then per symbol |d| x ("10" up or "11" down) and a '0'
         uint64_t p = base_bits[0] + sel_total;
         for (int t = 0; t < w; t++) p += tbl_bits[t];
-        int cur = len[w][0];
-        put_bits(words, p, (uint32_t)cur, 5); p += 5;
-        for (int v = 0; v < alpha; v++) {
-            const int target = len[w][v];
-            while (cur < target) { put_bits(words, p, 2u, 2); p += 2; cur++; }
-            while (cur > target) { put_bits(words, p, 3u, 2); p += 2; cur--; }
-            p += 1;  // '0'
+        if (lane == 0) put_bits(words, p, (uint32_t)len[w][0], 5);
+        p += 5;
+        for (int v0 = 0; v0 < alpha; v0 += 32) {
+            const int v = v0 + lane;
+            const int d = v < alpha ? (v == 0 ? 0 : (int)len[w][v] - (int)len[w][v - 1]) : 0;
+            const uint32_t nb = v < alpha ? 2u * (uint32_t)abs(d) + 1u : 0u;
+            const uint32_t incl = warp_incl_sum(nb);
+            uint64_t q = p + incl - nb;
+            for (int k = 0; k < abs(d); k++, q += 2) put_bits(words, q, d > 0 ? 2u : 3u, 2);
+            p += __shfl_sync(LFC_FULL, incl, 31);
         }
     }
-    // --- data: each thread packs its span into whole words; only the span's
-    // first and last words are shared with neighbours (atomicOr)
-    {
-        const uint64_t p0 = base_bits[1] + data_off, p1 = p0 + dbits;
-        uint64_t acc = 0;   // pending bits, left-aligned
-        int nacc = 0;
-        uint64_t wpos = p0 & ~31ull;  // bit position of the word being built
-        nacc = (int)(p0 - wpos);      // leading bits owned by the previous span (zeros)
-        for (int i = da; i < de; i++) {
-            const int t = sel[i / 50];
-            const uint32_t s = sym[i];
-            const int l = len[t][s];
-            acc |= (uint64_t)code[t][s] << (64 - nacc - l);
-            nacc += l;
-            if (nacc >= 32) {
-                const uint32_t word = (uint32_t)(acc >> 32);
-                if (wpos < p0) atomicOr(&words[wpos >> 5], word);
-                else words[wpos >> 5] = word;
-                acc <<= 32;
-                nacc -= 32;
-                wpos += 32;
-            }
+}
+
+__global__ void __launch_bounds__(kPackGroups) pack_data_kernel(const BlockState *__restrict__ st,
+                                                                const uint16_t *__restrict__ sym_all,
+                                                                const uint8_t *__restrict__ sel_all,
+                                                                const uint8_t *__restrict__ lens_all,
+                                                                const uint32_t *__restrict__ codes_all,
+                                                                const uint16_t *__restrict__ gbits_all,
+                                                                const int32_t *__restrict__ aux_all,
+                                                                uint32_t *__restrict__ packed_all, int64_t stream_words) {
+    __shared__ uint8_t len[kMaxGroups][kMaxAlpha];
+    __shared__ uint32_t code[kMaxGroups][kMaxAlpha];
+    __shared__ int sh[33];
+    const int b = blockIdx.y, tile = blockIdx.x;
+    const BlockState S = st[b];
+    if (tile * kPackGroups >= S.n_sel) return;
+    load_tables(lens_all, codes_all, b, S.n_groups, len, code);
+    const int gi = tile * kPackGroups + (int)threadIdx.x;
+    const int bits = gi < S.n_sel ? (int)gbits_all[(size_t)b * (kBlockCap / 2) + gi] : 0;
+    const int off = block_excl_sum<int>(bits, sh, nullptr);  // also orders the table loads
+    if (gi >= S.n_sel || bits == 0) return;
+    uint32_t *words = packed_all + (size_t)b * stream_words;
+    const uint64_t p0 = (uint64_t)S.data_bit0 + (uint32_t)aux_all[((size_t)b * kTilesPerBlock + tile) * 4 + 1] + off;
+    const int t = sel_all[(size_t)b * kMaxSelectors + gi];
+    const uint16_t *sym = sym_all + (size_t)b * kSymStride;
+    const int a = gi * 50, e = min(S.n_mtf, a + 50);
+    uint64_t acc = 0;                 // pending bits, left-aligned
+    uint64_t wpos = p0 & ~31ull;      // bit position of the word being built
+    int nacc = (int)(p0 - wpos);      // leading bits owned by the previous group (zeros)
+    for (int i = a; i < e; i++) {
+        const uint32_t sv = sym[i];
+        const int l = len[t][sv];
+        acc |= (uint64_t)code[t][sv] << (64 - nacc - l);
+        nacc += l;
+        if (nacc >= 32) {
+            const uint32_t word = bswap32((uint32_t)(acc >> 32));
+            if (wpos < p0) atomicOr(&words[wpos >> 5], word);  // shared with the previous group
+            else words[wpos >> 5] = word;
+            acc <<= 32;
+            nacc -= 32;
+            wpos += 32;
         }
-        if (nacc > 0 && p1 > p0) atomicOr(&words[wpos >> 5], (uint32_t)(acc >> 32));
     }
-    __syncthreads();
-    for (int64_t i = threadIdx.x; i < nwords; i += blockDim.x) words[i] = __byte_perm(words[i], 0, 0x0123);
-    if (threadIdx.x == 0) {
-        st[b].stream_bits = (uint32_t)total_bits;
-        st[b].stream_bytes = (uint32_t)(total_bits >> 3);
-    }
+    if (nacc > 0) atomicOr(&words[wpos >> 5], bswap32((uint32_t)(acc >> 32)));  // shared with the next
 }
 
 cudaError_t launch_mtf_rle2(lfc_plan P, int nblocks) {
@@ -749,9 +828,15 @@ cudaError_t launch_huffman(lfc_plan P, int nblocks) {
 
 cudaError_t launch_pack(lfc_plan P, int nblocks) {
     Workspace &ws = P->ws;
-    pack_kernel<<<nblocks, kPackThreads, 0, P->stream>>>(ws.bstate, ws.sym, ws.sel, ws.lens, ws.codes, ws.packed,
-                                                         ws.stream_words);
-    count_launches(P, 1);
+    // group bit lengths live in the MTF index slots, free once RLE2 has run
+    uint16_t *gbits = reinterpret_cast<uint16_t *>(ws.mtfidx);
+    const dim3 grid(kPackTiles, nblocks);
+    pack_bits_kernel<<<grid, kPackGroups, 0, P->stream>>>(ws.bstate, ws.sym, ws.sel, ws.lens, gbits, ws.tileaux);
+    pack_layout_kernel<<<nblocks, kLayoutThreads, 0, P->stream>>>(ws.bstate, ws.sel, ws.lens, ws.tileaux, ws.packed,
+                                                                  ws.stream_words);
+    pack_data_kernel<<<grid, kPackGroups, 0, P->stream>>>(ws.bstate, ws.sym, ws.sel, ws.lens, ws.codes, gbits,
+                                                          ws.tileaux, ws.packed, ws.stream_words);
+    count_launches(P, 3);
     return cudaGetLastError();
 }
 
