@@ -224,7 +224,7 @@ extern "C" int lfc_plan_block_capacity(lfc_plan P) { return P ? P->block_cap : 0
 static void free_ws(Workspace &w) {
     void *ptrs[] = {w.hist, w.summ, w.scores, w.choice, w.jframes, w.cand, w.l2tab, w.stream, w.blocks, w.bstate,
                     w.rle, w.sa, w.sa2, w.rank, w.act, w.act2, w.val, w.val2, w.keys, w.keys2, w.tilecnt, w.tileaux, w.bwt,
-                    w.mtfidx, w.mtflists, w.mtfrec, w.mtfreclen, w.sym, w.freq, w.sel, w.lens, w.codes, w.packed, w.cstream, w.masks, w.class_ids,
+                    w.mtfidx, w.mtflists, w.mtfrec, w.mtfreclen, w.sym, w.freq, w.rfreq, w.sel, w.lens, w.codes, w.packed, w.cstream, w.masks, w.class_ids,
                     w.act_total, w.block_dst, w.frame_crc, w.crc_part, w.chunk_desc, w.dec_tt};
     for (void *p : ptrs)
         if (p) cudaFree(p);
@@ -323,6 +323,7 @@ extern "C" int lfc_plan_create(const lfc_config *cfg, void *cuda_stream, lfc_pla
     AL(mtfreclen, (size_t)BC * kTilesPerBlock);
     AL(sym, (size_t)BC * (kBlockCap + 64));
     AL(freq, (size_t)BC * kMaxAlpha);
+    AL(rfreq, (size_t)BC * kMaxGroups * kMaxAlpha);
     AL(sel, (size_t)BC * kMaxSelectors);
     AL(lens, (size_t)BC * kMaxGroups * kMaxAlpha);
     AL(codes, (size_t)BC * kMaxGroups * kMaxAlpha);

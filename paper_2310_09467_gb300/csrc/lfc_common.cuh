@@ -192,6 +192,7 @@ struct Workspace {
     int32_t *mtfreclen = nullptr;  // block_cap * kTilesPerBlock
     uint16_t *sym = nullptr;       // block_cap * (kBlockCap + 1)
     uint32_t *freq = nullptr;      // block_cap * kMaxAlpha
+    uint32_t *rfreq = nullptr;     // block_cap * kMaxGroups * kMaxAlpha, counts of a refinement pass
     uint8_t *sel = nullptr;        // block_cap * kMaxSelectors
     uint8_t *lens = nullptr;       // block_cap * 6 * 258
     uint32_t *codes = nullptr;     // block_cap * 6 * 258

@@ -406,139 +406,262 @@ __global__ void __launch_bounds__(kRle2Threads) rle2_write_kernel(const BlockSta
 // non-decreasing weight); over-long codes halve the weights (1 + w/2).
 struct HuffScratch {
     uint32_t w[kMaxAlpha];
-    uint32_t nw[kMaxAlpha];         // joined-node weights
-    uint16_t order[kMaxAlpha];      // leaves sorted by (w, symbol)
-    uint16_t kid[2][kMaxAlpha];     // children of joined node k (node ids)
-    uint8_t depth[2 * kMaxAlpha];
+    uint32_t lw[kMaxAlpha];          // leaf weights in (weight, symbol) order
+    uint32_t nw[kMaxAlpha];          // joined-node weights
+    uint16_t order[kMaxAlpha];       // leaves sorted by (w, symbol)
+    uint16_t par[2 * kMaxAlpha];     // parent of a node (leaves, then joined nodes)
+    uint16_t dist[2 * kMaxAlpha];    // pointer-jumping distance to par
 };
 
+// Keys (w << 9 | symbol) are distinct, so a key's rank is the count of
+// smaller keys; w < 2^21 (counts of one block), so the key fits 30 bits.
+// Node depths by pointer jumping: after r rounds par[n] is n's 2^r-th
+// ancestor (capped at the root) and dist[n] the distance to it; 9 rounds
+// cover depths up to 511 >= alpha - 1.
 __device__ void huff_lengths_warp(const uint32_t *freq, int alpha, int max_len, uint8_t *len_out, HuffScratch &S) {
+    constexpr int kQ = (kMaxAlpha + 31) / 32;       // leaves per lane
+    constexpr int kN = (2 * kMaxAlpha + 31) / 32;   // nodes per lane
     const int lane = threadIdx.x & 31;
     for (int i = lane; i < alpha; i += 32) S.w[i] = freq[i] ? freq[i] : 1u;
     __syncwarp();
+    const int nodes = 2 * alpha - 1, root = 2 * alpha - 2;
+    int longest = 0;
     for (;;) {
-        for (int i = lane; i < alpha; i += 32) {
-            const uint32_t wi = S.w[i];
-            int r = 0;
-            for (int j = 0; j < alpha; j++) {
-                const uint32_t wj = S.w[j];
-                r += (wj < wi) || (wj == wi && j < i);
+        uint32_t myk[kQ], rk[kQ];
+#pragma unroll
+        for (int q = 0; q < kQ; q++) {
+            const int i = lane + 32 * q;
+            myk[q] = i < alpha ? ((S.w[i] << 9) | (uint32_t)i) : 0xFFFFFFFFu;
+            rk[q] = 0;
+        }
+        for (int j = 0; j < alpha; j++) {
+            const uint32_t kj = (S.w[j] << 9) | (uint32_t)j;
+#pragma unroll
+            for (int q = 0; q < kQ; q++) rk[q] += kj < myk[q];
+        }
+#pragma unroll
+        for (int q = 0; q < kQ; q++) {
+            const int i = lane + 32 * q;
+            if (i < alpha) {
+                S.order[rk[q]] = (uint16_t)i;
+                S.lw[rk[q]] = S.w[i];
             }
-            S.order[r] = (uint16_t)i;
         }
         __syncwarp();
-        int longest = 0;
         if (lane == 0) {
-            int la = 0, nb = 0, lb = 0;  // leaf cursor, joined count, joined cursor
+            // two-queue merge: the two smallest (weight, key) nodes, a leaf
+            // before a joined node of equal weight (its key is smaller)
+            int la = 0, lb = 0, nb = 0;
+            uint32_t ha = S.lw[0], hb = 0;
             for (int k = 0; k < alpha - 1; k++) {
                 int pick[2];
                 uint32_t pw[2];
+#pragma unroll
                 for (int q = 0; q < 2; q++) {
-                    const bool haveA = la < alpha, haveB = lb < nb;
-                    bool takeA;
-                    if (!haveB) takeA = true;
-                    else if (!haveA) takeA = false;
-                    else takeA = S.w[S.order[la]] <= S.nw[lb];  // equal weight: leaf (smaller key)
-                    if (takeA) { pick[q] = S.order[la]; pw[q] = S.w[S.order[la]]; la++; }
-                    else { pick[q] = alpha + lb; pw[q] = S.nw[lb]; lb++; }
+                    const bool takeA = lb >= nb || (la < alpha && ha <= hb);
+                    if (takeA) {
+                        pick[q] = S.order[la];
+                        pw[q] = ha;
+                        la++;
+                        ha = la < alpha ? S.lw[la] : 0u;
+                    } else {
+                        pick[q] = alpha + lb;
+                        pw[q] = hb;
+                        lb++;
+                        hb = lb < nb ? S.nw[lb] : 0u;
+                    }
                 }
-                S.kid[0][k] = (uint16_t)pick[0];
-                S.kid[1][k] = (uint16_t)pick[1];
-                S.nw[nb++] = pw[0] + pw[1];
+                const uint32_t sw = pw[0] + pw[1];
+                S.par[pick[0]] = (uint16_t)(alpha + k);
+                S.par[pick[1]] = (uint16_t)(alpha + k);
+                S.nw[nb] = sw;
+                if (lb == nb) hb = sw;  // the joined queue was empty
+                nb++;
             }
-            // depths top-down: root is joined node alpha - 2
-            S.depth[alpha + alpha - 2] = 0;
-            for (int k = alpha - 2; k >= 0; k--) {
-                const uint8_t d = S.depth[alpha + k] + 1;
-                S.depth[S.kid[0][k]] = d;
-                S.depth[S.kid[1][k]] = d;
-            }
-            for (int i = 0; i < alpha; i++) longest = max(longest, (int)S.depth[i]);
+            S.par[root] = (uint16_t)root;
         }
-        longest = __shfl_sync(LFC_FULL, longest, 0);
         __syncwarp();
+        uint16_t pn[kN], dn[kN];
+#pragma unroll
+        for (int q = 0; q < kN; q++) {
+            const int n = lane + 32 * q;
+            if (n < nodes) S.dist[n] = n == root ? 0 : 1;
+        }
+        __syncwarp();
+        for (int round = 0; round < 9; round++) {
+#pragma unroll
+            for (int q = 0; q < kN; q++) {
+                const int n = lane + 32 * q;
+                if (n < nodes) {
+                    const int pp = S.par[n];
+                    dn[q] = (uint16_t)(S.dist[n] + S.dist[pp]);
+                    pn[q] = S.par[pp];
+                }
+            }
+            __syncwarp();
+#pragma unroll
+            for (int q = 0; q < kN; q++) {
+                const int n = lane + 32 * q;
+                if (n < nodes) {
+                    S.dist[n] = dn[q];
+                    S.par[n] = pn[q];
+                }
+            }
+            __syncwarp();
+        }
+        int mx = 0;
+        for (int i = lane; i < alpha; i += 32) mx = max(mx, (int)S.dist[i]);
+        longest = __reduce_max_sync(LFC_FULL, (unsigned)mx);
         if (longest <= max_len) break;
         for (int i = lane; i < alpha; i += 32) S.w[i] = 1u + S.w[i] / 2u;
         __syncwarp();
     }
-    for (int i = lane; i < alpha; i += 32) len_out[i] = S.depth[i];
+    for (int i = lane; i < alpha; i += 32) len_out[i] = (uint8_t)S.dist[i];
     __syncwarp();
 }
 
-constexpr int kHuffThreads = 256;
+constexpr int kPackGroups = 128;                                           // selector groups per tile = threads
+constexpr int kPackTiles = (kMaxSelectors + kPackGroups - 1) / kPackGroups;  // 141
+constexpr int kTileSyms = kPackGroups * 50;                                   // symbols of a tile
 
-// One CTA per block: table count, initial partition by cumulative frequency,
-// four refinement passes (each 50-symbol group picks the cheapest table, ties
-// to the lower table, then every table is rebuilt from its groups' counts
-// with a 17-bit limit), canonical codes.
-__global__ void __launch_bounds__(kHuffThreads) huffman_kernel(BlockState *__restrict__ st, const uint16_t *__restrict__ sym_all,
-                                                               const uint32_t *__restrict__ freq_all, uint8_t *__restrict__ sel_all,
-                                                               uint8_t *__restrict__ lens_all, uint32_t *__restrict__ codes_all) {
-    __shared__ uint8_t len[kMaxGroups][kMaxAlpha];
-    __shared__ uint64_t packed[kMaxAlpha];
-    __shared__ uint32_t rfreq[kMaxGroups][kMaxAlpha];
-    __shared__ HuffScratch scratch[kMaxGroups];
+// Stage the symbols of a tile of selector groups in shared memory with
+// coalesced 16-byte loads (tile starts are 16-byte aligned); returns their count.
+__device__ __forceinline__ int stage_tile_syms(const uint16_t *sym, int tile, int n_mtf, uint16_t *ssym) {
+    const int a = tile * kTileSyms;
+    const int cnt = min(kTileSyms, n_mtf - a);
+    const int n8 = cnt >> 3;
+    const uint4 *src = reinterpret_cast<const uint4 *>(sym + a);
+    uint4 *dst = reinterpret_cast<uint4 *>(ssym);
+    for (int i = threadIdx.x; i < n8; i += blockDim.x) dst[i] = src[i];
+    for (int i = (n8 << 3) + threadIdx.x; i < cnt; i += blockDim.x) ssym[i] = sym[a + i];
+    return cnt;
+}
+
+// Table choice per block, in launches: the table count and the initial
+// partition by cumulative frequency (init); four refinement passes, each
+// "every 50-symbol group picks the cheapest table, ties to the lower" over
+// many CTAs (select) followed by "every table is rebuilt from its groups'
+// counts with a 17-bit limit" (build); canonical codes (codes).
+constexpr int kHuffBuildThreads = 32 * kMaxGroups;
+
+__global__ void __launch_bounds__(256) huff_init_kernel(BlockState *__restrict__ st, const uint32_t *__restrict__ freq_all,
+                                                        uint8_t *__restrict__ lens_all, uint32_t *__restrict__ rfreq_all) {
     const int b = blockIdx.x;
     const int n_mtf = st[b].n_mtf;
     const int alpha = st[b].n_in_use + 2;
     const int ng = n_mtf < 200 ? 2 : n_mtf < 600 ? 3 : n_mtf < 1200 ? 4 : n_mtf < 2400 ? 5 : 6;
-    const int nsel = (n_mtf + 49) / 50;
-    const uint16_t *sym = sym_all + (size_t)b * kSymStride;
-    const uint32_t *freq = freq_all + (size_t)b * kMaxAlpha;
-    uint8_t *sel = sel_all + (size_t)b * kMaxSelectors;
+    for (int i = threadIdx.x; i < kMaxGroups * kMaxAlpha; i += blockDim.x) rfreq_all[(size_t)b * kMaxGroups * kMaxAlpha + i] = 0;
     if (threadIdx.x == 0) {
+        const uint32_t *freq = freq_all + (size_t)b * kMaxAlpha;
+        uint8_t *len = lens_all + (size_t)b * kMaxGroups * kMaxAlpha;
         int64_t cum = 0;
         for (int v = 0; v < alpha; v++) {
             int64_t gsel = cum * ng / n_mtf;
             if (gsel > ng - 1) gsel = ng - 1;
-            for (int t = 0; t < ng; t++) len[t][v] = (uint8_t)(t == gsel ? 0 : 15);
+            for (int t = 0; t < ng; t++) len[t * kMaxAlpha + v] = (uint8_t)(t == gsel ? 0 : 15);
             cum += freq[v];
         }
         st[b].n_groups = ng;
-        st[b].n_sel = nsel;
+        st[b].n_sel = (n_mtf + 49) / 50;
+    }
+}
+
+// Thread per 50-symbol group: cost under every table (10-bit fields of one
+// 64-bit word per symbol; <= 50 x 17 bits), the cheapest table, and the
+// group's symbols added to that table's counts (RUNA / RUNB, the most common
+// symbols, in registers; the rest through shared memory, flushed per CTA).
+__global__ void __launch_bounds__(kPackGroups) huff_select_kernel(const BlockState *__restrict__ st,
+                                                                  const uint16_t *__restrict__ sym_all,
+                                                                  const uint8_t *__restrict__ lens_all,
+                                                                  uint8_t *__restrict__ sel_all, uint32_t *__restrict__ rfreq_all) {
+    __shared__ uint64_t packed[kMaxAlpha];
+    __shared__ uint32_t rf[kMaxGroups][kMaxAlpha];
+    __shared__ __align__(16) uint16_t ssym[kTileSyms];
+    const int b = blockIdx.y, tile = blockIdx.x;
+    const BlockState S = st[b];
+    const int ng = S.n_groups, nsel = S.n_sel, n_mtf = S.n_mtf, alpha = S.n_in_use + 2;
+    if (tile * kPackGroups >= nsel) return;
+    stage_tile_syms(sym_all + (size_t)b * kSymStride, tile, n_mtf, ssym);
+    const uint8_t *len = lens_all + (size_t)b * kMaxGroups * kMaxAlpha;
+    for (int v = threadIdx.x; v < alpha; v += blockDim.x) {
+        uint64_t pk = 0;
+        for (int t = 0; t < ng; t++) pk |= (uint64_t)len[t * kMaxAlpha + v] << (10 * t);
+        packed[v] = pk;
+    }
+    for (int i = threadIdx.x; i < kMaxGroups * kMaxAlpha; i += blockDim.x) (&rf[0][0])[i] = 0;
+    __syncthreads();
+    const int gi = tile * kPackGroups + (int)threadIdx.x;
+    int bt = -1;
+    uint32_t c0 = 0, c1 = 0;
+    if (gi < nsel) {
+        const uint16_t *sym = ssym - tile * kTileSyms;  // indexed by block position
+        const int a = gi * 50, e = min(n_mtf, a + 50);
+        uint64_t acc = 0;
+        for (int i = a; i < e; i++) acc += packed[sym[i]];
+        bt = 0;
+        uint32_t bc = (uint32_t)(acc & 1023u);
+        for (int t = 1; t < ng; t++) {
+            const uint32_t c = (uint32_t)((acc >> (10 * t)) & 1023u);
+            if (c < bc) { bc = c; bt = t; }
+        }
+        sel_all[(size_t)b * kMaxSelectors + gi] = (uint8_t)bt;
+        for (int i = a; i < e; i++) {
+            const uint32_t v = sym[i];
+            if (v == 0) c0++;
+            else if (v == 1) c1++;
+            else atomicAdd(&rf[bt][v], 1u);
+        }
+        if (c0) atomicAdd(&rf[bt][0], c0);
+        if (c1) atomicAdd(&rf[bt][1], c1);
     }
     __syncthreads();
+    uint32_t *rfreq = rfreq_all + (size_t)b * kMaxGroups * kMaxAlpha;
+    for (int i = threadIdx.x; i < ng * kMaxAlpha; i += blockDim.x) {
+        const uint32_t c = (&rf[0][0])[i];
+        if (c) atomicAdd(&rfreq[i], c);
+    }
+}
+
+// Warp per table: code lengths from the pass's counts, which are then
+// cleared for the next pass.
+__global__ void __launch_bounds__(kHuffBuildThreads) huff_build_kernel(const BlockState *__restrict__ st,
+                                                                       uint32_t *__restrict__ rfreq_all,
+                                                                       uint8_t *__restrict__ lens_all) {
+    __shared__ uint32_t cnt[kMaxGroups][kMaxAlpha];
+    __shared__ uint8_t lo[kMaxGroups][kMaxAlpha];
+    __shared__ HuffScratch scratch[kMaxGroups];
+    const int b = blockIdx.x;
+    const int ng = st[b].n_groups, alpha = st[b].n_in_use + 2;
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (w >= ng) return;
+    uint32_t *rfreq = rfreq_all + ((size_t)b * kMaxGroups + w) * kMaxAlpha;
+    for (int v = lane; v < alpha; v += 32) {
+        cnt[w][v] = rfreq[v];
+        rfreq[v] = 0;
+    }
+    __syncwarp();
+    huff_lengths_warp(cnt[w], alpha, 17, lo[w], scratch[w]);
+    uint8_t *len = lens_all + ((size_t)b * kMaxGroups + w) * kMaxAlpha;
+    for (int v = lane; v < alpha; v += 32) len[v] = lo[w][v];
+}
+
+// Canonical codes: by length, then symbol (lane 0 of the table's warp).
+__global__ void __launch_bounds__(kHuffBuildThreads) huff_codes_kernel(const BlockState *__restrict__ st,
+                                                                       const uint8_t *__restrict__ lens_all,
+                                                                       uint32_t *__restrict__ codes_all) {
+    const int b = blockIdx.x;
+    const int ng = st[b].n_groups, alpha = st[b].n_in_use + 2;
     const int w = threadIdx.x >> 5;
-    for (int iter = 0; iter < 4; iter++) {
-        for (int i = threadIdx.x; i < kMaxGroups * kMaxAlpha; i += blockDim.x) (&rfreq[0][0])[i] = 0;
-        for (int v = threadIdx.x; v < alpha; v += blockDim.x) {
-            uint64_t pk = 0;
-            for (int t = 0; t < ng; t++) pk |= (uint64_t)len[t][v] << (10 * t);
-            packed[v] = pk;
-        }
-        __syncthreads();
-        for (int gi = threadIdx.x; gi < nsel; gi += blockDim.x) {
-            const int a = gi * 50, e = min(n_mtf, a + 50);
-            uint64_t acc = 0;
-            for (int i = a; i < e; i++) acc += packed[sym[i]];
-            int bt = 0;
-            uint32_t bc = (uint32_t)(acc & 1023u);
-            for (int t = 1; t < ng; t++) {
-                const uint32_t c = (uint32_t)((acc >> (10 * t)) & 1023u);
-                if (c < bc) { bc = c; bt = t; }
-            }
-            sel[gi] = (uint8_t)bt;
-            for (int i = a; i < e; i++) atomicAdd(&rfreq[bt][sym[i]], 1u);
-        }
-        __syncthreads();
-        if (w < ng) huff_lengths_warp(rfreq[w], alpha, 17, len[w], scratch[w]);
-        __syncthreads();
-    }
-    // canonical codes: by length, then symbol
-    if (w < ng && (threadIdx.x & 31) == 0) {
-        uint32_t next[22];
-        uint32_t cnt[22];
-        for (int l = 0; l < 22; l++) cnt[l] = 0;
-        for (int v = 0; v < alpha; v++) cnt[len[w][v]]++;
-        uint32_t c = 0;
-        for (int l = 1; l <= 20; l++) { next[l] = c; c = (c + cnt[l]) << 1; }
-        uint32_t *codes = codes_all + ((size_t)b * kMaxGroups + w) * kMaxAlpha;
-        uint8_t *lo = lens_all + ((size_t)b * kMaxGroups + w) * kMaxAlpha;
-        for (int v = 0; v < alpha; v++) {
-            codes[v] = next[len[w][v]]++;
-            lo[v] = len[w][v];
-        }
-    }
+    if (w >= ng || (threadIdx.x & 31) != 0) return;
+    const uint8_t *len = lens_all + ((size_t)b * kMaxGroups + w) * kMaxAlpha;
+    uint32_t next[22];
+    uint32_t cnt[22];
+    for (int l = 0; l < 22; l++) cnt[l] = 0;
+    for (int v = 0; v < alpha; v++) cnt[len[v]]++;
+    uint32_t c = 0;
+    for (int l = 1; l <= 20; l++) { next[l] = c; c = (c + cnt[l]) << 1; }
+    uint32_t *codes = codes_all + ((size_t)b * kMaxGroups + w) * kMaxAlpha;
+    for (int v = 0; v < alpha; v++) codes[v] = next[len[v]]++;
 }
 
 // ------------------------------------------------------------ bit packing
@@ -586,8 +709,6 @@ __device__ __forceinline__ void set_last(int (&last)[kMaxGroups], int s, int i) 
 // offsets, the header, selector, code-length and trailer sections (2); each
 // group's codes from its bit offset, whole words stored, the two boundary
 // words OR-ed (3).
-constexpr int kPackGroups = 128;                                           // groups per tile = threads
-constexpr int kPackTiles = (kMaxSelectors + kPackGroups - 1) / kPackGroups;  // 141
 static_assert(kPackTiles <= kTilesPerBlock, "pack tile records live in the per-block tile scratch");
 constexpr int kLayoutThreads = 1024;
 
@@ -608,15 +729,17 @@ __global__ void __launch_bounds__(kPackGroups) pack_bits_kernel(const BlockState
                                                                 int32_t *__restrict__ aux_all) {
     __shared__ uint8_t len[kMaxGroups][kMaxAlpha];
     __shared__ int sh[33];
+    __shared__ __align__(16) uint16_t ssym[kTileSyms];
     const int b = blockIdx.y, tile = blockIdx.x;
     const BlockState S = st[b];
     if (tile * kPackGroups >= S.n_sel) return;
     load_tables(lens_all, nullptr, b, S.n_groups, len, nullptr);
+    stage_tile_syms(sym_all + (size_t)b * kSymStride, tile, S.n_mtf, ssym);
     __syncthreads();
     const int gi = tile * kPackGroups + (int)threadIdx.x;
     int bits = 0;
     if (gi < S.n_sel) {
-        const uint16_t *sym = sym_all + (size_t)b * kSymStride;
+        const uint16_t *sym = ssym - tile * kTileSyms;
         const uint8_t *lt = len[sel_all[(size_t)b * kMaxSelectors + gi]];
         const int a = gi * 50, e = min(S.n_mtf, a + 50);
         for (int i = a; i < e; i++) bits += lt[sym[i]];
@@ -771,10 +894,12 @@ __global__ void __launch_bounds__(kPackGroups) pack_data_kernel(const BlockState
     __shared__ uint8_t len[kMaxGroups][kMaxAlpha];
     __shared__ uint32_t code[kMaxGroups][kMaxAlpha];
     __shared__ int sh[33];
+    __shared__ __align__(16) uint16_t ssym[kTileSyms];
     const int b = blockIdx.y, tile = blockIdx.x;
     const BlockState S = st[b];
     if (tile * kPackGroups >= S.n_sel) return;
     load_tables(lens_all, codes_all, b, S.n_groups, len, code);
+    stage_tile_syms(sym_all + (size_t)b * kSymStride, tile, S.n_mtf, ssym);
     const int gi = tile * kPackGroups + (int)threadIdx.x;
     const int bits = gi < S.n_sel ? (int)gbits_all[(size_t)b * (kBlockCap / 2) + gi] : 0;
     const int off = block_excl_sum<int>(bits, sh, nullptr);  // also orders the table loads
@@ -782,7 +907,7 @@ __global__ void __launch_bounds__(kPackGroups) pack_data_kernel(const BlockState
     uint32_t *words = packed_all + (size_t)b * stream_words;
     const uint64_t p0 = (uint64_t)S.data_bit0 + (uint32_t)aux_all[((size_t)b * kTilesPerBlock + tile) * 4 + 1] + off;
     const int t = sel_all[(size_t)b * kMaxSelectors + gi];
-    const uint16_t *sym = sym_all + (size_t)b * kSymStride;
+    const uint16_t *sym = ssym - tile * kTileSyms;
     const int a = gi * 50, e = min(S.n_mtf, a + 50);
     uint64_t acc = 0;                 // pending bits, left-aligned
     uint64_t wpos = p0 & ~31ull;      // bit position of the word being built
@@ -821,8 +946,15 @@ cudaError_t launch_mtf_rle2(lfc_plan P, int nblocks) {
 
 cudaError_t launch_huffman(lfc_plan P, int nblocks) {
     Workspace &ws = P->ws;
-    huffman_kernel<<<nblocks, kHuffThreads, 0, P->stream>>>(ws.bstate, ws.sym, ws.freq, ws.sel, ws.lens, ws.codes);
-    count_launches(P, 1);
+    cudaStream_t s = P->stream;
+    huff_init_kernel<<<nblocks, 256, 0, s>>>(ws.bstate, ws.freq, ws.lens, ws.rfreq);
+    const dim3 grid(kPackTiles, nblocks);
+    for (int iter = 0; iter < 4; iter++) {
+        huff_select_kernel<<<grid, kPackGroups, 0, s>>>(ws.bstate, ws.sym, ws.lens, ws.sel, ws.rfreq);
+        huff_build_kernel<<<nblocks, kHuffBuildThreads, 0, s>>>(ws.bstate, ws.rfreq, ws.lens);
+    }
+    huff_codes_kernel<<<nblocks, kHuffBuildThreads, 0, s>>>(ws.bstate, ws.lens, ws.codes);
+    count_launches(P, 10);
     return cudaGetLastError();
 }
 
