@@ -13,9 +13,11 @@
 //  2. Prefix doubling on the groups still tied: rank[i] = head position of
 //     i's group in the suffix array; each round keys the tied elements by
 //     (rank[i] << 20 | rank[i + h]) (m < 2^20), sorts them with 5 stable LSD
-//     passes, splits groups, and doubles h. Groups left when h >= m hold
-//     identical rotations, already in start-index order (every pass is stable
-//     and the first starts from the identity).
+//     passes, splits groups, and doubles h. Here an element is one 64-bit
+//     word, the 40-bit key above the element (20 bits), and the passes sort
+//     bits 20..59 only. Groups left when h >= m hold identical rotations,
+//     already in start-index order (every pass is stable and the first starts
+//     from the identity).
 #include <climits>
 
 #include "lfc_common.cuh"
@@ -260,7 +262,9 @@ __global__ void __launch_bounds__(kSortThreads) key8_kernel(const BlockState *__
     }
 }
 
-// Round keys of the tied elements: rank[v] << 20 | rank[(v + h) mod m].
+// Round words of the tied elements: rank[v] << 40 | rank[(v + h) mod m] << 20 | v.
+constexpr uint64_t kElemMask = (1u << 20) - 1u;
+
 __global__ void __launch_bounds__(kSortThreads) key40_kernel(const int32_t *__restrict__ rs, const BlockState *__restrict__ st,
                                                              const int32_t *__restrict__ V_all, const int32_t *__restrict__ rank_all,
                                                              uint64_t *__restrict__ K_all) {
@@ -275,9 +279,14 @@ __global__ void __launch_bounds__(kSortThreads) key40_kernel(const int32_t *__re
         const int v = V_all[bo + k];
         int j = v + h;
         if (j >= s.m) j -= s.m;
-        K_all[bo + k] = ((uint64_t)(uint32_t)rank_all[bo + v] << 20) | (uint32_t)rank_all[bo + j];
+        K_all[bo + k] = ((uint64_t)(uint32_t)rank_all[bo + v] << 40) | ((uint64_t)(uint32_t)rank_all[bo + j] << 20) |
+                        (uint64_t)(uint32_t)v;
     }
 }
+
+// Digit position of a pass: phase 1 sorts all 64 key bits, a round bits 20..59.
+template <int MODE>
+__device__ __forceinline__ int digit_shift(int pass) { return (MODE == 0 ? 0 : 20) + 8 * pass; }
 
 // Per-tile digit histogram, stored digit-major: cnt[b][digit][tile]. A warp
 // whose 32 digits agree adds them with one atomic (long equal runs are the
@@ -297,7 +306,7 @@ __global__ void __launch_bounds__(kSortThreads) radix_hist_kernel(int pass, cons
     for (int i = threadIdx.x; i < NW * 256; i += kSortThreads) (&hst[0][0])[i] = 0;
     __syncthreads();
     const uint64_t *K = K_all + (size_t)b * kBlockCap;
-    const int shift = 8 * pass;
+    const int shift = digit_shift<MODE>(pass);
     uint32_t dg[kPerThread];
 #pragma unroll
     for (int r = 0; r < kPerThread; r++) {  // all loads in flight first
@@ -350,17 +359,20 @@ __global__ void __launch_bounds__(1024) radix_scan_kernel(const int32_t *__restr
 // placed in shared memory in digit order, then each digit's run is written
 // to its global offset with consecutive threads on consecutive addresses.
 constexpr size_t kScatterSmem = (size_t)kTile * 12 + (size_t)(kSortThreads / 32) * 256 * 4 + 2 * 256 * 4;
+// MODE 1 moves the words alone (Vin / Vout unused)
+constexpr size_t kScatterSmem1 = (size_t)kTile * 8 + (size_t)(kSortThreads / 32) * 256 * 4 + 2 * 256 * 4;
 
 template <int MODE>
-__global__ void __launch_bounds__(kSortThreads) radix_scatter_kernel(int pass, const int32_t *__restrict__ rs, const BlockState *__restrict__ st,
+__global__ void __launch_bounds__(kSortThreads, 3) radix_scatter_kernel(int pass, const int32_t *__restrict__ rs, const BlockState *__restrict__ st,
                                                                      const uint64_t *__restrict__ Kin_all, const int32_t *__restrict__ Vin_all,
                                                                      uint64_t *__restrict__ Kout_all, int32_t *__restrict__ Vout_all,
                                                                      const uint32_t *__restrict__ cnt_all) {
     constexpr int NW = kSortThreads / 32;
     extern __shared__ __align__(16) uint8_t smem[];
     uint64_t *sK = reinterpret_cast<uint64_t *>(smem);           // [kTile]
-    int32_t *sV = reinterpret_cast<int32_t *>(sK + kTile);        // [kTile]
-    uint32_t *wcnt = reinterpret_cast<uint32_t *>(sV + kTile);    // [NW][256]
+    int32_t *sV = reinterpret_cast<int32_t *>(sK + kTile);        // [kTile], MODE 0
+    uint32_t *wcnt = reinterpret_cast<uint32_t *>(MODE == 0 ? reinterpret_cast<uint8_t *>(sV + kTile)
+                                                            : reinterpret_cast<uint8_t *>(sK + kTile));  // [NW][256]
     uint32_t *loff = wcnt + NW * 256;                             // [256] tile-local start of a digit
     uint32_t *gbase = loff + 256;                                 // [256] global start of the tile's run
     __shared__ uint32_t sh[33];
@@ -369,7 +381,7 @@ __global__ void __launch_bounds__(kSortThreads) radix_scatter_kernel(int pass, c
     const int n = sort_count<MODE>(st[b], h);
     if (tile * kTile >= n) return;
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int shift = 8 * pass;
+    const int shift = digit_shift<MODE>(pass);
     for (int i = threadIdx.x; i < NW * 256; i += kSortThreads) wcnt[i] = 0;
     gbase[threadIdx.x] = cnt_all[((size_t)b * 256 + threadIdx.x) * kTilesPerBlock + tile];
     __syncthreads();
@@ -385,7 +397,7 @@ __global__ void __launch_bounds__(kSortThreads) radix_scatter_kernel(int pass, c
         const int k = tile * kTile + w * 512 + r * 32 + lane;
         const bool ok = k < n;
         keys[r] = ok ? Kin[k] : 0;
-        vals[r] = ok ? Vin[k] : 0;
+        vals[r] = (MODE == 0 && ok) ? Vin[k] : 0;
         const uint32_t d = (uint32_t)(keys[r] >> shift) & 255u;
         const uint32_t mm = __match_any_sync(LFC_FULL, ok ? d : 256u + lane);
         uint32_t before = 0;
@@ -413,7 +425,7 @@ __global__ void __launch_bounds__(kSortThreads) radix_scatter_kernel(int pass, c
         const uint32_t d = (uint32_t)(keys[r] >> shift) & 255u;
         const uint32_t pos = loff[d] + wcnt[w * 256 + d] + rnk[r];
         sK[pos] = keys[r];
-        sV[pos] = vals[r];
+        if (MODE == 0) sV[pos] = vals[r];
     }
     __syncthreads();
     const int cnt = min(kTile, n - tile * kTile);
@@ -427,7 +439,7 @@ __global__ void __launch_bounds__(kSortThreads) radix_scatter_kernel(int pass, c
             const uint32_t d = (uint32_t)(key >> shift) & 255u;
             const uint32_t g = gbase[d] + ((uint32_t)j - loff[d]);
             Kout[g] = key;
-            Vout[g] = sV[j];
+            if (MODE == 0) Vout[g] = sV[j];
         }
     }
 }
@@ -454,14 +466,15 @@ __global__ void __launch_bounds__(kSortThreads) heads_tile_kernel(const int32_t 
     int hmax = -1, tied = 0;
     if (k0 < n) {
         const int k1 = min(n, k0 + kPerThread);
-        uint64_t prevk = k0 > 0 ? K[k0 - 1] : 0;
-        uint64_t cur = K[k0];
+        const int ks = MODE == 0 ? 0 : 20;  // round words carry the element below the key
+        uint64_t prevk = k0 > 0 ? K[k0 - 1] >> ks : 0;
+        uint64_t cur = K[k0] >> ks;
         bool curhead = (k0 == 0) || cur != prevk;
         for (int k = k0; k < k1; k++) {
             bool nexthead = true;
             uint64_t nk = 0;
             if (k + 1 < n) {
-                nk = K[k + 1];
+                nk = K[k + 1] >> ks;
                 nexthead = nk != cur;
             }
             flags[k] = (uint8_t)curhead;
@@ -517,7 +530,8 @@ __global__ void __launch_bounds__(256) heads_scan_kernel(int32_t *__restrict__ r
 // next round's lists.
 template <int MODE>
 __global__ void __launch_bounds__(kSortThreads) heads_apply_kernel(const int32_t *__restrict__ rs, const BlockState *__restrict__ st,
-                                                                   const int32_t *__restrict__ sorted_all, int32_t *__restrict__ actA,
+                                                                   const int32_t *__restrict__ sorted_all, const uint64_t *__restrict__ words_all,
+                                                                   int32_t *__restrict__ actA,
                                                                    int32_t *__restrict__ actB,
                                                                    const uint8_t *__restrict__ flags_all, const int32_t *__restrict__ aux_all,
                                                                    int32_t *__restrict__ rank_all, int32_t *__restrict__ sa_all,
@@ -535,7 +549,8 @@ __global__ void __launch_bounds__(kSortThreads) heads_apply_kernel(const int32_t
     const int n = sort_count<MODE>(s, h);
     if (tile * kTile >= n) return;
     const size_t bo = (size_t)b * kBlockCap;
-    const int32_t *sorted = sorted_all + bo;
+    const int32_t *sorted = sorted_all + bo;   // MODE 0: the suffix array
+    const uint64_t *words = words_all + bo;    // MODE 1: sorted round words
     const int32_t *act = act_all + bo;
     const uint8_t *flags = flags_all + bo;
     const int32_t *aux = aux_all + ((size_t)b * kTilesPerBlock + tile) * 4;
@@ -560,7 +575,7 @@ __global__ void __launch_bounds__(kSortThreads) heads_apply_kernel(const int32_t
         const bool nh = (k + 1 >= n) || flags[k + 1];
         const int pos = MODE == 0 ? k : act[k];
         if (hd) carry = pos;
-        const int32_t v = sorted[k];
+        const int32_t v = MODE == 0 ? sorted[k] : (int32_t)(words[k] & kElemMask);
         rank[v] = carry;
         if (MODE == 1) sa[pos] = v;
         if (!(hd && nh)) {
@@ -621,8 +636,8 @@ static void radix_pass(lfc_plan P, cudaStream_t st, int nblocks, int tiles, int 
     dim3 grid(tiles, nblocks);
     radix_hist_kernel<MODE><<<grid, kSortThreads, 0, st>>>(pass, ws.act_total, ws.bstate, kin, ws.tilecnt);
     radix_scan_kernel<MODE><<<nblocks, 1024, 0, st>>>(ws.act_total, ws.bstate, ws.tilecnt);
-    radix_scatter_kernel<MODE><<<grid, kSortThreads, kScatterSmem, st>>>(pass, ws.act_total, ws.bstate, kin, vin, kout, vout,
-                                                                         ws.tilecnt);
+    radix_scatter_kernel<MODE><<<grid, kSortThreads, MODE == 0 ? kScatterSmem : kScatterSmem1, st>>>(
+        pass, ws.act_total, ws.bstate, kin, vin, kout, vout, ws.tilecnt);
     count_launches(P, 3);
 }
 
@@ -634,16 +649,16 @@ static void bwt_round(lfc_plan P, cudaStream_t st, int nblocks, int tiles, int m
     round_start_kernel<<<1, 1, 0, st>>>(ws.act_total, 0);
     dim3 g1(tiles, nblocks);
     key40_kernel<<<g1, kSortThreads, 0, st>>>(ws.act_total, ws.bstate, ws.val, ws.rank, ws.keys);
-    // 5 LSD passes over the 40-bit key: (keys, val) -> (keys2, val2) -> ... -> (keys2, val2)
+    // 5 LSD passes over bits 20..59 of the words: keys -> keys2 -> ... -> keys2
     for (int pass = 0; pass < 5; pass++) {
-        if (pass & 1) radix_pass<1>(P, st, nblocks, tiles, pass, ws.keys2, ws.val2, ws.keys, ws.val);
-        else radix_pass<1>(P, st, nblocks, tiles, pass, ws.keys, ws.val, ws.keys2, ws.val2);
+        if (pass & 1) radix_pass<1>(P, st, nblocks, tiles, pass, ws.keys2, nullptr, ws.keys, nullptr);
+        else radix_pass<1>(P, st, nblocks, tiles, pass, ws.keys, nullptr, ws.keys2, nullptr);
     }
     heads_tile_kernel<1><<<g1, kSortThreads, 0, st>>>(ws.act_total, ws.bstate, ws.keys2, ws.act, ws.act2, ws.bwt,
                                                       ws.tileaux);
     heads_scan_kernel<1><<<nblocks, 256, 0, st>>>(ws.act_total, ws.bstate, ws.tileaux);
-    heads_apply_kernel<1><<<g1, kSortThreads, 0, st>>>(ws.act_total, ws.bstate, ws.val2, ws.act, ws.act2, ws.bwt,
-                                                       ws.tileaux, ws.rank, ws.sa, ws.val);
+    heads_apply_kernel<1><<<g1, kSortThreads, 0, st>>>(ws.act_total, ws.bstate, nullptr, ws.keys2, ws.act, ws.act2,
+                                                       ws.bwt, ws.tileaux, ws.rank, ws.sa, ws.val);
     commit_round_kernel<<<(nblocks + 255) / 256, 256, 0, st>>>(ws.bstate, nblocks);
     round_end_kernel<<<1, 1, 0, st>>>(ws.act_total, max_m, cond, set_cond);
     count_launches(P, 7);
@@ -661,7 +676,7 @@ cudaError_t launch_bwt(lfc_plan P, int nblocks, int max_m) {
     const bool graph = cap == cudaStreamCaptureStatusActive;
     e = cudaFuncSetAttribute(radix_scatter_kernel<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kScatterSmem);
     if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(radix_scatter_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kScatterSmem);
+        e = cudaFuncSetAttribute(radix_scatter_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kScatterSmem1);
     if (e != cudaSuccess) return e;
     // phase 1: prefix keys, then 8 LSD passes (keys, sa) -> (keys2, sa2) -> ... -> (keys, sa)
     stage_begin(P, LFC_STAGE_BWT_SORT8);
@@ -677,8 +692,8 @@ cudaError_t launch_bwt(lfc_plan P, int nblocks, int max_m) {
     round_start_kernel<<<1, 1, 0, s>>>(ws.act_total, 1);
     heads_tile_kernel<0><<<grid, kSortThreads, 0, s>>>(ws.act_total, ws.bstate, ws.keys, ws.sa, ws.sa, ws.bwt, ws.tileaux);
     heads_scan_kernel<0><<<nblocks, 256, 0, s>>>(ws.act_total, ws.bstate, ws.tileaux);
-    heads_apply_kernel<0><<<grid, kSortThreads, 0, s>>>(ws.act_total, ws.bstate, ws.sa, ws.act, ws.act2, ws.bwt,
-                                                        ws.tileaux, ws.rank, ws.sa, ws.val);
+    heads_apply_kernel<0><<<grid, kSortThreads, 0, s>>>(ws.act_total, ws.bstate, ws.sa, nullptr, ws.act, ws.act2,
+                                                        ws.bwt, ws.tileaux, ws.rank, ws.sa, ws.val);
     commit_round_kernel<<<(nblocks + 255) / 256, 256, 0, s>>>(ws.bstate, nblocks);
     count_launches(P, 5);
     P->bwt_calls++;
