@@ -402,7 +402,7 @@ struct CompressDesc {
     Arena arena;
     std::vector<JudgeChunk> judge;
     CrcRun frame_crc;
-    size_t off_frame_crc = 0;
+    size_t off_frame_crc = 0, off_dst = 0;
     std::vector<CoderPass> passes;
     std::vector<FrameDev> fd;
     std::vector<uint8_t *> dst;
@@ -484,8 +484,10 @@ int build_judge(lfc_plan P, const lfc_frame *frames, int n, Arena &A, std::vecto
     return LFC_OK;
 }
 
+// d_dst (device array of the frames' stream slots, may be null): the chosen
+// stream of each frame is copied out of the judge's candidate streams.
 int run_judge(lfc_plan P, const std::vector<lfc_frame> &frames, const std::vector<JudgeChunk> &chunks,
-              const uint8_t *d_arena, uint8_t *d_choice, uint64_t *d_scores) {
+              const uint8_t *d_arena, uint8_t *d_choice, uint64_t *d_scores, uint8_t *const *d_dst = nullptr) {
     if (P->cnn && P->topk > 0) {
         const int r = cnn_propose(P->cnn, frames.data(), (int)frames.size(), P->ws.class_ids, P->topk, P->tau, P->ws.masks,
                                   P->stream);
@@ -495,6 +497,12 @@ int run_judge(lfc_plan P, const std::vector<lfc_frame> &frames, const std::vecto
     for (const JudgeChunk &C : chunks) {
         CK(launch_judge(P, reinterpret_cast<const JudgeFrame *>(d_arena + C.off_tables), C.nf, C.ctas, C.L,
                         d_arena + C.off_cand, C.nhist, d_scores, d_choice));
+        if (d_dst) {
+            stage_begin(P, LFC_STAGE_EMIT);
+            CK(launch_copy_chosen(P, reinterpret_cast<const JudgeFrame *>(d_arena + C.off_tables), C.nf,
+                                  d_arena + C.off_cand, d_choice, d_dst));
+            stage_end(P, LFC_STAGE_EMIT);
+        }
         f0 += C.nf;
     }
     return LFC_OK;
@@ -580,6 +588,7 @@ int build_compress(lfc_plan P, const lfc_frame *frames, int n, bool judge, size_
         raw[i] = reinterpret_cast<const uint8_t *>(frames[i].data);
         rawlen[i] = 2LL * frames[i].width * frames[i].height;
     }
+    D.off_dst = D.arena.put(D.dst.data(), sizeof(uint8_t *) * (size_t)n);
     const int nck = crc_count_chunks(rawlen.data(), n);
     D.off_frame_crc = D.arena.reserve(crc_table_bytes(nck, n));
     crc_build_tables(raw.data(), rawlen.data(), n, D.arena.host.data() + D.off_frame_crc, &D.frame_crc);
@@ -625,15 +634,17 @@ int run_compress(lfc_plan P, const CompressDesc &D, const uint8_t *d_arena, cons
                  uint64_t *d_out_sizes) {
     Workspace &ws = P->ws;
     const uint8_t *choice = d_choice;
-    if (!D.judge.empty()) {
-        const int r = run_judge(P, D.frames, D.judge, d_arena, ws.choice, ws.scores);
+    if (!D.judge.empty()) {  // the judge also copies out the chosen streams
+        const int r = run_judge(P, D.frames, D.judge, d_arena, ws.choice, ws.scores,
+                                reinterpret_cast<uint8_t *const *>(d_arena + D.off_dst));
         if (r) return r;
         choice = ws.choice;
+    } else {
+        stage_begin(P, LFC_STAGE_EMIT);
+        CK(launch_emit(D.fd.data(), choice, D.n, D.dst.data(), P->stream));
+        count_launches(P, (D.n + 7) / 8);
+        stage_end(P, LFC_STAGE_EMIT);
     }
-    stage_begin(P, LFC_STAGE_EMIT);
-    CK(launch_emit(D.fd.data(), choice, D.n, D.dst.data(), P->stream));
-    count_launches(P, (D.n + 7) / 8);
-    stage_end(P, LFC_STAGE_EMIT);
     stage_begin(P, LFC_STAGE_CRC);
     CK(launch_crc(P, d_arena + D.off_frame_crc, D.frame_crc, ws.frame_crc, 1));
     stage_end(P, LFC_STAGE_CRC);

@@ -388,6 +388,41 @@ struct EmitArgs {
 };
 
 // Stream of the chosen id: thread per output symbol, 2-D grid (chunk, frame).
+// The judge has already written every candidate's stream: copy the chosen
+// one of each frame of a judge launch to the frame's stream slot (16-byte
+// aligned slots; a byte tail for odd sizes).
+__global__ void copy_chosen_kernel(const JudgeFrame *__restrict__ frames, int nframes, const uint8_t *__restrict__ cand,
+                                   const uint8_t *__restrict__ choice, const uint8_t *__restrict__ cstream, int64_t cslot,
+                                   int kmax, uint8_t *const *__restrict__ dst) {
+    __shared__ int slot;
+    const int i = blockIdx.y;
+    const JudgeFrame &J = frames[i];
+    const int g = reinterpret_cast<const int32_t *>(frames + nframes)[i];  // frame index of the call
+    if (threadIdx.x == 0) {
+        slot = -1;
+        const int c = choice[g];
+        for (int k = 0; k < J.K; k++)
+            if (cand[J.cand_off + k] == c) { slot = k; break; }
+    }
+    __syncthreads();
+    if (slot < 0) return;  // the choice is always one of the frame's candidates
+    const uint8_t *src = cstream + ((size_t)i * kmax + slot) * (size_t)cslot;
+    uint8_t *d = dst[g];
+    const int64_t n = 2LL * J.F.W * J.F.H, n16 = n / 16;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < n16; q += stride)
+        reinterpret_cast<uint4 *>(d)[q] = __ldg(reinterpret_cast<const uint4 *>(src) + q);
+    for (int64_t q = n16 * 16 + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < n; q += stride) d[q] = src[q];
+}
+
+cudaError_t launch_copy_chosen(lfc_plan P, const JudgeFrame *d_frames, int nframes, const uint8_t *d_cand,
+                               const uint8_t *d_choice, uint8_t *const *d_dst) {
+    copy_chosen_kernel<<<dim3(64, nframes), 256, 0, P->stream>>>(d_frames, nframes, d_cand, d_choice, P->ws.cstream,
+                                                                  P->ws.cstream_slot, P->ws.cstream_kmax, d_dst);
+    count_launches(P, 1);
+    return cudaGetLastError();
+}
+
 __global__ void emit_kernel(EmitArgs args, const uint8_t *__restrict__ choice, int nframes) {
     const int f = blockIdx.y;
     if (f >= nframes) return;

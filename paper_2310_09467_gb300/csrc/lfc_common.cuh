@@ -273,6 +273,8 @@ struct JudgeLaunch {
 cudaError_t launch_judge(lfc_plan P, const JudgeFrame *d_frames, int nframes, int64_t total_ctas,
                          const JudgeLaunch &L, const uint8_t *d_cand, int64_t nhist,
                          uint64_t *d_scores, uint8_t *d_choice);
+cudaError_t launch_copy_chosen(lfc_plan P, const JudgeFrame *d_frames, int nframes, const uint8_t *d_cand,
+                               const uint8_t *d_choice, uint8_t *const *d_dst);
 cudaError_t launch_emit(const FrameDev *h_frames, const uint8_t *d_choice, int nframes,
                         uint8_t *const *h_dst, cudaStream_t s);
 cudaError_t launch_symbols_one(const FrameDev &F, int id, uint16_t *dst, cudaStream_t s);

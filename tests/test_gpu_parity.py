@@ -184,3 +184,18 @@ def test_decompress_rejects_corruption(lfc):
     with pytest.raises(lfc.LfcError) as ei:
         plan.decompress([_dev_bytes(blob)], [small])
     assert ei.value.status == 2
+
+
+def test_compress_given_choice(lfc):
+    """Caller-chosen ids skip the judge: the chosen stream is emitted directly."""
+    import torch
+    fr, p = _frames()[0]
+    plan = lfc.Plan(fr.shape[1], fr.shape[0], p, max_frames=2, block_bytes=20000)
+    d = lfc.to_device_frame(fr)
+    for cid in (0x00, 0x44, 0x27):
+        choice = torch.tensor([cid, cid], dtype=torch.uint8, device="cuda")
+        out, sizes, offs = plan.compress([d, d], p, choice=choice)
+        sz, host = sizes.cpu().numpy(), out.cpu().numpy()
+        ref = oracle.compress_id(fr, p, cid, block_bytes=20000)
+        for i in range(2):
+            assert host[offs[i]:offs[i] + sz[i]].tobytes() == ref, (cid, i)
