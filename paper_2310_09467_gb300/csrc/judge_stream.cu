@@ -129,6 +129,9 @@ __device__ __forceinline__ void emit_all_body(const JudgeFrame *__restrict__ fra
     const size_t cslot16 = (size_t)cslot / 2;
     // view-major write-out: thread j -> (u, si) = (j / ns, j % ns), rows v
     const int vm_j = threadIdx.x, vm_u = vm_j / ns, vm_si = vm_j - vm_u * ns;
+    // vector stores when every run start is aligned (slots are 256-byte aligned)
+    const bool raw2 = (W % 2) == 0 && ((s0 * p) % 2) == 0 && (nco % 2) == 0;
+    const bool vm8 = (ns % 8) == 0 && (W % 8) == 0 && (Nx % 8) == 0 && (s0 % 8) == 0;
 #pragma unroll
     for (int f = 0; f < 8; f++) {  // unrolled: the predictor of f is a constant
         if (!((fany >> f) & 1u)) continue;
@@ -169,12 +172,33 @@ __device__ __forceinline__ void emit_all_body(const JudgeFrame *__restrict__ fra
             const int k0 = slot_of[f][dom][0], k1 = slot_of[f][dom][1];
             if (k0 >= 0) {  // raw order: rows of nco consecutive symbols
                 uint16_t *dst = base + (size_t)k0 * cslot16 + (size_t)(t * p) * W + (size_t)s0 * p;
-                for (int r = 0; r < p; r++)
-                    for (int c = threadIdx.x; c < nco; c += blockDim.x) dst[(size_t)r * W + c] = src[r * nco + c];
+                if (raw2) {  // even row starts and widths: two symbols per store
+                    const int h = nco >> 1;
+                    for (int q = threadIdx.x; q < p * h; q += blockDim.x) {
+                        const int r = q / h, c2 = q - r * h;
+                        const uint32_t v2 = *reinterpret_cast<const uint32_t *>(src + r * nco + 2 * c2);
+                        *reinterpret_cast<uint32_t *>(dst + (size_t)r * W + 2 * c2) = v2;
+                    }
+                } else {
+                    for (int r = 0; r < p; r++)
+                        for (int c = threadIdx.x; c < nco; c += blockDim.x) dst[(size_t)r * W + c] = src[r * nco + c];
+                }
             }
             if (k1 >= 0) {  // view-major order: runs of ns symbols per (v, u)
                 uint16_t *dst = base + (size_t)k1 * cslot16 + (size_t)t * W + s0;
-                if (p * ns <= (int)blockDim.x) {
+                if (vm8) {  // 16-byte aligned runs of 8k symbols: 8 symbols per store
+                    const int hn = ns >> 3, items = p * p * hn;
+                    for (int q = threadIdx.x; q < items; q += blockDim.x) {
+                        const int hh = q % hn, vu = q / hn, u = vu % p, v = vu / p;
+                        const uint16_t *sp = src + v * nco + (8 * hh) * p + u;
+                        uint4 o;
+                        o.x = (uint32_t)sp[0] | ((uint32_t)sp[p] << 16);
+                        o.y = (uint32_t)sp[2 * p] | ((uint32_t)sp[3 * p] << 16);
+                        o.z = (uint32_t)sp[4 * p] | ((uint32_t)sp[5 * p] << 16);
+                        o.w = (uint32_t)sp[6 * p] | ((uint32_t)sp[7 * p] << 16);
+                        *reinterpret_cast<uint4 *>(dst + (size_t)v * Ny * W + (size_t)u * Nx + 8 * hh) = o;
+                    }
+                } else if (p * ns <= (int)blockDim.x) {
                     if (vm_j < p * ns)
                         for (int v = 0; v < p; v++)
                             dst[(size_t)v * Ny * W + (size_t)vm_u * Nx + vm_si] = src[v * nco + vm_si * p + vm_u];

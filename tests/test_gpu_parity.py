@@ -32,6 +32,7 @@ def _frames():
         (synth.beads(390, 260, 13, peak=200.0, seed=5), 13),
         (synth.beads(340, 260, 20, peak=500.0, seed=7), 20),   # 340 output columns per 17-lenslet row: > 256 threads
         (synth.cells(96, 102, 3, seed=8), 3),
+        (synth.beads(480, 240, 15, peak=300.0, seed=13), 15),  # 32 lenslets a row: vector-store paths
     ]
 
 
@@ -51,7 +52,7 @@ def test_symbols_all_ids(lfc):
         assert np.array_equal(got, oracle.symbols(fr, p, cid, prev=pv)), cid
 
 
-@pytest.mark.parametrize("k", range(6))
+@pytest.mark.parametrize("k", range(7))
 def test_judge_scores_and_choice(lfc, k):
     fr, p = _frames()[k]
     plan = lfc.Plan(fr.shape[1], fr.shape[0], p)
@@ -101,7 +102,7 @@ def test_bzip2_encode_bytes_identical(lfc, case):
         assert bz2.decompress(g) == b
 
 
-@pytest.mark.parametrize("k", range(6))
+@pytest.mark.parametrize("k", range(7))
 def test_compress_container_identical(lfc, k):
     fr, p = _frames()[k]
     plan = lfc.Plan(fr.shape[1], fr.shape[0], p, block_bytes=20000)
@@ -129,7 +130,7 @@ def _dev_bytes(blob):
     return torch.from_numpy(np.frombuffer(blob, dtype=np.uint8).copy()).cuda()
 
 
-@pytest.mark.parametrize("k", range(6))
+@pytest.mark.parametrize("k", range(7))
 def test_decompress_round_trip(lfc, k):
     import torch
     fr, p = _frames()[k]
