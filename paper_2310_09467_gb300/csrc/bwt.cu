@@ -606,27 +606,78 @@ __global__ void round_end_kernel(int32_t *rs, int max_m, cudaGraphConditionalHan
 }
 
 // L[j] = block[(SA[j] - 1) mod m]; origPtr = j with SA[j] = 0; bytes in use.
+// Each CTA also writes the MTF summary of its 4096-byte segment of L: the
+// distinct bytes ordered by last occurrence, latest first. Thread = 16
+// consecutive positions; the last position of each byte value comes from one
+// shared-memory max per distinct value of a thread's run; each value is then
+// marked at its last position and the marks are compacted from the top.
 __global__ void __launch_bounds__(kSortThreads) bwt_output_kernel(BlockState *__restrict__ st, const int32_t *__restrict__ sa_all,
-                                                                  const uint8_t *__restrict__ rle_all, uint8_t *__restrict__ L_all) {
-    __shared__ uint32_t used[8];
+                                                                  const uint8_t *__restrict__ rle_all, uint8_t *__restrict__ L_all,
+                                                                  uint8_t *__restrict__ rec_all, int32_t *__restrict__ reclen_all) {
+    __shared__ int32_t lastpos[256];
+    __shared__ uint16_t mark[kTile];  // value + 1 at its last position, 0 elsewhere
+    __shared__ int sh[33];
     const int b = blockIdx.y, tile = blockIdx.x;
     const int m = st[b].m;
     if (tile * kTile >= m) return;
-    if (threadIdx.x < 8) used[threadIdx.x] = 0;
+    lastpos[threadIdx.x] = -1;
+    for (int i = threadIdx.x; i < kTile; i += kSortThreads) mark[i] = 0;
     __syncthreads();
     const size_t bo = (size_t)b * kBlockCap;
-    for (int i = 0; i < kPerThread; i++) {
-        const int j = tile * kTile + i * kSortThreads + threadIdx.x;
+    const int jl = (int)threadIdx.x * kPerThread;  // tile-local start of the thread's run
+    const int j0 = tile * kTile + jl;
+    uint8_t c[kPerThread];
+#pragma unroll
+    for (int q = 0; q < kPerThread; q++) {
+        const int j = j0 + q;
+        c[q] = 0;
         if (j < m) {
             const int v = sa_all[bo + j];
-            const uint8_t c = rle_all[bo + (v == 0 ? m - 1 : v - 1)];
-            L_all[bo + j] = c;
+            c[q] = rle_all[bo + (v == 0 ? m - 1 : v - 1)];
             if (v == 0) st[b].orig_ptr = j;
-            atomicOr(&used[c >> 5], 1u << (c & 31));
         }
     }
+    if (j0 + kPerThread <= m) {
+        uint32_t pk[4];
+#pragma unroll
+        for (int w = 0; w < 4; w++)
+            pk[w] = (uint32_t)c[4 * w] | ((uint32_t)c[4 * w + 1] << 8) | ((uint32_t)c[4 * w + 2] << 16) |
+                    ((uint32_t)c[4 * w + 3] << 24);
+        *reinterpret_cast<uint4 *>(L_all + bo + j0) = make_uint4(pk[0], pk[1], pk[2], pk[3]);
+    } else {
+#pragma unroll
+        for (int q = 0; q < kPerThread; q++)
+            if (j0 + q < m) L_all[bo + j0 + q] = c[q];
+    }
+#pragma unroll
+    for (int q = kPerThread - 1; q >= 0; q--) {  // last occurrence in the run first
+        if (j0 + q >= m) continue;
+        bool seen = false;
+#pragma unroll
+        for (int r = q + 1; r < kPerThread; r++) seen |= (j0 + r < m) && c[r] == c[q];
+        if (!seen) atomicMax(&lastpos[c[q]], jl + q);
+    }
     __syncthreads();
-    if (threadIdx.x < 8 && used[threadIdx.x]) atomicOr(&st[b].in_use[threadIdx.x], used[threadIdx.x]);
+    const int x = threadIdx.x;
+    const int lp = lastpos[x];
+    if (lp >= 0) mark[lp] = (uint16_t)(x + 1);
+    const uint32_t present = __ballot_sync(LFC_FULL, lp >= 0);  // values 32 w .. 32 w + 31
+    if ((threadIdx.x & 31) == 0 && present) atomicOr(&st[b].in_use[threadIdx.x >> 5], present);
+    __syncthreads();
+    // compaction, highest positions first: thread t takes positions 4095 - 16 t - q
+    const int top = kTile - 1 - jl;
+    int cnt = 0;
+#pragma unroll
+    for (int q = 0; q < kPerThread; q++) cnt += mark[top - q] != 0;
+    int total;
+    int o = block_excl_sum<int>(cnt, sh, &total);
+    uint8_t *rec = rec_all + ((size_t)b * kTilesPerBlock + tile) * 256;
+#pragma unroll
+    for (int q = 0; q < kPerThread; q++) {
+        const uint16_t mv = mark[top - q];
+        if (mv) rec[o++] = (uint8_t)(mv - 1);
+    }
+    if (threadIdx.x == 0) reclen_all[(size_t)b * kTilesPerBlock + tile] = total;
 }
 
 template <int MODE>
@@ -746,7 +797,7 @@ cudaError_t launch_bwt(lfc_plan P, int nblocks, int max_m) {
     }
     stage_end(P, LFC_STAGE_BWT_REFINE);
     stage_begin(P, LFC_STAGE_BWT_OUT);
-    bwt_output_kernel<<<grid, kSortThreads, 0, s>>>(ws.bstate, ws.sa, ws.rle, ws.bwt);
+    bwt_output_kernel<<<grid, kSortThreads, 0, s>>>(ws.bstate, ws.sa, ws.rle, ws.bwt, ws.mtfrec, ws.mtfreclen);
     stage_end(P, LFC_STAGE_BWT_OUT);
     count_launches(P, 1);
     return cudaGetLastError();

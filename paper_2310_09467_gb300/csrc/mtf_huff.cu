@@ -27,85 +27,48 @@ __device__ __forceinline__ void build_seq_table(const uint32_t *in_use, uint8_t 
 }
 
 // ---------------------------------------------------- MTF: segment summaries
-__global__ void __launch_bounds__(32) mtf_summary_kernel(BlockState *__restrict__ st, const uint8_t *__restrict__ L_all,
-                                                         uint8_t *__restrict__ rec_all, int32_t *__restrict__ reclen_all) {
+// The summaries (distinct bytes of each 4096-byte segment of L by last use,
+// latest first) come from the BWT output kernel, as byte values.
+// One CTA per block: starting list of every segment, one list entry per
+// thread. Composing a segment's summary: its record first, then the old
+// list without the record's symbols (kept entries compacted by a scan).
+__global__ void __launch_bounds__(256) mtf_compose_kernel(const BlockState *__restrict__ st, const uint8_t *__restrict__ rec_all,
+                                                          const int32_t *__restrict__ reclen_all, uint8_t *__restrict__ lists_all) {
+    __shared__ uint8_t lst[256];
+    __shared__ uint8_t inr[256];
     __shared__ uint8_t seq[256];
-    __shared__ uint8_t seen[256];
-    const int b = blockIdx.y, g = blockIdx.x;
-    const int m = st[b].m;
-    const int s0 = g * kTile;
-    if (s0 >= m) return;
-    const int s1 = min(m, s0 + kTile);
-    uint32_t iu[8];
-    for (int i = 0; i < 8; i++) iu[i] = st[b].in_use[i];
-    if (threadIdx.x == 0) {
-        int n = 0;
-        for (int i = 0; i < 8; i++) n += __popc(iu[i]);
-        st[b].n_in_use = n;  // same value from every segment
-    }
     __shared__ uint32_t iush[8];
-    if (threadIdx.x < 8) iush[threadIdx.x] = iu[threadIdx.x];
-    __syncwarp();
-    build_seq_table(iush, seq);
-    for (int i = threadIdx.x; i < 256; i += 32) seen[i] = 0;
-    __syncwarp();
-    int n_in_use = 0;
-    for (int i = 0; i < 8; i++) n_in_use += __popc(iu[i]);
-    const uint8_t *L = L_all + (size_t)b * kBlockCap;
-    uint8_t *rec = rec_all + ((size_t)b * kTilesPerBlock + g) * 256;
-    const int lane = threadIdx.x;
-    int len = 0;
-    for (int wend = s1; wend > s0 && len < n_in_use; wend -= 32) {
-        const int ws0 = max(s0, wend - 32);
-        const int i = ws0 + lane;
-        const bool valid = i < wend;
-        const uint32_t s = valid ? seq[L[i]] : 0u;
-        const uint32_t mm = __match_any_sync(LFC_FULL, valid ? s : 256u + lane);
-        const bool leader = valid && (mm & lanemask_gt()) == 0;  // latest use in the window
-        const bool fresh = leader && !seen[s];
-        const uint32_t bal = __ballot_sync(LFC_FULL, fresh);
-        if (fresh) {
-            rec[len + __popc(bal & lanemask_gt())] = (uint8_t)s;  // later lanes first
-            seen[s] = 1;
-        }
-        len += __popc(bal);
-        __syncwarp();
-    }
-    if (lane == 0) reclen_all[(size_t)b * kTilesPerBlock + g] = len;
-}
-
-// One warp per block: starting list of every segment.
-__global__ void __launch_bounds__(32) mtf_compose_kernel(const BlockState *__restrict__ st, const uint8_t *__restrict__ rec_all,
-                                                         const int32_t *__restrict__ reclen_all, uint8_t *__restrict__ lists_all) {
-    __shared__ uint8_t lst[256], nxt[256], inr[256];
-    const int b = blockIdx.x;
+    __shared__ int32_t rl_s[kTilesPerBlock];
+    __shared__ int sh[33];
+    const int b = blockIdx.x, t = threadIdx.x;
     const int m = st[b].m;
+    if (t < 8) iush[t] = st[b].in_use[t];
+    __syncthreads();
+    build_seq_table(iush, seq);  // records hold byte values; lists hold their indices
     int n_in_use = 0;
-    for (int i = 0; i < 8; i++) n_in_use += __popc(st[b].in_use[i]);
+    for (int i = 0; i < 8; i++) n_in_use += __popc(iush[i]);
     const int ng = (m + kTile - 1) / kTile;
-    const int lane = threadIdx.x;
-    for (int i = lane; i < 256; i += 32) lst[i] = i < n_in_use ? (uint8_t)i : (uint8_t)0xFF;
-    __syncwarp();
+    for (int g = t; g < ng; g += 256) rl_s[g] = reclen_all[(size_t)b * kTilesPerBlock + g];
+    lst[t] = t < n_in_use ? (uint8_t)t : (uint8_t)0xFF;
+    const uint8_t *recb = rec_all + (size_t)b * kTilesPerBlock * 256;
+    uint8_t r_next = ng > 0 ? recb[t] : 0;
+    __syncthreads();
+    r_next = seq[r_next];
     for (int g = 0; g < ng; g++) {
-        uint8_t *out = lists_all + ((size_t)b * kTilesPerBlock + g) * 256;
-        for (int i = lane; i < 256; i += 32) out[i] = lst[i];
-        const uint8_t *rec = rec_all + ((size_t)b * kTilesPerBlock + g) * 256;
-        const int rl = reclen_all[(size_t)b * kTilesPerBlock + g];
-        for (int i = lane; i < 256; i += 32) inr[i] = 0;
-        __syncwarp();
-        for (int i = lane; i < rl; i += 32) { const uint8_t v = rec[i]; inr[v] = 1; nxt[i] = v; }
-        __syncwarp();
-        int pos = rl;
-        for (int c = 0; c < 256; c += 32) {
-            const int i = c + lane;
-            const bool keep = i < n_in_use && !inr[lst[i]];
-            const uint32_t bal = __ballot_sync(LFC_FULL, keep);
-            if (keep) nxt[pos + __popc(bal & lanemask_lt())] = lst[i];
-            pos += __popc(bal);
-        }
-        __syncwarp();
-        for (int i = lane; i < 256; i += 32) lst[i] = i < n_in_use ? nxt[i] : (uint8_t)0xFF;
-        __syncwarp();
+        lists_all[((size_t)b * kTilesPerBlock + g) * 256 + t] = lst[t];
+        const int rl = rl_s[g];
+        const uint8_t r = r_next;
+        if (g + 1 < ng) r_next = seq[recb[(size_t)(g + 1) * 256 + t]];
+        inr[t] = 0;
+        __syncthreads();
+        if (t < rl) inr[r] = 1;
+        __syncthreads();
+        const uint8_t x = lst[t];
+        const bool keep = t < n_in_use && !inr[x];
+        const int pos = rl + block_excl_sum<int>(keep ? 1 : 0, sh, nullptr);  // syncs: all of lst is read
+        if (keep) lst[pos] = x;
+        if (t < rl) lst[t] = r;
+        __syncthreads();
     }
 }
 
@@ -933,14 +896,13 @@ cudaError_t launch_mtf_rle2(lfc_plan P, int nblocks) {
     Workspace &ws = P->ws;
     cudaStream_t s = P->stream;
     dim3 grid(kTilesPerBlock, nblocks);
-    mtf_summary_kernel<<<grid, 32, 0, s>>>(ws.bstate, ws.bwt, ws.mtfrec, ws.mtfreclen);
-    mtf_compose_kernel<<<nblocks, 32, 0, s>>>(ws.bstate, ws.mtfrec, ws.mtfreclen, ws.mtflists);
+    mtf_compose_kernel<<<nblocks, 256, 0, s>>>(ws.bstate, ws.mtfrec, ws.mtfreclen, ws.mtflists);
     mtf_encode_kernel<<<grid, 32, 0, s>>>(ws.bstate, ws.bwt, ws.mtflists, ws.mtfidx);
     const dim3 g2(kTilesPerBlock, nblocks);  // RLE1 output <= 900000 = 220 tiles
     rle2_tile_kernel<<<g2, kRle2Threads, 0, s>>>(ws.bstate, ws.mtfidx, ws.tileaux);
     rle2_scan_kernel<<<nblocks, 32, 0, s>>>(ws.bstate, ws.tileaux, ws.sym, ws.freq);
     rle2_write_kernel<<<g2, kRle2Threads, 0, s>>>(ws.bstate, ws.mtfidx, ws.tileaux, ws.sym, ws.freq);
-    count_launches(P, 6);
+    count_launches(P, 5);
     return cudaGetLastError();
 }
 
