@@ -19,6 +19,11 @@
 //     already in start-index order (every pass is stable and the first starts
 //     from the identity).
 #include <climits>
+#include <utility>
+
+#ifndef LFC_PHASE1_BYTES
+#define LFC_PHASE1_BYTES 8
+#endif
 
 #include "lfc_common.cuh"
 
@@ -237,6 +242,10 @@ template <int MODE>
 __device__ __forceinline__ int round_h(const int32_t *rs) { return MODE == 0 ? 0 : rs[2]; }
 
 // Phase 1 keys: K[v] = bytes v .. v + 7 (cyclic) big-endian, element v.
+// Phase 1 sorts the first kPhase1Bytes bytes of every rotation; they sit in
+// the top bytes of the 64-bit key, so passes 8 - kPhase1Bytes .. 7 carry them.
+constexpr int kPhase1Bytes = LFC_PHASE1_BYTES;
+
 __global__ void __launch_bounds__(kSortThreads) key8_kernel(const BlockState *__restrict__ st,
                                                             const uint8_t *__restrict__ rle_all,
                                                             uint64_t *__restrict__ K_all, int32_t *__restrict__ V_all) {
@@ -256,8 +265,8 @@ __global__ void __launch_bounds__(kSortThreads) key8_kernel(const BlockState *__
         if (kl >= cnt) break;
         uint64_t key = 0;
 #pragma unroll
-        for (int q = 0; q < 8; q++) key = (key << 8) | sb[kl + q];
-        K[t0 + kl] = key;
+        for (int q = 0; q < kPhase1Bytes; q++) key = (key << 8) | sb[kl + q];
+        K[t0 + kl] = key << (8 * (8 - kPhase1Bytes));
         V[t0 + kl] = t0 + kl;
     }
 }
@@ -577,7 +586,7 @@ __global__ void __launch_bounds__(kSortThreads) heads_apply_kernel(const int32_t
         if (hd) carry = pos;
         const int32_t v = MODE == 0 ? sorted[k] : (int32_t)(words[k] & kElemMask);
         rank[v] = carry;
-        if (MODE == 1) sa[pos] = v;
+        if (MODE == 1 || sorted != sa) sa[pos] = v;
         if (!(hd && nh)) {
             act_out[off] = pos;
             val_out[off] = v;
@@ -594,7 +603,7 @@ __global__ void commit_round_kernel(BlockState *st, int nblocks) {
 __global__ void round_start_kernel(int32_t *rs, int first) {
     rs[0] = 0;
     rs[1] = 0;
-    if (first) { rs[2] = 8; rs[3] = 0; }
+    if (first) { rs[2] = kPhase1Bytes; rs[3] = 0; }
 }
 
 // End of a doubling round: double h; inside a graph, continue the WHILE node
@@ -734,16 +743,19 @@ cudaError_t launch_bwt(lfc_plan P, int nblocks, int max_m) {
     dim3 grid(tiles, nblocks);
     key8_kernel<<<grid, kSortThreads, 0, s>>>(ws.bstate, ws.rle, ws.keys, ws.sa);
     count_launches(P, 1);
-    for (int pass = 0; pass < 8; pass++) {
-        if (pass & 1) radix_pass<0>(P, s, nblocks, tiles, pass, ws.keys2, ws.sa2, ws.keys, ws.sa);
-        else radix_pass<0>(P, s, nblocks, tiles, pass, ws.keys, ws.sa, ws.keys2, ws.sa2);
+    uint64_t *kin = ws.keys, *kout = ws.keys2;
+    int32_t *vin = ws.sa, *vout = ws.sa2;
+    for (int pass = 8 - kPhase1Bytes; pass < 8; pass++) {
+        radix_pass<0>(P, s, nblocks, tiles, pass, kin, vin, kout, vout);
+        std::swap(kin, kout);
+        std::swap(vin, vout);
     }
-    stage_end(P, LFC_STAGE_BWT_SORT8);
+    stage_end(P, LFC_STAGE_BWT_SORT8);  // sorted keys / suffix array now in kin / vin
     stage_begin(P, LFC_STAGE_BWT_REFINE);
     round_start_kernel<<<1, 1, 0, s>>>(ws.act_total, 1);
-    heads_tile_kernel<0><<<grid, kSortThreads, 0, s>>>(ws.act_total, ws.bstate, ws.keys, ws.sa, ws.sa, ws.bwt, ws.tileaux);
+    heads_tile_kernel<0><<<grid, kSortThreads, 0, s>>>(ws.act_total, ws.bstate, kin, ws.sa, ws.sa, ws.bwt, ws.tileaux);
     heads_scan_kernel<0><<<nblocks, 256, 0, s>>>(ws.act_total, ws.bstate, ws.tileaux);
-    heads_apply_kernel<0><<<grid, kSortThreads, 0, s>>>(ws.act_total, ws.bstate, ws.sa, nullptr, ws.act, ws.act2,
+    heads_apply_kernel<0><<<grid, kSortThreads, 0, s>>>(ws.act_total, ws.bstate, vin, nullptr, ws.act, ws.act2,
                                                         ws.bwt, ws.tileaux, ws.rank, ws.sa, ws.val);
     commit_round_kernel<<<(nblocks + 255) / 256, 256, 0, s>>>(ws.bstate, nblocks);
     count_launches(P, 5);
@@ -783,7 +795,7 @@ cudaError_t launch_bwt(lfc_plan P, int nblocks, int max_m) {
         e = cudaStreamSynchronize(s);
         if (e != cudaSuccess) return e;
         int round = 0;
-        for (int h = 8; ws.h_act_total[0] > 0 && h < max_m; h *= 2, round++) {
+        for (int h = kPhase1Bytes; ws.h_act_total[0] > 0 && h < max_m; h *= 2, round++) {
             P->bwt_rounds++;
             P->bwt_tied_total += ws.h_act_total[0];
             if (round < 32) P->bwt_round_tied[round] += ws.h_act_total[0];
