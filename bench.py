@@ -33,12 +33,12 @@ METRIC = "raw MB/s compressed (exhaustive judge + bzip2 900k blocks + container)
 WORKLOAD = "2040x2040 uint16 LFM frames, 136x136 lenslets at pitch 15 (beads 20/2000 photons, cells 500)"
 
 
-def make_frames(per_kind: int):
-    from paper_2310_09467_gb300 import synth
+def make_frames(per_kind: int, rank: int = 0):
+    from paper_2310_09467_gb300 import replicas, synth
     out = []
     for i in range(per_kind):
         for k, (kind, level) in enumerate(KINDS):
-            seed = 1 + k + 3 * i
+            seed = replicas.frame_seed(rank, i, k, len(KINDS))
             if kind == "beads":
                 out.append(synth.beads(W, H, PITCH, peak=level, seed=seed))
             else:
@@ -321,15 +321,14 @@ def main():
 
     from paper_2310_09467_gb300 import build, lfc
 
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
+    from paper_2310_09467_gb300 import replicas
+    world, rank, local = replicas.rank_env()
     torch.cuda.set_device(local)
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl")
     build.build()
-    frames_np = make_frames(args.per_kind)
+    frames_np = make_frames(args.per_kind, rank)  # each rank its own frames
     n = len(frames_np)
     raw_bytes = sum(f.nbytes for f in frames_np)
     frames = [lfc.to_device_frame(f) for f in frames_np]
@@ -374,13 +373,8 @@ def main():
                                             zip(bc0["tied_per_round"] + [0] * 32, bc1["tied_per_round"])],
                 "elements_per_call": (bc1["input_bytes"] - bc0["input_bytes"]) / max(1, bc1["calls"] - bc0["calls"])}
     plan.set_timing(False)
-    total_ms = sum(step_ms)
-    if world > 1:
-        import torch.distributed as dist
-        t = torch.tensor([total_ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
-    value = world * raw_bytes * args.steps / 1e6 / (total_ms / 1e3)
+    total_ms, job_bytes = replicas.aggregate(sum(step_ms), raw_bytes * args.steps, device="cuda")
+    value = replicas.throughput_mbps(total_ms, job_bytes)
     sz = sizes.cpu().numpy()
     comp_bytes = int(sz.sum())
 
@@ -423,7 +417,8 @@ def main():
             d2h += s
         torch.cuda.synchronize()
         e2e_ms.append(1e3 * (time.perf_counter() - t0))
-    e2e_value = raw_bytes / 1e6 / (statistics.median(e2e_ms) / 1e3) * world
+    e2e_job_ms, e2e_bytes = replicas.aggregate(statistics.median(e2e_ms), raw_bytes, device="cuda")
+    e2e_value = replicas.throughput_mbps(e2e_job_ms, e2e_bytes)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
