@@ -225,7 +225,7 @@ static void free_ws(Workspace &w) {
     void *ptrs[] = {w.hist, w.summ, w.scores, w.choice, w.jframes, w.cand, w.l2tab, w.stream, w.blocks, w.bstate,
                     w.rle, w.sa, w.sa2, w.rank, w.act, w.act2, w.val, w.val2, w.keys, w.keys2, w.tilecnt, w.tileaux, w.bwt,
                     w.mtfidx, w.mtflists, w.mtfrec, w.mtfreclen, w.sym, w.freq, w.rfreq, w.sel, w.lens, w.codes, w.packed, w.cstream, w.masks, w.class_ids,
-                    w.act_total, w.block_dst, w.frame_crc, w.crc_part, w.chunk_desc, w.dec_tt};
+                    w.act_total, w.block_dst, w.frame_crc, w.crc_part, w.crc_part2, w.chunk_desc, w.dec_tt};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     if (w.h_act_total) cudaFreeHost(w.h_act_total);
@@ -332,11 +332,15 @@ extern "C" int lfc_plan_create(const lfc_config *cfg, void *cuda_stream, lfc_pla
     AL(block_dst, (size_t)BC);
     AL(frame_crc, (size_t)F);
     AL(crc_part, (size_t)ws.crc_part_cap);
+    AL(crc_part2, (size_t)ws.crc_part_cap);
 #undef AL
     if (e == cudaSuccess) e = cudaMalloc(&ws.chunk_desc, ws.chunk_desc_bytes);
     if (e == cudaSuccess) e = cudaMallocHost(reinterpret_cast<void **>(&ws.h_act_total), 4 * sizeof(int32_t));
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&P->aux_stream, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&P->cap_stream, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&P->side_stream, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&P->side_fork, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&P->side_join, cudaEventDisableTiming);
     if (e == cudaSuccess) e = init_l2_table(ws.l2tab, P->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(P->stream);
     if (e != cudaSuccess) {
@@ -360,6 +364,9 @@ extern "C" void lfc_plan_destroy(lfc_plan P) {
     free_ws(P->ws);
     if (P->aux_stream) cudaStreamDestroy(P->aux_stream);
     if (P->cap_stream) cudaStreamDestroy(P->cap_stream);
+    if (P->side_stream) cudaStreamDestroy(P->side_stream);
+    if (P->side_fork) cudaEventDestroy(P->side_fork);
+    if (P->side_join) cudaEventDestroy(P->side_join);
     delete P;
 }
 
@@ -531,9 +538,12 @@ int run_pass(lfc_plan P, const CoderPass &cp, const uint8_t *d_arena) {
     const int nb = cp.nblocks;
     for (const BlockDesc &b : cp.blocks) P->bwt_elements_in += b.len;
     CK(cudaMemsetAsync(ws.bstate, 0, sizeof(BlockState) * nb, P->stream));
-    stage_begin(P, LFC_STAGE_CRC);
-    CK(launch_crc(P, d_arena + cp.off_crc, cp.crc, &ws.bstate[0].crc, (int)(sizeof(BlockState) / 4)));
-    stage_end(P, LFC_STAGE_CRC);
+    // block CRCs on the side stream, overlapped with RLE1 and the BWT (each
+    // writes only its own word of the block state; packing reads it)
+    CK(cudaEventRecord(P->side_fork, P->stream));
+    CK(cudaStreamWaitEvent(P->side_stream, P->side_fork, 0));
+    CK(launch_crc(P, d_arena + cp.off_crc, cp.crc, &ws.bstate[0].crc, (int)(sizeof(BlockState) / 4), P->side_stream));
+    CK(cudaEventRecord(P->side_join, P->side_stream));
     stage_begin(P, LFC_STAGE_RLE1);
     CK(launch_rle1(P, nb, reinterpret_cast<const BlockDesc *>(d_arena + cp.off_blocks)));
     stage_end(P, LFC_STAGE_RLE1);
@@ -544,6 +554,7 @@ int run_pass(lfc_plan P, const CoderPass &cp, const uint8_t *d_arena) {
     stage_begin(P, LFC_STAGE_HUFFMAN);
     CK(launch_huffman(P, nb));
     stage_end(P, LFC_STAGE_HUFFMAN);
+    CK(cudaStreamWaitEvent(P->stream, P->side_join, 0));
     stage_begin(P, LFC_STAGE_PACK);
     CK(launch_pack(P, nb));
     stage_end(P, LFC_STAGE_PACK);
@@ -634,6 +645,11 @@ int run_compress(lfc_plan P, const CompressDesc &D, const uint8_t *d_arena, cons
                  uint64_t *d_out_sizes) {
     Workspace &ws = P->ws;
     const uint8_t *choice = d_choice;
+    // frame CRCs of the raw frames do not depend on the judge: side stream
+    CK(cudaEventRecord(P->side_fork, P->stream));
+    CK(cudaStreamWaitEvent(P->side_stream, P->side_fork, 0));
+    CK(launch_crc(P, d_arena + D.off_frame_crc, D.frame_crc, ws.frame_crc, 1, P->side_stream, ws.crc_part2));
+    CK(cudaEventRecord(P->side_join, P->side_stream));
     if (!D.judge.empty()) {  // the judge also copies out the chosen streams
         const int r = run_judge(P, D.frames, D.judge, d_arena, ws.choice, ws.scores,
                                 reinterpret_cast<uint8_t *const *>(d_arena + D.off_dst));
@@ -645,9 +661,7 @@ int run_compress(lfc_plan P, const CompressDesc &D, const uint8_t *d_arena, cons
         count_launches(P, (D.n + 7) / 8);
         stage_end(P, LFC_STAGE_EMIT);
     }
-    stage_begin(P, LFC_STAGE_CRC);
-    CK(launch_crc(P, d_arena + D.off_frame_crc, D.frame_crc, ws.frame_crc, 1));
-    stage_end(P, LFC_STAGE_CRC);
+    CK(cudaStreamWaitEvent(P->stream, P->side_join, 0));
     for (const CoderPass &cp : D.passes) {
         const int r = run_pass(P, cp, d_arena);
         if (r) return r;

@@ -173,11 +173,14 @@ void crc_build_tables(const uint8_t *const *ptr, const int64_t *len, int n, uint
 }
 
 // Launches a CRC run whose tables sit at d_tables (device).
-cudaError_t launch_crc(lfc_plan P, const uint8_t *d_tables, const CrcRun &run, uint32_t *out, int out_stride_words) {
+cudaError_t launch_crc(lfc_plan P, const uint8_t *d_tables, const CrcRun &run, uint32_t *out, int out_stride_words,
+                       cudaStream_t stream, uint32_t *part) {
     if (run.nchunks > P->ws.crc_part_cap) return cudaErrorInvalidValue;
-    if (run.nchunks) crc_chunk_kernel<<<(unsigned)run.nchunks, 256, 0, P->stream>>>(reinterpret_cast<const CrcChunk *>(d_tables), P->ws.crc_part);
-    crc_finish_kernel<<<(run.nranges + 127) / 128, 128, 0, P->stream>>>(
-        P->ws.crc_part, reinterpret_cast<const int32_t *>(d_tables + run.off_first),
+    if (!stream) stream = P->stream;
+    if (!part) part = P->ws.crc_part;
+    if (run.nchunks) crc_chunk_kernel<<<(unsigned)run.nchunks, 256, 0, stream>>>(reinterpret_cast<const CrcChunk *>(d_tables), part);
+    crc_finish_kernel<<<(run.nranges + 127) / 128, 128, 0, stream>>>(
+        part, reinterpret_cast<const int32_t *>(d_tables + run.off_first),
         reinterpret_cast<const uint32_t *>(d_tables + run.off_len), run.nranges, out, out_stride_words);
     count_launches(P, run.nchunks ? 2 : 1);
     return cudaGetLastError();

@@ -204,6 +204,7 @@ struct Workspace {
     uint64_t *block_dst = nullptr;     // block_cap: stream destination offsets
     uint32_t *frame_crc = nullptr;     // max_frames
     uint32_t *crc_part = nullptr;      // CRC partial remainders
+    uint32_t *crc_part2 = nullptr;   // partial remainders of the frame CRCs (side stream)
     int64_t crc_part_cap = 0;
     void *chunk_desc = nullptr;        // descriptor staging (CRC chunks, frame tables)
     size_t chunk_desc_bytes = 0;
@@ -217,6 +218,8 @@ struct lfc_plan_s {
     lfc_config cfg;
     cudaStream_t stream = nullptr;
     cudaStream_t aux_stream = nullptr;  // capture of conditional-node bodies
+    cudaStream_t side_stream = nullptr; // CRCs, overlapped with the judge and the BWT
+    cudaEvent_t side_fork = nullptr, side_join = nullptr;
     cudaStream_t cap_stream = nullptr;  // capture of batches
     int device = 0;
     std::string err;
@@ -287,7 +290,8 @@ struct CrcRun {
 int crc_count_chunks(const int64_t *len, int n);
 size_t crc_table_bytes(int nchunks, int n);
 void crc_build_tables(const uint8_t *const *ptr, const int64_t *len, int n, uint8_t *out, CrcRun *run);
-cudaError_t launch_crc(lfc_plan P, const uint8_t *d_tables, const CrcRun &run, uint32_t *out, int out_stride_words);
+cudaError_t launch_crc(lfc_plan P, const uint8_t *d_tables, const CrcRun &run, uint32_t *out, int out_stride_words,
+                       cudaStream_t stream = nullptr, uint32_t *part = nullptr);
 cudaError_t launch_block_crc(lfc_plan P, const BlockDesc *h_blocks, int nblocks, BlockState *d_state);
 cudaError_t launch_range_crc(lfc_plan P, const uint8_t *const *h_ptr, const int64_t *h_len, int n,
                              uint32_t *d_out);
