@@ -351,14 +351,19 @@ __global__ void __launch_bounds__(1024) radix_scan_kernel(const int32_t *__restr
     uint32_t *cnt = cnt_all + (size_t)b * 256 * kTilesPerBlock;
     const int per = (total + blockDim.x - 1) / blockDim.x;
     const int a = min(total, (int)threadIdx.x * per), e = min(total, a + per);
+    const int d0 = a / nt, t0 = a - d0 * nt;  // (digit, tile) of the first entry
     uint32_t sum = 0;
-    for (int q = a; q < e; q++) sum += cnt[(q / nt) * kTilesPerBlock + q % nt];
+    for (int q = a, d = d0, t = t0; q < e; q++) {
+        sum += cnt[d * kTilesPerBlock + t];
+        if (++t == nt) { t = 0; d++; }
+    }
     uint32_t off = block_excl_sum<uint32_t>(sum, sh, nullptr);
-    for (int q = a; q < e; q++) {
-        uint32_t &c = cnt[(q / nt) * kTilesPerBlock + q % nt];
+    for (int q = a, d = d0, t = t0; q < e; q++) {
+        uint32_t &c = cnt[d * kTilesPerBlock + t];
         const uint32_t v = c;
         c = off;
         off += v;
+        if (++t == nt) { t = 0; d++; }
     }
 }
 
