@@ -251,7 +251,7 @@ constexpr int kHot = 128;                                            // hot corn
 constexpr uint32_t kNoPred = 0xFFFF;
 
 size_t chain_smem_bytes() {
-    return (size_t)kHot * kHot * 4 + (size_t)kChainWarps * (256 * 2 + 256 + kChainChunk);
+    return (size_t)(kHot * kHot + 32) * 4 + (size_t)kChainWarps * (256 * 2 + 256 + kChainChunk);
 }
 int64_t chain_seg_bytes(int range_bytes) { return (int64_t)kChainWarps * range_bytes; }
 
@@ -286,10 +286,10 @@ __device__ __forceinline__ void chain_step(const uint8_t *stage, int pos, int li
     const uint32_t both = p | a;
     const uint32_t zb = __ballot_sync(LFC_FULL, pair && both == 0);
     c0 += __popc(zb);
-    if (pair && both != 0) {
-        if (both < (uint32_t)kHot) atomicAdd(&hot[p * kHot + a], 1u);
-        else atomicAdd(&ghist[(p << 8) | a], 1u);
-    }
+    const bool hotp = pair && both != 0 && both < (uint32_t)kHot;
+    // branch-free: lanes without a hot pair add 0 to their own dummy slot
+    atomicAdd(&hot[hotp ? p * kHot + a : kHot * kHot + lane], hotp ? 1u : 0u);
+    if (pair && both >= (uint32_t)kHot) atomicAdd(&ghist[(p << 8) | a], 1u);
     __syncwarp();
 }
 
@@ -299,7 +299,7 @@ chain_hist_kernel(const JudgeFrame *__restrict__ frames, int nframes, const uint
                   uint16_t *__restrict__ summ, int range_bytes) {
     extern __shared__ __align__(16) uint8_t smem[];
     uint32_t *hot = reinterpret_cast<uint32_t *>(smem);                      // [kHot][kHot]
-    uint16_t *pend_all = reinterpret_cast<uint16_t *>(hot + kHot * kHot);    // [warps][256]
+    uint16_t *pend_all = reinterpret_cast<uint16_t *>(hot + kHot * kHot + 32);    // [warps][256]
     uint8_t *first_all = reinterpret_cast<uint8_t *>(pend_all + kChainWarps * 256);  // [warps][256]
     uint8_t *stage_all = first_all + kChainWarps * 256;                       // [warps][512]
     const int fi = find_frame_s(frames, nframes, blockIdx.x);
