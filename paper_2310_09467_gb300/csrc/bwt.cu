@@ -478,9 +478,32 @@ __global__ void __launch_bounds__(kSortThreads) heads_tile_kernel(const int32_t 
     uint8_t *flags = flags_all + (size_t)b * kBlockCap;
     const int k0 = tile * kTile + threadIdx.x * kPerThread;
     int hmax = -1, tied = 0;
-    if (k0 < n) {
+    const int ks = MODE == 0 ? 0 : 20;  // round words carry the element below the key
+    if (k0 + kPerThread <= n) {  // full run: 16-byte loads of the keys, one 16-byte store of the flags
+        uint64_t kk[kPerThread];
+        const ulonglong2 *K2 = reinterpret_cast<const ulonglong2 *>(K + k0);
+#pragma unroll
+        for (int q = 0; q < kPerThread / 2; q++) {
+            const ulonglong2 v = K2[q];
+            kk[2 * q] = v.x >> ks;
+            kk[2 * q + 1] = v.y >> ks;
+        }
+        const bool last_head = k0 + kPerThread >= n || (K[k0 + kPerThread] >> ks) != kk[kPerThread - 1];
+        bool curhead = (k0 == 0) || kk[0] != (K[k0 - (k0 > 0)] >> ks);
+        uint32_t fl[4] = {0u, 0u, 0u, 0u};
+#pragma unroll
+        for (int q = 0; q < kPerThread; q++) {
+            const bool nexthead = q + 1 < kPerThread ? kk[q + 1] != kk[q] : last_head;
+            if (curhead) {
+                fl[q >> 2] |= 1u << (8 * (q & 3));
+                hmax = MODE == 0 ? k0 + q : act[k0 + q];
+            }
+            tied += !(curhead && nexthead);
+            curhead = nexthead;
+        }
+        *reinterpret_cast<uint4 *>(flags + k0) = make_uint4(fl[0], fl[1], fl[2], fl[3]);
+    } else if (k0 < n) {
         const int k1 = min(n, k0 + kPerThread);
-        const int ks = MODE == 0 ? 0 : 20;  // round words carry the element below the key
         uint64_t prevk = k0 > 0 ? K[k0 - 1] >> ks : 0;
         uint64_t cur = K[k0] >> ks;
         bool curhead = (k0 == 0) || cur != prevk;
@@ -575,15 +598,74 @@ __global__ void __launch_bounds__(kSortThreads) heads_apply_kernel(const int32_t
     const int k0 = tile * kTile + threadIdx.x * kPerThread;
     const int k1 = min(n, k0 + kPerThread);
     int mine = -1, tied = 0;
-    for (int k = k0; k < k1; k++) {
-        const bool hd = flags[k];
-        const bool nh = (k + 1 >= n) || flags[k + 1];
-        if (hd) mine = MODE == 0 ? k : act[k];
-        tied += !(hd && nh);
+    // a full run loads flags, positions and elements with 16-byte loads; the
+    // block scans are reached by every thread
+    const bool full = k0 + kPerThread <= n;
+    uint32_t fw[4] = {0u, 0u, 0u, 0u};
+    bool last_next = true;
+    int32_t pv[kPerThread];
+    if (full) {
+        const uint4 f4 = *reinterpret_cast<const uint4 *>(flags + k0);
+        fw[0] = f4.x; fw[1] = f4.y; fw[2] = f4.z; fw[3] = f4.w;
+        last_next = k0 + kPerThread >= n || flags[k0 + kPerThread];
+#pragma unroll
+        for (int q = 0; q < kPerThread; q += 4) {
+            if (MODE == 1) {
+                const int4 a4 = *reinterpret_cast<const int4 *>(act + k0 + q);
+                pv[q] = a4.x; pv[q + 1] = a4.y; pv[q + 2] = a4.z; pv[q + 3] = a4.w;
+            } else {
+                pv[q] = k0 + q; pv[q + 1] = k0 + q + 1; pv[q + 2] = k0 + q + 2; pv[q + 3] = k0 + q + 3;
+            }
+        }
+#pragma unroll
+        for (int q = 0; q < kPerThread; q++) {
+            const bool hd = (fw[q >> 2] >> (8 * (q & 3))) & 1u;
+            const bool nh = q + 1 < kPerThread ? ((fw[(q + 1) >> 2] >> (8 * ((q + 1) & 3))) & 1u) : last_next;
+            if (hd) mine = pv[q];
+            tied += !(hd && nh);
+        }
+    } else {
+        for (int k = k0; k < k1; k++) {
+            const bool hd = flags[k];
+            const bool nh = (k + 1 >= n) || flags[k + 1];
+            if (hd) mine = MODE == 0 ? k : act[k];
+            tied += !(hd && nh);
+        }
     }
     int carry = block_excl_max(mine, shm);
     carry = max(carry, aux[2]);
     int off = block_excl_sum<int>(tied, shs, nullptr) + aux[3];
+    if (full) {
+        int32_t vv[kPerThread];
+#pragma unroll
+        for (int q = 0; q < kPerThread; q += 4) {
+            if (MODE == 0) {
+                const int4 s4 = *reinterpret_cast<const int4 *>(sorted + k0 + q);
+                vv[q] = s4.x; vv[q + 1] = s4.y; vv[q + 2] = s4.z; vv[q + 3] = s4.w;
+            } else {
+                const ulonglong2 w0 = *reinterpret_cast<const ulonglong2 *>(words + k0 + q);
+                const ulonglong2 w1 = *reinterpret_cast<const ulonglong2 *>(words + k0 + q + 2);
+                vv[q] = (int32_t)(w0.x & kElemMask); vv[q + 1] = (int32_t)(w0.y & kElemMask);
+                vv[q + 2] = (int32_t)(w1.x & kElemMask); vv[q + 3] = (int32_t)(w1.y & kElemMask);
+            }
+        }
+#pragma unroll
+        for (int q = 0; q < kPerThread; q++) {
+            const bool hd = (fw[q >> 2] >> (8 * (q & 3))) & 1u;
+            const bool nh = q + 1 < kPerThread ? ((fw[(q + 1) >> 2] >> (8 * ((q + 1) & 3))) & 1u) : last_next;
+            const int pos = pv[q];
+            if (hd) carry = pos;
+            const int32_t v = vv[q];
+            rank[v] = carry;
+            if (MODE == 1 || sorted != sa) sa[pos] = v;
+            if (!(hd && nh)) {
+                act_out[off] = pos;
+                val_out[off] = v;
+                off++;
+            }
+        }
+        return;
+    }
     for (int k = k0; k < k1; k++) {
         const bool hd = flags[k];
         const bool nh = (k + 1 >= n) || flags[k + 1];

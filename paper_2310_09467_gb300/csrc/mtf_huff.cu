@@ -122,9 +122,10 @@ __global__ void __launch_bounds__(32) mtf_encode_kernel(const BlockState *__rest
         const uint32_t FO = __ballot_sync(LFC_FULL, fo);
         const uint32_t LAST = __ballot_sync(LFC_FULL, valid && (grp & gt) == 0);
         const uint32_t P = fo ? (uint32_t)posof[s] : 0u;
+        const uint32_t maxP = __reduce_max_sync(LFC_FULL, P);
+        const int pbits = 32 - __clz(maxP | 1u);  // bits of the deepest list position
         uint32_t gtm = 0, eqm = LFC_FULL;  // lanes with P_i > P
-#pragma unroll
-        for (int bb = 7; bb >= 0; bb--) {
+        for (int bb = pbits - 1; bb >= 0; bb--) {
             const uint32_t Bb = __ballot_sync(LFC_FULL, (P >> bb) & 1u);
             if ((P >> bb) & 1u) {
                 eqm &= Bb;
@@ -134,11 +135,11 @@ __global__ void __launch_bounds__(32) mtf_encode_kernel(const BlockState *__rest
             }
         }
         const int j = lower ? 31 - __clz(lower) : -1;
-        const uint32_t pp = lower ? (uint32_t)(j + 1) : 0u;  // prev + 1, in 0..32
+        const uint32_t pp = lower ? (uint32_t)(j + 1) : 0u;  // prev + 1, in 0..31 (j <= 30)
         const uint32_t T = (uint32_t)(j + 1);
         uint32_t gt2 = 0, eq2 = LFC_FULL;  // lanes with prev_i + 1 > j + 1
 #pragma unroll
-        for (int bb = 5; bb >= 0; bb--) {
+        for (int bb = 4; bb >= 0; bb--) {
             const uint32_t Bb = __ballot_sync(LFC_FULL, (pp >> bb) & 1u);
             if ((T >> bb) & 1u) {
                 eq2 &= Bb;
@@ -153,7 +154,6 @@ __global__ void __launch_bounds__(32) mtf_encode_kernel(const BlockState *__rest
         if (valid) out[i] = (uint8_t)idx;
         // list update
         const uint32_t D = __popc(FO);
-        const uint32_t maxP = __reduce_max_sync(LFC_FULL, P);
         if (lane < 8) WP[lane] = 0;
         __syncwarp();
         if (fo) atomicOr(&WP[P >> 5], 1u << (P & 31));
