@@ -723,14 +723,24 @@ __global__ void __launch_bounds__(kSortThreads) bwt_output_kernel(BlockState *__
     const int jl = (int)threadIdx.x * kPerThread;  // tile-local start of the thread's run
     const int j0 = tile * kTile + jl;
     uint8_t c[kPerThread];
+    int32_t sv[kPerThread];
+    if (j0 + kPerThread <= m) {  // full run: the suffix array by 16-byte loads
+#pragma unroll
+        for (int q = 0; q < kPerThread; q += 4) {
+            const int4 s4 = *reinterpret_cast<const int4 *>(sa_all + bo + j0 + q);
+            sv[q] = s4.x; sv[q + 1] = s4.y; sv[q + 2] = s4.z; sv[q + 3] = s4.w;
+        }
+    } else {
+#pragma unroll
+        for (int q = 0; q < kPerThread; q++) sv[q] = j0 + q < m ? sa_all[bo + j0 + q] : -1;
+    }
 #pragma unroll
     for (int q = 0; q < kPerThread; q++) {
-        const int j = j0 + q;
+        const int v = sv[q];
         c[q] = 0;
-        if (j < m) {
-            const int v = sa_all[bo + j];
+        if (v >= 0) {
             c[q] = rle_all[bo + (v == 0 ? m - 1 : v - 1)];
-            if (v == 0) st[b].orig_ptr = j;
+            if (v == 0) st[b].orig_ptr = j0 + q;
         }
     }
     if (j0 + kPerThread <= m) {
