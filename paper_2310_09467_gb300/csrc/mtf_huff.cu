@@ -285,8 +285,13 @@ __global__ void __launch_bounds__(32) rle2_scan_kernel(BlockState *__restrict__ 
         const int R = max(carryR, ex);
         int pre = 0;  // the zero run the tile starts with, if it ends in the tile
         if (valid && fs > ts) {
-            if (fs < te) pre = run_digits(fs - 1 - R);
-            else if (te == m) pre = run_digits(m - 1 - R);
+            if (fs < te) {
+                pre = run_digits(fs - 1 - R);
+            } else if (te == m || (t + 1 < ntile && aux[(t + 1) * 4 + 0] == te)) {
+                // no nonzero in the tile: the run ends at its last position when the
+                // block ends there or the next tile starts with a nonzero
+                pre = run_digits(te - 1 - R);
+            }
         }
         const int out = valid ? pre + lo : 0;
         const int incl = warp_incl_sum(out);

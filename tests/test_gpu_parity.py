@@ -90,9 +90,12 @@ def _coder_inputs():
     yield [b"aaaabbbb" * 90000]                                   # 720000 -> 900000 after RLE1
     yield [bytes(rng.integers(0, 256, 720000, dtype=np.uint8)), b"xyz" * 240000]
     yield [bytes(rng.integers(0, 2, 250000, dtype=np.uint8) * 255)]
+    # last columns b^8192 a^8192 and z^8192 x^8192 y^8192: zero MTF runs that fill whole
+    # 4096-position tiles and end exactly at a tile boundary
+    yield [b"ab" * 8192, b"xyz" * 8192]
 
 
-@pytest.mark.parametrize("case", range(7))
+@pytest.mark.parametrize("case", range(8))
 def test_bzip2_encode_bytes_identical(lfc, case):
     blocks = list(_coder_inputs())[case]
     plan = lfc.Plan(195, 195, 13, max_frames=4)
