@@ -1,0 +1,55 @@
+"""GPU parity at the benchmark's frame size (2040 x 2040, pitch 15): every
+judge score and the whole container against the oracle, bit-exact. These
+sizes span many chain CTAs, judge launches and coder tiles and blocks."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2310_09467_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def lfc():
+    import torch
+    from paper_2310_09467_gb300 import build, lfc as L
+    build.build()
+    torch.cuda.init()
+    return L
+
+
+@pytest.fixture(scope="module", params=["beads2000", "cells500"])
+def frame(request):
+    if request.param == "beads2000":
+        return synth.beads(2040, 2040, 15, peak=2000.0, seed=2)
+    return synth.cells(2040, 2040, 15, level=500.0, seed=3)
+
+
+def test_fullsize_judge_and_container(lfc, frame):
+    p = 15
+    plan = lfc.Plan(2040, 2040, p)
+    d = lfc.to_device_frame(frame)
+    choice, scores = plan.judge([d], p)
+    best, ref = oracle.judge(frame, p)
+    got = scores.cpu().numpy().view(np.uint64)[0]
+    assert [int(got[i]) for i in oracle.default_ids()] == ref
+    assert int(choice.cpu()[0]) == best
+    blob = plan.compress_to_bytes([d], p)[0]
+    assert blob == oracle.compress_id(frame, p, best)
+
+
+def test_fullsize_temporal(lfc):
+    """A series frame with its previous frame: 52 candidates, temporal base field."""
+    p = 15
+    vs = synth.VesselSeries(2040, 2040, p, seed=5)
+    f0, f1 = vs.frame(0), vs.frame(1)
+    plan = lfc.Plan(2040, 2040, p, max_frames=2, temporal=True)
+    d0, d1 = lfc.to_device_frame(f0), lfc.to_device_frame(f1)
+    choice, scores = plan.judge([d0, d1], p, prevs=[None, d0])
+    best, ref = oracle.judge(f1, p, oracle.default_ids(True), prev=f0)
+    got = scores.cpu().numpy().view(np.uint64)[1]
+    assert [int(got[i]) for i in oracle.default_ids(True)] == ref
+    assert int(choice.cpu()[1]) == best
+    blobs = plan.compress_to_bytes([d0, d1], p, prevs=[None, d0])
+    assert blobs[1] == oracle.compress_id(f1, p, best, prev=f0)

@@ -93,9 +93,11 @@ def _coder_inputs():
     # last columns b^8192 a^8192 and z^8192 x^8192 y^8192: zero MTF runs that fill whole
     # 4096-position tiles and end exactly at a tile boundary
     yield [b"ab" * 8192, b"xyz" * 8192]
+    # input runs filling whole RLE1 tiles and ending on tile boundaries
+    yield [b"a" * 8192 + b"b" * 5000 + b"c" * 4096 + bytes(range(256)) * 4, b"\x07" * 12288]
 
 
-@pytest.mark.parametrize("case", range(8))
+@pytest.mark.parametrize("case", range(9))
 def test_bzip2_encode_bytes_identical(lfc, case):
     blocks = list(_coder_inputs())[case]
     plan = lfc.Plan(195, 195, 13, max_frames=4)
