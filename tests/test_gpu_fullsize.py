@@ -37,6 +37,10 @@ def test_fullsize_judge_and_container(lfc, frame):
     assert int(choice.cpu()[0]) == best
     blob = plan.compress_to_bytes([d], p)[0]
     assert blob == oracle.compress_id(frame, p, best)
+    import torch
+    out = torch.empty(frame.shape, dtype=torch.int16, device="cuda")
+    plan.decompress([torch.from_numpy(np.frombuffer(blob, dtype=np.uint8).copy()).cuda()], [out])
+    assert np.array_equal(lfc.from_device_frame(out), frame)
 
 
 def test_fullsize_temporal(lfc):
