@@ -441,15 +441,19 @@ int build_judge(lfc_plan P, const lfc_frame *frames, int n, Arena &A, std::vecto
             JudgeFrame &J = jf[i];
             J.F = to_dev(fr, tmp);
             J.cand_off = (int32_t)cand.size();
-            uint32_t fset[2] = {0, 0};
+            uint32_t fset[2] = {0, 0}, fall[2] = {0, 0};  // f with a residual field / with any candidate
             for (uint8_t id : P->ids_spatial) cand.push_back(id);
             if (tmp)
                 for (uint8_t id : P->ids_temporal) cand.push_back(id);
             for (size_t k = J.cand_off; k < cand.size(); k++) {
                 const int id = cand[k], f = id & 15, dom = (id >> 4) & 3;
                 if (f && dom != 1) fset[(id >> 7) & 1] |= 1u << f;
+                if (f) fall[(id >> 7) & 1] |= 1u << f;
             }
-            C.L.nslots_max = std::max(C.L.nslots_max, std::max(__builtin_popcount(fset[0]), __builtin_popcount(fset[1])));
+            // shared-memory slots of the emission kernel: residual fields and symbol planes
+            for (int kd = 0; kd < 2; kd++)
+                C.L.nslots_max = std::max(C.L.nslots_max,
+                                          std::max(__builtin_popcount(fset[kd]), __builtin_popcount(fall[kd])));
             C.L.any_temporal |= tmp ? 1 : 0;
             C.L.max_p = std::max(C.L.max_p, fr.pitch);
             J.K = (int32_t)(cand.size() - J.cand_off);

@@ -42,10 +42,12 @@ __device__ __forceinline__ uint16_t zz16(int32_t e) {
     return (uint16_t)(((s << 1) ^ (s >> 31)) & 0xFFFF);
 }
 
+// nslots bounds both the residual fields (f with an intra or phase-space
+// candidate) and the symbol planes (f with an inter or phase-space candidate).
 size_t emit_all_smem_bytes(int p, int ts, int nslots) {
     const size_t cells = (size_t)(2 * p) * (size_t)((ts + 1) * p);
     const size_t outpx = (size_t)p * (size_t)(ts * p);
-    return cells * 2 * (size_t)(1 + nslots) + outpx * 2 * 3 + 256;
+    return cells * 2 * (size_t)(1 + nslots) + outpx * 2 * (size_t)(nslots > 0 ? nslots : 1) + 256;
 }
 
 // grid (tiles, frames, kind); kind 0 = raw base field, 1 = temporal difference.
@@ -132,84 +134,114 @@ __device__ __forceinline__ void emit_all_body(const JudgeFrame *__restrict__ fra
     // vector stores when every run start is aligned (slots are 256-byte aligned)
     const bool raw2 = (W % 2) == 0 && ((s0 * p) % 2) == 0 && (nco % 2) == 0;
     const bool vm8 = (ns % 8) == 0 && (W % 8) == 0 && (Nx % 8) == 0 && (s0 % 8) == 0;
+    // Writes the symbols get(r, c) of the tile's output pixels (row r of the
+    // lenslet row, column c) to candidate k0 in raw order and k1 in view-major
+    // order (view v = r, u = c mod p, lenslet s0 + c / p), consecutive threads
+    // on consecutive output positions.
+    auto write_both = [&](int k0, int k1, auto get) {
+        if (k0 >= 0) {
+            uint16_t *dst = base + (size_t)k0 * cslot16 + (size_t)(t * p) * W + (size_t)s0 * p;
+            if (raw2) {
+                const int h = nco >> 1;
+                for (int q = threadIdx.x; q < p * h; q += blockDim.x) {
+                    const int r = q / h, c2 = 2 * (q - r * h);
+                    *reinterpret_cast<uint32_t *>(dst + (size_t)r * W + c2) =
+                        (uint32_t)get(r, c2) | ((uint32_t)get(r, c2 + 1) << 16);
+                }
+            } else {
+                for (int r = 0; r < p; r++)
+                    for (int c = threadIdx.x; c < nco; c += blockDim.x) dst[(size_t)r * W + c] = get(r, c);
+            }
+        }
+        if (k1 >= 0) {
+            uint16_t *dst = base + (size_t)k1 * cslot16 + (size_t)t * W + s0;
+            if (vm8) {
+                const int hn = ns >> 3, items = p * p * hn;
+                for (int q = threadIdx.x; q < items; q += blockDim.x) {
+                    const int hh = q % hn, vu = q / hn, u = vu % p, v = vu / p;
+                    const int c = 8 * hh * p + u;
+                    uint4 o;
+                    o.x = (uint32_t)get(v, c) | ((uint32_t)get(v, c + p) << 16);
+                    o.y = (uint32_t)get(v, c + 2 * p) | ((uint32_t)get(v, c + 3 * p) << 16);
+                    o.z = (uint32_t)get(v, c + 4 * p) | ((uint32_t)get(v, c + 5 * p) << 16);
+                    o.w = (uint32_t)get(v, c + 6 * p) | ((uint32_t)get(v, c + 7 * p) << 16);
+                    *reinterpret_cast<uint4 *>(dst + (size_t)v * Ny * W + (size_t)u * Nx + 8 * hh) = o;
+                }
+            } else if (p * ns <= (int)blockDim.x) {
+                if (vm_j < p * ns)
+                    for (int v = 0; v < p; v++)
+                        dst[(size_t)v * Ny * W + (size_t)vm_u * Nx + vm_si] = get(v, vm_si * p + vm_u);
+            } else {
+                for (int v = 0; v < p; v++)
+                    for (int j = threadIdx.x; j < p * ns; j += blockDim.x) {
+                        const int u = j / ns, si = j - u * ns;
+                        dst[(size_t)v * Ny * W + (size_t)u * Nx + si] = get(v, si * p + u);
+                    }
+            }
+        }
+    };
+    // raw candidates (no predictor) and intra-lenslet candidates straight from
+    // the staged frame and the residual fields
+    if (fany & 1u)
+        write_both(slot_of[0][0][0], slot_of[0][0][1], [&](int r, int c) -> uint16_t {
+            const int32_t Xv = FVAL((p + r) * TC + p + c);
+            return kind ? zz16(Xv) : (uint16_t)Xv;
+        });
 #pragma unroll
-    for (int f = 0; f < 8; f++) {  // unrolled: the predictor of f is a constant
-        if (!((fany >> f) & 1u)) continue;
-        const bool n0 = slot_of[f][0][0] >= 0 || slot_of[f][0][1] >= 0;
-        const bool n1 = f && (slot_of[f][1][0] >= 0 || slot_of[f][1][1] >= 0);
-        const bool n2 = f && (slot_of[f][2][0] >= 0 || slot_of[f][2][1] >= 0);
-        const int16_t *Ef = E + (size_t)(f ? eslot_of[f] : 0) * cells;
+    for (int f = 1; f < 8; f++) {
+        if (!((fset >> f) & 1u) || (slot_of[f][0][0] < 0 && slot_of[f][0][1] < 0)) continue;
+        const int16_t *Ef = E + (size_t)eslot_of[f] * cells;
+        write_both(slot_of[f][0][0], slot_of[f][0][1],
+                   [&](int r, int c) -> uint16_t { return zz16(Ef[(p + r) * TC + p + c]); });
+    }
+    // inter-lenslet candidates of every f in one pass over the pixels, then
+    // the phase-space ones: symbols into planes of Sy, then written out
+    for (int dom = 1; dom <= 2; dom++) {
+        uint32_t fm = 0;
+        int plane[8];
+        int np = 0;
+#pragma unroll
+        for (int f = 1; f < 8; f++) {
+            plane[f] = -1;
+            if ((fany >> f) & 1u && (slot_of[f][dom][0] >= 0 || slot_of[f][dom][1] >= 0)) {
+                fm |= 1u << f;
+                plane[f] = np++;
+            }
+        }
+        if (!fm) continue;
         for (int c = threadIdx.x, sc = c / p; c < nco; c += blockDim.x, sc = c / p) {
             const int lx = p + c, s = s0 + sc;
             for (int r = 0; r < p; r++) {
                 const int idx = (p + r) * TC + lx, q = r * nco + c;
-                const int32_t Xv = FVAL(idx);
-                if (f == 0) {
-                    Sy[q] = kind ? zz16(Xv) : (uint16_t)Xv;
-                    continue;
-                }
-                if (n1) {
+                if (dom == 1) {
+                    const int32_t Xv = FVAL(idx);
                     const int32_t XA = s > 0 ? FVAL(idx - p) : 0;
                     const int32_t XB = t > 0 ? FVAL(idx - p * TC) : 0;
                     const int32_t XC = (s > 0 && t > 0) ? FVAL(idx - p * TC - p) : 0;
-                    Sy[npx + q] = zz16(Xv - g_pred(f, t, s, XA, XB, XC));
-                }
-                if (n0 || n2) {
-                    const int32_t e = Ef[idx];
-                    if (n0) Sy[q] = zz16(e);
-                    if (n2) {
+#pragma unroll
+                    for (int f = 1; f < 8; f++)
+                        if ((fm >> f) & 1u) Sy[(size_t)plane[f] * npx + q] = zz16(Xv - g_pred(f, t, s, XA, XB, XC));
+                } else {
+#pragma unroll
+                    for (int f = 1; f < 8; f++) {
+                        if (!((fm >> f) & 1u)) continue;
+                        const int16_t *Ef = E + (size_t)eslot_of[f] * cells;
+                        const int32_t e = Ef[idx];
                         const int32_t eA = s > 0 ? Ef[idx - p] : 0;
                         const int32_t eB = t > 0 ? Ef[idx - p * TC] : 0;
                         const int32_t eC = (s > 0 && t > 0) ? Ef[idx - p * TC - p] : 0;
-                        Sy[2 * npx + q] = zz16(e - g_pred(f, t, s, eA, eB, eC));
+                        Sy[(size_t)plane[f] * npx + q] = zz16(e - g_pred(f, t, s, eA, eB, eC));
                     }
                 }
             }
         }
         __syncthreads();
-        for (int dom = 0; dom < 3; dom++) {
-            const uint16_t *src = Sy + (size_t)dom * npx;
-            const int k0 = slot_of[f][dom][0], k1 = slot_of[f][dom][1];
-            if (k0 >= 0) {  // raw order: rows of nco consecutive symbols
-                uint16_t *dst = base + (size_t)k0 * cslot16 + (size_t)(t * p) * W + (size_t)s0 * p;
-                if (raw2) {  // even row starts and widths: two symbols per store
-                    const int h = nco >> 1;
-                    for (int q = threadIdx.x; q < p * h; q += blockDim.x) {
-                        const int r = q / h, c2 = q - r * h;
-                        const uint32_t v2 = *reinterpret_cast<const uint32_t *>(src + r * nco + 2 * c2);
-                        *reinterpret_cast<uint32_t *>(dst + (size_t)r * W + 2 * c2) = v2;
-                    }
-                } else {
-                    for (int r = 0; r < p; r++)
-                        for (int c = threadIdx.x; c < nco; c += blockDim.x) dst[(size_t)r * W + c] = src[r * nco + c];
-                }
-            }
-            if (k1 >= 0) {  // view-major order: runs of ns symbols per (v, u)
-                uint16_t *dst = base + (size_t)k1 * cslot16 + (size_t)t * W + s0;
-                if (vm8) {  // 16-byte aligned runs of 8k symbols: 8 symbols per store
-                    const int hn = ns >> 3, items = p * p * hn;
-                    for (int q = threadIdx.x; q < items; q += blockDim.x) {
-                        const int hh = q % hn, vu = q / hn, u = vu % p, v = vu / p;
-                        const uint16_t *sp = src + v * nco + (8 * hh) * p + u;
-                        uint4 o;
-                        o.x = (uint32_t)sp[0] | ((uint32_t)sp[p] << 16);
-                        o.y = (uint32_t)sp[2 * p] | ((uint32_t)sp[3 * p] << 16);
-                        o.z = (uint32_t)sp[4 * p] | ((uint32_t)sp[5 * p] << 16);
-                        o.w = (uint32_t)sp[6 * p] | ((uint32_t)sp[7 * p] << 16);
-                        *reinterpret_cast<uint4 *>(dst + (size_t)v * Ny * W + (size_t)u * Nx + 8 * hh) = o;
-                    }
-                } else if (p * ns <= (int)blockDim.x) {
-                    if (vm_j < p * ns)
-                        for (int v = 0; v < p; v++)
-                            dst[(size_t)v * Ny * W + (size_t)vm_u * Nx + vm_si] = src[v * nco + vm_si * p + vm_u];
-                } else {
-                    for (int v = 0; v < p; v++)
-                        for (int j = threadIdx.x; j < p * ns; j += blockDim.x) {
-                            const int u = j / ns, si = j - u * ns;
-                            dst[(size_t)v * Ny * W + (size_t)u * Nx + si] = src[v * nco + si * p + u];
-                        }
-                }
-            }
+#pragma unroll
+        for (int f = 1; f < 8; f++) {
+            if (!((fm >> f) & 1u)) continue;
+            const uint16_t *src = Sy + (size_t)plane[f] * npx;
+            write_both(slot_of[f][dom][0], slot_of[f][dom][1],
+                       [&](int r, int c) -> uint16_t { return src[r * nco + c]; });
         }
         __syncthreads();
     }
