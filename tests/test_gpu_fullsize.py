@@ -19,16 +19,18 @@ def lfc():
     return L
 
 
-@pytest.fixture(scope="module", params=["beads2000", "cells500"])
+@pytest.fixture(scope="module", params=["beads2000", "cells500", "beads1300"])
 def frame(request):
     if request.param == "beads2000":
-        return synth.beads(2040, 2040, 15, peak=2000.0, seed=2)
-    return synth.cells(2040, 2040, 15, level=500.0, seed=3)
+        return synth.beads(2040, 2040, 15, peak=2000.0, seed=2), 15
+    if request.param == "beads1300":  # 100 x 100 lenslets at pitch 13, seed 0
+        return synth.bead_frame_1300(seed=0), 13
+    return synth.cells(2040, 2040, 15, level=500.0, seed=3), 15
 
 
 def test_fullsize_judge_and_container(lfc, frame):
-    p = 15
-    plan = lfc.Plan(2040, 2040, p)
+    frame, p = frame
+    plan = lfc.Plan(frame.shape[1], frame.shape[0], p)
     d = lfc.to_device_frame(frame)
     choice, scores = plan.judge([d], p)
     best, ref = oracle.judge(frame, p)
