@@ -14,7 +14,7 @@ import os
 
 SPACE = {
     "emit_tile_lenslets": (4, 8, 16),
-    "chain_range_bytes": (8192, 16384, 32768),
+    "chain_range_bytes": (32768, 65536, 131072, 262144),
 }
 
 

@@ -160,8 +160,9 @@ extern "C" int lfc_plan_set_tuning(lfc_plan P, const lfc_tuning *t) {
         v.emit_tile_lenslets = t->emit_tile_lenslets;
     }
     if (t->chain_range_bytes) {
-        if (t->chain_range_bytes != 8192 && t->chain_range_bytes != 16384 && t->chain_range_bytes != 32768)
-            return fail(P, LFC_ERR_INVALID_ARG, "chain_range_bytes must be 8192, 16384 or 32768");
+        const int r = t->chain_range_bytes;
+        if (r != 16384 && r != 32768 && r != 65536 && r != 131072 && r != 262144)
+            return fail(P, LFC_ERR_INVALID_ARG, "chain_range_bytes must be 16384, 32768, 65536, 131072 or 262144");
         v.chain_range_bytes = t->chain_range_bytes;
     }
     if (t->judge_frames_per_launch) {
@@ -279,7 +280,7 @@ extern "C" int lfc_plan_create(const lfc_config *cfg, void *cuda_stream, lfc_pla
     P->judge_frames_cap = std::min(F, kJudgeFramesCap);
     P->block_cap = (int)std::max<int64_t>(bpf, std::min<int64_t>((int64_t)F * bpf, 192));
     const int JF = P->judge_frames_cap, BC = P->block_cap;
-    const int64_t seg_min = chain_seg_bytes(8192);  // smallest tunable segment
+    const int64_t seg_min = chain_seg_bytes(16384);  // smallest tunable segment
     const int64_t segs_max = (n_max + seg_min - 1) / seg_min;
     ws.summ_cap = (int64_t)JF * kMaxCand * segs_max;
     ws.cstream_kmax = K;

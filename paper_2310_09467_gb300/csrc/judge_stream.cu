@@ -11,8 +11,9 @@
 //    for every candidate of the kind and stored in the candidate's ordering
 //    (raw order: 480-byte row runs; view-major order: 32-byte runs).
 // 2. chain_hist_kernel: one CTA per segment of a candidate stream, one
-//    warp per range (8-32 KB, tuned) walking it 32 bytes a step (see below);
-//    the ranges are stitched per CTA and the CTAs by the fixup kernel.
+//    warp per range (16-128 KB, tuned), one lane per 32nd of the range
+//    walking it byte by byte (see below); the lanes' sub-ranges are stitched
+//    per warp, the ranges per CTA and the CTAs by the fixup kernel.
 #include "lfc_common.cuh"
 
 namespace lfc {
@@ -264,27 +265,26 @@ __global__ void __launch_bounds__(kEmitThreads) emit_all_kernel(const JudgeFrame
 // counts the pairs (pred of one occurrence of b, pred of the next one), plus
 // the pairs across bucket boundaries (fixup kernel).
 //
-// One warp walks a contiguous range of a candidate stream 32 bytes per step,
-// lane j on position 32 q + j. __match_any_sync groups the lanes holding the
-// same byte value; a lane's pending predecessor is that of the previous lane
-// of its group, or, for the group's first lane, the warp's table entry
-// (predecessor of the last occurrence so far, 0xFFFF before the first), which
-// the group's last lane then overwrites. The first occurrence of every value
-// in the range keeps its predecessor, so the CTA stitches its warps' ranges
-// in order afterwards. Pairs (x, y) with x, y < kHot are counted in shared
-// memory, the pair (0, 0) by a warp ballot into a register, all others with
-// fire-and-forget atomics into the L2-resident histogram. Bytes come in as
-// 512-byte chunks (one 16-byte load per lane, the next chunk in flight)
-// through a per-warp staging buffer.
-constexpr int kChainWarps = 16;
+// A warp takes a contiguous range of a candidate stream and gives each lane
+// one 32nd of it. A lane walks its sub-range byte by byte with a private
+// table over the 256 byte values: entry (b, lane) is one 32-bit word, bits
+// 0..15 the predecessor of the last occurrence of b so far (0xFFFF before
+// the first), bits 16..23 the predecessor of the first occurrence. The word
+// index is b * 32 + lane, so each lane stays in its own bank whatever the
+// bytes. 32 bytes at a time, all table words are read and rewritten first
+// (a load only waits on the lane's own earlier stores), then the pairs are
+// counted from the words read. Afterwards the lanes' tables are stitched in
+// lane order into the warp's, the warps' in order into the CTA's, the CTAs'
+// by the fixup kernel. Pairs (x, y) with x, y < kHot are counted in shared
+// memory, (0, 0) in a register, all others with fire-and-forget atomics into
+// the L2-resident histogram.
+constexpr int kChainWarps = 5;
 constexpr int kChainThreads = kChainWarps * 32;
-constexpr int kChainChunk = 512;
-constexpr int kHot = 128;                                            // hot corner side
+constexpr int kHot = 128;              // hot corner side
+constexpr int kChainTab = 256 * 32;    // table words of a warp
 constexpr uint32_t kNoPred = 0xFFFF;
 
-size_t chain_smem_bytes() {
-    return (size_t)(kHot * kHot + 32) * 4 + (size_t)kChainWarps * (256 * 2 + 256 + kChainChunk);
-}
+size_t chain_smem_bytes() { return (size_t)(kHot * kHot + 32) * 4 + (size_t)kChainWarps * kChainTab * 4; }
 int64_t chain_seg_bytes(int range_bytes) { return (int64_t)kChainWarps * range_bytes; }
 
 __device__ __forceinline__ int find_frame_s(const JudgeFrame *fr, int n, int64_t cta) {
@@ -296,44 +296,52 @@ __device__ __forceinline__ int find_frame_s(const JudgeFrame *fr, int n, int64_t
     return lo;
 }
 
-// One 32-byte step; FULL: all 32 positions exist.
-template <bool FULL>
-__device__ __forceinline__ void chain_step(const uint8_t *stage, int pos, int lim, uint32_t &carry, uint16_t *pend,
-                                           uint8_t *first, uint32_t *hot, uint32_t *ghist, uint32_t &c0,
-                                           uint32_t lt, uint32_t gt) {
-    const int lane = threadIdx.x & 31;
-    const bool valid = FULL || pos < lim;
-    const uint32_t b = valid ? stage[pos] : 0u;
-    uint32_t a = __shfl_up_sync(LFC_FULL, b, 1);
-    if (lane == 0) a = carry;
-    carry = __shfl_sync(LFC_FULL, b, 31);
-    const uint32_t grp = __match_any_sync(LFC_FULL, valid ? b : 256u + lane);
-    const uint32_t lower = grp & lt;
-    uint32_t p = __shfl_sync(LFC_FULL, a, lower ? 31 - __clz(lower) : lane);
-    if (valid && !lower) p = pend[b];
-    __syncwarp();
-    if (valid && !(grp & gt)) pend[b] = (uint16_t)a;
-    const bool pair = valid && p != kNoPred;
-    if (valid && !pair) first[b] = (uint8_t)a;
+// Count the pair (p, a): p the predecessor of the previous occurrence
+// (kNoPred: none, nothing counted), a that of this one.
+__device__ __forceinline__ void chain_count(uint32_t p, uint32_t a, uint32_t *hot, uint32_t *ghist, uint32_t &c0, int lane) {
+    const bool pair = p != kNoPred;
     const uint32_t both = p | a;
-    const uint32_t zb = __ballot_sync(LFC_FULL, pair && both == 0);
-    c0 += __popc(zb);
+    c0 += (pair && both == 0) ? 1u : 0u;
     const bool hotp = pair && both != 0 && both < (uint32_t)kHot;
     // branch-free: lanes without a hot pair add 0 to their own dummy slot
     atomicAdd(&hot[hotp ? p * kHot + a : kHot * kHot + lane], hotp ? 1u : 0u);
     if (pair && both >= (uint32_t)kHot) atomicAdd(&ghist[(p << 8) | a], 1u);
-    __syncwarp();
 }
 
-__global__ void __launch_bounds__(kChainThreads)
+__device__ __forceinline__ uint32_t byte_of(const uint32_t (&w)[8], int i) {
+    return __byte_perm(w[i >> 2], 0u, 0x4440u | (uint32_t)(i & 3));
+}
+
+// 32 stream bytes (w little-endian) after the byte prev; tl = the lane's
+// column of the table (word b * 32 of tl is entry b).
+__device__ __forceinline__ void chain_walk32(const uint32_t (&w)[8], uint32_t &prev, uint32_t *tl, uint32_t *hot,
+                                             uint32_t *ghist, uint32_t &c0, int lane) {
+    uint32_t e[32];
+#pragma unroll
+    for (int i = 0; i < 32; i++) {
+        const uint32_t b = byte_of(w, i);
+        const uint32_t a = i == 0 ? prev : byte_of(w, i - 1);
+        uint16_t *last = reinterpret_cast<uint16_t *>(tl + b * 32);
+        e[i] = *last;
+        *last = (uint16_t)a;
+    }
+#pragma unroll
+    for (int i = 0; i < 32; i++) {
+        const uint32_t b = byte_of(w, i);
+        const uint32_t a = i == 0 ? prev : byte_of(w, i - 1);
+        if (e[i] == kNoPred) reinterpret_cast<uint8_t *>(tl + b * 32)[2] = (uint8_t)a;
+        chain_count(e[i], a, hot, ghist, c0, lane);
+    }
+    prev = byte_of(w, 31);
+}
+
+__global__ void __launch_bounds__(kChainThreads, 1)
 chain_hist_kernel(const JudgeFrame *__restrict__ frames, int nframes, const uint8_t *__restrict__ cand,
                   const uint8_t *__restrict__ cstream, int64_t cslot, int kmax, uint32_t *__restrict__ hist,
                   uint16_t *__restrict__ summ, int range_bytes) {
     extern __shared__ __align__(16) uint8_t smem[];
-    uint32_t *hot = reinterpret_cast<uint32_t *>(smem);                      // [kHot][kHot]
-    uint16_t *pend_all = reinterpret_cast<uint16_t *>(hot + kHot * kHot + 32);    // [warps][256]
-    uint8_t *first_all = reinterpret_cast<uint8_t *>(pend_all + kChainWarps * 256);  // [warps][256]
-    uint8_t *stage_all = first_all + kChainWarps * 256;                       // [warps][512]
+    uint32_t *hot = reinterpret_cast<uint32_t *>(smem);                 // [kHot][kHot] + 32 dummies
+    uint32_t *tab_all = hot + kHot * kHot + 32;                          // [warps][256][32]
     const int fi = find_frame_s(frames, nframes, blockIdx.x);
     const JudgeFrame &J = frames[fi];
     const int64_t local = (int64_t)blockIdx.x - J.cta_base;
@@ -343,49 +351,90 @@ chain_hist_kernel(const JudgeFrame *__restrict__ frames, int nframes, const uint
     uint32_t *ghist = hist + (size_t)(J.hist_off + ci) * kHistBins;
     const int64_t n = 2LL * J.F.W * J.F.H;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int64_t ra64 = min(n, ((int64_t)seg * kChainWarps + warp) * range_bytes);
-    const int len = (int)(min(n, ra64 + range_bytes) - ra64);
-    uint16_t *pend = pend_all + warp * 256;
-    uint8_t *first = first_all + warp * 256;
-    uint8_t *stage = stage_all + warp * kChainChunk;
-    for (int i = threadIdx.x; i < kHot * kHot; i += kChainThreads) hot[i] = 0;
-    for (int k = lane; k < 256; k += 32) pend[k] = (uint16_t)kNoPred;
+    uint32_t *tab = tab_all + warp * kChainTab;
+    for (int i = threadIdx.x; i < kHot * kHot / 4; i += kChainThreads) reinterpret_cast<uint4 *>(hot)[i] = make_uint4(0, 0, 0, 0);
+    for (int i = lane; i < kChainTab / 4; i += 32) reinterpret_cast<uint4 *>(tab)[i] = make_uint4(~0u, ~0u, ~0u, ~0u);
     __syncthreads();
-    uint32_t carry = len > 0 ? (uint32_t)S[ra64 == 0 ? n - 1 : ra64 - 1] : 0u;
+    // the lane's sub-range [lo, hi) of the warp's range
+    const int sub = range_bytes >> 5;
+    const int64_t ra = ((int64_t)seg * kChainWarps + warp) * range_bytes;
+    const int64_t lo = min(n, ra + (int64_t)lane * sub), hi = min(n, lo + sub);
+    const int len = (int)(hi - lo);
     uint32_t c0 = 0;
-    const uint32_t lt = lanemask_lt(), gt = lanemask_gt();
-    const uint8_t *R = S + ra64;
-    const int full = len / kChainChunk;
-    uint4 nxt = full > 0 ? __ldg(reinterpret_cast<const uint4 *>(R) + lane) : make_uint4(0, 0, 0, 0);
-    for (int c = 0; c < full; c++) {
-        reinterpret_cast<uint4 *>(stage)[lane] = nxt;
-        if (c + 1 < full) nxt = __ldg(reinterpret_cast<const uint4 *>(R + (size_t)(c + 1) * kChainChunk) + lane);
-        __syncwarp();
+    uint32_t *tl = tab + lane;
+    if (len > 0) {
+        uint32_t prev = S[lo == 0 ? n - 1 : lo - 1];  // cyclic predecessor
+        const uint8_t *L = S + lo;                      // 16-byte aligned
+        const int full = len >> 6;
+        uint4 c[4], nx[4];
+#pragma unroll
+        for (int j = 0; j < 4; j++) c[j] = full > 0 ? __ldg(reinterpret_cast<const uint4 *>(L) + j) : make_uint4(0, 0, 0, 0);
 #pragma unroll 1
-        for (int q = 0; q < kChainChunk / 32; q++)
-            chain_step<true>(stage, q * 32 + lane, kChainChunk, carry, pend, first, hot, ghist, c0, lt, gt);
+        for (int k = 0; k < full; k++) {
+#pragma unroll
+            for (int j = 0; j < 4; j++)
+                nx[j] = k + 1 < full ? __ldg(reinterpret_cast<const uint4 *>(L + (size_t)(k + 1) * 64) + j)
+                                     : make_uint4(0, 0, 0, 0);
+            const uint32_t w0[8] = {c[0].x, c[0].y, c[0].z, c[0].w, c[1].x, c[1].y, c[1].z, c[1].w};
+            chain_walk32(w0, prev, tl, hot, ghist, c0, lane);
+            const uint32_t w1[8] = {c[2].x, c[2].y, c[2].z, c[2].w, c[3].x, c[3].y, c[3].z, c[3].w};
+            chain_walk32(w1, prev, tl, hot, ghist, c0, lane);
+#pragma unroll
+            for (int j = 0; j < 4; j++) c[j] = nx[j];
+        }
+        for (int k = full << 6; k < len; k++) {  // ragged end of the stream
+            const uint32_t b = L[k], a = prev;
+            uint16_t *last = reinterpret_cast<uint16_t *>(tl + b * 32);
+            const uint32_t p = *last;
+            *last = (uint16_t)a;
+            if (p == kNoPred) reinterpret_cast<uint8_t *>(tl + b * 32)[2] = (uint8_t)a;
+            chain_count(p, a, hot, ghist, c0, lane);
+            prev = b;
+        }
     }
-    const int rem = len - full * kChainChunk;
-    if (rem > 0) {
-        for (int k = lane; k < rem; k += 32) stage[k] = R[(size_t)full * kChainChunk + k];
-        __syncwarp();
-        for (int q = 0; q * 32 < rem; q++)
-            chain_step<false>(stage, q * 32 + lane, rem, carry, pend, first, hot, ghist, c0, lt, gt);
+    __syncwarp();
+    // stitch the lanes in order: a lane's first occurrence of b follows the
+    // last occurrence in the nearest lower lane holding b; word (b, 0) then
+    // takes the warp's first and last predecessors of b (none: left as is)
+    const uint32_t lt = lanemask_lt();
+#pragma unroll 8
+    for (int b = 0; b < 256; b++) {
+        const uint32_t e = tl[b * 32];
+        const uint32_t last = e & 0xFFFFu;
+        const bool valid = last != kNoPred;
+        const uint32_t m = __ballot_sync(LFC_FULL, valid);
+        const uint32_t f = (e >> 16) & 255u;
+        const uint32_t lower = m & lt;
+        const uint32_t pl = __shfl_sync(LFC_FULL, last, lower ? 31 - __clz(lower) : lane);
+        chain_count(valid && lower ? pl : kNoPred, f, hot, ghist, c0, lane);
+        const uint32_t f0 = __shfl_sync(LFC_FULL, f, m ? __ffs(m) - 1 : 0);
+        const uint32_t lz = __shfl_sync(LFC_FULL, last, m ? 31 - __clz(m) : 0);
+        if (lane == 0 && m) tl[b * 32] = (f0 << 16) | lz;  // only lane 0 read this word
     }
-    if (lane == 0 && c0) atomicAdd(&hot[0], c0);
+    if (c0) atomicAdd(&hot[0], c0);
     __syncthreads();
-    for (int i = threadIdx.x; i < kHot * kHot; i += kChainThreads) {
-        const uint32_t c = hot[i];
-        if (c) atomicAdd(&ghist[((uint32_t)(i / kHot) << 8) | (uint32_t)(i % kHot)], c);
+    constexpr int kFlush = 8;
+    for (int i0 = threadIdx.x; i0 < kHot * kHot; i0 += kFlush * kChainThreads) {
+        uint32_t v[kFlush];
+#pragma unroll
+        for (int j = 0; j < kFlush; j++) {
+            const int i = i0 + j * kChainThreads;
+            v[j] = i < kHot * kHot ? hot[i] : 0u;
+        }
+#pragma unroll
+        for (int j = 0; j < kFlush; j++) {
+            const uint32_t i = (uint32_t)(i0 + j * kChainThreads), p = i / kHot, a = i % kHot;
+            if (v[j]) atomicAdd(&ghist[(p << 8) | a], v[j]);
+        }
     }
-    // stitch the warps' ranges in order (thread b handles byte value b)
-    if (threadIdx.x < 256) {
-        const int bv = threadIdx.x;
+    // stitch the warps' ranges in order (thread per byte value)
+    for (int bv = threadIdx.x; bv < 256; bv += kChainThreads) {
         uint32_t f0 = kNoPred, cur = kNoPred;
         for (int w = 0; w < kChainWarps; w++) {
-            const uint32_t last = pend_all[w * 256 + bv];
+            const uint32_t e = tab_all[w * kChainTab + bv * 32];
+            const uint32_t last = e & 0xFFFFu;
             if (last == kNoPred) continue;
-            const uint32_t f = first_all[w * 256 + bv];
+            const uint32_t f = (e >> 16) & 255u;
             if (cur != kNoPred) atomicAdd(&ghist[(cur << 8) | f], 1u);
             else f0 = f;
             cur = last;

@@ -19,7 +19,7 @@ def test_batch_key_and_cache_round_trip(tmp_path):
     open(path, "w").write("not json")
     assert autotune.load_cache(path) == {}
     c = list(autotune.candidates(8))
-    assert len(c) == 3 * 3 * 2 and all(set(x) == {"emit_tile_lenslets", "chain_range_bytes",
+    assert len(c) == 3 * 4 * 2 and all(set(x) == {"emit_tile_lenslets", "chain_range_bytes",
                                                    "judge_frames_per_launch"} for x in c)
 
 
