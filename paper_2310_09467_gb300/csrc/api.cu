@@ -223,7 +223,7 @@ extern "C" const char *lfc_plan_last_error(lfc_plan P) { return P ? P->err.c_str
 extern "C" int lfc_plan_block_capacity(lfc_plan P) { return P ? P->block_cap : 0; }
 
 static void free_ws(Workspace &w) {
-    void *ptrs[] = {w.hist, w.summ, w.scores, w.choice, w.jframes, w.cand, w.l2tab, w.stream, w.blocks, w.bstate,
+    void *ptrs[] = {w.hist, w.summ, w.chain_first, w.scores, w.choice, w.jframes, w.cand, w.l2tab, w.stream, w.blocks, w.bstate,
                     w.rle, w.sa, w.sa2, w.rank, w.act, w.act2, w.val, w.val2, w.keys, w.keys2, w.tilecnt, w.tileaux, w.bwt,
                     w.mtfidx, w.mtflists, w.mtfrec, w.mtfreclen, w.sym, w.freq, w.rfreq, w.sel, w.lens, w.codes, w.packed, w.cstream, w.masks, w.class_ids,
                     w.act_total, w.block_dst, w.frame_crc, w.crc_part, w.crc_part2, w.chunk_desc, w.dec_tt};
@@ -335,6 +335,9 @@ extern "C" int lfc_plan_create(const lfc_config *cfg, void *cuda_stream, lfc_pla
     AL(crc_part, (size_t)ws.crc_part_cap);
     AL(crc_part2, (size_t)ws.crc_part_cap);
 #undef AL
+    if (e == cudaSuccess) e = query_nsmid(P->stream, &ws.chain_nsm);
+    if (e == cudaSuccess && ws.chain_nsm <= 0) e = cudaErrorUnknown;
+    if (e == cudaSuccess) e = dalloc(&ws.chain_first, chain_first_bytes(ws.chain_nsm));
     if (e == cudaSuccess) e = cudaMalloc(&ws.chunk_desc, ws.chunk_desc_bytes);
     if (e == cudaSuccess) e = cudaMallocHost(reinterpret_cast<void **>(&ws.h_act_total), 4 * sizeof(int32_t));
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&P->aux_stream, cudaStreamNonBlocking);

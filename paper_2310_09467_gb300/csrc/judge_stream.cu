@@ -267,25 +267,49 @@ __global__ void __launch_bounds__(kEmitThreads) emit_all_kernel(const JudgeFrame
 //
 // A warp takes a contiguous range of a candidate stream and gives each lane
 // one 32nd of it. A lane walks its sub-range byte by byte with a private
-// table over the 256 byte values: entry (b, lane) is one 32-bit word, bits
-// 0..15 the predecessor of the last occurrence of b so far (0xFFFF before
-// the first), bits 16..23 the predecessor of the first occurrence. The word
-// index is b * 32 + lane, so each lane stays in its own bank whatever the
-// bytes. 32 bytes at a time, all table words are read and rewritten first
-// (a load only waits on the lane's own earlier stores), then the pairs are
-// counted from the words read. Afterwards the lanes' tables are stitched in
+// table over the 256 byte values: entry (b, lane) is 16 bits, the
+// predecessor of the last occurrence of b so far (0xFFFF before the first),
+// kept in the word (b / 2) * 32 + lane, half b % 2, so each lane stays in its
+// own bank whatever the bytes. The predecessor of a lane's first occurrence
+// of b (written once per value, read once when stitching) goes to a global
+// scratch of the CTA's SM: the table's shared memory admits one CTA per SM.
+// 32 bytes at a time, all table entries are read and rewritten first (a
+// load only waits on the lane's own earlier stores), then the pairs are
+// counted from the entries read. Afterwards the lanes' tables are stitched in
 // lane order into the warp's, the warps' in order into the CTA's, the CTAs'
 // by the fixup kernel. Pairs (x, y) with x, y < kHot are counted in shared
 // memory, (0, 0) in a register, all others with fire-and-forget atomics into
 // the L2-resident histogram.
-constexpr int kChainWarps = 5;
+constexpr int kChainWarps = 10;
 constexpr int kChainThreads = kChainWarps * 32;
 constexpr int kHot = 128;              // hot corner side
-constexpr int kChainTab = 256 * 32;    // table words of a warp
+constexpr int kChainTab = 128 * 32;    // table words of a warp (two 16-bit entries each)
+constexpr int kChainFirst = 256 * 32;  // first-predecessor bytes of a warp, [b][lane]
 constexpr uint32_t kNoPred = 0xFFFF;
 
 size_t chain_smem_bytes() { return (size_t)(kHot * kHot + 32) * 4 + (size_t)kChainWarps * kChainTab * 4; }
 int64_t chain_seg_bytes(int range_bytes) { return (int64_t)kChainWarps * range_bytes; }
+size_t chain_first_bytes(int nsm) { return (size_t)nsm * kChainWarps * kChainFirst; }
+
+__global__ void nsmid_kernel(int32_t *out) {
+    uint32_t v;
+    asm("mov.u32 %0, %%nsmid;" : "=r"(v));
+    *out = (int32_t)v;
+}
+
+cudaError_t query_nsmid(cudaStream_t s, int *nsm) {
+    int32_t *d = nullptr;
+    cudaError_t e = cudaMalloc(&d, sizeof(int32_t));
+    if (e != cudaSuccess) return e;
+    nsmid_kernel<<<1, 1, 0, s>>>(d);
+    int32_t h = 0;
+    e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&h, d, sizeof(int32_t), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    cudaFree(d);
+    *nsm = h;
+    return e;
+}
 
 __device__ __forceinline__ int find_frame_s(const JudgeFrame *fr, int n, int64_t cta) {
     int lo = 0, hi = n - 1;
@@ -312,24 +336,29 @@ __device__ __forceinline__ uint32_t byte_of(const uint32_t (&w)[8], int i) {
     return __byte_perm(w[i >> 2], 0u, 0x4440u | (uint32_t)(i & 3));
 }
 
-// 32 stream bytes (w little-endian) after the byte prev; tl = the lane's
-// column of the table (word b * 32 of tl is entry b).
-__device__ __forceinline__ void chain_walk32(const uint32_t (&w)[8], uint32_t &prev, uint32_t *tl, uint32_t *hot,
-                                             uint32_t *ghist, uint32_t &c0, int lane) {
+// Entry b of a lane's table; tl = the table + lane (words).
+__device__ __forceinline__ uint16_t *chain_entry(uint32_t *tl, uint32_t b) {
+    return reinterpret_cast<uint16_t *>(tl + (b >> 1) * 32) + (b & 1);
+}
+
+// 32 stream bytes (w little-endian) after the byte prev; fl = the lane's
+// first-predecessor column (byte b * 32).
+__device__ __forceinline__ void chain_walk32(const uint32_t (&w)[8], uint32_t &prev, uint32_t *tl, uint8_t *fl,
+                                             uint32_t *hot, uint32_t *ghist, uint32_t &c0, int lane) {
     uint32_t e[32];
 #pragma unroll
     for (int i = 0; i < 32; i++) {
         const uint32_t b = byte_of(w, i);
         const uint32_t a = i == 0 ? prev : byte_of(w, i - 1);
-        uint16_t *last = reinterpret_cast<uint16_t *>(tl + b * 32);
-        e[i] = *last;
-        *last = (uint16_t)a;
+        uint16_t *en = chain_entry(tl, b);
+        e[i] = *en;
+        *en = (uint16_t)a;
     }
 #pragma unroll
     for (int i = 0; i < 32; i++) {
         const uint32_t b = byte_of(w, i);
         const uint32_t a = i == 0 ? prev : byte_of(w, i - 1);
-        if (e[i] == kNoPred) reinterpret_cast<uint8_t *>(tl + b * 32)[2] = (uint8_t)a;
+        if (e[i] == kNoPred) fl[b * 32] = (uint8_t)a;
         chain_count(e[i], a, hot, ghist, c0, lane);
     }
     prev = byte_of(w, 31);
@@ -338,10 +367,10 @@ __device__ __forceinline__ void chain_walk32(const uint32_t (&w)[8], uint32_t &p
 __global__ void __launch_bounds__(kChainThreads, 1)
 chain_hist_kernel(const JudgeFrame *__restrict__ frames, int nframes, const uint8_t *__restrict__ cand,
                   const uint8_t *__restrict__ cstream, int64_t cslot, int kmax, uint32_t *__restrict__ hist,
-                  uint16_t *__restrict__ summ, int range_bytes) {
+                  uint16_t *__restrict__ summ, int range_bytes, uint8_t *__restrict__ first_all, int nsm) {
     extern __shared__ __align__(16) uint8_t smem[];
     uint32_t *hot = reinterpret_cast<uint32_t *>(smem);                 // [kHot][kHot] + 32 dummies
-    uint32_t *tab_all = hot + kHot * kHot + 32;                          // [warps][256][32]
+    uint32_t *tab_all = hot + kHot * kHot + 32;                          // [warps][128][32]
     const int fi = find_frame_s(frames, nframes, blockIdx.x);
     const JudgeFrame &J = frames[fi];
     const int64_t local = (int64_t)blockIdx.x - J.cta_base;
@@ -351,6 +380,9 @@ chain_hist_kernel(const JudgeFrame *__restrict__ frames, int nframes, const uint
     uint32_t *ghist = hist + (size_t)(J.hist_off + ci) * kHistBins;
     const int64_t n = 2LL * J.F.W * J.F.H;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    uint32_t smid;
+    asm volatile("mov.u32 %0, %%smid;" : "=r"(smid));
+    uint8_t *fl = first_all + ((size_t)(smid % (uint32_t)nsm) * kChainWarps + warp) * kChainFirst + lane;
     uint32_t *tab = tab_all + warp * kChainTab;
     for (int i = threadIdx.x; i < kHot * kHot / 4; i += kChainThreads) reinterpret_cast<uint4 *>(hot)[i] = make_uint4(0, 0, 0, 0);
     for (int i = lane; i < kChainTab / 4; i += 32) reinterpret_cast<uint4 *>(tab)[i] = make_uint4(~0u, ~0u, ~0u, ~0u);
@@ -376,40 +408,50 @@ chain_hist_kernel(const JudgeFrame *__restrict__ frames, int nframes, const uint
                 nx[j] = k + 1 < full ? __ldg(reinterpret_cast<const uint4 *>(L + (size_t)(k + 1) * 64) + j)
                                      : make_uint4(0, 0, 0, 0);
             const uint32_t w0[8] = {c[0].x, c[0].y, c[0].z, c[0].w, c[1].x, c[1].y, c[1].z, c[1].w};
-            chain_walk32(w0, prev, tl, hot, ghist, c0, lane);
+            chain_walk32(w0, prev, tl, fl, hot, ghist, c0, lane);
             const uint32_t w1[8] = {c[2].x, c[2].y, c[2].z, c[2].w, c[3].x, c[3].y, c[3].z, c[3].w};
-            chain_walk32(w1, prev, tl, hot, ghist, c0, lane);
+            chain_walk32(w1, prev, tl, fl, hot, ghist, c0, lane);
 #pragma unroll
             for (int j = 0; j < 4; j++) c[j] = nx[j];
         }
         for (int k = full << 6; k < len; k++) {  // ragged end of the stream
             const uint32_t b = L[k], a = prev;
-            uint16_t *last = reinterpret_cast<uint16_t *>(tl + b * 32);
-            const uint32_t p = *last;
-            *last = (uint16_t)a;
-            if (p == kNoPred) reinterpret_cast<uint8_t *>(tl + b * 32)[2] = (uint8_t)a;
+            uint16_t *en = chain_entry(tl, b);
+            const uint32_t p = *en;
+            *en = (uint16_t)a;
+            if (p == kNoPred) fl[b * 32] = (uint8_t)a;
             chain_count(p, a, hot, ghist, c0, lane);
             prev = b;
         }
     }
     __syncwarp();
     // stitch the lanes in order: a lane's first occurrence of b follows the
-    // last occurrence in the nearest lower lane holding b; word (b, 0) then
-    // takes the warp's first and last predecessors of b (none: left as is)
+    // last occurrence in the nearest lower lane holding b. The warp's result
+    // for b, (first << 16) | last (last 0xFFFF: none), then goes to word
+    // (b / 2) * 32 + b % 2 of its table, whose entries are all read by then.
     const uint32_t lt = lanemask_lt();
+    uint32_t keep = 0;
 #pragma unroll 8
     for (int b = 0; b < 256; b++) {
-        const uint32_t e = tl[b * 32];
-        const uint32_t last = e & 0xFFFFu;
+        const uint32_t last = *chain_entry(tl, b);
         const bool valid = last != kNoPred;
         const uint32_t m = __ballot_sync(LFC_FULL, valid);
-        const uint32_t f = (e >> 16) & 255u;
+        const uint32_t f = __ldcg(fl + b * 32);  // meaningful where valid
         const uint32_t lower = m & lt;
         const uint32_t pl = __shfl_sync(LFC_FULL, last, lower ? 31 - __clz(lower) : lane);
         chain_count(valid && lower ? pl : kNoPred, f, hot, ghist, c0, lane);
         const uint32_t f0 = __shfl_sync(LFC_FULL, f, m ? __ffs(m) - 1 : 0);
         const uint32_t lz = __shfl_sync(LFC_FULL, last, m ? 31 - __clz(m) : 0);
-        if (lane == 0 && m) tl[b * 32] = (f0 << 16) | lz;  // only lane 0 read this word
+        const uint32_t res = (f0 << 16) | lz;
+        if (b & 1) {
+            __syncwarp();
+            if (lane == 0) {
+                tab[(b >> 1) * 32] = keep;
+                tab[(b >> 1) * 32 + 1] = res;
+            }
+        } else {
+            keep = res;
+        }
     }
     if (c0) atomicAdd(&hot[0], c0);
     __syncthreads();
@@ -431,7 +473,7 @@ chain_hist_kernel(const JudgeFrame *__restrict__ frames, int nframes, const uint
     for (int bv = threadIdx.x; bv < 256; bv += kChainThreads) {
         uint32_t f0 = kNoPred, cur = kNoPred;
         for (int w = 0; w < kChainWarps; w++) {
-            const uint32_t e = tab_all[w * kChainTab + bv * 32];
+            const uint32_t e = tab_all[w * kChainTab + (bv >> 1) * 32 + (bv & 1)];
             const uint32_t last = e & 0xFFFFu;
             if (last == kNoPred) continue;
             const uint32_t f = (e >> 16) & 255u;
@@ -464,7 +506,7 @@ cudaError_t launch_chain_hist(lfc_plan P, const JudgeFrame *d_frames, int nframe
     if (e != cudaSuccess) return e;
     chain_hist_kernel<<<(unsigned)total_ctas, kChainThreads, smem, P->stream>>>(
         d_frames, nframes, d_cand, P->ws.cstream, P->ws.cstream_slot, P->ws.cstream_kmax, P->ws.hist, P->ws.summ,
-        range_bytes);
+        range_bytes, P->ws.chain_first, P->ws.chain_nsm);
     count_launches(P, 1);
     return cudaGetLastError();
 }

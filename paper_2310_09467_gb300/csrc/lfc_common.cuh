@@ -156,6 +156,8 @@ struct Workspace {
     // judge
     uint32_t *hist = nullptr;      // judge_frames_cap * kMaxCand * 65536
     uint16_t *summ = nullptr;      // per judge CTA: first[256], last[256]
+    uint8_t *chain_first = nullptr;  // per SM: the chain kernel's first-predecessor bytes
+    int chain_nsm = 0;               // SM slots of chain_first (%nsmid)
     uint64_t *scores = nullptr;    // max_frames * 256
     uint8_t *choice = nullptr;     // max_frames
     JudgeFrame *jframes = nullptr; // judge_frames_cap
@@ -266,6 +268,8 @@ size_t judge_smem_bytes(int maxW);
 size_t emit_all_smem_bytes(int p, int ts, int nslots);
 size_t chain_smem_bytes();
 int64_t chain_seg_bytes(int range_bytes);  // stream bytes one chain CTA covers
+size_t chain_first_bytes(int nsm);          // chain_first bytes for nsm SM slots
+cudaError_t query_nsmid(cudaStream_t s, int *nsm);
 cudaError_t launch_emit_all(lfc_plan P, const JudgeFrame *d_frames, int nframes, const uint8_t *d_cand, int max_tiles,
                             int TS, int nslots_max, int any_temporal, int max_p);
 cudaError_t launch_chain_hist(lfc_plan P, const JudgeFrame *d_frames, int nframes, const uint8_t *d_cand, int64_t total_ctas,
