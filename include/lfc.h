@@ -208,10 +208,12 @@ int lfc_decompress(lfc_plan plan, const uint8_t *const *h_in, const uint64_t *h_
  * never results.
  *   emit_tile_lenslets      lenslets per row tile of the candidate emission
  *                           kernel: 4, 8 or 16 (default 16);
- *   chain_range_bytes       bytes of a candidate stream one warp of the
- *                           pair-chain kernel walks (a 32nd per lane):
- *                           16384, 32768, 65536, 131072 or 262144
- *                           (default 131072);
+ *   chain_range_bytes       upper bound on the bytes of a candidate stream
+ *                           one warp of the pair-chain kernel walks (a 32nd
+ *                           per lane): 16384, 32768, 65536, 131072 or 262144
+ *                           (default 131072); each launch evens the ranges
+ *                           out below it so that its CTAs fill whole waves
+ *                           of the device's SMs;
  *   judge_frames_per_launch frames per judge launch, 1 .. the plan's
  *                           min(max_frames, 8) (default: that maximum).
  * Errors: INVALID_ARG for values outside these sets. */

@@ -245,6 +245,8 @@ extern "C" int lfc_plan_create(const lfc_config *cfg, void *cuda_stream, lfc_pla
     if (P->cfg.keyframe_interval <= 0) P->cfg.keyframe_interval = 16;
     P->stream = reinterpret_cast<cudaStream_t>(cuda_stream);
     cudaGetDevice(&P->device);
+    if (cudaDeviceGetAttribute(&P->sm_count, cudaDevAttrMultiProcessorCount, P->device) != cudaSuccess || P->sm_count <= 0)
+        P->sm_count = 1;
     // candidate ids
     bool any = false;
     for (int i = 0; i < 4; i++) any |= cfg->candidate_mask[i] != 0;
@@ -425,14 +427,50 @@ bool capturing(lfc_plan P) {
     return cudaStreamIsCapturing(P->stream, &st) == cudaSuccess && st != cudaStreamCaptureStatusNone;
 }
 
+// Bytes a chain warp walks in one launch: at most the tuned range, chosen so
+// that the launch's CTAs fill whole waves of one CTA per SM. A candidate
+// range r gives sum_f K_f ceil(n_f / seg(r)) CTAs; its cost is taken as the
+// waves those need times (r + a fixed per-CTA share of 8 KB). Candidates: the
+// equal splits of the largest stream into s >= s0 segments (s0 the count at
+// the tuned range), at most 2 s0, a multiple of 512 bytes, >= 16 KB.
+int chain_range_for(lfc_plan P, const lfc_frame *frames, int nf) {
+    const int tuned = P->tune.chain_range_bytes;
+    int64_t n_max = 0;
+    int k_spatial = (int)P->ids_spatial.size(), k_all = k_spatial + (int)P->ids_temporal.size();
+    for (int i = 0; i < nf; i++) n_max = std::max<int64_t>(n_max, 2LL * frames[i].width * frames[i].height);
+    if (n_max <= 0) return tuned;
+    const int64_t w = chain_seg_bytes(1);  // warps per CTA
+    const int64_t s0 = std::max<int64_t>(1, (n_max + w * tuned - 1) / (w * tuned));
+    int best = tuned;
+    double best_cost = -1.0;
+    for (int64_t s = s0; s <= 2 * s0; s++) {
+        int64_t r = (n_max + w * s - 1) / (w * s);
+        r = (r + 511) / 512 * 512;
+        if (r > tuned || r < 16384) continue;
+        int64_t ctas = 0;
+        for (int i = 0; i < nf; i++) {
+            const int64_t nb = 2LL * frames[i].width * frames[i].height;
+            const int K = (frames[i].prev != nullptr && !P->ids_temporal.empty()) ? k_all : k_spatial;
+            ctas += (int64_t)K * ((nb + w * r - 1) / (w * r));
+        }
+        const int64_t waves = (ctas + P->sm_count - 1) / P->sm_count;
+        const double cost = (double)waves * (double)(r + 8192);
+        if (best_cost < 0 || cost < best_cost) {
+            best_cost = cost;
+            best = (int)r;
+        }
+    }
+    return best;
+}
+
 int build_judge(lfc_plan P, const lfc_frame *frames, int n, Arena &A, std::vector<JudgeChunk> &out) {
     Workspace &ws = P->ws;
-    const int range = P->tune.chain_range_bytes;
-    const int64_t seg_bytes = chain_seg_bytes(range);
     const int per_launch = P->tune.judge_frames_per_launch > 0 ? P->tune.judge_frames_per_launch : P->judge_frames_cap;
     for (int f0 = 0; f0 < n; f0 += per_launch) {
         const int f1 = std::min(n, f0 + per_launch);
         const int nf = f1 - f0;
+        const int range = chain_range_for(P, frames + f0, nf);
+        const int64_t seg_bytes = chain_seg_bytes(range);
         std::vector<JudgeFrame> jf(nf);
         std::vector<int32_t> frame_index(nf), hist_frame;
         std::vector<uint8_t> cand;

@@ -224,6 +224,7 @@ struct lfc_plan_s {
     cudaEvent_t side_fork = nullptr, side_join = nullptr;
     cudaStream_t cap_stream = nullptr;  // capture of batches
     int device = 0;
+    int sm_count = 0;  // streaming multiprocessors of the device
     std::string err;
     std::vector<uint8_t> ids_spatial;   // judged for every frame
     std::vector<uint8_t> ids_temporal;  // judged for frames with prev
