@@ -352,18 +352,35 @@ __global__ void __launch_bounds__(1024) radix_scan_kernel(const int32_t *__restr
     const int per = (total + blockDim.x - 1) / blockDim.x;
     const int a = min(total, (int)threadIdx.x * per), e = min(total, a + per);
     const int d0 = a / nt, t0 = a - d0 * nt;  // (digit, tile) of the first entry
+    // batches of independent loads: a thread's entries cost a few round trips
+    constexpr int kBatch = 16;
     uint32_t sum = 0;
-    for (int q = a, d = d0, t = t0; q < e; q++) {
-        sum += cnt[d * kTilesPerBlock + t];
-        if (++t == nt) { t = 0; d++; }
+    for (int q0 = a, d = d0, t = t0; q0 < e; q0 += kBatch) {
+        uint32_t v[kBatch];
+#pragma unroll
+        for (int j = 0; j < kBatch; j++) {
+            v[j] = q0 + j < e ? cnt[d * kTilesPerBlock + t] : 0u;
+            if (++t == nt) { t = 0; d++; }
+        }
+#pragma unroll
+        for (int j = 0; j < kBatch; j++) sum += v[j];
     }
     uint32_t off = block_excl_sum<uint32_t>(sum, sh, nullptr);
-    for (int q = a, d = d0, t = t0; q < e; q++) {
-        uint32_t &c = cnt[d * kTilesPerBlock + t];
-        const uint32_t v = c;
-        c = off;
-        off += v;
-        if (++t == nt) { t = 0; d++; }
+    for (int q0 = a, d = d0, t = t0; q0 < e; q0 += kBatch) {
+        uint32_t v[kBatch];
+        int dj[kBatch], tj[kBatch];
+#pragma unroll
+        for (int j = 0; j < kBatch; j++) {
+            dj[j] = d;
+            tj[j] = t;
+            v[j] = q0 + j < e ? cnt[d * kTilesPerBlock + t] : 0u;
+            if (++t == nt) { t = 0; d++; }
+        }
+#pragma unroll
+        for (int j = 0; j < kBatch; j++) {
+            if (q0 + j < e) cnt[dj[j] * kTilesPerBlock + tj[j]] = off;
+            off += v[j];
+        }
     }
 }
 

@@ -429,29 +429,42 @@ chain_hist_kernel(const JudgeFrame *__restrict__ frames, int nframes, const uint
     // last occurrence in the nearest lower lane holding b. The warp's result
     // for b, (first << 16) | last (last 0xFFFF: none), then goes to word
     // (b / 2) * 32 + b % 2 of its table, whose entries are all read by then.
+    // The first predecessors come from global memory 32 values ahead.
     const uint32_t lt = lanemask_lt();
     uint32_t keep = 0;
-#pragma unroll 8
-    for (int b = 0; b < 256; b++) {
-        const uint32_t last = *chain_entry(tl, b);
-        const bool valid = last != kNoPred;
-        const uint32_t m = __ballot_sync(LFC_FULL, valid);
-        const uint32_t f = __ldcg(fl + b * 32);  // meaningful where valid
-        const uint32_t lower = m & lt;
-        const uint32_t pl = __shfl_sync(LFC_FULL, last, lower ? 31 - __clz(lower) : lane);
-        chain_count(valid && lower ? pl : kNoPred, f, hot, ghist, c0, lane);
-        const uint32_t f0 = __shfl_sync(LFC_FULL, f, m ? __ffs(m) - 1 : 0);
-        const uint32_t lz = __shfl_sync(LFC_FULL, last, m ? 31 - __clz(m) : 0);
-        const uint32_t res = (f0 << 16) | lz;
-        if (b & 1) {
-            __syncwarp();
-            if (lane == 0) {
-                tab[(b >> 1) * 32] = keep;
-                tab[(b >> 1) * 32 + 1] = res;
+    uint32_t fv[32];
+#pragma unroll
+    for (int j = 0; j < 32; j++) fv[j] = __ldcg(fl + j * 32);
+#pragma unroll 1
+    for (int b0 = 0; b0 < 256; b0 += 32) {
+        uint32_t fn[32];
+#pragma unroll
+        for (int j = 0; j < 32; j++) fn[j] = b0 + 32 < 256 ? __ldcg(fl + (b0 + 32 + j) * 32) : 0u;
+#pragma unroll
+        for (int j = 0; j < 32; j++) {
+            const int b = b0 + j;
+            const uint32_t last = *chain_entry(tl, b);
+            const bool valid = last != kNoPred;
+            const uint32_t m = __ballot_sync(LFC_FULL, valid);
+            const uint32_t f = fv[j];  // meaningful where valid
+            const uint32_t lower = m & lt;
+            const uint32_t pl = __shfl_sync(LFC_FULL, last, lower ? 31 - __clz(lower) : lane);
+            chain_count(valid && lower ? pl : kNoPred, f, hot, ghist, c0, lane);
+            const uint32_t f0 = __shfl_sync(LFC_FULL, f, m ? __ffs(m) - 1 : 0);
+            const uint32_t lz = __shfl_sync(LFC_FULL, last, m ? 31 - __clz(m) : 0);
+            const uint32_t res = (f0 << 16) | lz;
+            if (j & 1) {
+                __syncwarp();
+                if (lane == 0) {
+                    tab[(b >> 1) * 32] = keep;
+                    tab[(b >> 1) * 32 + 1] = res;
+                }
+            } else {
+                keep = res;
             }
-        } else {
-            keep = res;
         }
+#pragma unroll
+        for (int j = 0; j < 32; j++) fv[j] = fn[j];
     }
     if (c0) atomicAdd(&hot[0], c0);
     __syncthreads();
