@@ -43,6 +43,18 @@ __device__ __forceinline__ uint16_t zz16(int32_t e) {
     return (uint16_t)(((s << 1) ^ (s >> 31)) & 0xFFFF);
 }
 
+// Division by a per-CTA constant d (1 <= d < 2^16) as a multiply-high by
+// m = ceil(2^32 / d): floor(n * m / 2^32) = floor(n / d) exactly for
+// n < 2^16, because n * (m d - 2^32) < 2^32. Every index divided here (tile
+// pixels, runs, views) stays below 2^16.
+struct DivU16 {
+    uint64_t m;
+    uint32_t d;
+    __device__ explicit DivU16(uint32_t d_) : m(((1ull << 32) + d_ - 1) / d_), d(d_) {}
+    __device__ __forceinline__ uint32_t div(uint32_t n) const { return (uint32_t)(((uint64_t)n * m) >> 32); }
+    __device__ __forceinline__ uint32_t mod(uint32_t n) const { return n - div(n) * d; }
+};
+
 // nslots bounds both the residual fields (f with an intra or phase-space
 // candidate) and the symbol planes (f with an inter or phase-space candidate).
 size_t emit_all_smem_bytes(int p, int ts, int nslots) {
@@ -96,6 +108,7 @@ __device__ __forceinline__ void emit_all_body(const JudgeFrame *__restrict__ fra
             slot_of[id & 15][(id >> 4) & 3][(id >> 6) & 1] = (int16_t)k;
         }
     }
+    const DivU16 div_p((uint32_t)p);
     const int y0 = (t - 1) * p, x0 = (s0 - 1) * p;
     for (int lx = threadIdx.x; lx < ncols; lx += blockDim.x) {  // column per thread, rows in a loop
         const int x = x0 + lx;
@@ -114,7 +127,7 @@ __device__ __forceinline__ void emit_all_body(const JudgeFrame *__restrict__ fra
 #define FVAL(idx) (kind ? (int32_t)(int16_t)Fb[idx] : (int32_t)Fb[idx])  // kind is a template constant
     // intra residual fields (signed 16-bit) for every f in use
     for (int lx = threadIdx.x; lx < ncols; lx += blockDim.x) {
-        const int u = lx % p;
+        const int u = (int)div_p.mod((uint32_t)lx);
         for (int ly = 0; ly < TR; ly++) {
             const int v = ly < p ? ly : ly - p;  // TR = 2p rows
             const int idx = ly * TC + lx;
@@ -131,10 +144,12 @@ __device__ __forceinline__ void emit_all_body(const JudgeFrame *__restrict__ fra
     uint16_t *base = reinterpret_cast<uint16_t *>(cstream + (size_t)fi * kmax * (size_t)cslot);
     const size_t cslot16 = (size_t)cslot / 2;
     // view-major write-out: thread j -> (u, si) = (j / ns, j % ns), rows v
-    const int vm_j = threadIdx.x, vm_u = vm_j / ns, vm_si = vm_j - vm_u * ns;
+    const DivU16 div_ns((uint32_t)ns);
+    const int vm_j = threadIdx.x, vm_u = (int)div_ns.div((uint32_t)vm_j), vm_si = vm_j - vm_u * ns;
     // vector stores when every run start is aligned (slots are 256-byte aligned)
     const bool raw2 = (W % 2) == 0 && ((s0 * p) % 2) == 0 && (nco % 2) == 0;
     const bool vm8 = (ns % 8) == 0 && (W % 8) == 0 && (Nx % 8) == 0 && (s0 % 8) == 0;
+    const DivU16 div_h((uint32_t)max(nco >> 1, 1)), div_hn((uint32_t)max(ns >> 3, 1));
     // Writes the symbols get(r, c) of the tile's output pixels (row r of the
     // lenslet row, column c) to candidate k0 in raw order and k1 in view-major
     // order (view v = r, u = c mod p, lenslet s0 + c / p), consecutive threads
@@ -145,7 +160,7 @@ __device__ __forceinline__ void emit_all_body(const JudgeFrame *__restrict__ fra
             if (raw2) {
                 const int h = nco >> 1;
                 for (int q = threadIdx.x; q < p * h; q += blockDim.x) {
-                    const int r = q / h, c2 = 2 * (q - r * h);
+                    const int r = (int)div_h.div((uint32_t)q), c2 = 2 * (q - r * h);
                     *reinterpret_cast<uint32_t *>(dst + (size_t)r * W + c2) =
                         (uint32_t)get(r, c2) | ((uint32_t)get(r, c2 + 1) << 16);
                 }
@@ -159,7 +174,8 @@ __device__ __forceinline__ void emit_all_body(const JudgeFrame *__restrict__ fra
             if (vm8) {
                 const int hn = ns >> 3, items = p * p * hn;
                 for (int q = threadIdx.x; q < items; q += blockDim.x) {
-                    const int hh = q % hn, vu = q / hn, u = vu % p, v = vu / p;
+                    const int vu = (int)div_hn.div((uint32_t)q), hh = q - vu * hn;
+                    const int v = (int)div_p.div((uint32_t)vu), u = vu - v * p;
                     const int c = 8 * hh * p + u;
                     uint4 o;
                     o.x = (uint32_t)get(v, c) | ((uint32_t)get(v, c + p) << 16);
@@ -175,7 +191,7 @@ __device__ __forceinline__ void emit_all_body(const JudgeFrame *__restrict__ fra
             } else {
                 for (int v = 0; v < p; v++)
                     for (int j = threadIdx.x; j < p * ns; j += blockDim.x) {
-                        const int u = j / ns, si = j - u * ns;
+                        const int u = (int)div_ns.div((uint32_t)j), si = j - u * ns;
                         dst[(size_t)v * Ny * W + (size_t)u * Nx + si] = get(v, si * p + u);
                     }
             }
@@ -210,7 +226,8 @@ __device__ __forceinline__ void emit_all_body(const JudgeFrame *__restrict__ fra
             }
         }
         if (!fm) continue;
-        for (int c = threadIdx.x, sc = c / p; c < nco; c += blockDim.x, sc = c / p) {
+        for (int c = threadIdx.x; c < nco; c += blockDim.x) {
+            const int sc = (int)div_p.div((uint32_t)c);
             const int lx = p + c, s = s0 + sc;
             for (int r = 0; r < p; r++) {
                 const int idx = (p + r) * TC + lx, q = r * nco + c;
