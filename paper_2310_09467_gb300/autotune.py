@@ -1,5 +1,5 @@
-"""Autotuner of the judge's tile shapes (emission tile width, pair-chain range
-per warp, frames per judge launch).
+"""Autotuner of the judge's tile shapes (emission tile width, upper bound on
+the pair-chain range per warp, frames per judge launch).
 
 The knobs change speed only, never results. For a batch the tuner times
 every setting with CUDA events on the plan's stream, keeps the fastest, and
