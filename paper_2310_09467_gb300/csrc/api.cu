@@ -337,6 +337,13 @@ extern "C" int lfc_plan_create(const lfc_config *cfg, void *cuda_stream, lfc_pla
     AL(crc_part, (size_t)ws.crc_part_cap);
     AL(crc_part2, (size_t)ws.crc_part_cap);
 #undef AL
+    // The chain kernel's first-predecessor scratch has one slot per SM, which
+    // its shared-memory footprint makes exclusive (no two CTAs fit an SM).
+    int smem_sm = 0;
+    if (e == cudaSuccess &&
+        cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, P->device) == cudaSuccess &&
+        2 * chain_smem_bytes() <= (size_t)smem_sm)
+        e = cudaErrorNotSupported;
     if (e == cudaSuccess) e = query_nsmid(P->stream, &ws.chain_nsm);
     if (e == cudaSuccess && ws.chain_nsm <= 0) e = cudaErrorUnknown;
     if (e == cudaSuccess) e = dalloc(&ws.chain_first, chain_first_bytes(ws.chain_nsm));
