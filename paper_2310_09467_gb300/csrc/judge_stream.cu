@@ -10,10 +10,11 @@
 //    are formed once in shared memory; then every pixel's symbol is produced
 //    for every candidate of the kind and stored in the candidate's ordering
 //    (raw order: 480-byte row runs; view-major order: 32-byte runs).
-// 2. chain_hist_kernel: one CTA per segment of a candidate stream, one
-//    warp per range (16-128 KB, tuned), one lane per 32nd of the range
-//    walking it byte by byte (see below); the lanes' sub-ranges are stitched
-//    per warp, the ranges per CTA and the CTAs by the fixup kernel.
+// 2. chain_hist_kernel: one CTA (10 warps) per segment of a candidate
+//    stream, one warp per range (at most the tuned 16-256 KB, evened out per
+//    launch), one lane per 32nd of the range walking it byte by byte (see
+//    below); the lanes' sub-ranges are stitched per warp, the ranges per CTA
+//    and the CTAs by the fixup kernel.
 #include "lfc_common.cuh"
 
 namespace lfc {
