@@ -101,6 +101,6 @@ def test_chain_split_matches_oracle(case, range_bytes):
 
 
 def test_chain_split_total():
-    # n pairs in all: one per position, minus nothing (cyclic stream)
+    # n - 1 pairs: one per adjacent entries of the n-entry last column
     S = np.random.default_rng(3).integers(0, 40, 4000, dtype=np.uint8)
     assert model_hist(S, 512).sum() == len(S) - 1
