@@ -1,8 +1,11 @@
 """Oracle pins for the prediction part (Sec. 2.1.1) and the orderings.
 
 Pins: hand-computed lossless-JPEG values (tests/golden/predictor_2x2.txt),
-closed-form residuals on planes and lenslet-periodic frames, the sub-aperture
-mosaic property of the view-major ordering, and exact round trips.
+hand-computed inter-lenslet and phase-space symbols of a frame whose left and
+top neighbouring lenslets differ (tests/golden/predictor_inter_phase_2x2.txt),
+closed-form residuals on planes, lenslet-periodic frames and lenslet ramps,
+the sub-aperture mosaic property of the view-major ordering, and exact round
+trips.
 """
 import os
 
@@ -146,3 +149,77 @@ def test_round_trip_all_ids(p, Ny, Nx):
         z = oracle.symbols(fr, p, cid, prev=pv)
         back = oracle.inverse_symbols(z, fr.shape[1], fr.shape[0], p, cid, prev=pv)
         assert np.array_equal(back, fr), cid
+
+
+GOLDEN_IP = os.path.join(os.path.dirname(__file__), "golden", "predictor_inter_phase_2x2.txt")
+
+
+def _inter_phase_golden():
+    frame, syms = [], []
+    for line in open(GOLDEN_IP):
+        parts = line.split()
+        if not parts or parts[0].startswith("#"):
+            continue
+        if parts[0] == "frame":
+            frame.append([int(v) for v in parts[1:]])
+        elif parts[0] == "sym":
+            syms.append((int(parts[1]), int(parts[2]), [int(v) for v in parts[3:]]))
+    return np.array(frame, dtype=np.uint16), syms
+
+
+@pytest.mark.parametrize("case", range(4))
+def test_inter_phase_golden_orientation(case):
+    """Hand-computed symbols of a 2x2-lenslet frame whose left and top
+    neighbouring lenslets differ, so that swapping A (left lenslet) and B (top
+    lenslet), or the x - p and y - p strides, changes the result."""
+    frame, syms = _inter_phase_golden()
+    f, dom, exp = syms[case]
+    z = oracle.symbols(frame, 2, oracle.make_id(f, dom, 0, 0))
+    assert [int(v) for v in z] == exp
+    back = oracle.inverse_symbols(z, 4, 4, 2, oracle.make_id(f, dom, 0, 0))
+    assert np.array_equal(back, frame)
+
+
+def _lenslet_ramp(p, Ny, Nx, c0, a, b):
+    """Frame constant inside each lenslet, a linear ramp across lenslets:
+    X = c0 + a s + b t for lenslet column s and row t."""
+    t = np.arange(Ny * p)[:, None] // p
+    s = np.arange(Nx * p)[None, :] // p
+    return (c0 + a * s + b * t).astype(np.uint16)
+
+
+def _ramp_interior_residual(f, a, b):
+    # A = X - a (left lenslet), B = X - b (top lenslet), C = X - a - b.
+    return {1: a, 2: b, 3: a + b, 4: 0, 5: a - (a // 2), 6: b - (b // 2), 7: -((-(a + b)) // 2)}[f]
+
+
+@pytest.mark.parametrize("f", range(1, 8))
+@pytest.mark.parametrize("a,b", [(7, -3), (-5, 12)])
+def test_inter_lenslet_ramp_closed_form(f, a, b):
+    """Closed form on a lenslet ramp: first lenslet row predicts from the left
+    lenslet (residual a), first lenslet column from the top one (residual b),
+    inside the grid the predictor function of (A, B, C) = (X - a, X - b,
+    X - a - b). The residuals are the same at every view (u, v)."""
+    p, Ny, Nx = 3, 4, 5
+    fr = _lenslet_ramp(p, Ny, Nx, 1000, a, b)
+    z = oracle.symbols(fr, p, oracle.make_id(f, 1, 0, 0)).reshape(fr.shape)
+    t = np.arange(Ny * p)[:, None] // p + np.zeros((1, Nx * p), dtype=np.int64)
+    s = np.arange(Nx * p)[None, :] // p + np.zeros((Ny * p, 1), dtype=np.int64)
+    d = np.where((t == 0) & (s == 0), fr.astype(np.int64),
+                 np.where(t == 0, a, np.where(s == 0, b, _ramp_interior_residual(f, a, b))))
+    assert np.array_equal(z, _zz(d))
+
+
+@pytest.mark.parametrize("f", range(1, 8))
+@pytest.mark.parametrize("a,b", [(7, -3), (-5, 12)])
+def test_phase_space_ramp_closed_form(f, a, b):
+    """Phase space on the same ramp: inside a lenslet every intra residual is 0
+    except the origin view's, which is the pixel itself; the second (inter)
+    stage therefore leaves the inter-lenslet closed form at view (0, 0) and 0
+    at every other view."""
+    p, Ny, Nx = 3, 4, 5
+    fr = _lenslet_ramp(p, Ny, Nx, 1000, a, b)
+    z = oracle.symbols(fr, p, oracle.make_id(f, 2, 0, 0)).reshape(fr.shape)
+    zi = oracle.symbols(fr, p, oracle.make_id(f, 1, 0, 0)).reshape(fr.shape)
+    origin = (np.arange(Ny * p)[:, None] % p == 0) & (np.arange(Nx * p)[None, :] % p == 0)
+    assert np.array_equal(z, np.where(origin, zi, 0))
