@@ -126,6 +126,11 @@ const char *lfc_plan_last_error(lfc_plan plan);
  *   d_choice   device, n bytes: best id per frame.
  *   d_scores   device, n * 256 uint64 or NULL: score of id c of frame i at
  *              [i * 256 + c]; entries of ids not judged are left untouched.
+ * The pair-histogram kernel keeps per-SM scratch in the plan's workspace:
+ * a plan's judge work (lfc_judge, lfc_compress, lfc_propose's judged frames,
+ * replays of its batches) must not overlap on the GPU. The plan's stream
+ * serialises its own calls; a batch replayed on the plan's stream keeps that
+ * order too.
  * Errors: INVALID_ARG (n > max_frames, geometry beyond the plan), CUDA. */
 int lfc_judge(lfc_plan plan, const lfc_frame *h_frames, int n, uint8_t *d_choice, uint64_t *d_scores);
 
@@ -280,13 +285,19 @@ int lfc_plan_bwt_counters(lfc_plan plan, int64_t *out, int n);
  *   d_scores   device, 256 uint64 or NULL: score of id c at [c] for the
  *              judged ids, other entries untouched;
  *   cuda_stream the stream to run on (NULL = legacy default stream).
- * The first call on a device sets up that device's scratch (looks up its
- * address and fills the log2 table, synchronising cuda_stream); make that
- * first call before any stream capture. All calls share the one array and
- * leave their contents in it; each call clears what must start at zero, and
- * calls whose work overlaps on the GPU (other streams, other host threads)
- * race on it. Asynchronous after set-up. Errors: INVALID_ARG (sizes beyond
- * the limits above, bad ids), CUDA. */
+ * The first call on a device looks up the array's device address, which
+ * loads the library's device code on that device if it is not loaded yet;
+ * make that first call before any stream capture. Every call looks the
+ * address up again (it changes when the device's context is re-created, e.g.
+ * after cudaDeviceReset) and launches a small kernel that rebuilds the log2
+ * table when the array does not hold it yet (the array starts zeroed in
+ * every new context); no call synchronises. All calls share the one array
+ * and leave their contents in it; each call clears what must start at zero,
+ * and calls whose work overlaps on the GPU (other streams, other host
+ * threads) race on it. If a CUDA error from earlier work is pending on the
+ * calling thread, the call returns CUDA without launching anything and
+ * leaves that error in place. Errors: INVALID_ARG (sizes beyond the limits
+ * above, bad ids), CUDA. */
 int lfc_judge_noalloc(const lfc_frame *h_frame, const uint8_t *h_ids, int n_ids, uint8_t *d_choice,
                       uint64_t *d_scores, void *cuda_stream);
 

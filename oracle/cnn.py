@@ -14,8 +14,17 @@ library's design, written plainly in numpy fp64:
   pool       mean over all 256 x 256 positions;
   linear     C -> K logits, bias; softmax; cross-entropy with the label.
 
+The network's stated precision is BF16 weights and activations with FP32
+accumulation. ``forward`` and ``backward`` take an optional ``act_round``
+applied where a BF16 network stores a tensor: every convolution's output
+after its ReLU and, going back, every convolution's pre-activation gradient
+after its ReLU mask. With ``bf16`` there (and BF16-rounded inputs and
+weights) the fp64 oracle differs from a BF16/FP32 implementation only by the
+FP32 accumulation order; without it, it is the exact fp64 network.
+
 Pins: finite differences of the loss (all parameters, tiny sizes), the
-convolution against scipy.signal.correlate, softmax-CE gradient in closed form.
+convolution against scipy.signal.correlate, softmax-CE gradient in closed form,
+the BF16 rounding against hand-worked bit patterns.
 """
 from __future__ import annotations
 
@@ -24,6 +33,17 @@ import math
 import numpy as np
 
 THUMB = 256
+
+
+def bf16(a) -> np.ndarray:
+    """Round to the nearest BF16 value (ties to even), returned as fp64.
+    BF16 keeps the sign, the 8-bit exponent and the top 7 mantissa bits of an
+    IEEE-754 binary32 value; the value is first taken to binary32."""
+    f = np.asarray(a, dtype=np.float32)
+    u = f.view(np.uint32).astype(np.uint64)
+    keep_odd = (u >> 16) & 1
+    u = ((u + 0x7FFF + keep_odd) >> 16) << 16
+    return u.astype(np.uint32).view(np.float32).astype(np.float64)
 
 
 def block_mean(img: np.ndarray, bs: int) -> np.ndarray:
@@ -81,12 +101,15 @@ def conv3x3(x: np.ndarray, w: np.ndarray, b: np.ndarray) -> np.ndarray:
     return y
 
 
-def forward(P: dict, x: np.ndarray):
-    """x [2, H, W] -> (logits [K], cache)."""
+def forward(P: dict, x: np.ndarray, act_round=None):
+    """x [2, H, W] -> (logits [K], cache). act_round, if given, is applied to
+    every convolution's output after its ReLU."""
     acts = [x]
     h = x
     for l in range(4):
         h = np.maximum(conv3x3(h, P["w%d" % l], P["b%d" % l]), 0.0)
+        if act_round is not None:
+            h = act_round(h)
         acts.append(h)
     g = h.mean(axis=(1, 2))
     logits = g @ P["wl"] + P["bl"]
@@ -103,9 +126,11 @@ def loss(P: dict, x: np.ndarray, label: int) -> float:
     return float(-np.log(softmax(logits)[label]))
 
 
-def backward(P: dict, x: np.ndarray, label: int):
-    """Gradients of the cross-entropy loss with respect to every parameter."""
-    logits, (acts, g) = forward(P, x)
+def backward(P: dict, x: np.ndarray, label: int, act_round=None):
+    """Gradients of the cross-entropy loss with respect to every parameter.
+    act_round, if given, is applied to the stored activations (as in
+    forward) and to every pre-activation gradient after the ReLU mask."""
+    logits, (acts, g) = forward(P, x, act_round)
     dz = softmax(logits)
     dz[label] -= 1.0                                   # d loss / d logits
     G = {"wl": np.outer(g, dz), "bl": dz.copy()}
@@ -114,6 +139,8 @@ def backward(P: dict, x: np.ndarray, label: int):
     dh = np.broadcast_to(dg[:, None, None] / (h.shape[1] * h.shape[2]), h.shape).copy()
     for l in range(3, -1, -1):
         dpre = dh * (acts[l + 1] > 0)                  # through the ReLU
+        if act_round is not None:
+            dpre = act_round(dpre)
         xin = acts[l]
         Cin, H, W = xin.shape
         xp = np.zeros((Cin, H + 2, W + 2))

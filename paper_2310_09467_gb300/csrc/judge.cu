@@ -1,24 +1,34 @@
-// judge.cu -- prediction, symbol map, orderings and the two-dimensional image
-// entropy criterion (Sec. 2.1.1, Sec. 2.1.2, Eq. (1), Fig. 2a/2c).
+// judge.cu -- per-pixel prediction, the score and choice stages of the
+// two-dimensional image entropy criterion, and the allocation-free judge
+// (Sec. 2.1.1, Sec. 2.1.2, Eq. (1), Fig. 2a/2c).
 //
-// The judge never materialises a candidate stream or its judge-BWT. Sorting
-// the rotations of S by their first byte only, with ties in generation order,
-// puts the rotations that start with byte b in increasing start order; their
-// last bytes are the predecessors S[i-1] of the occurrences i of b. So the
-// last column L is the concatenation over b = 0..255 of those predecessor
-// lists, and the 16-bit pairs of adjacent L entries are
+// What lfc_judge and lfc_compress use from this file: the segment fixup
+// (cross-CTA chain links and the bucket-boundary pairs), the fixed-point log2
+// table, the entropy score sum_t P_t L2(P_t), the argmax, the copy of each
+// frame's chosen candidate stream out of the judge's candidate streams, and
+// the per-pixel symbol kernels for caller-given ids (emit_kernel) and for
+// lfc_symbols. Candidate emission and the pair histograms of those calls run
+// in judge_stream.cu.
+//
+// The pair counting rests on this: sorting the rotations of S by their first
+// byte only, ties in generation order, puts the rotations that start with
+// byte b in increasing start order, and their last bytes are the
+// predecessors S[i-1] of the occurrences i of b. The last column L is the
+// concatenation over b = 0..255 of those predecessor lists, so the 16-bit
+// pairs of adjacent L entries are
 //   (S[i-1], S[j-1]) for consecutive occurrences i < j of the same byte b,
 //   (last predecessor of bucket b, first predecessor of the next non-empty
 //    bucket)  -- at most 255 bucket-boundary pairs,
-// with S[-1] = S[n-1]. Each warp walks its rows of the stream in 32-byte
-// windows: __match_any_sync finds equal bytes in the window, a per-warp table
-// carries the last predecessor of every byte value across windows, and the
-// pairs are counted in a shared-memory histogram with warp-aggregated
-// atomics. Per-warp and per-CTA first/last predecessor tables stitch the
-// chains across warps, CTAs and buckets in a small fixup kernel.
+// with S[-1] = S[n-1].
+//
+// judge_hist_kernel serves only lfc_judge_noalloc (end of the file): it
+// computes the symbols of its rows on the fly (no candidate stream in
+// memory) and walks them in 32-byte windows, __match_any_sync finding equal
+// bytes in a window and a per-warp table carrying the last predecessor of
+// every byte value across windows; pairs go to a shared-memory histogram
+// with warp-aggregated atomics, and per-warp / per-segment first and last
+// predecessor tables stitch the chains in the fixup kernel.
 #include "lfc_common.cuh"
-
-#include <mutex>
 
 namespace lfc {
 
@@ -477,18 +487,21 @@ cudaError_t launch_symbols_one(const FrameDev &F, int id, uint16_t *dst, cudaStr
 namespace lfc {
 
 constexpr int kNoAllocRowsPerSeg = 128;
-constexpr int kNoAllocMaxSegs = 32;  // frames up to 32 * 128 = 4096 rows
-constexpr int kNoAllocMaxDevices = 64;
+constexpr int kNoAllocMaxSegs = 32;      // frames up to 32 * 128 = 4096 rows
+constexpr int kNoAllocMaxWidth = 2656;   // judge_smem_bytes(2656) = 227 KB, the per-CTA limit
+constexpr uint32_t kNoAllocTableMagic = 0x4C325442u;  // marks a filled log2 table
 
 struct NoAllocScratch {
     uint32_t hist[kHistBins];                 // one candidate's pair histogram
-    uint64_t l2tab[kHistBins];                // fixed-point log2 table, filled at set-up
+    uint64_t l2tab[kHistBins];                // fixed-point log2 table
     uint16_t summ[kNoAllocMaxSegs * 512];     // per-segment first/last tables
     uint64_t scores[256];                     // score by id
     JudgeFrame jf_one[256];                   // candidate i: K = 1, cand_off = i
     JudgeFrame jf_all;                        // all candidates, for the argmax
     int32_t zero[4];                          // frame_index / hist_frame tables = {0}
     uint8_t cand[256];
+    uint32_t table_magic;                     // kNoAllocTableMagic once l2tab holds the table
+    uint32_t table_done;                      // CTAs of the filling launch that have finished
 };
 
 static __device__ __align__(256) NoAllocScratch g_noalloc_scratch;
@@ -497,6 +510,25 @@ struct IdList {
     uint8_t id[256];
     int32_t n;
 };
+
+// Fills the log2 table unless the array already holds it. The array starts
+// zeroed whenever the library's device code is loaded into a context (a new
+// process, or a context re-created after a device reset), so the marker is
+// then missing and the table is rebuilt; otherwise every CTA returns at once.
+// The last CTA to finish sets the marker, so no CTA of a later launch can see
+// the marker before the whole table is written.
+__global__ void __launch_bounds__(1024) noalloc_table_kernel(NoAllocScratch *s) {
+    if (*reinterpret_cast<volatile uint32_t *>(&s->table_magic) == kNoAllocTableMagic) return;
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    s->l2tab[c] = log2_fx((uint32_t)c);
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0 && atomicAdd(&s->table_done, 1u) == gridDim.x - 1) {
+        s->table_done = 0;
+        __threadfence();
+        atomicExch(&s->table_magic, kNoAllocTableMagic);
+    }
+}
 
 __global__ void noalloc_describe_kernel(NoAllocScratch *s, FrameDev F, IdList ids, int segs) {
     const int i = threadIdx.x;
@@ -526,28 +558,6 @@ __global__ void noalloc_copy_scores_kernel(const NoAllocScratch *s, IdList ids, 
     if (i < ids.n) out[ids.id[i]] = s->scores[ids.id[i]];
 }
 
-static std::mutex g_noalloc_mu;
-static NoAllocScratch *g_noalloc_ptr[kNoAllocMaxDevices];
-
-// Per-device set-up on the first call: the array's device address (host code
-// may not use the symbol itself) and the log2 table, filled synchronously.
-static int noalloc_setup(cudaStream_t st, NoAllocScratch **out) {
-    int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess) return LFC_ERR_CUDA;
-    if (dev < 0 || dev >= kNoAllocMaxDevices) return LFC_ERR_INVALID_ARG;
-    std::lock_guard<std::mutex> lock(g_noalloc_mu);
-    if (!g_noalloc_ptr[dev]) {
-        void *p = nullptr;
-        if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) return LFC_ERR_CUDA;
-        NoAllocScratch *s = reinterpret_cast<NoAllocScratch *>(p);
-        l2_table_kernel<<<kHistBins / 256, 256, 0, st>>>(s->l2tab);
-        if (cudaGetLastError() != cudaSuccess || cudaStreamSynchronize(st) != cudaSuccess) return LFC_ERR_CUDA;
-        g_noalloc_ptr[dev] = s;
-    }
-    *out = g_noalloc_ptr[dev];
-    return LFC_OK;
-}
-
 }  // namespace lfc
 
 extern "C" int lfc_judge_noalloc(const lfc_frame *frame, const uint8_t *h_ids, int n_ids, uint8_t *d_choice,
@@ -558,7 +568,7 @@ extern "C" int lfc_judge_noalloc(const lfc_frame *frame, const uint8_t *h_ids, i
     const int W = frame->width, H = frame->height, p = frame->pitch;
     if (W <= 0 || H <= 0 || p <= 0 || W % p || H % p || (int64_t)W * H * 2 > ((int64_t)1 << 26))
         return LFC_ERR_INVALID_ARG;
-    if (judge_smem_bytes(W) > 232448 || H > kNoAllocMaxSegs * kNoAllocRowsPerSeg) return LFC_ERR_INVALID_ARG;
+    if (W > kNoAllocMaxWidth || H > kNoAllocMaxSegs * kNoAllocRowsPerSeg) return LFC_ERR_INVALID_ARG;
     IdList ids;
     ids.n = n_ids;
     for (int i = 0; i < n_ids; i++) {
@@ -568,9 +578,25 @@ extern "C" int lfc_judge_noalloc(const lfc_frame *frame, const uint8_t *h_ids, i
         ids.id[i] = (uint8_t)id;
     }
     cudaStream_t st = reinterpret_cast<cudaStream_t>(cuda_stream);
-    NoAllocScratch *s = nullptr;
-    int rc = noalloc_setup(st, &s);
-    if (rc != LFC_OK) return rc;
+    // An error left pending by earlier work on this thread would be taken
+    // for this call's own: refuse to start, and leave it in place.
+    if (cudaPeekAtLastError() != cudaSuccess) return LFC_ERR_CUDA;
+    // The array's device address, looked up on every call (host code may not
+    // use the symbol itself, and the address changes if the context is
+    // re-created).
+    void *sp = nullptr;
+    if (cudaGetSymbolAddress(&sp, g_noalloc_scratch) != cudaSuccess || !sp) {
+        cudaGetLastError();
+        return LFC_ERR_CUDA;
+    }
+    NoAllocScratch *s = reinterpret_cast<NoAllocScratch *>(sp);
+    // One value for every call (the largest frame allowed), so that callers
+    // on several host threads never set different limits.
+    if (cudaFuncSetAttribute(judge_hist_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)judge_smem_bytes(kNoAllocMaxWidth)) != cudaSuccess) {
+        cudaGetLastError();
+        return LFC_ERR_CUDA;
+    }
     FrameDev F;
     F.X = frame->data;
     F.prev = frame->prev;
@@ -581,14 +607,18 @@ extern "C" int lfc_judge_noalloc(const lfc_frame *frame, const uint8_t *h_ids, i
     F.Ny = H / p;
     const int segs = (H + kNoAllocRowsPerSeg - 1) / kNoAllocRowsPerSeg;
     const size_t smem = judge_smem_bytes(W);
-    if (cudaFuncSetAttribute(judge_hist_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
-        return LFC_ERR_CUDA;
+    noalloc_table_kernel<<<kHistBins / 1024, 1024, 0, st>>>(s);
     noalloc_describe_kernel<<<1, 256, 0, st>>>(s, F, ids, segs);
+    if (cudaGetLastError() != cudaSuccess) return LFC_ERR_CUDA;
     for (int i = 0; i < n_ids; i++) {
-        if (cudaMemsetAsync(s->hist, 0, sizeof(s->hist), st) != cudaSuccess) return LFC_ERR_CUDA;
+        if (cudaMemsetAsync(s->hist, 0, sizeof(s->hist), st) != cudaSuccess) {
+            cudaGetLastError();
+            return LFC_ERR_CUDA;
+        }
         judge_hist_kernel<<<segs, kJudgeWarps * 32, smem, st>>>(&s->jf_one[i], 1, s->cand, s->hist, s->summ, W);
         judge_fixup_kernel<<<1, 256, 0, st>>>(&s->jf_one[i], s->zero, s->cand, s->hist, s->summ);
         entropy_kernel<<<1, 1024, 0, st>>>(s->hist, s->l2tab, &s->jf_one[i], s->zero, s->cand, s->scores, s->zero);
+        if (cudaGetLastError() != cudaSuccess) return LFC_ERR_CUDA;
     }
     argmax_kernel<<<1, 32, 0, st>>>(&s->jf_all, 1, s->cand, s->scores, d_choice, s->zero);
     if (d_scores) noalloc_copy_scores_kernel<<<1, 256, 0, st>>>(s, ids, d_scores);

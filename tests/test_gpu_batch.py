@@ -1,7 +1,8 @@
 """Uneven frame batches captured once as a CUDA graph (lfc_batch_*): every
-replay must produce exactly the containers lfc_compress produces for the
-data the frame buffers hold at launch time, including a temporal frame and
-the device-driven suffix-sort rounds."""
+replay must produce exactly the oracle's containers (judge over the plan's
+candidates, then the coder) for the data the frame buffers hold at launch
+time, and the containers lfc_compress produces, including a temporal frame
+and the device-driven suffix-sort rounds."""
 import numpy as np
 import pytest
 
@@ -40,9 +41,11 @@ def test_batch_graph_matches_compress_twice():
         batch.launch()
         torch.cuda.synchronize()
         got = batch.to_bytes()
+        for k, (blob, (f, p, j)) in enumerate(zip(got, frames)):
+            pv = frames[j][0] if j is not None else None
+            best, _ = oracle.judge(f, p, oracle.default_ids(pv is not None), prev=pv)
+            assert blob == oracle.compress_id(f, p, best, prev=pv, block_bytes=25000), (rnd, k)
+            assert np.array_equal(oracle.decompress(blob, prev=pv), f)
         ref = plan.compress_to_bytes(dev, pitches, prevs=prevs)
         assert got == ref, rnd
-        for blob, (f, p, j) in zip(got, frames):
-            pv = frames[j][0] if j is not None else None
-            assert np.array_equal(oracle.decompress(blob, prev=pv), f)
     batch.close()

@@ -1,7 +1,14 @@
 """Learned proposal on the GPU against the fp64 oracle (oracle/cnn.py):
-thumbnails, forward, backward (BF16-rounded inputs and weights on the oracle
-side, FP32 accumulation on the GPU), the Adam update in closed form, the
-proposal's top-k / tau masks and its use by lfc_compress."""
+thumbnails, forward, backward, the Adam update in closed form, the proposal's
+top-k / tau masks and its use by lfc_compress.
+
+The oracle stores BF16 where the network's stated precision puts BF16
+(inputs, convolution weights, activations, pre-activation gradients) and
+accumulates in fp64; the GPU accumulates in FP32. Every probability and every
+gradient element is compared on its own: within 1e-2 of its value plus 1e-3 of
+the largest magnitude in its tensor (the floor covers elements that cancel to
+near zero, where FP32 accumulation order and a rare BF16 re-rounding or ReLU
+mask flip dominate)."""
 import numpy as np
 import pytest
 
@@ -10,13 +17,6 @@ from oracle import cnn as ocnn
 from paper_2310_09467_gb300 import synth
 
 pytestmark = pytest.mark.gpu
-
-
-def bf16_round(a):
-    f = np.asarray(a, dtype=np.float32)
-    u = f.view(np.uint32).astype(np.uint64)
-    u = (u + 0x7FFF + ((u >> 16) & 1)) & 0xFFFF0000
-    return u.astype(np.uint32).view(np.float32).astype(np.float64)
 
 
 @pytest.fixture(scope="module")
@@ -54,25 +54,30 @@ def test_forward_and_backward_match_oracle(L):
     net.set_params(net.flat_from_dict(P))
     net.set_thumbnails(torch.from_numpy(x.astype(np.float32)).cuda())
     probs = net.forward(n).cpu().numpy()
-    Pr = {k: (bf16_round(v) if k.startswith("w") and k != "wl" else v) for k, v in P.items()}
-    xr = bf16_round(x)
+    Pr = {k: (ocnn.bf16(v) if k.startswith("w") and k != "wl" else v) for k, v in P.items()}
+    xr = ocnn.bf16(x)
     labels = np.array([3, 17], dtype=np.int32)
     ref_p, ref_g = [], None
     for b in range(n):
-        logits, _ = ocnn.forward(Pr, xr[b])
+        logits, _ = ocnn.forward(Pr, xr[b], ocnn.bf16)
         ref_p.append(ocnn.softmax(logits))
-        g = ocnn.backward(Pr, xr[b], int(labels[b]))
+        g = ocnn.backward(Pr, xr[b], int(labels[b]), ocnn.bf16)
         ref_g = g if ref_g is None else {k: ref_g[k] + g[k] for k in g}
     ref_p = np.array(ref_p)
-    assert np.allclose(probs, ref_p, rtol=3e-2, atol=2e-3), np.max(np.abs(probs - ref_p))
+    bad = np.abs(probs - ref_p) > 1e-2 * ref_p + 1e-5
+    assert not bad.any(), ("probs", int(bad.sum()), float(np.max(np.abs(probs - ref_p) / (ref_p + 1e-5))))
     loss = net.backward(torch.from_numpy(labels).cuda()).cpu().numpy()
-    assert np.allclose(loss, [-np.log(ref_p[b][labels[b]]) for b in range(n)], rtol=3e-2, atol=1e-3)
+    ref_loss = np.array([-np.log(ref_p[b][labels[b]]) for b in range(n)])
+    assert np.all(np.abs(loss - ref_loss) <= 1e-2 * ref_loss + 1e-5), (loss, ref_loss)
     _, g = net.get_params(grads=True)
     G = net.dict_from_flat(g)
     for k in ref_g:
         r = ref_g[k] / n
-        err = np.linalg.norm(G[k] - r) / max(np.linalg.norm(r), 1e-12)
-        assert err < 5e-2, (k, err)
+        bound = 1e-2 * np.abs(r) + 1e-3 * np.abs(r).max()
+        err = np.abs(G[k] - r)
+        worst = int(np.argmax(err / bound))
+        assert np.all(err <= bound), (k, int((err > bound).sum()), r.size, float(err.flat[worst]),
+                                      float(r.flat[worst]), float(np.abs(r).max()))
 
 
 def test_adam_step_closed_form(L):

@@ -67,3 +67,33 @@ def test_thumbnail_definition():
     big = np.full((600, 300), 150, dtype=np.uint16)
     tb = cnn.thumbnail(big, 15)  # bs = 3 -> 200 x 100 blocks of value log1p(50)/8
     assert np.allclose(tb[0, :200, :100], np.log1p(50) / 8) and tb[0, 200:].sum() == 0
+
+
+def test_bf16_rounding_bit_patterns():
+    """BF16 = the top 16 bits of binary32, rounded to nearest, ties to even
+    (hand-worked bit patterns)."""
+    cases = [
+        (1.0, 1.0),                          # 0x3F800000 exact
+        (1.0 + 2.0 ** -8, 1.0),              # 0x3F808000: tie, kept bit 0 -> down
+        (1.0 + 3 * 2.0 ** -8, 1.0 + 2.0 ** -6),  # 0x3F818000: tie, kept bit 1 -> up
+        (1.0 + 2.0 ** -8 + 2.0 ** -20, 1.0 + 2.0 ** -7),  # above the tie -> up
+        (-2.5, -2.5),                        # exact
+        (0.1, 0.10009765625),                # 0x3DCCCCCD -> 0x3DCD0000
+        (0.0, 0.0),
+    ]
+    for v, exp in cases:
+        assert cnn.bf16(v) == exp, (v, cnn.bf16(v), exp)
+
+
+def test_rounding_hook_identity_is_the_fp64_network():
+    rng = np.random.default_rng(3)
+    P = cnn.init_params(C=3, K=4, seed=4)
+    x = rng.normal(size=(2, 6, 5))
+    G0 = cnn.backward(P, x, 1)
+    G1 = cnn.backward(P, x, 1, act_round=lambda a: a)
+    for k in G0:
+        assert np.array_equal(G0[k], G1[k])
+    Gq = cnn.backward(P, x, 1, act_round=cnn.bf16)
+    # BF16 storage changes the gradients by a few BF16 units at most
+    for k in G0:
+        assert np.allclose(Gq[k], G0[k], rtol=5e-2, atol=5e-2 * np.abs(G0[k]).max())
