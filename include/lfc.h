@@ -158,7 +158,8 @@ size_t lfc_max_compressed_bytes(int32_t width, int32_t height, int32_t block_byt
  *   d_choice    device n ids to use, or NULL to run lfc_judge first.
  *   out_cap     bytes available at d_out; CAPACITY if below the slot sum.
  * The call blocks the host until the stream has finished the BWT rounds
- * (it reads per-round active counts). Errors: INVALID_ARG, CAPACITY, CUDA. */
+ * (it reads per-round active counts). Errors: INVALID_ARG, CAPACITY, CUDA,
+ * TIMEOUT (a bounded wait of the suffix sort gave up; see wait_budget_ms). */
 int lfc_compress(lfc_plan plan, const lfc_frame *h_frames, int n, const uint8_t *d_choice,
                  uint8_t *d_out, size_t out_cap, uint64_t *d_out_sizes);
 
@@ -171,7 +172,8 @@ int lfc_compress(lfc_plan plan, const lfc_frame *h_frames, int n, const uint8_t 
  * synchronous. lfc_batch_launch replays it on the plan's stream with the data
  * the frame buffers hold at that time; outputs land as for lfc_compress.
  * Batches share the plan's workspace: launches on one plan are serialised by
- * its stream. Errors: as lfc_compress, plus NOMEM, CUDA. */
+ * its stream. A bounded wait that gives up during a replay is reported by
+ * lfc_plan_device_status. Errors: as lfc_compress, plus NOMEM, CUDA. */
 typedef struct lfc_batch_s *lfc_batch;
 int lfc_batch_create(lfc_plan plan, const lfc_frame *h_frames, int n, const uint8_t *d_choice, uint8_t *d_out,
                      size_t out_cap, uint64_t *d_out_sizes, lfc_batch *out);
@@ -183,10 +185,25 @@ void lfc_batch_destroy(lfc_batch batch);
  * 1 <= size <= 720000 and n_blocks <= the plan's block capacity
  * (lfc_plan_block_capacity). Stream b is written at d_out + b * out_stride,
  * its byte count to d_stream_sizes[b]; out_stride must be at least
- * lfc_max_stream_bytes(max size). Errors: INVALID_ARG, CAPACITY, CUDA. */
+ * lfc_max_stream_bytes(max size). Errors: INVALID_ARG, CAPACITY, CUDA,
+ * TIMEOUT (as lfc_compress). */
 int lfc_bzip2_encode(lfc_plan plan, const uint8_t *d_in, const uint64_t *h_offsets,
                      const uint32_t *h_sizes, int n_blocks, uint8_t *d_out, size_t out_stride,
                      uint32_t *d_stream_sizes);
+
+/* The Burrows-Wheeler transform of arbitrary byte blocks exactly as the
+ * coder computes it inside lfc_bzip2_encode (bzip2 format, Sec. 2.1.3): RLE1
+ * of the block, then the sort of all cyclic rotations, identical rotations
+ * by start index; the last column goes out. Block b is d_in[h_offsets[b] ..
+ * + h_sizes[b]), 1 <= size <= 720000, n_blocks <= the plan's block capacity.
+ * Its last column is written at d_L + b * L_stride (device; L_stride must
+ * hold the RLE1 length bound min(900000, 5/4 size + 4)), its length (the RLE1
+ * length) to d_len[b] and the row of the rotation starting at 0 to
+ * d_orig[b] (both device). Used to compare the paper's first-byte judge with
+ * the entropy of the real transform. Errors: INVALID_ARG, CAPACITY, CUDA,
+ * TIMEOUT (as lfc_compress). */
+int lfc_bwt_blocks(lfc_plan plan, const uint8_t *d_in, const uint64_t *h_offsets, const uint32_t *h_sizes,
+                   int n_blocks, uint8_t *d_L, size_t L_stride, uint32_t *d_len, uint32_t *d_orig);
 
 /* Worst-case bytes of one stream holding block_bytes input bytes. */
 size_t lfc_max_stream_bytes(int32_t block_bytes);
@@ -220,16 +237,43 @@ int lfc_decompress(lfc_plan plan, const uint8_t *const *h_in, const uint64_t *h_
  *                           out below it so that its CTAs fill whole waves
  *                           of the device's SMs;
  *   judge_frames_per_launch frames per judge launch, 1 .. the plan's
- *                           min(max_frames, 8) (default: that maximum).
+ *                           min(max_frames, 8) (default: that maximum);
+ *   wait_budget_ms          how long one bounded device wait may last
+ *                           before the kernel gives up and the call returns
+ *                           LFC_ERR_TIMEOUT, 1 .. 60000 (default 1000). The
+ *                           suffix sort's radix passes wait on each other
+ *                           (every tile waits for the digit counts of the
+ *                           block's earlier tiles); such waits always end in
+ *                           a correct run, so the budget only bounds a fault.
  * Errors: INVALID_ARG for values outside these sets. */
 typedef struct {
     int32_t emit_tile_lenslets;
     int32_t chain_range_bytes;
     int32_t judge_frames_per_launch;
-    int32_t reserved;
+    int32_t wait_budget_ms;
 } lfc_tuning;
 int lfc_plan_set_tuning(lfc_plan plan, const lfc_tuning *tuning);
 int lfc_plan_get_tuning(lfc_plan plan, lfc_tuning *tuning);
+
+/* Device status of the plan's bounded waits: synchronises the plan's
+ * stream and returns LFC_ERR_TIMEOUT if a device wait has given up since the
+ * last call (for example in a replayed batch, whose launch returns before the
+ * GPU runs it), clearing that state; LFC_OK otherwise. lfc_compress and
+ * lfc_bzip2_encode report a wait that gives up in their own calls (they read
+ * the suffix sort's state) and start from a clear state. Errors: CUDA. */
+int lfc_plan_device_status(lfc_plan plan);
+
+/* Fault injection for tests of the bounded waits (host side: nothing on the
+ * GPU faults). LFC_FAULT_SORT_WITHHOLD: in the next suffix sort the first
+ * tile of the first block sorts its elements but never publishes its digit
+ * counts, so the block's later tiles wait for a flag that nothing sets, give
+ * up after the plan's wait budget and the call returns LFC_ERR_TIMEOUT
+ * (its output is void). The fault is set on the device, asynchronously on
+ * the plan's stream, and fires in the next suffix sort that runs there (an
+ * lfc_compress, lfc_bzip2_encode or batch replay), once; the plan stays
+ * usable. LFC_FAULT_NONE cancels a pending fault. Errors: INVALID_ARG, CUDA. */
+enum { LFC_FAULT_NONE = 0, LFC_FAULT_SORT_WITHHOLD = 1 };
+int lfc_plan_inject_fault(lfc_plan plan, int fault);
 
 /* Stage timing (tracing). With timing enabled the plan records CUDA events on
  * its stream around each stage below and accumulates their device time; the

@@ -12,6 +12,7 @@ using namespace lfc;
 namespace {
 
 constexpr int kJudgeFramesCap = 8;
+constexpr int kDefaultWaitMs = 1000;  // bounded device waits give up after this long
 
 int fail(lfc_plan P, int code, const std::string &what, cudaError_t e = cudaSuccess) {
     if (P) {
@@ -170,7 +171,13 @@ extern "C" int lfc_plan_set_tuning(lfc_plan P, const lfc_tuning *t) {
             return fail(P, LFC_ERR_INVALID_ARG, "judge_frames_per_launch outside 1..min(max_frames, 8)");
         v.judge_frames_per_launch = t->judge_frames_per_launch;
     }
+    if (t->wait_budget_ms) {
+        if (t->wait_budget_ms < 1 || t->wait_budget_ms > 60000)
+            return fail(P, LFC_ERR_INVALID_ARG, "wait_budget_ms outside 1..60000");
+        v.wait_budget_ms = t->wait_budget_ms;
+    }
     P->tune = v;
+    P->wait_cycles = (long long)(v.wait_budget_ms ? v.wait_budget_ms : kDefaultWaitMs) * P->sm_clock_khz;
     return LFC_OK;
 }
 
@@ -178,6 +185,7 @@ extern "C" int lfc_plan_get_tuning(lfc_plan P, lfc_tuning *t) {
     if (!P || !t) return LFC_ERR_INVALID_ARG;
     *t = P->tune;
     if (t->judge_frames_per_launch == 0) t->judge_frames_per_launch = P->judge_frames_cap;
+    if (t->wait_budget_ms == 0) t->wait_budget_ms = kDefaultWaitMs;
     return LFC_OK;
 }
 
@@ -191,6 +199,25 @@ extern "C" int lfc_plan_bwt_counters(lfc_plan P, int64_t *out, int n) {
     if (k < n) out[k++] = head[2];
     for (int r = 0; r < 32 && k < n; r++) out[k++] = P->bwt_round_tied[r];
     return k;
+}
+
+extern "C" int lfc_plan_inject_fault(lfc_plan P, int fault) {
+    if (!P || fault < 0 || fault > LFC_FAULT_SORT_WITHHOLD) return LFC_ERR_INVALID_ARG;
+    // the device word is read by the next suffix sort that runs on the GPU
+    // (a call's or a replayed batch's); the withholding tile clears it
+    CK(cudaMemsetAsync(P->ws.act_total + kSortFaultWord, fault ? 1 : 0, sizeof(int32_t), P->stream));
+    return LFC_OK;
+}
+
+extern "C" int lfc_plan_device_status(lfc_plan P) {
+    if (!P) return LFC_ERR_INVALID_ARG;
+    int32_t st = 0;
+    CK(cudaMemcpyAsync(&st, P->ws.act_total + kSortStickyWord, sizeof(int32_t), cudaMemcpyDeviceToHost, P->stream));
+    CK(cudaStreamSynchronize(P->stream));
+    if (st == 0) return LFC_OK;
+    CK(cudaMemsetAsync(P->ws.act_total + kSortStickyWord, 0, sizeof(int32_t), P->stream));
+    CK(cudaStreamSynchronize(P->stream));
+    return st == LFC_ERR_TIMEOUT ? fail(P, LFC_ERR_TIMEOUT, "a bounded device wait gave up") : fail(P, LFC_ERR_CUDA, "device status");
 }
 
 extern "C" const char *lfc_status_string(int s) {
@@ -224,7 +251,7 @@ extern "C" int lfc_plan_block_capacity(lfc_plan P) { return P ? P->block_cap : 0
 
 static void free_ws(Workspace &w) {
     void *ptrs[] = {w.hist, w.summ, w.chain_first, w.scores, w.choice, w.jframes, w.cand, w.l2tab, w.stream, w.blocks, w.bstate,
-                    w.rle, w.sa, w.sa2, w.rank, w.act, w.act2, w.val, w.val2, w.keys, w.keys2, w.tilecnt, w.tileaux, w.bwt,
+                    w.rle, w.sa, w.sa2, w.rank, w.act, w.act2, w.val, w.val2, w.keys, w.keys2, w.lbstat, w.dhist, w.tileaux, w.bwt,
                     w.mtfidx, w.mtflists, w.mtfrec, w.mtfreclen, w.sym, w.freq, w.rfreq, w.sel, w.lens, w.codes, w.packed, w.cstream, w.masks, w.class_ids,
                     w.act_total, w.block_dst, w.frame_crc, w.crc_part, w.crc_part2, w.chunk_desc, w.dec_tt};
     for (void *p : ptrs)
@@ -247,6 +274,9 @@ extern "C" int lfc_plan_create(const lfc_config *cfg, void *cuda_stream, lfc_pla
     cudaGetDevice(&P->device);
     if (cudaDeviceGetAttribute(&P->sm_count, cudaDevAttrMultiProcessorCount, P->device) != cudaSuccess || P->sm_count <= 0)
         P->sm_count = 1;
+    if (cudaDeviceGetAttribute(&P->sm_clock_khz, cudaDevAttrClockRate, P->device) != cudaSuccess || P->sm_clock_khz <= 0)
+        P->sm_clock_khz = 2100000;
+    P->wait_cycles = (long long)kDefaultWaitMs * P->sm_clock_khz;
     // candidate ids
     bool any = false;
     for (int i = 0; i < 4; i++) any |= cfg->candidate_mask[i] != 0;
@@ -317,7 +347,9 @@ extern "C" int lfc_plan_create(const lfc_config *cfg, void *cuda_stream, lfc_pla
     AL(val2, (size_t)BC * kBlockCap);
     AL(keys, (size_t)BC * kBlockCap);
     AL(keys2, (size_t)BC * kBlockCap);
-    AL(tilecnt, (size_t)BC * 256 * kTilesPerBlock);
+    ws.lbstat_words = (size_t)BC * kTilesPerBlock * 256;
+    AL(lbstat, 2 * ws.lbstat_words);
+    AL(dhist, (size_t)BC * 8 * 256);
     AL(tileaux, (size_t)BC * kTilesPerBlock * 4);
     AL(bwt, (size_t)BC * kBlockCap);
     AL(mtfidx, (size_t)BC * kBlockCap);
@@ -331,7 +363,7 @@ extern "C" int lfc_plan_create(const lfc_config *cfg, void *cuda_stream, lfc_pla
     AL(lens, (size_t)BC * kMaxGroups * kMaxAlpha);
     AL(codes, (size_t)BC * kMaxGroups * kMaxAlpha);
     AL(packed, (size_t)BC * ws.stream_words);
-    AL(act_total, (size_t)4);
+    AL(act_total, (size_t)kSortCtlHead + BC + 1);
     AL(block_dst, (size_t)BC);
     AL(frame_crc, (size_t)F);
     AL(crc_part, (size_t)ws.crc_part_cap);
@@ -348,7 +380,8 @@ extern "C" int lfc_plan_create(const lfc_config *cfg, void *cuda_stream, lfc_pla
     if (e == cudaSuccess && ws.chain_nsm <= 0) e = cudaErrorUnknown;
     if (e == cudaSuccess) e = dalloc(&ws.chain_first, chain_first_bytes(ws.chain_nsm));
     if (e == cudaSuccess) e = cudaMalloc(&ws.chunk_desc, ws.chunk_desc_bytes);
-    if (e == cudaSuccess) e = cudaMallocHost(reinterpret_cast<void **>(&ws.h_act_total), 4 * sizeof(int32_t));
+    if (e == cudaSuccess) e = cudaMallocHost(reinterpret_cast<void **>(&ws.h_act_total), kSortCtlHead * sizeof(int32_t));
+    if (e == cudaSuccess) e = cudaMemsetAsync(ws.act_total, 0, ((size_t)kSortCtlHead + BC + 1) * sizeof(int32_t), P->stream);
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&P->aux_stream, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&P->cap_stream, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&P->side_stream, cudaStreamNonBlocking);
@@ -600,7 +633,9 @@ int run_pass(lfc_plan P, const CoderPass &cp, const uint8_t *d_arena) {
     stage_begin(P, LFC_STAGE_RLE1);
     CK(launch_rle1(P, nb, reinterpret_cast<const BlockDesc *>(d_arena + cp.off_blocks)));
     stage_end(P, LFC_STAGE_RLE1);
+    P->bwt_timed_out = false;
     CK(launch_bwt(P, nb, cp.max_m));
+    if (P->bwt_timed_out) return fail(P, LFC_ERR_TIMEOUT, "suffix sort: a bounded look-back wait gave up");
     stage_begin(P, LFC_STAGE_MTF);
     CK(launch_mtf_rle2(P, nb));
     stage_end(P, LFC_STAGE_MTF);
@@ -787,6 +822,39 @@ extern "C" int lfc_bzip2_encode(lfc_plan P, const uint8_t *d_in, const uint64_t 
     stage_begin(P, LFC_STAGE_CONTAINER);
     CK(launch_copy_streams(P, n_blocks, d_out, out_stride, d_stream_sizes));
     stage_end(P, LFC_STAGE_CONTAINER);
+    return LFC_OK;
+}
+
+extern "C" int lfc_bwt_blocks(lfc_plan P, const uint8_t *d_in, const uint64_t *h_offsets, const uint32_t *h_sizes,
+                              int n_blocks, uint8_t *d_L, size_t L_stride, uint32_t *d_len, uint32_t *d_orig) {
+    if (!P || !d_in || !h_offsets || !h_sizes || !d_L || !d_len || !d_orig || n_blocks < 1)
+        return fail(P, LFC_ERR_INVALID_ARG, "lfc_bwt_blocks: bad arguments");
+    if (n_blocks > P->block_cap) return fail(P, LFC_ERR_INVALID_ARG, "lfc_bwt_blocks: too many blocks");
+    CoderPass cp;
+    uint32_t max_size = 0;
+    for (int b = 0; b < n_blocks; b++) {
+        if (h_sizes[b] < 1 || h_sizes[b] > (uint32_t)kMaxBlockBytes)
+            return fail(P, LFC_ERR_INVALID_ARG, "lfc_bwt_blocks: block size outside 1..720000");
+        BlockDesc d;
+        d.src = d_in + h_offsets[b];
+        d.len = (int32_t)h_sizes[b];
+        d.frame = -1;
+        cp.blocks.push_back(d);
+        max_size = std::max(max_size, h_sizes[b]);
+    }
+    const size_t need = std::min<size_t>((size_t)kRleCap, (size_t)max_size + max_size / 4 + 4);
+    if (L_stride < need) return fail(P, LFC_ERR_CAPACITY, "lfc_bwt_blocks: L_stride below the RLE1 bound");
+    Arena A;
+    build_pass(A, cp);
+    int r = stage_arena(P, A);
+    if (r) return r;
+    const BlockDesc *d_blocks = reinterpret_cast<const BlockDesc *>(reinterpret_cast<const uint8_t *>(P->ws.chunk_desc) + cp.off_blocks);
+    CK(cudaMemsetAsync(P->ws.bstate, 0, sizeof(BlockState) * cp.nblocks, P->stream));
+    CK(launch_rle1(P, cp.nblocks, d_blocks));
+    P->bwt_timed_out = false;
+    CK(launch_bwt(P, cp.nblocks, cp.max_m));
+    if (P->bwt_timed_out) return fail(P, LFC_ERR_TIMEOUT, "suffix sort: a bounded look-back wait gave up");
+    CK(launch_copy_bwt(P, cp.nblocks, d_L, L_stride, d_len, d_orig));
     return LFC_OK;
 }
 

@@ -3,11 +3,17 @@
 // public bzip2 format).
 //
 // BWT = sort of all cyclic rotations, ties between identical rotations by
-// start index. Two phases over all blocks of a pass at once, one CTA per
-// (4096-element tile, block), block-major so a block's data stays in L2
-// while its tiles run. Every element carries its sort key: a radix pass
-// reads (key, element) pairs coalesced, ranks each tile by digit in shared
-// memory and writes each digit's run of the tile contiguously.
+// start index. Two phases over all blocks of a pass at once. Every element
+// carries its sort key. A radix pass is one persistent kernel whose CTAs
+// take 4096-element tiles from a device work queue, tile-major over the
+// blocks so that a block has only a few tiles in flight: a CTA reads its tile's
+// (key, element) pairs coalesced, ranks them by digit in shared memory,
+// publishes the tile's digit counts and adds up the counts of the block's
+// earlier tiles as they are published (decoupled look-back: a tile only waits
+// on tiles taken from the queue before it, every wait bounded by a cycle
+// budget), then writes each digit's run of the tile contiguously. The
+// block's digit totals for every pass come from the kernel that builds the
+// keys, so a pass needs no separate histogram or scan launch.
 //  1. Keys = the first 8 bytes of each rotation (big-endian), built from
 //     sequential reads; 8 stable LSD passes of 8-bit digits.
 //  2. Prefix doubling on the groups still tied: rank[i] = head position of
@@ -18,6 +24,7 @@
 //     bits 20..59 only. Groups left when h >= m hold identical rotations,
 //     already in start-index order (every pass is stable and the first starts
 //     from the identity).
+#include <algorithm>
 #include <climits>
 #include <utility>
 
@@ -241,15 +248,83 @@ __device__ __forceinline__ int sort_count(const BlockState &s, int h) {
 template <int MODE>
 __device__ __forceinline__ int round_h(const int32_t *rs) { return MODE == 0 ? 0 : rs[2]; }
 
+// Sort state in device memory (rs): tied elements after a round, their
+// per-block maximum, the shift h, the round number; the abort word (nonzero
+// once a bounded wait has given up in this suffix sort: every later sort
+// kernel returns at once), the fault-injection word (test hook), the two work
+// queues of the radix passes (by pass parity), the work items of the current
+// pass, the sticky status (kept until the host reads it), and from
+// kRsTileOff on the per-block prefix of tile counts (nblocks + 1 entries).
+enum : int {
+    kRsTied = 0, kRsTiedMax = 1, kRsH = 2, kRsRound = 3, kRsAbort = 4, kRsFault = kSortFaultWord, kRsQueue = 6,
+    kRsItems = 8, kRsSticky = kSortStickyWord, kRsTileOff = 16
+};
+static_assert(kRsTileOff == kSortCtlHead, "sort control layout");
+
+// Look-back status word of one digit of one tile: bits 30-31 a flag, bits
+// 0-29 a count (at most kBlockCap < 2^30).
+constexpr uint32_t kLbAgg = 1u << 30;   // the tile's own count
+constexpr uint32_t kLbIncl = 2u << 30;  // count of this tile and every earlier tile of the block
+constexpr uint32_t kLbCount = (1u << 30) - 1u;
+constexpr size_t kLbBlockWords = (size_t)kTilesPerBlock * 256;  // one block's words in one status array
+constexpr int kSweepPasses = 8;  // digit-histogram rows per block (phase 1: 8 passes, a round: 5)
+
+__device__ __forceinline__ uint32_t ld_acquire_u32(const uint32_t *p) {
+    uint32_t v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ void st_release_u32(uint32_t *p, uint32_t v) {
+    asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+__device__ __forceinline__ int ld_volatile_i32(const int32_t *p) { return *reinterpret_cast<const volatile int32_t *>(p); }
+
+// Adds this thread's digits of key (one digit per pass, pass q at bit
+// shift0 + 8 q) to the tile histogram hst[q][256]; a warp whose 32 digits
+// agree adds them with one atomic.
+template <int NPASS>
+__device__ __forceinline__ void tile_digits(uint64_t key, bool ok, int shift0, uint32_t (*hst)[256]) {
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int q = 0; q < NPASS; q++) {
+        const uint32_t d = ok ? (uint32_t)(key >> (shift0 + 8 * q)) & 255u : 0xFFFFFFFFu;
+        const uint32_t d0 = __shfl_sync(LFC_FULL, d, 0);
+        if (__all_sync(LFC_FULL, d == d0)) {
+            if (lane == 0 && d0 != 0xFFFFFFFFu) atomicAdd(&hst[q][d0], 32u);
+        } else if (d != 0xFFFFFFFFu) {
+            atomicAdd(&hst[q][d], 1u);
+        }
+    }
+}
+
+// Adds a tile histogram to the block's digit totals dhist[b][q][256].
+template <int NPASS>
+__device__ __forceinline__ void flush_digits(uint32_t (*hst)[256], uint32_t *dhist_b) {
+    for (int i = threadIdx.x; i < NPASS * 256; i += blockDim.x) {
+        const uint32_t c = (&hst[0][0])[i];
+        if (c) atomicAdd(dhist_b + i, c);
+    }
+}
+
+__global__ void zero_u32_kernel(uint32_t *p, size_t n) {
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) p[i] = 0;
+}
+
 // Phase 1 keys: K[v] = bytes v .. v + 7 (cyclic) big-endian, element v.
 // Phase 1 sorts the first kPhase1Bytes bytes of every rotation; they sit in
 // the top bytes of the 64-bit key, so passes 8 - kPhase1Bytes .. 7 carry them.
 constexpr int kPhase1Bytes = LFC_PHASE1_BYTES;
 
+// Also adds the tile's digits of every pass to the block's totals and clears
+// the tile's look-back status words in both status arrays (the first pass
+// reads array 0 and clears array 1 for the second, and so on).
 __global__ void __launch_bounds__(kSortThreads) key8_kernel(const BlockState *__restrict__ st,
                                                             const uint8_t *__restrict__ rle_all,
-                                                            uint64_t *__restrict__ K_all, int32_t *__restrict__ V_all) {
+                                                            uint64_t *__restrict__ K_all, int32_t *__restrict__ V_all,
+                                                            uint32_t *__restrict__ dhist_all, uint32_t *__restrict__ lb_all,
+                                                            size_t lb_array_words) {
     __shared__ uint8_t sb[kTile + 8];
+    __shared__ uint32_t hst[kSweepPasses][256];
     const int b = blockIdx.y, tile = blockIdx.x;
     const int m = st[b].m;
     const int t0 = tile * kTile;
@@ -257,18 +332,28 @@ __global__ void __launch_bounds__(kSortThreads) key8_kernel(const BlockState *__
     const int cnt = min(kTile, m - t0);
     const uint8_t *rle = rle_all + (size_t)b * kBlockCap;
     for (int i = threadIdx.x; i < cnt + 7; i += kSortThreads) sb[i] = rle[(t0 + i) % m];
+    for (int i = threadIdx.x; i < kSweepPasses * 256; i += kSortThreads) (&hst[0][0])[i] = 0;
+    uint32_t *lbt = lb_all + (size_t)b * kLbBlockWords + (size_t)tile * 256;
+    lbt[threadIdx.x] = 0;
+    lbt[lb_array_words + threadIdx.x] = 0;
     __syncthreads();
     uint64_t *K = K_all + (size_t)b * kBlockCap;
     int32_t *V = V_all + (size_t)b * kBlockCap;
     for (int r = 0; r < kPerThread; r++) {
         const int kl = r * kSortThreads + threadIdx.x;
-        if (kl >= cnt) break;
+        const bool ok = kl < cnt;
         uint64_t key = 0;
+        if (ok) {
 #pragma unroll
-        for (int q = 0; q < kPhase1Bytes; q++) key = (key << 8) | sb[kl + q];
-        K[t0 + kl] = key << (8 * (8 - kPhase1Bytes));
-        V[t0 + kl] = t0 + kl;
+            for (int q = 0; q < kPhase1Bytes; q++) key = (key << 8) | sb[kl + q];
+            key <<= 8 * (8 - kPhase1Bytes);
+            K[t0 + kl] = key;
+            V[t0 + kl] = t0 + kl;
+        }
+        tile_digits<kSweepPasses>(key, ok, 0, hst);
     }
+    __syncthreads();
+    flush_digits<kSweepPasses>(hst, dhist_all + (size_t)b * kSweepPasses * 256);
 }
 
 // Round words of the tied elements: rank[v] << 40 | rank[(v + h) mod m] << 20 | v.
@@ -276,20 +361,61 @@ constexpr uint64_t kElemMask = (1u << 20) - 1u;
 
 __global__ void __launch_bounds__(kSortThreads) key40_kernel(const int32_t *__restrict__ rs, const BlockState *__restrict__ st,
                                                              const int32_t *__restrict__ V_all, const int32_t *__restrict__ rank_all,
-                                                             uint64_t *__restrict__ K_all) {
+                                                             uint64_t *__restrict__ K_all, uint32_t *__restrict__ dhist_all) {
+    __shared__ uint32_t hst[5][256];
+    if (rs[kRsAbort]) return;
     const int b = blockIdx.y, tile = blockIdx.x;
     const int h = rs[2];
     const BlockState s = st[b];
     const int n = sort_count<1>(s, h);
+    if (tile * kTile >= n) return;
+    for (int i = threadIdx.x; i < 5 * 256; i += kSortThreads) (&hst[0][0])[i] = 0;
+    __syncthreads();
     const size_t bo = (size_t)b * kBlockCap;
     for (int r = 0; r < kPerThread; r++) {
         const int k = tile * kTile + r * kSortThreads + threadIdx.x;
-        if (k >= n) break;
-        const int v = V_all[bo + k];
-        int j = v + h;
-        if (j >= s.m) j -= s.m;
-        K_all[bo + k] = ((uint64_t)(uint32_t)rank_all[bo + v] << 40) | ((uint64_t)(uint32_t)rank_all[bo + j] << 20) |
-                        (uint64_t)(uint32_t)v;
+        const bool ok = k < n;
+        uint64_t word = 0;
+        if (ok) {
+            const int v = V_all[bo + k];
+            int j = v + h;
+            if (j >= s.m) j -= s.m;
+            word = ((uint64_t)(uint32_t)rank_all[bo + v] << 40) | ((uint64_t)(uint32_t)rank_all[bo + j] << 20) |
+                   (uint64_t)(uint32_t)v;
+            K_all[bo + k] = word;
+        }
+        tile_digits<5>(word, ok, 20, hst);
+    }
+    __syncthreads();
+    flush_digits<5>(hst, dhist_all + (size_t)b * kSweepPasses * 256);
+}
+
+// Work items of the radix passes of a phase or round, tile-major: item i is
+// tile i / nblocks of block i % nblocks, so that the tiles in flight spread
+// over all blocks and a tile's earlier tiles of the same block have mostly
+// finished (a look-back then stops within a few steps). Per block its tile
+// count ceil(n_b / kTile) goes to rs[kRsTileOff + b]; rs[kRsItems] = the
+// largest count x nblocks (items past a block's last tile are skipped); both
+// work queues start empty. One CTA.
+template <int MODE>
+__global__ void __launch_bounds__(1024) sort_items_kernel(int32_t *__restrict__ rs, const BlockState *__restrict__ st, int nblocks) {
+    __shared__ int smax;
+    const bool abort = rs[kRsAbort] != 0;
+    const int h = round_h<MODE>(rs);
+    if (threadIdx.x == 0) smax = 0;
+    __syncthreads();
+    int mx = 0;
+    for (int b = threadIdx.x; b < nblocks; b += blockDim.x) {
+        const int t = abort ? 0 : (sort_count<MODE>(st[b], h) + kTile - 1) / kTile;
+        rs[kRsTileOff + b] = t;
+        mx = max(mx, t);
+    }
+    atomicMax(&smax, mx);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        rs[kRsItems] = smax * nblocks;
+        rs[kRsQueue] = 0;
+        rs[kRsQueue + 1] = 0;
     }
 }
 
@@ -297,107 +423,39 @@ __global__ void __launch_bounds__(kSortThreads) key40_kernel(const int32_t *__re
 template <int MODE>
 __device__ __forceinline__ int digit_shift(int pass) { return (MODE == 0 ? 0 : 20) + 8 * pass; }
 
-// Per-tile digit histogram, stored digit-major: cnt[b][digit][tile]. A warp
-// whose 32 digits agree adds them with one atomic (long equal runs are the
-// norm in these streams).
-// Round state in device memory: rs[0] tied elements after the round, rs[1]
-// their per-block maximum, rs[2] the shift h, rs[3] the round number.
-template <int MODE>
-__global__ void __launch_bounds__(kSortThreads) radix_hist_kernel(int pass, const int32_t *__restrict__ rs, const BlockState *__restrict__ st,
-                                                                  const uint64_t *__restrict__ K_all, uint32_t *__restrict__ cnt_all) {
-    constexpr int NW = kSortThreads / 32;
-    __shared__ uint32_t hst[NW][256];
-    const int b = blockIdx.y, tile = blockIdx.x;
-    const int h = round_h<MODE>(rs);
-    const int n = sort_count<MODE>(st[b], h);
-    if (tile * kTile >= n) return;
-    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    for (int i = threadIdx.x; i < NW * 256; i += kSortThreads) (&hst[0][0])[i] = 0;
-    __syncthreads();
-    const uint64_t *K = K_all + (size_t)b * kBlockCap;
-    const int shift = digit_shift<MODE>(pass);
-    uint32_t dg[kPerThread];
-#pragma unroll
-    for (int r = 0; r < kPerThread; r++) {  // all loads in flight first
-        const int k = tile * kTile + w * 512 + r * 32 + lane;
-        dg[r] = k < n ? (uint32_t)(K[k] >> shift) & 255u : 0xFFFFFFFFu;
-    }
-#pragma unroll
-    for (int r = 0; r < kPerThread; r++) {
-        const uint32_t d = dg[r];
-        const uint32_t d0 = __shfl_sync(LFC_FULL, d, 0);
-        if (__all_sync(LFC_FULL, d == d0)) {
-            if (lane == 0 && d0 != 0xFFFFFFFFu) atomicAdd(&hst[w][d0], 32u);
-        } else if (d != 0xFFFFFFFFu) {
-            atomicAdd(&hst[w][d], 1u);
-        }
-    }
-    __syncthreads();
-    uint32_t c = 0;
-    for (int i = 0; i < NW; i++) c += hst[i][threadIdx.x];
-    cnt_all[((size_t)b * 256 + threadIdx.x) * kTilesPerBlock + tile] = c;
-}
-
-// Exclusive scan of a block's counts in (digit, tile) order, in place.
-template <int MODE>
-__global__ void __launch_bounds__(1024) radix_scan_kernel(const int32_t *__restrict__ rs, const BlockState *__restrict__ st, uint32_t *__restrict__ cnt_all) {
-    __shared__ uint32_t sh[33];
-    const int b = blockIdx.x;
-    const int h = round_h<MODE>(rs);
-    const int n = sort_count<MODE>(st[b], h);
-    if (n == 0) return;
-    const int nt = (n + kTile - 1) / kTile;
-    const int total = 256 * nt;
-    uint32_t *cnt = cnt_all + (size_t)b * 256 * kTilesPerBlock;
-    const int per = (total + blockDim.x - 1) / blockDim.x;
-    const int a = min(total, (int)threadIdx.x * per), e = min(total, a + per);
-    const int d0 = a / nt, t0 = a - d0 * nt;  // (digit, tile) of the first entry
-    // batches of independent loads: a thread's entries cost a few round trips
-    constexpr int kBatch = 16;
-    uint32_t sum = 0;
-    for (int q0 = a, d = d0, t = t0; q0 < e; q0 += kBatch) {
-        uint32_t v[kBatch];
-#pragma unroll
-        for (int j = 0; j < kBatch; j++) {
-            v[j] = q0 + j < e ? cnt[d * kTilesPerBlock + t] : 0u;
-            if (++t == nt) { t = 0; d++; }
-        }
-#pragma unroll
-        for (int j = 0; j < kBatch; j++) sum += v[j];
-    }
-    uint32_t off = block_excl_sum<uint32_t>(sum, sh, nullptr);
-    for (int q0 = a, d = d0, t = t0; q0 < e; q0 += kBatch) {
-        uint32_t v[kBatch];
-        int dj[kBatch], tj[kBatch];
-#pragma unroll
-        for (int j = 0; j < kBatch; j++) {
-            dj[j] = d;
-            tj[j] = t;
-            v[j] = q0 + j < e ? cnt[d * kTilesPerBlock + t] : 0u;
-            if (++t == nt) { t = 0; d++; }
-        }
-#pragma unroll
-        for (int j = 0; j < kBatch; j++) {
-            if (q0 + j < e) cnt[dj[j] * kTilesPerBlock + tj[j]] = off;
-            off += v[j];
-        }
-    }
-}
-
-// Stable scatter of (key, element) pairs: warp w owns elements
-// [w*512, (w+1)*512) of the tile, taken 32 at a time in order; equal digits
-// are ranked with __match_any_sync and a per-warp running count. The tile is
-// placed in shared memory in digit order, then each digit's run is written
-// to its global offset with consecutive threads on consecutive addresses.
+// One stable LSD pass of (key, element) pairs (MODE 0) or round words (MODE
+// 1, the element rides in the word) over every block of the pass.
+// Persistent: CTAs take tiles from the pass's work queue until it is empty
+// (tile-major order, see sort_items_kernel).
+// Per tile: warp w ranks elements [w*512, (w+1)*512) of the tile 32 at a
+// time in order (equal digits by __match_any_sync and a per-warp running
+// count), giving the tile's count c[d] of every digit d; thread d publishes
+// c[d] (flag "aggregate"; tile 0: "inclusive"), adds the published counts of
+// the block's earlier tiles back to the nearest "inclusive" one, publishes
+// its own inclusive count, and the run of digit d starts at (elements of the
+// block with a smaller digit, from the block's digit totals) + (elements of
+// digit d in earlier tiles). Tiles are placed in shared memory in digit
+// order and each digit's run is written with consecutive threads on
+// consecutive addresses.
+// A tile waits only on tiles taken from the queue before it, which are held
+// by running CTAs, so the waits always end; each is still bounded by
+// `budget` clock cycles, after which the CTA raises the abort word and every
+// sort kernel of this suffix sort returns at once (LFC_ERR_TIMEOUT).
+// Status words of the pass live in array par = pass parity; each tile clears
+// its words in the other array for the next pass (which runs on the same or
+// fewer tiles of every block).
 constexpr size_t kScatterSmem = (size_t)kTile * 12 + (size_t)(kSortThreads / 32) * 256 * 4 + 2 * 256 * 4;
 // MODE 1 moves the words alone (Vin / Vout unused)
 constexpr size_t kScatterSmem1 = (size_t)kTile * 8 + (size_t)(kSortThreads / 32) * 256 * 4 + 2 * 256 * 4;
+constexpr int kSweepCtasPerSm = 3;
 
 template <int MODE>
-__global__ void __launch_bounds__(kSortThreads, 3) radix_scatter_kernel(int pass, const int32_t *__restrict__ rs, const BlockState *__restrict__ st,
-                                                                     const uint64_t *__restrict__ Kin_all, const int32_t *__restrict__ Vin_all,
-                                                                     uint64_t *__restrict__ Kout_all, int32_t *__restrict__ Vout_all,
-                                                                     const uint32_t *__restrict__ cnt_all) {
+__global__ void __launch_bounds__(kSortThreads, kSweepCtasPerSm)
+radix_sweep_kernel(int pass, int nblocks, int32_t *__restrict__ rs, const BlockState *__restrict__ st,
+                   const uint64_t *__restrict__ Kin_all, const int32_t *__restrict__ Vin_all,
+                   uint64_t *__restrict__ Kout_all, int32_t *__restrict__ Vout_all,
+                   const uint32_t *__restrict__ dhist_all, uint32_t *__restrict__ lb_all, size_t lb_array_words,
+                   long long budget) {
     constexpr int NW = kSortThreads / 32;
     extern __shared__ __align__(16) uint8_t smem[];
     uint64_t *sK = reinterpret_cast<uint64_t *>(smem);           // [kTile]
@@ -407,71 +465,121 @@ __global__ void __launch_bounds__(kSortThreads, 3) radix_scatter_kernel(int pass
     uint32_t *loff = wcnt + NW * 256;                             // [256] tile-local start of a digit
     uint32_t *gbase = loff + 256;                                 // [256] global start of the tile's run
     __shared__ uint32_t sh[33];
-    const int b = blockIdx.y, tile = blockIdx.x;
+    __shared__ int s_item, s_abort, s_fault;
     const int h = round_h<MODE>(rs);
-    const int n = sort_count<MODE>(st[b], h);
-    if (tile * kTile >= n) return;
-    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int par = MODE == 0 ? (pass & 1) : ((rs[kRsRound] + pass) & 1);
+    uint32_t *lb = lb_all + (size_t)par * lb_array_words;
+    uint32_t *lb_next = lb_all + (size_t)(par ^ 1) * lb_array_words;
+    int32_t *queue = rs + kRsQueue + par;
+    if (blockIdx.x == 0 && threadIdx.x == 0) rs[kRsQueue + (par ^ 1)] = 0;  // the next pass's queue
+    const int total = rs[kRsItems];
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31, d = threadIdx.x;
     const int shift = digit_shift<MODE>(pass);
-    for (int i = threadIdx.x; i < NW * 256; i += kSortThreads) wcnt[i] = 0;
-    gbase[threadIdx.x] = cnt_all[((size_t)b * 256 + threadIdx.x) * kTilesPerBlock + tile];
-    __syncthreads();
-    const size_t bo = (size_t)b * kBlockCap;
-    const uint64_t *Kin = Kin_all + bo;
-    const int32_t *Vin = Vin_all + bo;
-    uint64_t keys[kPerThread];
-    int32_t vals[kPerThread];
-    uint32_t rnk[kPerThread];
     const uint32_t lt = lanemask_lt(), gt = lanemask_gt();
+    for (;;) {
+        if (threadIdx.x == 0) {
+            s_item = atomicAdd(queue, 1);
+            s_abort = ld_volatile_i32(rs + kRsAbort);
+            s_fault = ld_volatile_i32(rs + kRsFault);
+        }
+        for (int i = threadIdx.x; i < NW * 256; i += kSortThreads) wcnt[i] = 0;
+        __syncthreads();
+        const int item = s_item;
+        if (item >= total || s_abort) break;
+        const int tile = item / nblocks, b = item - tile * nblocks;
+        if (tile >= rs[kRsTileOff + b]) {  // past the block's last tile
+            __syncthreads();
+            continue;
+        }
+        const int n = sort_count<MODE>(st[b], h);
+        const size_t bo = (size_t)b * kBlockCap;
+        const uint64_t *Kin = Kin_all + bo;
+        const int32_t *Vin = Vin_all + bo;
+        uint64_t keys[kPerThread];
+        int32_t vals[kPerThread];
+        uint32_t rnk[kPerThread];
 #pragma unroll
-    for (int r = 0; r < kPerThread; r++) {
-        const int k = tile * kTile + w * 512 + r * 32 + lane;
-        const bool ok = k < n;
-        keys[r] = ok ? Kin[k] : 0;
-        vals[r] = (MODE == 0 && ok) ? Vin[k] : 0;
-        const uint32_t d = (uint32_t)(keys[r] >> shift) & 255u;
-        const uint32_t mm = __match_any_sync(LFC_FULL, ok ? d : 256u + lane);
-        uint32_t before = 0;
-        if (ok) before = wcnt[w * 256 + d];
-        __syncwarp();
-        if (ok && (mm & gt) == 0) wcnt[w * 256 + d] = before + __popc(mm);
-        __syncwarp();
-        rnk[r] = ok ? before + __popc(mm & lt) : 0xFFFFFFFFu;
-    }
-    __syncthreads();
-    {   // per digit: exclusive prefix over warps, then over digits
-        const int d = threadIdx.x;
-        uint32_t acc = 0;
+        for (int r = 0; r < kPerThread; r++) {
+            const int k = tile * kTile + w * 512 + r * 32 + lane;
+            const bool ok = k < n;
+            keys[r] = ok ? Kin[k] : 0;
+            vals[r] = (MODE == 0 && ok) ? Vin[k] : 0;
+            const uint32_t dg = (uint32_t)(keys[r] >> shift) & 255u;
+            const uint32_t mm = __match_any_sync(LFC_FULL, ok ? dg : 256u + lane);
+            uint32_t before = 0;
+            if (ok) before = wcnt[w * 256 + dg];
+            __syncwarp();
+            if (ok && (mm & gt) == 0) wcnt[w * 256 + dg] = before + __popc(mm);
+            __syncwarp();
+            rnk[r] = ok ? before + __popc(mm & lt) : 0xFFFFFFFFu;
+        }
+        __syncthreads();
+        // per digit: exclusive prefix over warps, the tile's count, then over digits
+        uint32_t cnt_d = 0;
         for (int ww = 0; ww < NW; ww++) {
             const uint32_t c = wcnt[ww * 256 + d];
-            wcnt[ww * 256 + d] = acc;
-            acc += c;
+            wcnt[ww * 256 + d] = cnt_d;
+            cnt_d += c;
         }
-        loff[d] = block_excl_sum<uint32_t>(acc, sh, nullptr);
-    }
-    __syncthreads();
+        loff[d] = block_excl_sum<uint32_t>(cnt_d, sh, nullptr);
+        // decoupled look-back over the block's earlier tiles
+        uint32_t *lbb = lb + (size_t)b * kLbBlockWords;
+        const bool withhold = s_fault != 0 && b == 0 && tile == 0;  // fault injection: never publish
+        if (!withhold) st_release_u32(lbb + (size_t)tile * 256 + d, (tile == 0 ? kLbIncl : kLbAgg) | cnt_d);
+        uint32_t excl = 0;
+        bool gave_up = false;
+        if (tile > 0) {
+            const long long t0 = clock64();
+            int tp = tile - 1;
+            for (;;) {
+                const uint32_t sv = ld_acquire_u32(lbb + (size_t)tp * 256 + d);
+                if (sv & (kLbAgg | kLbIncl)) {
+                    excl += sv & kLbCount;
+                    if ((sv & kLbIncl) || tp == 0) break;
+                    tp--;
+                    continue;
+                }
+                if (ld_volatile_i32(rs + kRsAbort)) { gave_up = true; break; }
+                if (clock64() - t0 > budget) {
+                    gave_up = true;
+                    atomicCAS(rs + kRsAbort, 0, (int)LFC_ERR_TIMEOUT);
+                    atomicCAS(rs + kRsSticky, 0, (int)LFC_ERR_TIMEOUT);
+                    break;
+                }
+                __nanosleep(64);
+            }
+            if (!gave_up) st_release_u32(lbb + (size_t)tile * 256 + d, kLbIncl | (excl + cnt_d));
+        }
+        lb_next[(size_t)b * kLbBlockWords + (size_t)tile * 256 + d] = 0;
+        const uint32_t below = block_excl_sum<uint32_t>(
+            dhist_all[((size_t)b * kSweepPasses + pass) * 256 + d], sh, nullptr);  // block elements with a smaller digit
+        gbase[d] = below + excl;
+        if (withhold && d == 0) atomicExch(rs + kRsFault, 0);  // the fault fires once
+        if (__syncthreads_or(gave_up)) break;
 #pragma unroll
-    for (int r = 0; r < kPerThread; r++) {
-        if (rnk[r] == 0xFFFFFFFFu) continue;
-        const uint32_t d = (uint32_t)(keys[r] >> shift) & 255u;
-        const uint32_t pos = loff[d] + wcnt[w * 256 + d] + rnk[r];
-        sK[pos] = keys[r];
-        if (MODE == 0) sV[pos] = vals[r];
-    }
-    __syncthreads();
-    const int cnt = min(kTile, n - tile * kTile);
-    uint64_t *Kout = Kout_all + bo;
-    int32_t *Vout = Vout_all + bo;
-#pragma unroll 4
-    for (int r = 0; r < kPerThread; r++) {
-        const int j = r * kSortThreads + threadIdx.x;
-        if (j < cnt) {
-            const uint64_t key = sK[j];
-            const uint32_t d = (uint32_t)(key >> shift) & 255u;
-            const uint32_t g = gbase[d] + ((uint32_t)j - loff[d]);
-            Kout[g] = key;
-            if (MODE == 0) Vout[g] = sV[j];
+        for (int r = 0; r < kPerThread; r++) {
+            if (rnk[r] == 0xFFFFFFFFu) continue;
+            const uint32_t dg = (uint32_t)(keys[r] >> shift) & 255u;
+            const uint32_t pos = loff[dg] + wcnt[w * 256 + dg] + rnk[r];
+            sK[pos] = keys[r];
+            if (MODE == 0) sV[pos] = vals[r];
         }
+        __syncthreads();
+        const int cnt = min(kTile, n - tile * kTile);
+        uint64_t *Kout = Kout_all + bo;
+        int32_t *Vout = Vout_all + bo;
+#pragma unroll 4
+        for (int r = 0; r < kPerThread; r++) {
+            const int j = r * kSortThreads + threadIdx.x;
+            if (j < cnt) {
+                const uint64_t key = sK[j];
+                const uint32_t dg = (uint32_t)(key >> shift) & 255u;
+                const uint32_t g = gbase[dg] + ((uint32_t)j - loff[dg]);
+                Kout[g] = key;
+                if (MODE == 0) Vout[g] = sV[j];
+            }
+        }
+        __syncthreads();
     }
 }
 
@@ -485,6 +593,7 @@ __global__ void __launch_bounds__(kSortThreads) heads_tile_kernel(const int32_t 
                                                                   const uint64_t *__restrict__ keys_all, const int32_t *__restrict__ actA,
                                                                   const int32_t *__restrict__ actB,
                                                                   uint8_t *__restrict__ flags_all, int32_t *__restrict__ aux_all) {
+    if (rs[kRsAbort]) return;
     const int b = blockIdx.y, tile = blockIdx.x;
     const int h = round_h<MODE>(rs);
     const BlockState s = st[b];
@@ -559,6 +668,7 @@ template <int MODE>
 __global__ void __launch_bounds__(256) heads_scan_kernel(int32_t *__restrict__ rs, BlockState *__restrict__ st, int32_t *__restrict__ aux_all) {
     __shared__ int32_t shm[33];
     __shared__ int32_t shs[33];
+    if (rs[kRsAbort]) return;
     const int b = blockIdx.x;
     const int h = round_h<MODE>(rs);
     int32_t *counters = rs;
@@ -592,6 +702,7 @@ __global__ void __launch_bounds__(kSortThreads) heads_apply_kernel(const int32_t
                                                                    int32_t *__restrict__ val_out_all) {
     __shared__ int32_t shm[33];
     __shared__ int32_t shs[33];
+    if (rs[kRsAbort]) return;
     const int b = blockIdx.y, tile = blockIdx.x;
     const int h = round_h<MODE>(rs);
     // round r reads list A (r even) or B (r odd) and writes the other; the
@@ -711,11 +822,12 @@ __global__ void round_start_kernel(int32_t *rs, int first) {
 }
 
 // End of a doubling round: double h; inside a graph, continue the WHILE node
-// while tied elements remain and h is below the largest block length.
+// while tied elements remain, h is below the largest block length and no
+// wait has given up.
 __global__ void round_end_kernel(int32_t *rs, int max_m, cudaGraphConditionalHandle cond, int set_cond) {
     rs[2] *= 2;
     rs[3] += 1;
-    if (set_cond) cudaGraphSetConditional(cond, (rs[0] > 0 && rs[2] < max_m) ? 1u : 0u);
+    if (set_cond) cudaGraphSetConditional(cond, (rs[kRsAbort] == 0 && rs[0] > 0 && rs[2] < max_m) ? 1u : 0u);
 }
 
 // L[j] = block[(SA[j] - 1) mod m]; origPtr = j with SA[j] = 0; bytes in use.
@@ -724,9 +836,13 @@ __global__ void round_end_kernel(int32_t *rs, int max_m, cudaGraphConditionalHan
 // consecutive positions; the last position of each byte value comes from one
 // shared-memory max per distinct value of a thread's run; each value is then
 // marked at its last position and the marks are compacted from the top.
+// After an aborted sort the suffix array is incomplete: the kernel then
+// takes the identity order instead, so that every later stage still reads
+// in-range values (the call reports LFC_ERR_TIMEOUT and its output is void).
 __global__ void __launch_bounds__(kSortThreads) bwt_output_kernel(BlockState *__restrict__ st, const int32_t *__restrict__ sa_all,
                                                                   const uint8_t *__restrict__ rle_all, uint8_t *__restrict__ L_all,
-                                                                  uint8_t *__restrict__ rec_all, int32_t *__restrict__ reclen_all) {
+                                                                  uint8_t *__restrict__ rec_all, int32_t *__restrict__ reclen_all,
+                                                                  const int32_t *__restrict__ rs) {
     __shared__ int32_t lastpos[256];
     __shared__ uint16_t mark[kTile];  // value + 1 at its last position, 0 elsewhere
     __shared__ int sh[33];
@@ -741,7 +857,10 @@ __global__ void __launch_bounds__(kSortThreads) bwt_output_kernel(BlockState *__
     const int j0 = tile * kTile + jl;
     uint8_t c[kPerThread];
     int32_t sv[kPerThread];
-    if (j0 + kPerThread <= m) {  // full run: the suffix array by 16-byte loads
+    if (rs[kRsAbort]) {
+#pragma unroll
+        for (int q = 0; q < kPerThread; q++) sv[q] = j0 + q < m ? j0 + q : -1;
+    } else if (j0 + kPerThread <= m) {  // full run: the suffix array by 16-byte loads
 #pragma unroll
         for (int q = 0; q < kPerThread; q += 4) {
             const int4 s4 = *reinterpret_cast<const int4 *>(sa_all + bo + j0 + q);
@@ -803,16 +922,41 @@ __global__ void __launch_bounds__(kSortThreads) bwt_output_kernel(BlockState *__
     if (threadIdx.x == 0) reclen_all[(size_t)b * kTilesPerBlock + tile] = total;
 }
 
+// Copies every block's last column out (lfc_bwt_blocks): stride bytes per
+// block, its length (the RLE1 length) and its origin row.
+__global__ void copy_bwt_kernel(const BlockState *__restrict__ st, const uint8_t *__restrict__ L_all, uint8_t *__restrict__ out,
+                                size_t stride, uint32_t *__restrict__ len, uint32_t *__restrict__ orig) {
+    const int b = blockIdx.y;
+    const int m = st[b].m;
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        len[b] = (uint32_t)m;
+        orig[b] = (uint32_t)st[b].orig_ptr;
+    }
+    const uint8_t *src = L_all + (size_t)b * kBlockCap;
+    uint8_t *dst = out + (size_t)b * stride;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < m; i += gridDim.x * blockDim.x) dst[i] = src[i];
+}
+
+cudaError_t launch_copy_bwt(lfc_plan P, int nblocks, uint8_t *d_L, size_t stride, uint32_t *d_len, uint32_t *d_orig) {
+    copy_bwt_kernel<<<dim3(64, nblocks), 256, 0, P->stream>>>(P->ws.bstate, P->ws.bwt, d_L, stride, d_len, d_orig);
+    count_launches(P, 1);
+    return cudaGetLastError();
+}
+
 template <int MODE>
-static void radix_pass(lfc_plan P, cudaStream_t st, int nblocks, int tiles, int pass, const uint64_t *kin, const int32_t *vin,
+static void sweep_pass(lfc_plan P, cudaStream_t st, int nblocks, int ctas, int pass, const uint64_t *kin, const int32_t *vin,
                        uint64_t *kout, int32_t *vout) {
     Workspace &ws = P->ws;
-    dim3 grid(tiles, nblocks);
-    radix_hist_kernel<MODE><<<grid, kSortThreads, 0, st>>>(pass, ws.act_total, ws.bstate, kin, ws.tilecnt);
-    radix_scan_kernel<MODE><<<nblocks, 1024, 0, st>>>(ws.act_total, ws.bstate, ws.tilecnt);
-    radix_scatter_kernel<MODE><<<grid, kSortThreads, MODE == 0 ? kScatterSmem : kScatterSmem1, st>>>(
-        pass, ws.act_total, ws.bstate, kin, vin, kout, vout, ws.tilecnt);
-    count_launches(P, 3);
+    radix_sweep_kernel<MODE><<<ctas, kSortThreads, MODE == 0 ? kScatterSmem : kScatterSmem1, st>>>(
+        pass, nblocks, ws.act_total, ws.bstate, kin, vin, kout, vout, ws.dhist, ws.lbstat, ws.lbstat_words,
+        P->wait_cycles);
+    count_launches(P, 1);
+}
+
+static int sweep_ctas(lfc_plan P, int nblocks, int tiles) {
+    const long long items = (long long)nblocks * tiles;
+    const long long cap = (long long)P->sm_count * kSweepCtasPerSm;
+    return (int)std::max<long long>(1, std::min(items, cap));
 }
 
 // One prefix-doubling round over the tied elements (h and the parity of the
@@ -821,12 +965,17 @@ static void bwt_round(lfc_plan P, cudaStream_t st, int nblocks, int tiles, int m
                       int set_cond) {
     Workspace &ws = P->ws;
     round_start_kernel<<<1, 1, 0, st>>>(ws.act_total, 0);
+    const size_t nd = (size_t)nblocks * kSweepPasses * 256;
+    zero_u32_kernel<<<(unsigned)std::min<size_t>(64, (nd + 255) / 256), 256, 0, st>>>(ws.dhist, nd);
     dim3 g1(tiles, nblocks);
-    key40_kernel<<<g1, kSortThreads, 0, st>>>(ws.act_total, ws.bstate, ws.val, ws.rank, ws.keys);
+    key40_kernel<<<g1, kSortThreads, 0, st>>>(ws.act_total, ws.bstate, ws.val, ws.rank, ws.keys, ws.dhist);
+    sort_items_kernel<1><<<1, 1024, 0, st>>>(ws.act_total, ws.bstate, nblocks);
+    count_launches(P, 4);
     // 5 LSD passes over bits 20..59 of the words: keys -> keys2 -> ... -> keys2
+    const int ctas = sweep_ctas(P, nblocks, tiles);
     for (int pass = 0; pass < 5; pass++) {
-        if (pass & 1) radix_pass<1>(P, st, nblocks, tiles, pass, ws.keys2, nullptr, ws.keys, nullptr);
-        else radix_pass<1>(P, st, nblocks, tiles, pass, ws.keys, nullptr, ws.keys2, nullptr);
+        if (pass & 1) sweep_pass<1>(P, st, nblocks, ctas, pass, ws.keys2, nullptr, ws.keys, nullptr);
+        else sweep_pass<1>(P, st, nblocks, ctas, pass, ws.keys, nullptr, ws.keys2, nullptr);
     }
     heads_tile_kernel<1><<<g1, kSortThreads, 0, st>>>(ws.act_total, ws.bstate, ws.keys2, ws.act, ws.act2, ws.bwt,
                                                       ws.tileaux);
@@ -835,7 +984,7 @@ static void bwt_round(lfc_plan P, cudaStream_t st, int nblocks, int tiles, int m
                                                        ws.bwt, ws.tileaux, ws.rank, ws.sa, ws.val);
     commit_round_kernel<<<(nblocks + 255) / 256, 256, 0, st>>>(ws.bstate, nblocks);
     round_end_kernel<<<1, 1, 0, st>>>(ws.act_total, max_m, cond, set_cond);
-    count_launches(P, 7);
+    count_launches(P, 5);
 }
 
 cudaError_t launch_bwt(lfc_plan P, int nblocks, int max_m) {
@@ -848,19 +997,29 @@ cudaError_t launch_bwt(lfc_plan P, int nblocks, int max_m) {
     e = cudaStreamIsCapturing(s, &cap);
     if (e != cudaSuccess) return e;
     const bool graph = cap == cudaStreamCaptureStatusActive;
-    e = cudaFuncSetAttribute(radix_scatter_kernel<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kScatterSmem);
+    e = cudaFuncSetAttribute(radix_sweep_kernel<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kScatterSmem);
     if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(radix_scatter_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kScatterSmem1);
+        e = cudaFuncSetAttribute(radix_sweep_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kScatterSmem1);
     if (e != cudaSuccess) return e;
-    // phase 1: prefix keys, then 8 LSD passes (keys, sa) -> (keys2, sa2) -> ... -> (keys, sa)
+    // a new suffix sort: no wait has given up yet (outside graphs the sticky
+    // status is reported by this call, so it starts clear as well)
+    e = cudaMemsetAsync(ws.act_total + kRsAbort, 0, sizeof(int32_t), s);
+    if (e == cudaSuccess && !graph) e = cudaMemsetAsync(ws.act_total + kRsSticky, 0, sizeof(int32_t), s);
+    if (e != cudaSuccess) return e;
+    // phase 1: prefix keys and the digit totals of all passes, then 8 LSD
+    // passes (keys, sa) -> (keys2, sa2) -> ... -> (keys, sa)
     stage_begin(P, LFC_STAGE_BWT_SORT8);
     dim3 grid(tiles, nblocks);
-    key8_kernel<<<grid, kSortThreads, 0, s>>>(ws.bstate, ws.rle, ws.keys, ws.sa);
-    count_launches(P, 1);
+    const size_t nd = (size_t)nblocks * kSweepPasses * 256;
+    zero_u32_kernel<<<(unsigned)std::min<size_t>(64, (nd + 255) / 256), 256, 0, s>>>(ws.dhist, nd);
+    key8_kernel<<<grid, kSortThreads, 0, s>>>(ws.bstate, ws.rle, ws.keys, ws.sa, ws.dhist, ws.lbstat, ws.lbstat_words);
+    sort_items_kernel<0><<<1, 1024, 0, s>>>(ws.act_total, ws.bstate, nblocks);
+    count_launches(P, 3);
     uint64_t *kin = ws.keys, *kout = ws.keys2;
     int32_t *vin = ws.sa, *vout = ws.sa2;
+    const int ctas = sweep_ctas(P, nblocks, tiles);
     for (int pass = 8 - kPhase1Bytes; pass < 8; pass++) {
-        radix_pass<0>(P, s, nblocks, tiles, pass, kin, vin, kout, vout);
+        sweep_pass<0>(P, s, nblocks, ctas, pass, kin, vin, kout, vout);
         std::swap(kin, kout);
         std::swap(vin, vout);
     }
@@ -904,26 +1063,28 @@ cudaError_t launch_bwt(lfc_plan P, int nblocks, int max_m) {
         e = cudaStreamUpdateCaptureDependencies(s, &node, nullptr, 1, cudaStreamSetCaptureDependencies);
         if (e != cudaSuccess) return e;
     } else {
-        e = cudaMemcpyAsync(ws.h_act_total, ws.act_total, 4 * sizeof(int32_t), cudaMemcpyDeviceToHost, s);
+        e = cudaMemcpyAsync(ws.h_act_total, ws.act_total, kSortCtlHead * sizeof(int32_t), cudaMemcpyDeviceToHost, s);
         if (e != cudaSuccess) return e;
         e = cudaStreamSynchronize(s);
         if (e != cudaSuccess) return e;
         int round = 0;
-        for (int h = kPhase1Bytes; ws.h_act_total[0] > 0 && h < max_m; h *= 2, round++) {
+        for (int h = kPhase1Bytes; ws.h_act_total[kRsAbort] == 0 && ws.h_act_total[0] > 0 && h < max_m; h *= 2, round++) {
             P->bwt_rounds++;
             P->bwt_tied_total += ws.h_act_total[0];
             if (round < 32) P->bwt_round_tied[round] += ws.h_act_total[0];
             const int t1 = (ws.h_act_total[1] + kTile - 1) / kTile;
             bwt_round(P, s, nblocks, t1, max_m, cudaGraphConditionalHandle{}, 0);
-            e = cudaMemcpyAsync(ws.h_act_total, ws.act_total, 4 * sizeof(int32_t), cudaMemcpyDeviceToHost, s);
+            e = cudaMemcpyAsync(ws.h_act_total, ws.act_total, kSortCtlHead * sizeof(int32_t), cudaMemcpyDeviceToHost, s);
             if (e != cudaSuccess) return e;
             e = cudaStreamSynchronize(s);
             if (e != cudaSuccess) return e;
         }
+        if (ws.h_act_total[kRsAbort] != 0) P->bwt_timed_out = true;
     }
     stage_end(P, LFC_STAGE_BWT_REFINE);
     stage_begin(P, LFC_STAGE_BWT_OUT);
-    bwt_output_kernel<<<grid, kSortThreads, 0, s>>>(ws.bstate, ws.sa, ws.rle, ws.bwt, ws.mtfrec, ws.mtfreclen);
+    bwt_output_kernel<<<grid, kSortThreads, 0, s>>>(ws.bstate, ws.sa, ws.rle, ws.bwt, ws.mtfrec, ws.mtfreclen,
+                                                     ws.act_total);
     stage_end(P, LFC_STAGE_BWT_OUT);
     count_launches(P, 1);
     return cudaGetLastError();

@@ -286,18 +286,23 @@ __global__ void __launch_bounds__(kEmitThreads) emit_all_kernel(const JudgeFrame
 // A warp takes a contiguous range of a candidate stream and gives each lane
 // one 32nd of it. A lane walks its sub-range byte by byte with a private
 // table over the 256 byte values: entry (b, lane) is 16 bits, the
-// predecessor of the last occurrence of b so far (0xFFFF before the first),
-// kept in the word (b / 2) * 32 + lane, half b % 2, so each lane stays in its
-// own bank whatever the bytes. The predecessor of a lane's first occurrence
-// of b (written once per value, read once when stitching) goes to a global
-// scratch of the CTA's SM: the table's shared memory admits one CTA per SM.
-// 32 bytes at a time, all table entries are read and rewritten first (a
-// load only waits on the lane's own earlier stores), then the pairs are
-// counted from the entries read. Afterwards the lanes' tables are stitched in
-// lane order into the warp's, the warps' in order into the CTA's, the CTAs'
-// by the fixup kernel. Pairs (x, y) with x, y < kHot are counted in shared
-// memory, (0, 0) in a register, all others with fire-and-forget atomics into
-// the L2-resident histogram.
+// predecessor p of the last occurrence of b so far, kept as p * 128 so that
+// a pair's hot-corner index is one addition (0xFFFF before the first
+// occurrence), in the word (b / 2) * 32 + lane, half b % 2, so each lane
+// stays in its own bank whatever the bytes. The predecessor of a lane's
+// first occurrence of b (written once per value, read once when stitching)
+// goes to a global scratch of the CTA's SM: the table's shared memory admits
+// one CTA per SM. 32 bytes at a time, all table entries are read and
+// rewritten first (a load only waits on the lane's own earlier stores), then
+// the pairs are counted from the entries read. Afterwards the lanes' tables
+// are stitched in lane order into the warp's, the warps' in order into the
+// CTA's, the CTAs' by the fixup kernel. Pairs (x, y) with x, y < kHot are
+// counted in shared memory: (0, 0) in the lane's own slot (no two lanes of a
+// warp share its bank), added to bin (0, 0) at the end, the others in the
+// hot corner; all other pairs go with fire-and-forget atomics to the
+// L2-resident histogram. Every byte issues exactly one shared atomic (+0 to
+// the lane's slot when its pair is counted elsewhere or it has none), so the
+// walk has no branch on the data.
 constexpr int kChainWarps = 10;
 constexpr int kChainThreads = kChainWarps * 32;
 constexpr int kHot = 128;              // hot corner side
@@ -306,6 +311,7 @@ constexpr int kChainFirst = 256 * 32;  // first-predecessor bytes of a warp, [b]
 constexpr uint32_t kNoPred = 0xFFFF;
 
 size_t chain_smem_bytes() { return (size_t)(kHot * kHot + 32) * 4 + (size_t)kChainWarps * kChainTab * 4; }
+constexpr uint32_t kHotBins = kHot * kHot;  // (p * 128 + a) for p, a < 128; then one slot per lane
 int64_t chain_seg_bytes(int range_bytes) { return (int64_t)kChainWarps * range_bytes; }
 size_t chain_first_bytes(int nsm) { return (size_t)nsm * kChainWarps * kChainFirst; }
 
@@ -338,16 +344,16 @@ __device__ __forceinline__ int find_frame_s(const JudgeFrame *fr, int n, int64_t
     return lo;
 }
 
-// Count the pair (p, a): p the predecessor of the previous occurrence
-// (kNoPred: none, nothing counted), a that of this one.
-__device__ __forceinline__ void chain_count(uint32_t p, uint32_t a, uint32_t *hot, uint32_t *ghist, uint32_t &c0, int lane) {
-    const bool pair = p != kNoPred;
-    const uint32_t both = p | a;
-    c0 += (pair && both == 0) ? 1u : 0u;
-    const bool hotp = pair && both != 0 && both < (uint32_t)kHot;
-    // branch-free: lanes without a hot pair add 0 to their own dummy slot
-    atomicAdd(&hot[hotp ? p * kHot + a : kHot * kHot + lane], hotp ? 1u : 0u);
-    if (pair && both >= (uint32_t)kHot) atomicAdd(&ghist[(p << 8) | a], 1u);
+// Count the pair (p, a) of a chain: e the table entry of the previous
+// occurrence (p * 128, kNoPred: none, nothing counted), a the predecessor of
+// this one. (0, 0) adds 1 to the lane's own slot, another pair of bytes
+// below kHot adds 1 to its hot-corner bin, every other lane adds 0 to its
+// slot; pairs outside the corner go to the global histogram.
+__device__ __forceinline__ void chain_count(uint32_t e, uint32_t a, uint32_t *hot, uint32_t *ghist, uint32_t slot) {
+    const uint32_t t = e + a;                              // p * 128 + a
+    const bool in_hot = (e | (a << 7)) < kHotBins;         // p < 128 and a < 128 (never for kNoPred)
+    atomicAdd(&hot[(in_hot && t != 0u) ? t : slot], in_hot ? 1u : 0u);
+    if (e != kNoPred && !in_hot) atomicAdd(&ghist[(e << 1) | a], 1u);  // (p << 8) | a
 }
 
 __device__ __forceinline__ uint32_t byte_of(const uint32_t (&w)[8], int i) {
@@ -362,7 +368,7 @@ __device__ __forceinline__ uint16_t *chain_entry(uint32_t *tl, uint32_t b) {
 // 32 stream bytes (w little-endian) after the byte prev; fl = the lane's
 // first-predecessor column (byte b * 32).
 __device__ __forceinline__ void chain_walk32(const uint32_t (&w)[8], uint32_t &prev, uint32_t *tl, uint8_t *fl,
-                                             uint32_t *hot, uint32_t *ghist, uint32_t &c0, int lane) {
+                                             uint32_t *hot, uint32_t *ghist, uint32_t slot) {
     uint32_t e[32];
 #pragma unroll
     for (int i = 0; i < 32; i++) {
@@ -370,14 +376,14 @@ __device__ __forceinline__ void chain_walk32(const uint32_t (&w)[8], uint32_t &p
         const uint32_t a = i == 0 ? prev : byte_of(w, i - 1);
         uint16_t *en = chain_entry(tl, b);
         e[i] = *en;
-        *en = (uint16_t)a;
+        *en = (uint16_t)(a << 7);
     }
 #pragma unroll
     for (int i = 0; i < 32; i++) {
         const uint32_t b = byte_of(w, i);
         const uint32_t a = i == 0 ? prev : byte_of(w, i - 1);
         if (e[i] == kNoPred) fl[b * 32] = (uint8_t)a;
-        chain_count(e[i], a, hot, ghist, c0, lane);
+        chain_count(e[i], a, hot, ghist, slot);
     }
     prev = byte_of(w, 31);
 }
@@ -402,7 +408,7 @@ chain_hist_kernel(const JudgeFrame *__restrict__ frames, int nframes, const uint
     asm volatile("mov.u32 %0, %%smid;" : "=r"(smid));
     uint8_t *fl = first_all + ((size_t)(smid % (uint32_t)nsm) * kChainWarps + warp) * kChainFirst + lane;
     uint32_t *tab = tab_all + warp * kChainTab;
-    for (int i = threadIdx.x; i < kHot * kHot / 4; i += kChainThreads) reinterpret_cast<uint4 *>(hot)[i] = make_uint4(0, 0, 0, 0);
+    for (int i = threadIdx.x; i < (kHotBins + 32) / 4; i += kChainThreads) reinterpret_cast<uint4 *>(hot)[i] = make_uint4(0, 0, 0, 0);
     for (int i = lane; i < kChainTab / 4; i += 32) reinterpret_cast<uint4 *>(tab)[i] = make_uint4(~0u, ~0u, ~0u, ~0u);
     __syncthreads();
     // the lane's sub-range [lo, hi) of the warp's range
@@ -410,7 +416,7 @@ chain_hist_kernel(const JudgeFrame *__restrict__ frames, int nframes, const uint
     const int64_t ra = ((int64_t)seg * kChainWarps + warp) * range_bytes;
     const int64_t lo = min(n, ra + (int64_t)lane * sub), hi = min(n, lo + sub);
     const int len = (int)(hi - lo);
-    uint32_t c0 = 0;
+    const uint32_t slot = kHotBins + (uint32_t)lane;
     uint32_t *tl = tab + lane;
     if (len > 0) {
         uint32_t prev = S[lo == 0 ? n - 1 : lo - 1];  // cyclic predecessor
@@ -426,27 +432,28 @@ chain_hist_kernel(const JudgeFrame *__restrict__ frames, int nframes, const uint
                 nx[j] = k + 1 < full ? __ldg(reinterpret_cast<const uint4 *>(L + (size_t)(k + 1) * 64) + j)
                                      : make_uint4(0, 0, 0, 0);
             const uint32_t w0[8] = {c[0].x, c[0].y, c[0].z, c[0].w, c[1].x, c[1].y, c[1].z, c[1].w};
-            chain_walk32(w0, prev, tl, fl, hot, ghist, c0, lane);
+            chain_walk32(w0, prev, tl, fl, hot, ghist, slot);
             const uint32_t w1[8] = {c[2].x, c[2].y, c[2].z, c[2].w, c[3].x, c[3].y, c[3].z, c[3].w};
-            chain_walk32(w1, prev, tl, fl, hot, ghist, c0, lane);
+            chain_walk32(w1, prev, tl, fl, hot, ghist, slot);
 #pragma unroll
             for (int j = 0; j < 4; j++) c[j] = nx[j];
         }
         for (int k = full << 6; k < len; k++) {  // ragged end of the stream
             const uint32_t b = L[k], a = prev;
             uint16_t *en = chain_entry(tl, b);
-            const uint32_t p = *en;
-            *en = (uint16_t)a;
-            if (p == kNoPred) fl[b * 32] = (uint8_t)a;
-            chain_count(p, a, hot, ghist, c0, lane);
+            const uint32_t e = *en;
+            *en = (uint16_t)(a << 7);
+            if (e == kNoPred) fl[b * 32] = (uint8_t)a;
+            chain_count(e, a, hot, ghist, slot);
             prev = b;
         }
     }
     __syncwarp();
     // stitch the lanes in order: a lane's first occurrence of b follows the
     // last occurrence in the nearest lower lane holding b. The warp's result
-    // for b, (first << 16) | last (last 0xFFFF: none), then goes to word
-    // (b / 2) * 32 + b % 2 of its table, whose entries are all read by then.
+    // for b, (first << 16) | last (last as a table entry: p * 128, 0xFFFF:
+    // none), then goes to word (b / 2) * 32 + b % 2 of its table, whose
+    // entries are all read by then.
     // The first predecessors come from global memory 32 values ahead.
     const uint32_t lt = lanemask_lt();
     uint32_t keep = 0;
@@ -467,7 +474,7 @@ chain_hist_kernel(const JudgeFrame *__restrict__ frames, int nframes, const uint
             const uint32_t f = fv[j];  // meaningful where valid
             const uint32_t lower = m & lt;
             const uint32_t pl = __shfl_sync(LFC_FULL, last, lower ? 31 - __clz(lower) : lane);
-            chain_count(valid && lower ? pl : kNoPred, f, hot, ghist, c0, lane);
+            chain_count(valid && lower ? pl : kNoPred, f, hot, ghist, slot);
             const uint32_t f0 = __shfl_sync(LFC_FULL, f, m ? __ffs(m) - 1 : 0);
             const uint32_t lz = __shfl_sync(LFC_FULL, last, m ? 31 - __clz(m) : 0);
             const uint32_t res = (f0 << 16) | lz;
@@ -484,7 +491,11 @@ chain_hist_kernel(const JudgeFrame *__restrict__ frames, int nframes, const uint
 #pragma unroll
         for (int j = 0; j < 32; j++) fv[j] = fn[j];
     }
-    if (c0) atomicAdd(&hot[0], c0);
+    __syncthreads();
+    if (warp == 0) {  // the lanes' (0, 0) counts into bin (0, 0)
+        const uint32_t z = warp_sum(hot[kHotBins + lane]);
+        if (lane == 0 && z) hot[0] += z;
+    }
     __syncthreads();
     constexpr int kFlush = 8;
     for (int i0 = threadIdx.x; i0 < kHot * kHot; i0 += kFlush * kChainThreads) {
@@ -505,16 +516,16 @@ chain_hist_kernel(const JudgeFrame *__restrict__ frames, int nframes, const uint
         uint32_t f0 = kNoPred, cur = kNoPred;
         for (int w = 0; w < kChainWarps; w++) {
             const uint32_t e = tab_all[w * kChainTab + (bv >> 1) * 32 + (bv & 1)];
-            const uint32_t last = e & 0xFFFFu;
+            const uint32_t last = e & 0xFFFFu;  // p * 128
             if (last == kNoPred) continue;
             const uint32_t f = (e >> 16) & 255u;
-            if (cur != kNoPred) atomicAdd(&ghist[(cur << 8) | f], 1u);
+            if (cur != kNoPred) atomicAdd(&ghist[(cur << 1) | f], 1u);  // (p << 8) | f
             else f0 = f;
             cur = last;
         }
         uint16_t *out = summ + (size_t)(J.summ_off + (int64_t)ci * J.segs + seg) * 512;
         out[bv] = (uint16_t)f0;
-        out[256 + bv] = (uint16_t)cur;
+        out[256 + bv] = (uint16_t)(cur == kNoPred ? kNoPred : cur >> 7);
     }
 }
 

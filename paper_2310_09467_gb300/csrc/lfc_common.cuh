@@ -25,6 +25,9 @@ constexpr int kMaxGroups = 6;
 constexpr int kMaxSelectors = 18002;
 constexpr int kHistBins = 65536;
 constexpr int kMaxCand = 52;                         // 26 spatial + 26 temporal by default
+constexpr int kSortCtlHead = 16;                     // sort state words before the per-block tile offsets
+constexpr int kSortFaultWord = 5;                    // sort state word of the fault-injection test hook
+constexpr int kSortStickyWord = 9;                   // sort state word kept until lfc_plan_device_status reads it
 
 #define LFC_FULL 0xffffffffu
 
@@ -185,7 +188,9 @@ struct Workspace {
     int32_t *val2 = nullptr;
     uint64_t *keys = nullptr;      // sort keys riding with sa / val, block_cap * kBlockCap
     uint64_t *keys2 = nullptr;
-    uint32_t *tilecnt = nullptr;   // block_cap * 256 * kTilesPerBlock
+    uint32_t *lbstat = nullptr;    // radix look-back status, 2 arrays of block_cap * kTilesPerBlock * 256
+    size_t lbstat_words = 0;       // words of one of those arrays
+    uint32_t *dhist = nullptr;     // per block and radix pass: digit totals, block_cap * 8 * 256
     int32_t *tileaux = nullptr;    // block_cap * kTilesPerBlock * 4
     uint8_t *bwt = nullptr;        // L column
     uint8_t *mtfidx = nullptr;
@@ -200,8 +205,8 @@ struct Workspace {
     uint32_t *codes = nullptr;     // block_cap * 6 * 258
     uint32_t *packed = nullptr;    // block_cap * stream_words
     int64_t stream_words = 0;
-    int32_t *act_total = nullptr;  // device counter (1)
-    int32_t *h_act_total = nullptr;// pinned host mirror
+    int32_t *act_total = nullptr;  // sort state: kSortCtlHead words + block_cap + 1 tile offsets
+    int32_t *h_act_total = nullptr;// pinned host mirror of the first kSortCtlHead words
     // container assembly
     uint64_t *block_dst = nullptr;     // block_cap: stream destination offsets
     uint32_t *frame_crc = nullptr;     // max_frames
@@ -245,6 +250,9 @@ struct lfc_plan_s {
     double stage_ms[LFC_NUM_STAGES] = {};
     int64_t bwt_calls = 0, bwt_rounds = 0, bwt_tied_total = 0, bwt_elements = 0, bwt_elements_in = 0;
     int64_t bwt_round_tied[32] = {};
+    long long wait_cycles = 0;          // bounded device waits: budget in SM clock cycles
+    int sm_clock_khz = 0;
+    bool bwt_timed_out = false;         // a wait of the last suffix sort gave up
     int64_t stage_spans[LFC_NUM_STAGES] = {};
 };
 
@@ -304,6 +312,7 @@ cudaError_t launch_range_crc(lfc_plan P, const uint8_t *const *h_ptr, const int6
 // bwt.cu
 cudaError_t launch_rle1(lfc_plan P, int nblocks, const BlockDesc *d_blocks);
 cudaError_t launch_bwt(lfc_plan P, int nblocks, int max_m);
+cudaError_t launch_copy_bwt(lfc_plan P, int nblocks, uint8_t *d_L, size_t stride, uint32_t *d_len, uint32_t *d_orig);
 
 // mtf_huff.cu
 cudaError_t launch_mtf_rle2(lfc_plan P, int nblocks);

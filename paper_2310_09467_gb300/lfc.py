@@ -31,7 +31,8 @@ EXPORTS = ["lfc_plan_create", "lfc_plan_destroy", "lfc_plan_last_error", "lfc_ju
            "lfc_plan_set_tuning", "lfc_plan_get_tuning",
            "lfc_cnn_create", "lfc_cnn_destroy", "lfc_cnn_last_error", "lfc_cnn_param_count", "lfc_cnn_set_params",
            "lfc_cnn_get_params", "lfc_cnn_thumbnails", "lfc_cnn_set_thumbnails", "lfc_cnn_forward", "lfc_cnn_backward",
-           "lfc_cnn_adam_step", "lfc_plan_set_proposal", "lfc_propose"]
+           "lfc_cnn_adam_step", "lfc_plan_set_proposal", "lfc_propose", "lfc_plan_device_status",
+           "lfc_plan_inject_fault", "lfc_bwt_blocks"]
 
 STAGES = ["judge_hist", "judge_score", "emit", "crc", "rle1", "bwt_sort8", "bwt_refine", "bwt_out", "mtf",
           "huffman", "pack", "container", "judge_emit"]
@@ -52,7 +53,7 @@ class Config(ctypes.Structure):
 
 class Tuning(ctypes.Structure):
     _fields_ = [("emit_tile_lenslets", ctypes.c_int32), ("chain_range_bytes", ctypes.c_int32),
-                ("judge_frames_per_launch", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("judge_frames_per_launch", ctypes.c_int32), ("wait_budget_ms", ctypes.c_int32)]
 
 
 class Frame(ctypes.Structure):
@@ -109,6 +110,9 @@ def load():
         "lfc_propose": (i32, [P, ctypes.POINTER(Frame), i32, P]),
         "lfc_batch_destroy": (None, [P]),
         "lfc_judge_noalloc": (i32, [ctypes.POINTER(Frame), ctypes.POINTER(ctypes.c_uint8), i32, P, P, P]),
+        "lfc_plan_device_status": (i32, [P]),
+        "lfc_plan_inject_fault": (i32, [P, i32]),
+        "lfc_bwt_blocks": (i32, [P, P, ctypes.POINTER(u64), ctypes.POINTER(ctypes.c_uint32), i32, P, sz, P, P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -124,6 +128,15 @@ def max_compressed_bytes(width: int, height: int, block_bytes: int = 0) -> int:
 
 def max_stream_bytes(block_bytes: int) -> int:
     return int(load().lfc_max_stream_bytes(block_bytes))
+
+
+def default_ids(temporal=False):
+    """The plan's default candidate ids (include/lfc.h id layout): f in
+    {0, 4, 5, 6, 7} x domains 0-2 (f = 0 only in domain 0) x 2 orderings, 26
+    ids ascending; with ``temporal`` also the same 26 with bit 7 set."""
+    ids = sorted([o << 6 for o in (0, 1)] + [f | (d << 4) | (o << 6) for o in (0, 1) for d in (0, 1, 2)
+                                              for f in (4, 5, 6, 7)])
+    return ids + [i | 0x80 for i in ids] if temporal else ids
 
 
 def mask_from_ids(ids):
@@ -194,15 +207,25 @@ class Plan:
         self._check(self.lib.lfc_plan_timing(self.h, ms, sp, n), "lfc_plan_timing")
         return {k: (ms[i], sp[i]) for i, k in enumerate(STAGES)}
 
-    def set_tuning(self, emit_tile_lenslets=0, chain_range_bytes=0, judge_frames_per_launch=0):
-        t = Tuning(emit_tile_lenslets, chain_range_bytes, judge_frames_per_launch, 0)
+    def set_tuning(self, emit_tile_lenslets=0, chain_range_bytes=0, judge_frames_per_launch=0, wait_budget_ms=0):
+        t = Tuning(emit_tile_lenslets, chain_range_bytes, judge_frames_per_launch, wait_budget_ms)
         self._check(self.lib.lfc_plan_set_tuning(self.h, ctypes.byref(t)), "lfc_plan_set_tuning")
+
+    def inject_fault(self, fault=1):
+        """Test hook (lfc_plan_inject_fault): 1 = the next suffix sort's first
+        tile withholds its look-back status, so its waiters time out."""
+        self._check(self.lib.lfc_plan_inject_fault(self.h, fault), "lfc_plan_inject_fault")
+
+    def device_status(self):
+        """LFC status of the plan's bounded device waits since the last check
+        (lfc_plan_device_status); synchronises the plan's stream."""
+        return int(self.lib.lfc_plan_device_status(self.h))
 
     def get_tuning(self):
         t = Tuning()
         self._check(self.lib.lfc_plan_get_tuning(self.h, ctypes.byref(t)), "lfc_plan_get_tuning")
         return {"emit_tile_lenslets": t.emit_tile_lenslets, "chain_range_bytes": t.chain_range_bytes,
-                "judge_frames_per_launch": t.judge_frames_per_launch}
+                "judge_frames_per_launch": t.judge_frames_per_launch, "wait_budget_ms": t.wait_budget_ms}
 
     def launch_count(self):
         return int(self.lib.lfc_plan_launch_count(self.h))
@@ -323,6 +346,21 @@ class Plan:
         host = out.cpu().numpy()
         sz = ss.cpu().numpy()
         return [host[i * stride:i * stride + int(sz[i])].tobytes() for i in range(len(blocks))]
+
+    def bwt_blocks(self, data, offsets, sizes_in):
+        """Device bytes ``data`` split at offsets/sizes -> (L columns as a
+        uint8 tensor of n x stride, lengths, origin rows) of RLE1 + BWT."""
+        torch = _torch()
+        nb = len(offsets)
+        offs = (ctypes.c_uint64 * nb)(*[int(o) for o in offsets])
+        szs = (ctypes.c_uint32 * nb)(*[int(s) for s in sizes_in])
+        stride = 900000
+        L = torch.empty(nb * stride, dtype=torch.uint8, device=data.device)
+        ln = torch.empty(nb, dtype=torch.int32, device=data.device)
+        orig = torch.empty(nb, dtype=torch.int32, device=data.device)
+        rc = self.lib.lfc_bwt_blocks(self.h, _ptr(data), offs, szs, nb, _ptr(L), stride, _ptr(ln), _ptr(orig))
+        self._check(rc, "lfc_bwt_blocks")
+        return L.view(nb, stride), ln, orig
 
     def decompress(self, blobs, outs, prevs=None):
         """blobs: list of uint8 CUDA tensors (one container each); outs: frame tensors."""

@@ -107,6 +107,26 @@ def test_bzip2_encode_bytes_identical(lfc, case):
         assert bz2.decompress(g) == b
 
 
+@pytest.mark.parametrize("case", range(9))
+def test_bwt_blocks_identical(lfc, case):
+    """lfc_bwt_blocks: the coder's RLE1 + full rotation sort on its own, last
+    column and origin row of every block equal to the oracle's."""
+    import torch
+    blocks = list(_coder_inputs())[case]
+    plan = lfc.Plan(195, 195, 13, max_frames=4)
+    buf = b"".join(blocks)
+    data = torch.from_numpy(np.frombuffer(buf, dtype=np.uint8).copy()).cuda()
+    offs = np.cumsum([0] + [len(b) for b in blocks])[:-1]
+    L, ln, orig = plan.bwt_blocks(data, offs, [len(b) for b in blocks])
+    L, ln, orig = L.cpu().numpy(), ln.cpu().numpy(), orig.cpu().numpy()
+    for i, b in enumerate(blocks):
+        r = oracle.rle1(b)
+        refL, refo = oracle.bwt(r)
+        assert int(ln[i]) == r.size
+        assert np.array_equal(L[i, :r.size], refL)
+        assert int(orig[i]) == refo
+
+
 @pytest.mark.parametrize("k", range(7))
 def test_compress_container_identical(lfc, k):
     fr, p = _frames()[k]
