@@ -1,0 +1,112 @@
+"""Quality of the entropy criterion (the paper's Sec. 3 claim that the
+two-dimensional image entropy of Eq. (1) picks the predictor with the best
+compression ratio, Fig. 4b-4d).
+
+For one frame, every candidate id is
+  * scored by the library's judge (the paper's first-byte judge-BWT, Eq. (1));
+  * compressed for real by the library (lfc_compress with the id given), which
+    gives its true container size;
+  * scored by a "full-BWT" judge: the same bigram entropy taken on the last
+    column of the real Burrows-Wheeler transform of each bzip2 block
+    (lfc_bwt_blocks), the transform the coder actually applies.
+The report compares the three picks. Host code only orders library calls and
+computes report statistics; no step of the method runs here.
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+
+
+def _full_bwt_bits(L_rows, lengths):
+    """Bigram information of the real last columns: sum over blocks of
+    (pairs) x (entropy in bits of the adjacent-pair distribution), i.e.
+    -sum_t P_t log2(P_t / N) per block, N its number of pairs."""
+    bits = 0.0
+    for row, m in zip(L_rows, lengths):
+        m = int(m)
+        if m < 2:
+            continue
+        L = row[:m].astype(np.uint32)
+        pairs = (L[:-1] << 8) | L[1:]
+        c = np.bincount(pairs, minlength=65536).astype(np.float64)
+        c = c[c > 0]
+        n = float(m - 1)
+        bits += float(-(c * np.log2(c / n)).sum())
+    return bits
+
+
+def study_frame(plan, lfc, frame_np, pitch, ids, block_bytes=720000, prev_np=None):
+    """Judge scores, true container sizes and full-BWT bigram bits of every id
+    in ``ids`` for one frame. Returns a dict of per-id lists (ids order) and
+    the three picks."""
+    import torch
+    d = lfc.to_device_frame(frame_np)
+    dp = None if prev_np is None else lfc.to_device_frame(prev_np)
+    choice, scores = plan.judge([d], pitch, prevs=None if dp is None else [dp])
+    sc = scores.cpu().numpy().view(np.uint64)[0]
+    judge_pick = int(choice.cpu()[0])
+    sizes, full_bits = [], []
+    for cid in ids:
+        ch = torch.tensor([cid], dtype=torch.uint8, device="cuda")
+        _, sz, _ = plan.compress([d], pitch, prevs=None if dp is None else [dp], choice=ch)
+        sizes.append(int(sz.cpu()[0]))
+        z = plan.symbols(d, pitch, cid, prev=dp)
+        S = z.view(torch.uint8).reshape(-1)
+        n = S.numel()
+        offs = list(range(0, n, block_bytes))
+        L, ln, _ = plan.bwt_blocks(S, offs, [min(block_bytes, n - o) for o in offs])
+        full_bits.append(_full_bwt_bits(L.cpu().numpy(), ln.cpu().numpy()))
+    true_pick = ids[int(np.argmin(sizes))]  # ties: lowest id (ids ascending)
+    full_pick = ids[int(np.argmin(full_bits))]
+    return {"ids": list(ids), "scores": [int(sc[i]) for i in ids], "sizes": sizes, "full_bwt_bits": full_bits,
+            "judge_pick": judge_pick, "true_pick": true_pick, "full_bwt_pick": full_pick}
+
+
+def summarize(res, raw_bytes):
+    """Gaps of the picks to the true best, ratios and rank agreement."""
+    ids, sizes = res["ids"], res["sizes"]
+    size_of = dict(zip(ids, sizes))
+    best = size_of[res["true_pick"]]
+
+    def gap(cid):
+        return 100.0 * (size_of[cid] - best) / best
+
+    def ranks(v):
+        return np.argsort(np.argsort(np.asarray(v, dtype=np.float64), kind="stable"), kind="stable")
+
+    # Spearman: higher judge score should mean a smaller container
+    rs = ranks([-s for s in res["scores"]])
+    rt = ranks(sizes)
+    rf = ranks(res["full_bwt_bits"])
+    k = len(ids)
+    spearman = lambda a, b: 1.0 - 6.0 * float(((a - b) ** 2).sum()) / (k * (k * k - 1))
+    return {"judge_pick": res["judge_pick"], "true_pick": res["true_pick"], "full_bwt_pick": res["full_bwt_pick"],
+            "judge_gap_pct": gap(res["judge_pick"]), "full_bwt_gap_pct": gap(res["full_bwt_pick"]),
+            "ratio_best": raw_bytes / best, "ratio_judge": raw_bytes / size_of[res["judge_pick"]],
+            "bits_per_dim_best": 8.0 * best / (raw_bytes / 2),
+            "spearman_judge_vs_size": spearman(rs, rt), "spearman_full_bwt_vs_size": spearman(rf, rt),
+            "ratio_by_id": {"0x%02x" % c: raw_bytes / s for c, s in zip(ids, sizes)}}
+
+
+def domain_table(res, raw_bytes, f=6, ordering=0):
+    """Ratio of no prediction and of the intra-lenslet, inter-lenslet and
+    phase-space domains for one predictor function (Fig. 4d uses
+    B + (A - C)/2, f = 6) in one ordering."""
+    size_of = dict(zip(res["ids"], res["sizes"]))
+    o = ordering << 6
+    out = {"none": raw_bytes / size_of[0x00 | o]}
+    for name, dom in (("intra", 0), ("inter", 1), ("phase", 2)):
+        cid = f | (dom << 4) | o
+        if cid in size_of:
+            out[name] = raw_bytes / size_of[cid]
+    return out
+
+
+def bits_saved(res, raw_bytes):
+    """Bits per pixel the best candidate saves over no prediction (the
+    paper's 'bits/dim' gain, Fig. 4b)."""
+    size_of = dict(zip(res["ids"], res["sizes"]))
+    npx = raw_bytes / 2
+    return 8.0 * (size_of[0x00] - min(res["sizes"])) / npx if math.isfinite(npx) else 0.0

@@ -565,16 +565,23 @@ extern "C" int lfc_cnn_thumbnails(lfc_cnn C, const lfc_frame *h_frames, int n, f
     return cnn_thumbs(C, h_frames, n, d_thumbs);
 }
 
+// Caller FP32 thumbnails (planar n x 2 x 256 x 256) into the network input
+// (NHWC BF16, channels 2..15 zero), round to nearest even.
+__global__ void set_thumbs_kernel(const float *__restrict__ th, int n, bf16 *__restrict__ x0) {
+    const size_t total = (size_t)n * kPix;
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x) {
+        const size_t b = i / kPix, pix = i % kPix;
+        bf16 *o = x0 + i * kC0;
+        o[0] = __float2bfloat16(th[(b * 2) * kPix + pix]);
+        o[1] = __float2bfloat16(th[(b * 2 + 1) * kPix + pix]);
+        for (int c = 2; c < kC0; c++) o[c] = __float2bfloat16(0.f);
+    }
+}
+
 extern "C" int lfc_cnn_set_thumbnails(lfc_cnn C, const float *d_thumbs, int n) {
     if (!C || !d_thumbs || n < 1 || n > C->max_batch) return cnn_fail(C, LFC_ERR_INVALID_ARG, "lfc_cnn_set_thumbnails");
-    // (BF16 rounding of caller-provided FP32 thumbnails, for tests and tools)
-    std::vector<float> h((size_t)n * 2 * kPix);
-    CKC(cudaMemcpy(h.data(), d_thumbs, h.size() * 4, cudaMemcpyDeviceToHost));
-    std::vector<bf16> x((size_t)n * kPix * kC0, __float2bfloat16(0.f));
-    for (int b = 0; b < n; b++)
-        for (int p = 0; p < kPix; p++)
-            for (int c = 0; c < 2; c++) x[((size_t)b * kPix + p) * kC0 + c] = __float2bfloat16(h[((size_t)b * 2 + c) * kPix + p]);
-    CKC(cudaMemcpy(C->x0, x.data(), x.size() * 2, cudaMemcpyHostToDevice));
+    set_thumbs_kernel<<<(unsigned)std::min<size_t>(4096, ((size_t)n * kPix + 255) / 256), 256, 0, C->stream>>>(d_thumbs, n, C->x0);
+    CKC(cudaGetLastError());
     return LFC_OK;
 }
 

@@ -31,6 +31,88 @@ def make_frames(fields, levels=PHOTON_LEVELS, draws=1, seed0=0):
     return frames
 
 
+def make_dataset(plan, net, fields, pitch, class_ids, levels=PHOTON_LEVELS, draws=1, seed0=0, chunk=8):
+    """Thumbnails (FP32, n x 2 x 256 x 256, lfc_cnn_thumbnails) and
+    exhaustive-judge labels (lfc_judge) of every field x photon level x noise
+    draw. Frames are drawn on the device a chunk at a time and dropped once
+    judged, so a training set of thousands of 2040 x 2040 frames keeps only
+    its thumbnails (0.5 MB each). The plan and the network must take
+    ``chunk`` frames per call."""
+    import torch
+
+    from . import synth
+    pos = {c: i for i, c in enumerate(class_ids)}
+    dev_fields = [(kind, torch.as_tensor(sub, dtype=torch.float32, device="cuda")) for kind, sub in fields]
+    specs = [(kind, sub, lv) for kind, sub in dev_fields for lv in levels for _ in range(draws)]
+    thumbs, labels = [], []
+    for i in range(0, len(specs), chunk):
+        frames = []
+        for j, (kind, sub, lv) in enumerate(specs[i:i + chunk]):
+            scale = lv * (0.25 if kind == "cells" else 1.0)
+            frames.append(synth.photons_to_frame_torch(sub, scale, seed0 + i + j))
+        ch, _ = plan.judge(frames, pitch)
+        labels.extend(pos[int(c)] for c in ch.cpu().numpy())
+        thumbs.append(net.thumbnails(frames, pitch, want=True))
+    return torch.cat(thumbs), torch.tensor(labels, dtype=torch.int32, device="cuda")
+
+
+def train_thumbs(net, thumbs, labels, epochs=10, batch=32, lr=2e-3, seed=0, log=None):
+    """Adam on mean cross-entropy over stored thumbnails (cosine learning
+    rate); returns the per-epoch mean losses."""
+    import torch
+    rng = np.random.default_rng(seed)
+    n = thumbs.shape[0]
+    hist = []
+    step = 0
+    total_steps = epochs * max(1, n // batch)
+    for ep in range(epochs):
+        order = torch.as_tensor(rng.permutation(n), device="cuda")
+        losses = []
+        for b0 in range(0, n - batch + 1, batch):
+            idx = order[b0:b0 + batch]
+            net.set_thumbnails(thumbs[idx])
+            loss = net.backward(labels[idx])
+            cur_lr = lr * 0.5 * (1 + np.cos(np.pi * step / max(1, total_steps)))
+            net.adam_step(float(cur_lr))
+            losses.append(loss.mean())
+            step += 1
+        m = float(torch.stack(losses).mean()) if losses else float("nan")
+        hist.append(m)
+        if log:
+            log("epoch %d loss %.4f" % (ep, m))
+    return hist
+
+
+def accuracy_thumbs(net, thumbs, labels, topk=1, batch=32):
+    import torch
+    hits = 0
+    for b0 in range(0, thumbs.shape[0], batch):
+        th = thumbs[b0:b0 + batch]
+        net.set_thumbnails(th)
+        probs = net.forward(th.shape[0])
+        top = torch.topk(probs, topk, dim=1).indices
+        hits += int((top == labels[b0:b0 + th.shape[0]].long()[:, None]).any(dim=1).sum())
+    return hits / thumbs.shape[0]
+
+
+def proposal_ms_per_frame(plan, frames, pitch, chunk=8, reps=3):
+    """Device time of the proposal alone (lfc_propose: thumbnails, the four
+    convolutions, pooling, softmax and the candidate masks) per frame, CUDA
+    events on the plan's stream."""
+    import torch
+    st = plan.stream
+    for i in range(0, len(frames), chunk):
+        plan.propose(frames[i:i + chunk], pitch)
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(st)
+    for _ in range(reps):
+        for i in range(0, len(frames), chunk):
+            plan.propose(frames[i:i + chunk], pitch)
+    b.record(st)
+    b.synchronize()
+    return a.elapsed_time(b) / (reps * len(frames))
+
+
 def labels_for(plan, frames, pitch, class_ids, chunk=8):
     """Exhaustive-judge choice of every frame as a class index."""
     import torch
