@@ -251,7 +251,7 @@ extern "C" int lfc_plan_block_capacity(lfc_plan P) { return P ? P->block_cap : 0
 
 static void free_ws(Workspace &w) {
     void *ptrs[] = {w.hist, w.summ, w.chain_first, w.scores, w.choice, w.jframes, w.cand, w.l2tab, w.stream, w.blocks, w.bstate,
-                    w.rle, w.sa, w.sa2, w.rank, w.act, w.act2, w.val, w.val2, w.keys, w.keys2, w.lbstat, w.dhist, w.tileaux, w.bwt,
+                    w.rle, w.sa, w.sa2, w.rank, w.act, w.act2, w.val, w.val2, w.keys, w.keys2, w.lbstat, w.dhist, w.segbig, w.tileaux, w.bwt,
                     w.mtfidx, w.mtflists, w.mtfrec, w.mtfreclen, w.sym, w.freq, w.rfreq, w.sel, w.lens, w.codes, w.packed, w.cstream, w.masks, w.class_ids,
                     w.act_total, w.block_dst, w.frame_crc, w.crc_part, w.crc_part2, w.chunk_desc, w.dec_tt};
     for (void *p : ptrs)
@@ -350,6 +350,7 @@ extern "C" int lfc_plan_create(const lfc_config *cfg, void *cuda_stream, lfc_pla
     ws.lbstat_words = (size_t)BC * kTilesPerBlock * 256;
     AL(lbstat, 2 * ws.lbstat_words);
     AL(dhist, (size_t)BC * 8 * 256);
+    AL(segbig, (size_t)BC);
     AL(tileaux, (size_t)BC * kTilesPerBlock * 4);
     AL(bwt, (size_t)BC * kBlockCap);
     AL(mtfidx, (size_t)BC * kBlockCap);

@@ -315,16 +315,20 @@ __global__ void zero_u32_kernel(uint32_t *p, size_t n) {
 // the top bytes of the 64-bit key, so passes 8 - kPhase1Bytes .. 7 carry them.
 constexpr int kPhase1Bytes = LFC_PHASE1_BYTES;
 
-// Also adds the tile's digits of every pass to the block's totals and clears
-// the tile's look-back status words in both status arrays (the first pass
-// reads array 0 and clears array 1 for the second, and so on).
+// Also adds the tile's bytes to the block's byte histogram and clears the
+// tile's look-back status words in both status arrays (the first pass reads
+// array 0 and clears array 1 for the second, and so on). Over all rotations
+// of a block, the digit of every pass (one byte of each rotation's prefix)
+// takes each byte position of the block exactly once, so the digit totals
+// of all 8 passes equal the block's byte histogram: one histogram serves
+// every pass.
 __global__ void __launch_bounds__(kSortThreads) key8_kernel(const BlockState *__restrict__ st,
                                                             const uint8_t *__restrict__ rle_all,
                                                             uint64_t *__restrict__ K_all, int32_t *__restrict__ V_all,
                                                             uint32_t *__restrict__ dhist_all, uint32_t *__restrict__ lb_all,
                                                             size_t lb_array_words) {
     __shared__ uint8_t sb[kTile + 8];
-    __shared__ uint32_t hst[kSweepPasses][256];
+    __shared__ uint32_t hst[1][256];
     const int b = blockIdx.y, tile = blockIdx.x;
     const int m = st[b].m;
     const int t0 = tile * kTile;
@@ -332,7 +336,7 @@ __global__ void __launch_bounds__(kSortThreads) key8_kernel(const BlockState *__
     const int cnt = min(kTile, m - t0);
     const uint8_t *rle = rle_all + (size_t)b * kBlockCap;
     for (int i = threadIdx.x; i < cnt + 7; i += kSortThreads) sb[i] = rle[(t0 + i) % m];
-    for (int i = threadIdx.x; i < kSweepPasses * 256; i += kSortThreads) (&hst[0][0])[i] = 0;
+    hst[0][threadIdx.x] = 0;
     uint32_t *lbt = lb_all + (size_t)b * kLbBlockWords + (size_t)tile * 256;
     lbt[threadIdx.x] = 0;
     lbt[lb_array_words + threadIdx.x] = 0;
@@ -350,10 +354,10 @@ __global__ void __launch_bounds__(kSortThreads) key8_kernel(const BlockState *__
             K[t0 + kl] = key;
             V[t0 + kl] = t0 + kl;
         }
-        tile_digits<kSweepPasses>(key, ok, 0, hst);
+        tile_digits<1>((uint64_t)sb[kl], ok, 0, hst);  // the tile's own byte
     }
     __syncthreads();
-    flush_digits<kSweepPasses>(hst, dhist_all + (size_t)b * kSweepPasses * 256);
+    flush_digits<1>(hst, dhist_all + (size_t)b * kSweepPasses * 256);
 }
 
 // Round words of the tied elements: rank[v] << 40 | rank[(v + h) mod m] << 20 | v.
@@ -361,30 +365,44 @@ constexpr uint64_t kElemMask = (1u << 20) - 1u;
 
 __global__ void __launch_bounds__(kSortThreads) key40_kernel(const int32_t *__restrict__ rs, const BlockState *__restrict__ st,
                                                              const int32_t *__restrict__ V_all, const int32_t *__restrict__ rank_all,
-                                                             uint64_t *__restrict__ K_all, uint32_t *__restrict__ dhist_all) {
-    __shared__ uint32_t hst[5][256];
+                                                             uint64_t *__restrict__ K_all, int32_t *__restrict__ big) {
     if (rs[kRsAbort]) return;
     const int b = blockIdx.y, tile = blockIdx.x;
     const int h = rs[2];
     const BlockState s = st[b];
     const int n = sort_count<1>(s, h);
     if (tile * kTile >= n) return;
-    for (int i = threadIdx.x; i < 5 * 256; i += kSortThreads) (&hst[0][0])[i] = 0;
-    __syncthreads();
+    if (tile == 0 && threadIdx.x == 0) big[b] = 0;  // set again by the segmented sort if a group is too large
     const size_t bo = (size_t)b * kBlockCap;
     for (int r = 0; r < kPerThread; r++) {
         const int k = tile * kTile + r * kSortThreads + threadIdx.x;
+        if (k >= n) break;
+        const int v = V_all[bo + k];
+        int j = v + h;
+        if (j >= s.m) j -= s.m;
+        K_all[bo + k] = ((uint64_t)(uint32_t)rank_all[bo + v] << 40) | ((uint64_t)(uint32_t)rank_all[bo + j] << 20) |
+                        (uint64_t)(uint32_t)v;
+    }
+}
+
+// Digit totals of the 5 round passes, for the blocks the segmented sort
+// flagged (the only ones that take the radix passes).
+__global__ void __launch_bounds__(kSortThreads) round_digits_kernel(const int32_t *__restrict__ rs, const BlockState *__restrict__ st,
+                                                                    const uint64_t *__restrict__ K_all, uint32_t *__restrict__ dhist_all,
+                                                                    const int32_t *__restrict__ big) {
+    __shared__ uint32_t hst[5][256];
+    if (rs[kRsAbort]) return;
+    const int b = blockIdx.y, tile = blockIdx.x;
+    if (!big[b]) return;
+    const int n = sort_count<1>(st[b], rs[2]);
+    if (tile * kTile >= n) return;
+    for (int i = threadIdx.x; i < 5 * 256; i += kSortThreads) (&hst[0][0])[i] = 0;
+    __syncthreads();
+    const uint64_t *K = K_all + (size_t)b * kBlockCap;
+    for (int r = 0; r < kPerThread; r++) {
+        const int k = tile * kTile + r * kSortThreads + threadIdx.x;
         const bool ok = k < n;
-        uint64_t word = 0;
-        if (ok) {
-            const int v = V_all[bo + k];
-            int j = v + h;
-            if (j >= s.m) j -= s.m;
-            word = ((uint64_t)(uint32_t)rank_all[bo + v] << 40) | ((uint64_t)(uint32_t)rank_all[bo + j] << 20) |
-                   (uint64_t)(uint32_t)v;
-            K_all[bo + k] = word;
-        }
-        tile_digits<5>(word, ok, 20, hst);
+        tile_digits<5>(ok ? K[k] : 0ull, ok, 20, hst);
     }
     __syncthreads();
     flush_digits<5>(hst, dhist_all + (size_t)b * kSweepPasses * 256);
@@ -397,8 +415,11 @@ __global__ void __launch_bounds__(kSortThreads) key40_kernel(const int32_t *__re
 // count ceil(n_b / kTile) goes to rs[kRsTileOff + b]; rs[kRsItems] = the
 // largest count x nblocks (items past a block's last tile are skipped); both
 // work queues start empty. One CTA.
+// In a round (MODE 1) only the blocks flagged by the segmented sort (a group
+// longer than its window) take the radix passes.
 template <int MODE>
-__global__ void __launch_bounds__(1024) sort_items_kernel(int32_t *__restrict__ rs, const BlockState *__restrict__ st, int nblocks) {
+__global__ void __launch_bounds__(1024) sort_items_kernel(int32_t *__restrict__ rs, const BlockState *__restrict__ st, int nblocks,
+                                                          const int32_t *__restrict__ big) {
     __shared__ int smax;
     const bool abort = rs[kRsAbort] != 0;
     const int h = round_h<MODE>(rs);
@@ -406,7 +427,8 @@ __global__ void __launch_bounds__(1024) sort_items_kernel(int32_t *__restrict__ 
     __syncthreads();
     int mx = 0;
     for (int b = threadIdx.x; b < nblocks; b += blockDim.x) {
-        const int t = abort ? 0 : (sort_count<MODE>(st[b], h) + kTile - 1) / kTile;
+        const bool take = !abort && (MODE == 0 || big[b] != 0);
+        const int t = take ? (sort_count<MODE>(st[b], h) + kTile - 1) / kTile : 0;
         rs[kRsTileOff + b] = t;
         mx = max(mx, t);
     }
@@ -419,10 +441,149 @@ __global__ void __launch_bounds__(1024) sort_items_kernel(int32_t *__restrict__ 
     }
 }
 
+// Segmented sort of a doubling round. The tied elements of a block are
+// listed in suffix-array order, so their round words rank[v] << 40 |
+// rank[v + h] << 20 | v are already sorted by the group rank (the top bits);
+// a round only has to order each group by the rest of the word (v breaks the
+// ties, which keeps identical rotations in start order). A CTA takes the
+// groups whose head lies in its 4096-element tile (the window [lo, hi) runs
+// from the first head at or after the tile start to the first head at or
+// after the tile end), sorts the window's words in shared memory and writes
+// them back to the same indices. Groups of at most kSegSmall elements rank
+// each word by counting the smaller words of its group; a window with a larger
+// group is sorted whole by a bitonic network. A window longer than kSegCap
+// (a group longer than kSegCap - kTile + 1) flags its block, which then takes
+// the radix passes instead.
+constexpr int kSegCap = 8192;
+constexpr int kSegThreads = 512;
+constexpr int kSegSmall = 256;
+constexpr size_t kSegSmem = (size_t)kSegCap * 8;
+
+// First index in [k, limit) whose group rank differs from r (limit if none);
+// read 32 words at a time by one warp (all lanes call it).
+__device__ __forceinline__ int next_head(const uint64_t *K, int k, int limit, uint64_t r) {
+    const int lane = threadIdx.x & 31;
+    for (; k < limit; k += 32) {
+        const int i = k + lane;
+        const bool diff = i < limit && (K[i] >> 40) != r;
+        const uint32_t m = __ballot_sync(LFC_FULL, diff);
+        if (m) return k + __ffs(m) - 1;
+    }
+    return limit;
+}
+
+__global__ void __launch_bounds__(kSegThreads) segsort_kernel(const int32_t *__restrict__ rs, const BlockState *__restrict__ st,
+                                                              const uint64_t *__restrict__ K_all, uint64_t *__restrict__ Kout_all,
+                                                              int32_t *__restrict__ big) {
+    extern __shared__ __align__(16) uint64_t sw[];  // [kSegCap]
+    __shared__ int s_lo, s_hi, s_gmax;
+    if (rs[kRsAbort]) return;
+    const int b = blockIdx.y, tile = blockIdx.x;
+    const int h = rs[2];
+    const int n = sort_count<1>(st[b], h);
+    const int t0 = tile * kTile;
+    if (t0 >= n) return;
+    const size_t bo = (size_t)b * kBlockCap;
+    const uint64_t *K = K_all + bo;
+    if (threadIdx.x < 32) {
+        // window: skip the group begun before the tile, extend past the tile end
+        // to the end of the last group; every scan stops after kSegCap words
+        int lo = t0;
+        if (t0 > 0) lo = next_head(K, t0, min(n, t0 + kSegCap), K[t0 - 1] >> 40);
+        const int te = min(n, t0 + kTile);
+        int hi = te;
+        if (lo < te && te < n) hi = next_head(K, te, min(n, lo + kSegCap + 1), K[te - 1] >> 40);
+        if (threadIdx.x == 0) {
+            s_lo = lo;
+            s_hi = hi;
+            s_gmax = 0;
+        }
+    }
+    __syncthreads();
+    const int lo = s_lo, hi = s_hi, cnt = hi - lo;
+    if (cnt <= 0) return;  // the tile lies inside a group begun earlier
+    if (cnt > kSegCap || (lo > t0 && lo - t0 >= kSegCap)) {
+        if (threadIdx.x == 0) atomicExch(&big[b], 1);
+        return;
+    }
+    for (int i = threadIdx.x; i < cnt; i += kSegThreads) sw[i] = K[lo + i];
+    __syncthreads();
+    // element i (thread i % kSegThreads): its group's bounds by scanning from
+    // i while the group rank holds (at most kSegSmall + 1 words either way),
+    // then its rank inside the group by counting the group's smaller words,
+    // and the word goes straight to that index of the output (the writes of a
+    // window stay inside it). Neighbouring lanes hold neighbouring words of
+    // mostly the same group, so the counting reads are broadcasts. A window
+    // holding a larger group is sorted whole below and written again.
+    uint64_t *Kout = Kout_all + bo + lo;
+    bool gbig = false;
+    for (int i = threadIdx.x; i < cnt; i += kSegThreads) {
+        const uint64_t w = sw[i], r = w >> 40;
+        int gs = i;
+        while (gs > 0 && (sw[gs - 1] >> 40) == r && i - gs < kSegSmall) gs--;
+        int ge = i + 1;
+        while (ge < cnt && (sw[ge] >> 40) == r && ge - gs <= kSegSmall) ge++;
+        if (ge - gs > kSegSmall) {
+            gbig = true;
+        } else {
+            int c = gs;
+            for (int j = gs; j < ge; j++) c += sw[j] < w;
+            Kout[c] = w;
+        }
+    }
+    if (gbig) s_gmax = kSegSmall + 1;
+    __syncthreads();
+    if (s_gmax > kSegSmall) {
+        // bitonic sort of the whole window, padded to a power of two
+        int np = 1;
+        while (np < cnt) np <<= 1;
+        for (int i = cnt + threadIdx.x; i < np; i += kSegThreads) sw[i] = ~0ull;
+        __syncthreads();
+        for (int k = 2; k <= np; k <<= 1) {
+            for (int j = k >> 1; j > 0; j >>= 1) {
+                for (int i = threadIdx.x; i < np; i += kSegThreads) {
+                    const int l = i ^ j;
+                    if (l > i) {
+                        const uint64_t x = sw[i], y = sw[l];
+                        const bool up = (i & k) == 0;
+                        if ((x > y) == up) {
+                            sw[i] = y;
+                            sw[l] = x;
+                        }
+                    }
+                }
+                __syncthreads();
+            }
+        }
+        for (int i = threadIdx.x; i < cnt; i += kSegThreads) Kout[i] = sw[i];
+    }
+}
+
 // Digit position of a pass: phase 1 sorts all 64 key bits, a round bits 20..59.
 template <int MODE>
 __device__ __forceinline__ int digit_shift(int pass) { return (MODE == 0 ? 0 : 20) + 8 * pass; }
 
+// One stable LSD pass of (key, element) pairs (MODE 0) or round words (MODE
+// 1, the element rides in the word) over every block of the pass.
+// Persistent: CTAs take tiles from the pass's work queue until it is empty
+// (tile-major order, see sort_items_kernel).
+// Per tile: warp w ranks elements [w*512, (w+1)*512) of the tile 32 at a
+// time in order (equal digits by __match_any_sync and a per-warp running
+// count), giving the tile's count c[d] of every digit d; thread d publishes
+// c[d] (flag "aggregate"; tile 0: "inclusive"), adds the published counts of
+// the block's earlier tiles back to the nearest "inclusive" one, publishes
+// its own inclusive count, and the run of digit d starts at (elements of the
+// block with a smaller digit, from the block's digit totals) + (elements of
+// digit d in earlier tiles). Tiles are placed in shared memory in digit
+// order and each digit's run is written with consecutive threads on
+// consecutive addresses.
+// A tile waits only on tiles taken from the queue before it, which are held
+// by running CTAs, so the waits always end; each is still bounded by
+// `budget` clock cycles, after which the CTA raises the abort word and every
+// sort kernel of this suffix sort returns at once (LFC_ERR_TIMEOUT).
+// Status words of the pass live in array par = pass parity; each tile clears
+// its words in the other array for the next pass (which runs on the same or
+// fewer tiles of every block).
 // One stable LSD pass of (key, element) pairs (MODE 0) or round words (MODE
 // 1, the element rides in the word) over every block of the pass.
 // Persistent: CTAs take tiles from the pass's work queue until it is empty
@@ -551,8 +712,9 @@ radix_sweep_kernel(int pass, int nblocks, int32_t *__restrict__ rs, const BlockS
             if (!gave_up) st_release_u32(lbb + (size_t)tile * 256 + d, kLbIncl | (excl + cnt_d));
         }
         lb_next[(size_t)b * kLbBlockWords + (size_t)tile * 256 + d] = 0;
+        const int drow = MODE == 0 ? 0 : pass;  // phase 1: every pass has the block's byte histogram
         const uint32_t below = block_excl_sum<uint32_t>(
-            dhist_all[((size_t)b * kSweepPasses + pass) * 256 + d], sh, nullptr);  // block elements with a smaller digit
+            dhist_all[((size_t)b * kSweepPasses + drow) * 256 + d], sh, nullptr);  // block elements with a smaller digit
         gbase[d] = below + excl;
         if (withhold && d == 0) atomicExch(rs + kRsFault, 0);  // the fault fires once
         if (__syncthreads_or(gave_up)) break;
@@ -968,10 +1130,14 @@ static void bwt_round(lfc_plan P, cudaStream_t st, int nblocks, int tiles, int m
     const size_t nd = (size_t)nblocks * kSweepPasses * 256;
     zero_u32_kernel<<<(unsigned)std::min<size_t>(64, (nd + 255) / 256), 256, 0, st>>>(ws.dhist, nd);
     dim3 g1(tiles, nblocks);
-    key40_kernel<<<g1, kSortThreads, 0, st>>>(ws.act_total, ws.bstate, ws.val, ws.rank, ws.keys, ws.dhist);
-    sort_items_kernel<1><<<1, 1024, 0, st>>>(ws.act_total, ws.bstate, nblocks);
-    count_launches(P, 4);
-    // 5 LSD passes over bits 20..59 of the words: keys -> keys2 -> ... -> keys2
+    key40_kernel<<<g1, kSortThreads, 0, st>>>(ws.act_total, ws.bstate, ws.val, ws.rank, ws.keys, ws.segbig);
+    // groups within their windows: keys -> keys2 directly; blocks with a
+    // longer group are flagged and take the 5 LSD passes over bits 20..59 of
+    // the words instead: keys -> keys2 -> ... -> keys2
+    segsort_kernel<<<g1, kSegThreads, kSegSmem, st>>>(ws.act_total, ws.bstate, ws.keys, ws.keys2, ws.segbig);
+    round_digits_kernel<<<g1, kSortThreads, 0, st>>>(ws.act_total, ws.bstate, ws.keys, ws.dhist, ws.segbig);
+    sort_items_kernel<1><<<1, 1024, 0, st>>>(ws.act_total, ws.bstate, nblocks, ws.segbig);
+    count_launches(P, 6);
     const int ctas = sweep_ctas(P, nblocks, tiles);
     for (int pass = 0; pass < 5; pass++) {
         if (pass & 1) sweep_pass<1>(P, st, nblocks, ctas, pass, ws.keys2, nullptr, ws.keys, nullptr);
@@ -1000,6 +1166,7 @@ cudaError_t launch_bwt(lfc_plan P, int nblocks, int max_m) {
     e = cudaFuncSetAttribute(radix_sweep_kernel<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kScatterSmem);
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(radix_sweep_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kScatterSmem1);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(segsort_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSegSmem);
     if (e != cudaSuccess) return e;
     // a new suffix sort: no wait has given up yet (outside graphs the sticky
     // status is reported by this call, so it starts clear as well)
@@ -1013,7 +1180,7 @@ cudaError_t launch_bwt(lfc_plan P, int nblocks, int max_m) {
     const size_t nd = (size_t)nblocks * kSweepPasses * 256;
     zero_u32_kernel<<<(unsigned)std::min<size_t>(64, (nd + 255) / 256), 256, 0, s>>>(ws.dhist, nd);
     key8_kernel<<<grid, kSortThreads, 0, s>>>(ws.bstate, ws.rle, ws.keys, ws.sa, ws.dhist, ws.lbstat, ws.lbstat_words);
-    sort_items_kernel<0><<<1, 1024, 0, s>>>(ws.act_total, ws.bstate, nblocks);
+    sort_items_kernel<0><<<1, 1024, 0, s>>>(ws.act_total, ws.bstate, nblocks, nullptr);
     count_launches(P, 3);
     uint64_t *kin = ws.keys, *kout = ws.keys2;
     int32_t *vin = ws.sa, *vout = ws.sa2;

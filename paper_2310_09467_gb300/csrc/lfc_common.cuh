@@ -191,6 +191,7 @@ struct Workspace {
     uint32_t *lbstat = nullptr;    // radix look-back status, 2 arrays of block_cap * kTilesPerBlock * 256
     size_t lbstat_words = 0;       // words of one of those arrays
     uint32_t *dhist = nullptr;     // per block and radix pass: digit totals, block_cap * 8 * 256
+    int32_t *segbig = nullptr;     // per block: a doubling round has a group longer than the segmented sort's window
     int32_t *tileaux = nullptr;    // block_cap * kTilesPerBlock * 4
     uint8_t *bwt = nullptr;        // L column
     uint8_t *mtfidx = nullptr;
