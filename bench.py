@@ -327,6 +327,8 @@ def run_series(args):
         torch.cuda.synchronize()
         ms = []
         st = plan.stream
+        clocks = Clocks(int(os.environ.get("LOCAL_RANK", "0")))
+        clocks.start()
         for _ in range(args.steps):
             a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             a.record(st)
@@ -334,6 +336,7 @@ def run_series(args):
             b.record(st)
             b.synchronize()
             ms.append(a.elapsed_time(b))
+        out["clocks_temporal" if temporal else "clocks_spatial"] = clocks.stop()
         comp = int(batch.sizes.cpu().numpy().sum())
         if temporal:
             ids = []
@@ -350,7 +353,8 @@ def run_series(args):
             "config": {"workload": "time series: %d frames 2040x2040 p15 vessel, keyframe every %d, one graph launch" % (n, G),
                        "candidates": "52 (26 spatial + 26 temporal) on non-keyframes"},
             "ratio": out["temporal"]["ratio"], "ratio_without_temporal": out["spatial"]["ratio"],
-            "MBps_without_temporal": out["spatial"]["MBps"], "frames_choosing_temporal": out["temporal_ids"]}
+            "MBps_without_temporal": out["spatial"]["MBps"], "frames_choosing_temporal": out["temporal_ids"],
+            "clocks": out["clocks_temporal"]}
     print(json.dumps(line))
     return 0
 
@@ -394,7 +398,10 @@ def run_learned(args):
     train_s = time.time() - t2
     acc1 = learn.accuracy(net, test_frames, test_labels, PITCH, 1)
     acc3 = learn.accuracy(net, test_frames, test_labels, PITCH, 3)
+    clocks = Clocks(int(os.environ.get("LOCAL_RANK", "0")))
+    clocks.start()
     res = learn.evaluate(plan, net, class_ids, test_frames, PITCH)
+    clk = clocks.stop()
     plan.set_proposal(net, class_ids, 3, 0.0)
     prop_ms = learn.proposal_ms_per_frame(plan, test_frames[:64], PITCH)
     plan.set_proposal(None, class_ids, 1, 0.0)
@@ -409,7 +416,7 @@ def run_learned(args):
             "exhaustive_MBps": res["exhaustive"]["fps"] * raw / 1e6,
             "settings": {k: {kk: (round(vv, 4) if isinstance(vv, float) else vv) for kk, vv in v.items()}
                          for k, v in res.items()},
-            "proposal_ms_per_frame": prop_ms,
+            "proposal_ms_per_frame": prop_ms, "clocks": clk,
             "test_accuracy": {"top1": acc1, "top3": acc3}, "train_loss": [round(x, 4) for x in hist],
             "label_hist": np.bincount(labels.cpu().numpy(), minlength=len(class_ids)).tolist(),
             "seconds": {"fields": gen_s, "frames_and_labels": label_s, "train": train_s}}
