@@ -269,13 +269,16 @@ constexpr uint32_t kLbCount = (1u << 30) - 1u;
 constexpr size_t kLbBlockWords = (size_t)kTilesPerBlock * 256;  // one block's words in one status array
 constexpr int kSweepPasses = 8;  // digit-histogram rows per block (phase 1: 8 passes, a round: 5)
 
-__device__ __forceinline__ uint32_t ld_acquire_u32(const uint32_t *p) {
+// A status word carries its flag and count in one 32-bit value and nothing
+// else is read on its strength, so relaxed device-scope accesses suffice (no
+// fence: publishing does not wait for the tile's earlier scatter writes).
+__device__ __forceinline__ uint32_t ld_status(const uint32_t *p) {
     uint32_t v;
-    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
     return v;
 }
-__device__ __forceinline__ void st_release_u32(uint32_t *p, uint32_t v) {
-    asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+__device__ __forceinline__ void st_status(uint32_t *p, uint32_t v) {
+    asm volatile("st.relaxed.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
 __device__ __forceinline__ int ld_volatile_i32(const int32_t *p) { return *reinterpret_cast<const volatile int32_t *>(p); }
 
@@ -686,14 +689,14 @@ radix_sweep_kernel(int pass, int nblocks, int32_t *__restrict__ rs, const BlockS
         // decoupled look-back over the block's earlier tiles
         uint32_t *lbb = lb + (size_t)b * kLbBlockWords;
         const bool withhold = s_fault != 0 && b == 0 && tile == 0;  // fault injection: never publish
-        if (!withhold) st_release_u32(lbb + (size_t)tile * 256 + d, (tile == 0 ? kLbIncl : kLbAgg) | cnt_d);
+        if (!withhold) st_status(lbb + (size_t)tile * 256 + d, (tile == 0 ? kLbIncl : kLbAgg) | cnt_d);
         uint32_t excl = 0;
         bool gave_up = false;
         if (tile > 0) {
             const long long t0 = clock64();
             int tp = tile - 1;
             for (;;) {
-                const uint32_t sv = ld_acquire_u32(lbb + (size_t)tp * 256 + d);
+                const uint32_t sv = ld_status(lbb + (size_t)tp * 256 + d);
                 if (sv & (kLbAgg | kLbIncl)) {
                     excl += sv & kLbCount;
                     if ((sv & kLbIncl) || tp == 0) break;
@@ -709,7 +712,7 @@ radix_sweep_kernel(int pass, int nblocks, int32_t *__restrict__ rs, const BlockS
                 }
                 __nanosleep(64);
             }
-            if (!gave_up) st_release_u32(lbb + (size_t)tile * 256 + d, kLbIncl | (excl + cnt_d));
+            if (!gave_up) st_status(lbb + (size_t)tile * 256 + d, kLbIncl | (excl + cnt_d));
         }
         lb_next[(size_t)b * kLbBlockWords + (size_t)tile * 256 + d] = 0;
         const int drow = MODE == 0 ? 0 : pass;  // phase 1: every pass has the block's byte histogram

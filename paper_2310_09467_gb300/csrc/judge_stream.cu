@@ -421,24 +421,25 @@ chain_hist_kernel(const JudgeFrame *__restrict__ frames, int nframes, const uint
     if (len > 0) {
         uint32_t prev = S[lo == 0 ? n - 1 : lo - 1];  // cyclic predecessor
         const uint8_t *L = S + lo;                      // 16-byte aligned
-        const int full = len >> 6;
-        uint4 c[4], nx[4];
-#pragma unroll
-        for (int j = 0; j < 4; j++) c[j] = full > 0 ? __ldg(reinterpret_cast<const uint4 *>(L) + j) : make_uint4(0, 0, 0, 0);
+        const int full = len >> 5;  // 32-byte steps, the next one loaded while this one is walked
+        uint4 c0 = make_uint4(0, 0, 0, 0), c1 = c0;
+        if (full > 0) {
+            c0 = __ldg(reinterpret_cast<const uint4 *>(L));
+            c1 = __ldg(reinterpret_cast<const uint4 *>(L) + 1);
+        }
 #pragma unroll 1
         for (int k = 0; k < full; k++) {
-#pragma unroll
-            for (int j = 0; j < 4; j++)
-                nx[j] = k + 1 < full ? __ldg(reinterpret_cast<const uint4 *>(L + (size_t)(k + 1) * 64) + j)
-                                     : make_uint4(0, 0, 0, 0);
-            const uint32_t w0[8] = {c[0].x, c[0].y, c[0].z, c[0].w, c[1].x, c[1].y, c[1].z, c[1].w};
-            chain_walk32(w0, prev, tl, fl, hot, ghist, slot);
-            const uint32_t w1[8] = {c[2].x, c[2].y, c[2].z, c[2].w, c[3].x, c[3].y, c[3].z, c[3].w};
-            chain_walk32(w1, prev, tl, fl, hot, ghist, slot);
-#pragma unroll
-            for (int j = 0; j < 4; j++) c[j] = nx[j];
+            uint4 n0 = make_uint4(0, 0, 0, 0), n1 = n0;
+            if (k + 1 < full) {
+                n0 = __ldg(reinterpret_cast<const uint4 *>(L + (size_t)(k + 1) * 32));
+                n1 = __ldg(reinterpret_cast<const uint4 *>(L + (size_t)(k + 1) * 32) + 1);
+            }
+            const uint32_t w[8] = {c0.x, c0.y, c0.z, c0.w, c1.x, c1.y, c1.z, c1.w};
+            chain_walk32(w, prev, tl, fl, hot, ghist, slot);
+            c0 = n0;
+            c1 = n1;
         }
-        for (int k = full << 6; k < len; k++) {  // ragged end of the stream
+        for (int k = full << 5; k < len; k++) {  // ragged end of the stream
             const uint32_t b = L[k], a = prev;
             uint16_t *en = chain_entry(tl, b);
             const uint32_t e = *en;
