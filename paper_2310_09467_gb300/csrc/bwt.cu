@@ -480,6 +480,7 @@ __global__ void __launch_bounds__(kSegThreads) segsort_kernel(const int32_t *__r
                                                               int32_t *__restrict__ big) {
     extern __shared__ __align__(16) uint64_t sw[];  // [kSegCap]
     __shared__ int s_lo, s_hi, s_gmax;
+    __shared__ int s_last[kSegCap / 32], s_first[kSegCap / 32], s_scan[33];
     if (rs[kRsAbort]) return;
     const int b = blockIdx.y, tile = blockIdx.x;
     const int h = rs[2];
@@ -511,21 +512,57 @@ __global__ void __launch_bounds__(kSegThreads) segsort_kernel(const int32_t *__r
     }
     for (int i = threadIdx.x; i < cnt; i += kSegThreads) sw[i] = K[lo + i];
     __syncthreads();
-    // element i (thread i % kSegThreads): its group's bounds by scanning from
-    // i while the group rank holds (at most kSegSmall + 1 words either way),
-    // then its rank inside the group by counting the group's smaller words,
-    // and the word goes straight to that index of the output (the writes of a
-    // window stay inside it). Neighbouring lanes hold neighbouring words of
-    // mostly the same group, so the counting reads are broadcasts. A window
-    // holding a larger group is sorted whole below and written again.
+    // Group bounds in O(1) per word: word i (thread i % kSegThreads, so a
+    // warp holds the 32 consecutive words of a chunk) is a head if its group
+    // rank differs from word i - 1's; inside a chunk the last head at or
+    // before i and the first head after i come from the warp's ballot of
+    // head flags, across chunks from a scan over the chunks' last and first
+    // heads (exclusive max going up, exclusive max of cnt - first head going
+    // down). Then the word's rank inside its group is the count of the
+    // group's smaller words, and the word goes straight to that index of the
+    // output (the writes of a window stay inside it). Neighbouring lanes hold
+    // neighbouring words of mostly the same group, so the counting reads are
+    // broadcasts. A window holding a group longer than kSegSmall is sorted
+    // whole below and written again.
+    constexpr int kChunks = kSegCap / 32;
+    const int lane = threadIdx.x & 31;
+    for (int i = threadIdx.x; i < kChunks * 32; i += kSegThreads) {
+        const bool hd = i < cnt && (i == 0 || (sw[i] >> 40) != (sw[i - 1] >> 40));
+        const uint32_t m = __ballot_sync(LFC_FULL, hd);
+        if (lane == 0) {
+            const int base = i;  // i is the chunk's first word here
+            s_last[i >> 5] = m ? base + 31 - __clz(m) : -1;
+            s_first[i >> 5] = m ? base + __ffs(m) - 1 : -1;
+        }
+    }
+    __syncthreads();
+    {
+        const int t = threadIdx.x;
+        const int up = t < kChunks ? s_last[t] : -1;
+        const int cd = kChunks - 1 - t;  // chunks taken from the top going down
+        const int dn = (t < kChunks && s_first[cd] >= 0) ? cnt - s_first[cd] : -1;
+        const int before = block_excl_max(up, s_scan);  // last head in a lower chunk
+        const int after = block_excl_max(dn, s_scan);   // cnt - first head in a higher chunk
+        __syncthreads();
+        if (t < kChunks) {
+            s_last[t] = before;
+            s_first[cd] = after >= 0 ? cnt - after : cnt;
+        }
+    }
+    __syncthreads();
     uint64_t *Kout = Kout_all + bo + lo;
     bool gbig = false;
-    for (int i = threadIdx.x; i < cnt; i += kSegThreads) {
-        const uint64_t w = sw[i], r = w >> 40;
-        int gs = i;
-        while (gs > 0 && (sw[gs - 1] >> 40) == r && i - gs < kSegSmall) gs--;
-        int ge = i + 1;
-        while (ge < cnt && (sw[ge] >> 40) == r && ge - gs <= kSegSmall) ge++;
+    const uint32_t le = lanemask_lt() | (1u << lane), gtm = lanemask_gt();
+    for (int i0 = (int)(threadIdx.x & ~31u); i0 < cnt; i0 += kSegThreads) {
+        const int i = i0 + lane;
+        const bool in = i < cnt;
+        const uint64_t w = in ? sw[i] : 0ull;
+        const bool hd = in && (i == 0 || (w >> 40) != (sw[i - 1] >> 40));
+        const uint32_t m = __ballot_sync(LFC_FULL, hd);
+        if (!in) continue;
+        const uint32_t ml = m & le, mg = m & gtm;
+        const int gs = ml ? i0 + 31 - __clz(ml) : s_last[i0 >> 5];
+        const int ge = mg ? i0 + __ffs(mg) - 1 : s_first[i0 >> 5];
         if (ge - gs > kSegSmall) {
             gbig = true;
         } else {

@@ -147,10 +147,13 @@ __device__ __forceinline__ void emit_all_body(const JudgeFrame *__restrict__ fra
     // view-major write-out: thread j -> (u, si) = (j / ns, j % ns), rows v
     const DivU16 div_ns((uint32_t)ns);
     const int vm_j = threadIdx.x, vm_u = (int)div_ns.div((uint32_t)vm_j), vm_si = vm_j - vm_u * ns;
-    // vector stores when every run start is aligned (slots are 256-byte aligned)
+    // vector stores when every run start is aligned (slots are 256-byte aligned;
+    // raw rows: W and the tile's first column multiples of 8 pixels keep every
+    // 8-pixel run on a 16-byte boundary)
+    const bool raw8 = (W % 8) == 0 && ((s0 * p) % 8) == 0 && (nco % 8) == 0;
     const bool raw2 = (W % 2) == 0 && ((s0 * p) % 2) == 0 && (nco % 2) == 0;
     const bool vm8 = (ns % 8) == 0 && (W % 8) == 0 && (Nx % 8) == 0 && (s0 % 8) == 0;
-    const DivU16 div_h((uint32_t)max(nco >> 1, 1)), div_hn((uint32_t)max(ns >> 3, 1));
+    const DivU16 div_h((uint32_t)max(nco >> 1, 1)), div_h8((uint32_t)max(nco >> 3, 1)), div_hn((uint32_t)max(ns >> 3, 1));
     // Writes the symbols get(r, c) of the tile's output pixels (row r of the
     // lenslet row, column c) to candidate k0 in raw order and k1 in view-major
     // order (view v = r, u = c mod p, lenslet s0 + c / p), consecutive threads
@@ -158,7 +161,18 @@ __device__ __forceinline__ void emit_all_body(const JudgeFrame *__restrict__ fra
     auto write_both = [&](int k0, int k1, auto get) {
         if (k0 >= 0) {
             uint16_t *dst = base + (size_t)k0 * cslot16 + (size_t)(t * p) * W + (size_t)s0 * p;
-            if (raw2) {
+            if (raw8) {  // 8 pixels per 16-byte store
+                const int h = nco >> 3;
+                for (int q = threadIdx.x; q < p * h; q += blockDim.x) {
+                    const int r = (int)div_h8.div((uint32_t)q), c8 = 8 * (q - r * h);
+                    uint4 o;
+                    o.x = (uint32_t)get(r, c8) | ((uint32_t)get(r, c8 + 1) << 16);
+                    o.y = (uint32_t)get(r, c8 + 2) | ((uint32_t)get(r, c8 + 3) << 16);
+                    o.z = (uint32_t)get(r, c8 + 4) | ((uint32_t)get(r, c8 + 5) << 16);
+                    o.w = (uint32_t)get(r, c8 + 6) | ((uint32_t)get(r, c8 + 7) << 16);
+                    *reinterpret_cast<uint4 *>(dst + (size_t)r * W + c8) = o;
+                }
+            } else if (raw2) {
                 const int h = nco >> 1;
                 for (int q = threadIdx.x; q < p * h; q += blockDim.x) {
                     const int r = (int)div_h.div((uint32_t)q), c2 = 2 * (q - r * h);
