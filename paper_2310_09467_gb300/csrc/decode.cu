@@ -4,8 +4,10 @@
 // One CTA per bzip2 stream. Every read of the coded stream is checked
 // against its length and every write against its buffer, so corrupt input
 // ends in an error flag, never an out-of-bounds access.
-//  1. thread 0: headers, tables, Huffman decoding, inverse RUNA/RUNB and MTF
-//     (sequential by nature) -> the BWT last column L;
+//  1. thread 0: headers and tables; the CTA: a lookup table per Huffman
+//     table (codes up to 10 bits in one lookup); warp 0: Huffman decoding,
+//     inverse RUNA/RUNB and MTF (sequential by nature; the MTF list in the
+//     warp's registers) -> the BWT last column L;
 //  2. the CTA: LF mapping T[j] = C[L[j]] + rank of j among equal bytes (a
 //     stable counting sort of L with per-warp counters);
 //  3. 1024 walkers invert the BWT: each starts at its own row (walker 0 at
@@ -35,19 +37,43 @@ struct DecBlock {
     int32_t pad;
 };
 
+// MSB-first bit reader over a bounded byte string: up to 64 bits buffered
+// left-aligned, each byte loaded once. get(k) (k <= 32) past the end sets
+// err and returns 0; peek(k) pads with zeros past the end.
 struct BitReader {
     const uint8_t *p;
-    int64_t nbits, pos;
+    int64_t nbytes, next;  // bytes in the string, next byte to load
+    uint64_t buf;          // buffered bits, left-aligned
+    int bcnt;              // buffered bit count
     bool err;
-    __device__ uint32_t get(int k) {
-        if (pos + k > nbits) { err = true; pos = nbits; return 0; }
-        uint32_t v = 0;
-        for (int i = 0; i < k; i++) {
-            const int64_t q = pos + i;
-            v = (v << 1) | ((p[q >> 3] >> (7 - (q & 7))) & 1u);
+    __device__ void init(const uint8_t *src, int64_t n) {
+        p = src;
+        nbytes = n;
+        next = 0;
+        buf = 0;
+        bcnt = 0;
+        err = false;
+    }
+    __device__ __forceinline__ void refill() {
+        while (bcnt <= 56 && next < nbytes) {
+            buf |= (uint64_t)p[next++] << (56 - bcnt);
+            bcnt += 8;
         }
-        pos += k;
-        return v;
+    }
+    __device__ __forceinline__ uint32_t peek(int k) {
+        if (bcnt < k) refill();
+        return (uint32_t)(buf >> (64 - k));
+    }
+    __device__ __forceinline__ bool skip(int k) {
+        if (bcnt < k) refill();
+        if (bcnt < k) { err = true; bcnt = 0; buf = 0; return false; }
+        buf <<= k;
+        bcnt -= k;
+        return true;
+    }
+    __device__ __forceinline__ uint32_t get(int k) {
+        const uint32_t v = peek(k);
+        return skip(k) ? v : 0u;
     }
 };
 
@@ -82,6 +108,9 @@ struct DecShared {
     uint8_t len[6][258];
     int32_t first[6][22], count[6][22], pidx[6][22];
     uint16_t perm[6][258];
+    uint16_t lut[6][1 << 10];  // next 10 bits -> (symbol << 5) | code length, 0: longer code
+    BitReader br;              // the header reader, handed from the parse to the decode loop
+    int32_t alpha, block_max;
     uint32_t red[32];
     int32_t status, nblock, orig, n_in_use, n_groups, n_sel, out_len;
     uint32_t stored_crc;
@@ -110,9 +139,9 @@ __global__ void __launch_bounds__(kDecThreads) bzip2_decode_kernel(const DecBloc
     }
     if (tid == 0) {
         S.status = DEC_OK;
-        BitReader br{D.src, D.src_len * 8, 0, false};
+        BitReader br;
+        br.init(D.src, D.src_len);
         int st = DEC_OK;
-        int nblock = 0;
         do {
             if (br.get(8) != 'B' || br.get(8) != 'Z' || br.get(8) != 'h') { st = DEC_BAD_MAGIC; break; }
             const uint32_t lvl = br.get(8);
@@ -178,8 +207,54 @@ __global__ void __launch_bounds__(kDecThreads) bzip2_decode_kernel(const DecBloc
                     code = (code + cnt) << 1;
                 }
             }
-            // Huffman decoding with inverse RUNA/RUNB and MTF
-            for (int k = 0; k < niu; k++) S.mtf[k] = (uint8_t)k;
+            S.n_in_use = niu;
+            S.n_groups = ng;
+            S.n_sel = nsel;
+            S.alpha = alpha;
+            S.block_max = block_max;
+            S.orig = orig;
+            S.br = br;
+        } while (0);
+        S.status = st;
+    }
+    __syncthreads();
+    if (S.status != DEC_OK) {
+        if (tid == 0) status[b] = S.status;
+        return;
+    }
+    // lookup tables: entry i of table t decodes the code whose first bits are
+    // i (as 10 bits), if that code is at most 10 bits long
+    for (int q = tid; q < S.n_groups * 1024; q += blockDim.x) {
+        const int t = q >> 10, i = q & 1023;
+        uint16_t e = 0;
+        for (int l = 1; l <= 10; l++) {
+            const uint32_t d = (uint32_t)((int32_t)(i >> (10 - l)) - S.first[t][l]);
+            if (d < (uint32_t)S.count[t][l]) {
+                e = (uint16_t)((S.perm[t][S.pidx[t][l] + (int)d] << 5) | l);
+                break;
+            }
+        }
+        S.lut[t][i] = e;
+    }
+    __syncthreads();
+    if (tid < 32) {
+        // warp 0 decodes: every lane keeps the same bit reader and takes the
+        // same branches (its loads are broadcasts); the MTF list lives in
+        // registers, 8 bytes per lane (lane l holds positions 8l .. 8l + 7,
+        // position 8l + k in bits 8k), so moving index j to the front is a
+        // shift by one byte of positions 1 .. j with the byte carried in from
+        // the lane below, whatever j is
+        const int lane = tid;
+        BitReader br = S.br;
+        const int niu = S.n_in_use, nsel = S.n_sel, alpha = S.alpha, block_max = S.block_max;
+        uint64_t lst = 0;
+        for (int k = 7; k >= 0; k--) {
+            const int v = 8 * lane + k;
+            lst = (lst << 8) | (uint64_t)(v < niu ? v : 0);
+        }
+        int st = DEC_OK;
+        int nblock = 0;
+        do {
             int gi = 0, in_group = 0, t = 0;
             int64_t run = 0, run_w = 1;
             for (;;) {
@@ -189,15 +264,22 @@ __global__ void __launch_bounds__(kDecThreads) bzip2_decode_kernel(const DecBloc
                     in_group = 50;
                 }
                 in_group--;
-                int32_t c = 0;
                 int s = -1;
-                for (int l = 1; l <= 20; l++) {
-                    c = (c << 1) | (int32_t)br.get(1);
-                    if (br.err) break;
-                    const uint32_t d = (uint32_t)(c - S.first[t][l]);
-                    if (d < (uint32_t)S.count[t][l]) { s = S.perm[t][S.pidx[t][l] + (int)d]; break; }
+                const uint32_t e = S.lut[t][br.peek(10)];
+                if (e) {
+                    if (!br.skip(e & 31)) { st = DEC_TRUNC; break; }
+                    s = e >> 5;
+                } else {  // a code longer than 10 bits: canonical search from 11 bits
+                    int32_t c = (int32_t)br.peek(10);
+                    if (!br.skip(10)) { st = DEC_TRUNC; break; }
+                    for (int l = 11; l <= 20; l++) {
+                        c = (c << 1) | (int32_t)br.get(1);
+                        if (br.err) break;
+                        const uint32_t d = (uint32_t)(c - S.first[t][l]);
+                        if (d < (uint32_t)S.count[t][l]) { s = S.perm[t][S.pidx[t][l] + (int)d]; break; }
+                    }
+                    if (br.err) { st = DEC_TRUNC; break; }
                 }
-                if (br.err) { st = DEC_TRUNC; break; }
                 if (s < 0) { st = DEC_BAD_DATA; break; }
                 if (s <= 1) {
                     run += (int64_t)(s + 1) * run_w;
@@ -207,26 +289,39 @@ __global__ void __launch_bounds__(kDecThreads) bzip2_decode_kernel(const DecBloc
                 }
                 if (run > 0) {
                     if (nblock + run > block_max || nblock + run > kBlockCap) { st = DEC_OVERFLOW; break; }
-                    const uint8_t v = S.seq_to_unseq[S.mtf[0]];
-                    for (int64_t q = 0; q < run; q++) L[nblock++] = v;
+                    const uint8_t v = S.seq_to_unseq[__shfl_sync(LFC_FULL, (uint32_t)lst, 0) & 255u];
+                    for (int64_t q = lane; q < run; q += 32) L[nblock + q] = v;
+                    nblock += (int)run;
                     run = 0;
                     run_w = 1;
                 }
                 if (s == alpha - 1) break;  // EOB
-                const int j = s - 1;
+                const int j = s - 1;  // >= 1
                 if (j >= niu) { st = DEC_BAD_DATA; break; }
-                const uint8_t v = S.mtf[j];
-                for (int q = j; q > 0; q--) S.mtf[q] = S.mtf[q - 1];
-                S.mtf[0] = v;
+                const uint64_t holder = __shfl_sync(LFC_FULL, lst, j >> 3);
+                const uint32_t v = (uint32_t)(holder >> (8 * (j & 7))) & 255u;
+                const uint64_t below = __shfl_up_sync(LFC_FULL, lst, 1) >> 56;  // position 8l - 1
+                const uint64_t shifted = (lst << 8) | (lane > 0 ? below : 0ull);
+                // this lane's positions 8l + k in [1, j]
+                const int k0 = lane == 0 ? 1 : 0, k1 = min(7, j - 8 * lane);
+                uint64_t msk = 0;
+                if (k1 >= k0) {
+                    const uint64_t upto = k1 == 7 ? ~0ull : ((1ull << (8 * (k1 + 1))) - 1ull);
+                    msk = upto & ~((1ull << (8 * k0)) - 1ull);
+                }
+                lst = (shifted & msk) | (lst & ~msk);
+                if (lane == 0) lst = (lst & ~0xFFull) | v;
                 if (nblock >= block_max || nblock >= kBlockCap) { st = DEC_OVERFLOW; break; }
-                L[nblock++] = S.seq_to_unseq[v];
+                if (lane == 0) L[nblock] = S.seq_to_unseq[v];
+                nblock++;
             }
             if (st != DEC_OK) break;
-            if (orig >= nblock) { st = DEC_BAD_ORIG; break; }
-            S.orig = orig;
+            if (S.orig >= nblock) { st = DEC_BAD_ORIG; break; }
         } while (0);
-        S.status = st;
-        S.nblock = nblock;
+        if (lane == 0) {
+            S.status = st;
+            S.nblock = nblock;
+        }
     }
     __syncthreads();
     if (S.status != DEC_OK) {
