@@ -556,17 +556,18 @@ def main():
     # the other modelled kernels are listed too. judge_hist: chain_hist_kernel
     # reads every candidate stream once, K n per frame; judge_emit:
     # emit_all_kernel reads the frame and writes the K candidate streams,
-    # (K + 1) n per frame (n = 2 W H bytes); bwt_sort8: the 8 phase-1 passes of
-    # radix_sweep_kernel<0> over the E RLE1 elements of a step: the first reads
-    # the bytes (1 B) and writes (key, element) pairs (12 B), the other seven
-    # read and write pairs (24 B): (13 + 7 x 24) E per step, 8 launches (the
-    # stage also holds the byte histogram and the work-item kernel, ~3 % of it).
+    # (K + 1) n per frame (n = 2 W H bytes); bwt_sort8: the 8 phase-1 LSD
+    # passes of radix_sweep_kernel<0> over the E RLE1 elements of a step, each
+    # reading and writing every 12-byte (key, element) pair: 8 x 24 E per step,
+    # 8 launches (the keys, byte histograms and work items are the bwt_keys
+    # stage).
     K = 26
     elems = (bc1["input_bytes"] - bc0["input_bytes"]) / max(1, bc1["calls"] - bc0["calls"]) * args.steps
     models = {"judge_hist": ("chain_hist_kernel", K * raw_bytes * args.steps, "K*n per frame, K=26, n=2*W*H", None),
               "judge_emit": ("emit_all_kernel", (K + 1) * raw_bytes * args.steps, "(K+1)*n per frame, K=26, n=2*W*H", None),
-              "bwt_sort8": ("radix_sweep_kernel", (13 + 7 * 24) * elems,
-                            "(13 + 7*24) B per RLE1 element over the 8 phase-1 passes", 8 * args.steps)}
+              "bwt_sort8": ("radix_sweep_kernel", 8 * 24 * elems,
+                            "24 B per RLE1 element per phase-1 pass (12-byte pair read and written), 8 passes",
+                            8 * args.steps)}
     peak, peak_kind = peaks()
     lines = {}
     for key, (kname, kbytes, kmodel, nl) in models.items():

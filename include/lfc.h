@@ -287,7 +287,7 @@ enum {
     LFC_STAGE_EMIT,           /* chosen symbol streams */
     LFC_STAGE_CRC,            /* raw-frame and block CRCs */
     LFC_STAGE_RLE1,
-    LFC_STAGE_BWT_SORT8,      /* 8-byte prefix radix sort */
+    LFC_STAGE_BWT_SORT8,      /* 8-byte prefix radix sort: the 8 LSD passes */
     LFC_STAGE_BWT_REFINE,     /* prefix-doubling rounds */
     LFC_STAGE_BWT_OUT,        /* last column, origin, bytes in use */
     LFC_STAGE_MTF,            /* MTF and RUNA/RUNB coding */
@@ -295,6 +295,7 @@ enum {
     LFC_STAGE_PACK,
     LFC_STAGE_CONTAINER,
     LFC_STAGE_JUDGE_EMIT,     /* every candidate stream of the judged frames */
+    LFC_STAGE_BWT_KEYS,       /* prefix keys, byte histograms, sort work items */
     LFC_NUM_STAGES
 };
 int lfc_plan_set_timing(lfc_plan plan, int enable);

@@ -893,7 +893,14 @@ __global__ void __launch_bounds__(256) heads_scan_kernel(int32_t *__restrict__ r
 
 // Pass B: rank[v] = head position of v's group; the suffix array takes the
 // sorted tied elements (MODE 1); elements still tied are compacted into the
-// next round's lists.
+// next round's lists. A thread walks 16 consecutive elements for the scans
+// (the last head before each element, the compacted offsets) and stages per
+// element its group's head and its offset in the compacted lists (-1: not
+// tied) in shared memory; the outputs are then written by consecutive
+// threads on consecutive elements, so the suffix-array and list stores are
+// coalesced (only rank[v] is a scatter).
+__device__ __forceinline__ int pad32(int i) { return i + (i >> 5); }  // conflict-free for both access patterns
+
 template <int MODE>
 __global__ void __launch_bounds__(kSortThreads) heads_apply_kernel(const int32_t *__restrict__ rs, const BlockState *__restrict__ st,
                                                                    const int32_t *__restrict__ sorted_all, const uint64_t *__restrict__ words_all,
@@ -904,6 +911,8 @@ __global__ void __launch_bounds__(kSortThreads) heads_apply_kernel(const int32_t
                                                                    int32_t *__restrict__ val_out_all) {
     __shared__ int32_t shm[33];
     __shared__ int32_t shs[33];
+    __shared__ int32_t s_head[kTile + kTile / 32];  // head position of the element's group
+    __shared__ int32_t s_off[kTile + kTile / 32];   // offset in the compacted lists, -1: not tied
     if (rs[kRsAbort]) return;
     const int b = blockIdx.y, tile = blockIdx.x;
     const int h = round_h<MODE>(rs);
@@ -925,11 +934,13 @@ __global__ void __launch_bounds__(kSortThreads) heads_apply_kernel(const int32_t
     int32_t *sa = sa_all + bo;
     int32_t *act_out = act_out_all + bo;
     int32_t *val_out = val_out_all + bo;
-    const int k0 = tile * kTile + threadIdx.x * kPerThread;
+    const int t0 = tile * kTile;
+    const int kl0 = threadIdx.x * kPerThread;
+    const int k0 = t0 + kl0;
     const int k1 = min(n, k0 + kPerThread);
     int mine = -1, tied = 0;
-    // a full run loads flags, positions and elements with 16-byte loads; the
-    // block scans are reached by every thread
+    // a full run loads flags and positions with 16-byte loads; the block
+    // scans are reached by every thread
     const bool full = k0 + kPerThread <= n;
     uint32_t fw[4] = {0u, 0u, 0u, 0u};
     bool last_next = true;
@@ -966,48 +977,35 @@ __global__ void __launch_bounds__(kSortThreads) heads_apply_kernel(const int32_t
     carry = max(carry, aux[2]);
     int off = block_excl_sum<int>(tied, shs, nullptr) + aux[3];
     if (full) {
-        int32_t vv[kPerThread];
-#pragma unroll
-        for (int q = 0; q < kPerThread; q += 4) {
-            if (MODE == 0) {
-                const int4 s4 = *reinterpret_cast<const int4 *>(sorted + k0 + q);
-                vv[q] = s4.x; vv[q + 1] = s4.y; vv[q + 2] = s4.z; vv[q + 3] = s4.w;
-            } else {
-                const ulonglong2 w0 = *reinterpret_cast<const ulonglong2 *>(words + k0 + q);
-                const ulonglong2 w1 = *reinterpret_cast<const ulonglong2 *>(words + k0 + q + 2);
-                vv[q] = (int32_t)(w0.x & kElemMask); vv[q + 1] = (int32_t)(w0.y & kElemMask);
-                vv[q + 2] = (int32_t)(w1.x & kElemMask); vv[q + 3] = (int32_t)(w1.y & kElemMask);
-            }
-        }
 #pragma unroll
         for (int q = 0; q < kPerThread; q++) {
             const bool hd = (fw[q >> 2] >> (8 * (q & 3))) & 1u;
             const bool nh = q + 1 < kPerThread ? ((fw[(q + 1) >> 2] >> (8 * ((q + 1) & 3))) & 1u) : last_next;
-            const int pos = pv[q];
-            if (hd) carry = pos;
-            const int32_t v = vv[q];
-            rank[v] = carry;
-            if (MODE == 1 || sorted != sa) sa[pos] = v;
-            if (!(hd && nh)) {
-                act_out[off] = pos;
-                val_out[off] = v;
-                off++;
-            }
+            if (hd) carry = pv[q];
+            s_head[pad32(kl0 + q)] = carry;
+            s_off[pad32(kl0 + q)] = (hd && nh) ? -1 : off++;
         }
-        return;
+    } else {
+        for (int k = k0; k < k1; k++) {
+            const bool hd = flags[k];
+            const bool nh = (k + 1 >= n) || flags[k + 1];
+            if (hd) carry = MODE == 0 ? k : act[k];
+            s_head[pad32(k - t0)] = carry;
+            s_off[pad32(k - t0)] = (hd && nh) ? -1 : off++;
+        }
     }
-    for (int k = k0; k < k1; k++) {
-        const bool hd = flags[k];
-        const bool nh = (k + 1 >= n) || flags[k + 1];
+    __syncthreads();
+    const int cnt = min(kTile, n - t0);
+    for (int j = threadIdx.x; j < cnt; j += kSortThreads) {
+        const int k = t0 + j;
         const int pos = MODE == 0 ? k : act[k];
-        if (hd) carry = pos;
         const int32_t v = MODE == 0 ? sorted[k] : (int32_t)(words[k] & kElemMask);
-        rank[v] = carry;
+        rank[v] = s_head[pad32(j)];
         if (MODE == 1 || sorted != sa) sa[pos] = v;
-        if (!(hd && nh)) {
-            act_out[off] = pos;
-            val_out[off] = v;
-            off++;
+        const int o = s_off[pad32(j)];
+        if (o >= 0) {
+            act_out[o] = pos;
+            val_out[o] = v;
         }
     }
 }
@@ -1215,7 +1213,7 @@ cudaError_t launch_bwt(lfc_plan P, int nblocks, int max_m) {
     if (e != cudaSuccess) return e;
     // phase 1: prefix keys and the digit totals of all passes, then 8 LSD
     // passes (keys, sa) -> (keys2, sa2) -> ... -> (keys, sa)
-    stage_begin(P, LFC_STAGE_BWT_SORT8);
+    stage_begin(P, LFC_STAGE_BWT_KEYS);
     dim3 grid(tiles, nblocks);
     const size_t nd = (size_t)nblocks * kSweepPasses * 256;
     zero_u32_kernel<<<(unsigned)std::min<size_t>(64, (nd + 255) / 256), 256, 0, s>>>(ws.dhist, nd);
@@ -1224,6 +1222,8 @@ cudaError_t launch_bwt(lfc_plan P, int nblocks, int max_m) {
     count_launches(P, 3);
     uint64_t *kin = ws.keys, *kout = ws.keys2;
     int32_t *vin = ws.sa, *vout = ws.sa2;
+    stage_end(P, LFC_STAGE_BWT_KEYS);
+    stage_begin(P, LFC_STAGE_BWT_SORT8);
     const int ctas = sweep_ctas(P, nblocks, tiles);
     for (int pass = 8 - kPhase1Bytes; pass < 8; pass++) {
         sweep_pass<0>(P, s, nblocks, ctas, pass, kin, vin, kout, vout);

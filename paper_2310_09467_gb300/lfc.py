@@ -35,7 +35,7 @@ EXPORTS = ["lfc_plan_create", "lfc_plan_destroy", "lfc_plan_last_error", "lfc_ju
            "lfc_plan_inject_fault", "lfc_bwt_blocks"]
 
 STAGES = ["judge_hist", "judge_score", "emit", "crc", "rle1", "bwt_sort8", "bwt_refine", "bwt_out", "mtf",
-          "huffman", "pack", "container", "judge_emit"]
+          "huffman", "pack", "container", "judge_emit", "bwt_keys"]
 
 
 class LfcError(RuntimeError):
