@@ -419,11 +419,26 @@ __global__ void __launch_bounds__(kSortThreads) round_digits_kernel(const int32_
 // largest count x nblocks (items past a block's last tile are skipped); both
 // work queues start empty. One CTA.
 // In a round (MODE 1) only the blocks flagged by the segmented sort (a group
-// longer than its window) take the radix passes.
+// longer than its window) take the radix passes. In phase 1 (MODE 0) it also
+// writes row 1 of every block's digit totals: the exclusive prefix of row 0
+// (the byte histogram), i.e. the block's elements with a smaller digit, the
+// same for every pass and tile.
 template <int MODE>
 __global__ void __launch_bounds__(1024) sort_items_kernel(int32_t *__restrict__ rs, const BlockState *__restrict__ st, int nblocks,
-                                                          const int32_t *__restrict__ big) {
+                                                          const int32_t *__restrict__ big, uint32_t *__restrict__ dhist_all) {
     __shared__ int smax;
+    if (MODE == 0) {
+        const int lane = threadIdx.x & 31;
+        for (int bb = threadIdx.x >> 5; bb < nblocks; bb += blockDim.x >> 5) {
+            uint32_t *row = dhist_all + (size_t)bb * kSweepPasses * 256;
+            uint32_t c[8], t = 0;
+#pragma unroll
+            for (int i = 0; i < 8; i++) { c[i] = row[lane * 8 + i]; t += c[i]; }
+            uint32_t x = warp_incl_sum(t) - t;
+#pragma unroll
+            for (int i = 0; i < 8; i++) { row[256 + lane * 8 + i] = x; x += c[i]; }
+        }
+    }
     const bool abort = rs[kRsAbort] != 0;
     const int h = round_h<MODE>(rs);
     if (threadIdx.x == 0) smax = 0;
@@ -677,11 +692,16 @@ radix_sweep_kernel(int pass, int nblocks, int32_t *__restrict__ rs, const BlockS
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31, d = threadIdx.x;
     const int shift = digit_shift<MODE>(pass);
     const uint32_t lt = lanemask_lt(), gt = lanemask_gt();
+    // the next work item is taken while the current one is sorted (its ticket
+    // is larger, so every tile still only waits on tiles taken before it)
+    int nxt = 0;
+    if (threadIdx.x == 0) nxt = atomicAdd(queue, 1);
     for (;;) {
         if (threadIdx.x == 0) {
-            s_item = atomicAdd(queue, 1);
+            s_item = nxt;
             s_abort = ld_volatile_i32(rs + kRsAbort);
             s_fault = ld_volatile_i32(rs + kRsFault);
+            nxt = atomicAdd(queue, 1);
         }
         for (int i = threadIdx.x; i < NW * 256; i += kSortThreads) wcnt[i] = 0;
         __syncthreads();
@@ -694,6 +714,8 @@ radix_sweep_kernel(int pass, int nblocks, int32_t *__restrict__ rs, const BlockS
         }
         const int n = sort_count<MODE>(st[b], h);
         const size_t bo = (size_t)b * kBlockCap;
+        // phase 1: the block's elements with a smaller digit (row 1, see sort_items_kernel)
+        const uint32_t below1 = MODE == 0 ? dhist_all[((size_t)b * kSweepPasses + 1) * 256 + d] : 0u;
         const uint64_t *Kin = Kin_all + bo;
         const int32_t *Vin = Vin_all + bo;
         uint64_t keys[kPerThread];
@@ -752,9 +774,9 @@ radix_sweep_kernel(int pass, int nblocks, int32_t *__restrict__ rs, const BlockS
             if (!gave_up) st_status(lbb + (size_t)tile * 256 + d, kLbIncl | (excl + cnt_d));
         }
         lb_next[(size_t)b * kLbBlockWords + (size_t)tile * 256 + d] = 0;
-        const int drow = MODE == 0 ? 0 : pass;  // phase 1: every pass has the block's byte histogram
-        const uint32_t below = block_excl_sum<uint32_t>(
-            dhist_all[((size_t)b * kSweepPasses + drow) * 256 + d], sh, nullptr);  // block elements with a smaller digit
+        const uint32_t below = MODE == 0 ? below1
+                                         : block_excl_sum<uint32_t>(dhist_all[((size_t)b * kSweepPasses + pass) * 256 + d],
+                                                                    sh, nullptr);  // block elements with a smaller digit
         gbase[d] = below + excl;
         if (withhold && d == 0) atomicExch(rs + kRsFault, 0);  // the fault fires once
         if (__syncthreads_or(gave_up)) break;
@@ -1174,7 +1196,7 @@ static void bwt_round(lfc_plan P, cudaStream_t st, int nblocks, int tiles, int m
     // the words instead: keys -> keys2 -> ... -> keys2
     segsort_kernel<<<g1, kSegThreads, kSegSmem, st>>>(ws.act_total, ws.bstate, ws.keys, ws.keys2, ws.segbig);
     round_digits_kernel<<<g1, kSortThreads, 0, st>>>(ws.act_total, ws.bstate, ws.keys, ws.dhist, ws.segbig);
-    sort_items_kernel<1><<<1, 1024, 0, st>>>(ws.act_total, ws.bstate, nblocks, ws.segbig);
+    sort_items_kernel<1><<<1, 1024, 0, st>>>(ws.act_total, ws.bstate, nblocks, ws.segbig, nullptr);
     count_launches(P, 6);
     const int ctas = sweep_ctas(P, nblocks, tiles);
     for (int pass = 0; pass < 5; pass++) {
@@ -1218,7 +1240,7 @@ cudaError_t launch_bwt(lfc_plan P, int nblocks, int max_m) {
     const size_t nd = (size_t)nblocks * kSweepPasses * 256;
     zero_u32_kernel<<<(unsigned)std::min<size_t>(64, (nd + 255) / 256), 256, 0, s>>>(ws.dhist, nd);
     key8_kernel<<<grid, kSortThreads, 0, s>>>(ws.bstate, ws.rle, ws.keys, ws.sa, ws.dhist, ws.lbstat, ws.lbstat_words);
-    sort_items_kernel<0><<<1, 1024, 0, s>>>(ws.act_total, ws.bstate, nblocks, nullptr);
+    sort_items_kernel<0><<<1, 1024, 0, s>>>(ws.act_total, ws.bstate, nblocks, nullptr, ws.dhist);
     count_launches(P, 3);
     uint64_t *kin = ws.keys, *kout = ws.keys2;
     int32_t *vin = ws.sa, *vout = ws.sa2;
