@@ -64,6 +64,8 @@ def _load():
         "lfc_orc_compress_id": (i64, [P, P, i32, i32, i32, i32, i32, P, i64]),
         "lfc_orc_compress": (i64, [P, P, i32, i32, i32, P, i32, i32, P, i64, P]),
         "lfc_orc_container_info": (i32, [P, i64, P, P, P, P]),
+        "lfc_orc_realign": (None, [P, i64, i32, P]),
+        "lfc_orc_unrealign": (None, [P, i64, i32, P]),
         "lfc_orc_decompress": (i32, [P, i64, P, P]),
     }
     for name, (res, args) in sig.items():
@@ -93,9 +95,14 @@ def id_valid(cid: int) -> bool:
     return bool(_load().lfc_orc_id_valid(int(cid)))
 
 
-def make_id(f: int, domain: int = 0, ordering: int = 0, temporal: int = 0) -> int:
-    """Candidate id bit layout: f | domain << 4 | ordering << 6 | temporal << 7."""
-    return f | (domain << 4) | (ordering << 6) | (temporal << 7)
+def make_id(f: int, domain: int = 0, ordering: int = 0, temporal: int = 0, planar: int = 0) -> int:
+    """Candidate id bit layout: f | planar << 3 | domain << 4 | ordering << 6 | temporal << 7."""
+    return f | (planar << 3) | (domain << 4) | (ordering << 6) | (temporal << 7)
+
+
+def planar_ids(temporal: bool = False) -> list[int]:
+    """The default set with the planar byte layout (bit 3) instead."""
+    return [c | 8 for c in default_ids(temporal)]
 
 
 def default_ids(temporal: bool = False) -> list[int]:
@@ -135,10 +142,20 @@ def inverse_symbols(stream, W: int, H: int, pitch: int, cid: int, prev=None) -> 
     return out
 
 
-def stream_bytes(sym: np.ndarray) -> np.ndarray:
-    """Realign uint16 symbols to bytes, (lo, hi) per symbol."""
-    return _u16(sym).view(np.uint8).copy() if np.little_endian else \
-        _u16(sym).byteswap().view(np.uint8).copy()
+def stream_bytes(sym: np.ndarray, planar: bool = False) -> np.ndarray:
+    """Realign uint16 symbols to bytes (lfc_orc_realign): (lo, hi) per
+    symbol, or planar (all high bytes, then all low bytes)."""
+    z = _u16(sym).ravel()
+    out = np.empty(2 * z.size, dtype=np.uint8)
+    _load().lfc_orc_realign(_ptr(z), z.size, 1 if planar else 0, _ptr(out))
+    return out
+
+
+def unrealign(S, planar: bool = False) -> np.ndarray:
+    S = _u8(S)
+    z = np.empty(S.size // 2, dtype=np.uint16)
+    _load().lfc_orc_unrealign(_ptr(S), z.size, 1 if planar else 0, _ptr(z))
+    return z
 
 
 # --------------------------------------------------------------------- judge

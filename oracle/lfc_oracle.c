@@ -16,6 +16,9 @@
  *   lfc_orc_symbols / lfc_orc_inverse_symbols : exact inverse (round trip),
  *       textbook lossless-JPEG predictor values on hand-made frames, the
  *       ordering is a bijection on pixel indices.
+ *   lfc_orc_realign / lfc_orc_unrealign       : the coded blocks, decoded by
+ *       the stock bzip2 decoder, are the frame's byte planes (numpy) for
+ *       layout 1 and its little-endian bytes for layout 0.
  *   lfc_orc_judge_last / lfc_orc_bigram      : brute force "generate every
  *       rotation, stable sort by first byte, take the last column".
  *   lfc_orc_log2_fx / lfc_orc_score          : closed forms (constant input
@@ -39,12 +42,15 @@
 /* ------------------------------------------------------------------------ */
 /* Candidate id (Sec. 2.1.4: the predictor is one unsigned 8-bit integer).   */
 /* Library reading of the missing Fig. 3 table:                             */
-/*   bits 0-3 predictor function f (0 none, 1..7 lossless-JPEG set)         */
+/*   bits 0-2 predictor function f (0 none, 1..7 lossless-JPEG set)         */
+/*   bit  3   byte layout of the realigned stream (0 (lo, hi) per symbol,   */
+/*            1 split into planes: every high byte, then every low byte)    */
 /*   bits 4-5 domain (0 intra-lenslet, 1 inter-lenslet, 2 phase space)      */
 /*   bit  6   ordering (0 lenslet-major raw layout, 1 view-major)           */
 /*   bit  7   temporal delta against the previous frame                     */
 /* ------------------------------------------------------------------------ */
-#define ID_F(id) ((id) & 15)
+#define ID_F(id) ((id) & 7)
+#define ID_PLANAR(id) (((id) >> 3) & 1)
 #define ID_DOMAIN(id) (((id) >> 4) & 3)
 #define ID_ORDER(id) (((id) >> 6) & 1)
 #define ID_TEMPORAL(id) (((id) >> 7) & 1)
@@ -52,7 +58,6 @@
 int lfc_orc_id_valid(int id)
 {
     if (id < 0 || id > 255) return 0;
-    if (ID_F(id) > 7) return 0;
     if (ID_DOMAIN(id) > 2) return 0;
     if (ID_F(id) == 0 && ID_DOMAIN(id) != 0) return 0;
     return 1;
@@ -230,6 +235,33 @@ int lfc_orc_symbols(const uint16_t *X, const uint16_t *prev, int W, int H, int p
     return 0;
 }
 
+/* Realign the uint16 symbol stream to the byte string that is judged and
+ * coded (Sec. 2.1.2: the 16-bit predicted image realigned as an 8-bit string;
+ * Fig. 2c splits each 16-bit value into its high and low 8 bits). Layout 0:
+ * (lo, hi) per symbol; layout 1 (planar): the high bytes of all symbols in
+ * stream order, then their low bytes. */
+void lfc_orc_realign(const uint16_t *z, int64_t nsym, int planar, uint8_t *S)
+{
+    for (int64_t k = 0; k < nsym; k++) {
+        if (planar) {
+            S[k] = (uint8_t)(z[k] >> 8);
+            S[nsym + k] = (uint8_t)(z[k] & 0xFF);
+        } else {
+            S[2 * k] = (uint8_t)(z[k] & 0xFF);
+            S[2 * k + 1] = (uint8_t)(z[k] >> 8);
+        }
+    }
+}
+
+/* Inverse of lfc_orc_realign. */
+void lfc_orc_unrealign(const uint8_t *S, int64_t nsym, int planar, uint16_t *z)
+{
+    for (int64_t k = 0; k < nsym; k++) {
+        if (planar) z[k] = (uint16_t)(((uint16_t)S[k] << 8) | S[nsym + k]);
+        else z[k] = (uint16_t)(S[2 * k] | ((uint16_t)S[2 * k + 1] << 8));
+    }
+}
+
 /* Inverse of lfc_orc_symbols (Fig. 2b: the inverse predictor chosen by the
  * header). Pixels are restored in raster order, which is causal for every
  * domain: each neighbour used above lies above or to the left. */
@@ -369,10 +401,7 @@ int lfc_orc_judge(const uint16_t *X, const uint16_t *prev, int W, int H, int p,
     uint64_t best_score = 0;
     for (int c = 0; c < K; c++) {
         if (lfc_orc_symbols(X, prev, W, H, p, ids[c], z) != 0) { best = -1; break; }
-        for (int64_t k = 0; k < nsym; k++) {
-            S[2 * k] = (uint8_t)(z[k] & 0xFF);
-            S[2 * k + 1] = (uint8_t)(z[k] >> 8);
-        }
+        lfc_orc_realign(z, nsym, ID_PLANAR(ids[c]), S);
         lfc_orc_judge_last(S, n, L);
         lfc_orc_bigram(L, n, hist);
         uint64_t sc = lfc_orc_score(hist);
@@ -938,12 +967,8 @@ int64_t lfc_orc_compress_id(const uint16_t *X, const uint16_t *prev, int W, int 
     uint8_t *S = (uint8_t *)malloc((size_t)n);
     uint8_t *raw = (uint8_t *)malloc((size_t)n);
     lfc_orc_symbols(X, prev, W, H, p, id, z);
-    for (int64_t k = 0; k < nsym; k++) {
-        S[2 * k] = (uint8_t)(z[k] & 0xFF);
-        S[2 * k + 1] = (uint8_t)(z[k] >> 8);
-        raw[2 * k] = (uint8_t)(X[k] & 0xFF);
-        raw[2 * k + 1] = (uint8_t)(X[k] >> 8);
-    }
+    lfc_orc_realign(z, nsym, ID_PLANAR(id), S);
+    lfc_orc_realign(X, nsym, 0, raw); /* the CRC covers the raw frame, (lo, hi) per pixel */
     memcpy(out, "LFC1", 4);
     wr16(out + 4, 1);
     wr16(out + 6, ID_TEMPORAL(id) ? 1u : 0u);
@@ -1017,7 +1042,7 @@ int lfc_orc_decompress(const uint8_t *in, int64_t n, const uint16_t *prev, uint1
         o += sz;
     }
     if (rc == 0) {
-        for (int64_t k = 0; k < nsym; k++) z[k] = (uint16_t)(S[2 * k] | ((uint16_t)S[2 * k + 1] << 8));
+        lfc_orc_unrealign(S, nsym, ID_PLANAR(id), z);
         lfc_orc_inverse_symbols(z, prev, W, H, p, id, X);
         uint8_t *raw = S; /* reuse as the raw frame bytes */
         for (int64_t k = 0; k < nsym; k++) { raw[2 * k] = (uint8_t)(X[k] & 0xFF); raw[2 * k + 1] = (uint8_t)(X[k] >> 8); }

@@ -94,3 +94,25 @@ def test_judge_matches_fp64_argmin():
         N = 2 * fr.size - 1
         for cid, sc, e in zip(ids, scores, H):
             assert abs((math.log2(N) - sc / (N * 2 ** 32)) - e) < 1e-7
+
+
+def test_judge_planar_against_brute_force():
+    """The planar layout's score: brute-force judge-BWT over the byte planes
+    of the symbols (numpy), scored by the closed-form-pinned fixed point."""
+    from paper_2310_09467_gb300 import synth
+    fr = synth.beads(26, 26, 13, peak=200.0, seed=2)
+    p = 13
+    ids = [oracle.make_id(0), oracle.make_id(0, planar=1), oracle.make_id(5, 2, 1), oracle.make_id(5, 2, 1, planar=1)]
+    best, scores = oracle.judge(fr, p, ids)
+    for cid, sc in zip(ids, scores):
+        z = oracle.symbols(fr, p, cid).astype(np.uint16)
+        if cid & 8:
+            S = list((z >> 8).astype(np.uint8)) + list((z & 0xFF).astype(np.uint8))
+        else:
+            S = list(z.astype("<u2").view(np.uint8))
+        L = brute_judge_last([int(v) for v in S])
+        h = np.zeros(65536, dtype=np.uint32)
+        for a, b in zip(L[:-1], L[1:]):
+            h[(a << 8) | b] += 1
+        assert sc == oracle.score(h), hex(cid)
+    assert best == ids[int(np.argmax(np.array(scores, dtype=object)))]

@@ -128,7 +128,8 @@ def test_temporal_zero_motion():
 
 def test_invalid_ids_rejected():
     assert not oracle.id_valid(0x10)   # f = 0 needs domain 0
-    assert not oracle.id_valid(0x08)   # f = 8 undefined
+    assert oracle.id_valid(0x08)       # bit 3 is the planar byte layout, not part of f
+    assert not oracle.id_valid(0x18)   # f = 0 needs domain 0 in either layout
     assert not oracle.id_valid(0x34)   # domain 3 undefined
     assert len(oracle.default_ids()) == 26
     assert len(oracle.default_ids(True)) == 52
