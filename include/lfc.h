@@ -46,9 +46,12 @@ typedef enum {
 /* Candidate (predictor) id: one unsigned 8-bit integer, stored in the header
  * (Sec. 2.1.4). The paper's mapping table (Fig. 3) is not available; this
  * library's layout is
- *   bits 0-3  f: 0 none, 1 A, 2 B, 3 C, 4 A+B-C, 5 A+(B-C)/2, 6 B+(A-C)/2,
+ *   bits 0-2  f: 0 none, 1 A, 2 B, 3 C, 4 A+B-C, 5 A+(B-C)/2, 6 B+(A-C)/2,
  *             7 (A+B)/2  -- the lossless-JPEG set of Sec. 3 / Fig. 3b, with
  *             A = left, B = top, C = top-left and floor division;
+ *   bit  3    byte layout of the realigned stream (Sec. 2.1.2, Fig. 2c):
+ *             0 (lo, hi) per symbol, 1 planar -- the high bytes of all
+ *             symbols in stream order, then their low bytes;
  *   bits 4-5  domain: 0 intra-lenslet (neighbouring pixels in one microlens),
  *             1 inter-lenslet (same pixel of the neighbouring microlenses),
  *             2 phase space (intra residual predicted again across
@@ -56,9 +59,10 @@ typedef enum {
  *   bit  6    ordering: 0 raw lenslet-major layout, 1 view-major mosaic
  *             out[v*Ny + t][u*Nx + s] = in[t*p + v][s*p + u];
  *   bit  7    temporal: predict the difference to the previous raw frame.
- * Valid ids: f <= 7, domain <= 2, and f == 0 only with domain 0. */
+ * Valid ids: domain <= 2, and f == 0 only with domain 0. */
 #define LFC_ID(f, domain, ordering, temporal) \
     ((uint8_t)((f) | ((domain) << 4) | ((ordering) << 6) | ((temporal) << 7)))
+#define LFC_ID_PLANAR(id) ((uint8_t)((id) | 8))
 
 /* Largest input block per bzip2 stream. RLE1 grows a block by at most 5/4,
  * so a block always fits one level-9 bzip2 block (900000 bytes). */
@@ -115,7 +119,7 @@ const char *lfc_plan_last_error(lfc_plan plan);
 
 /* Two-dimensional image entropy criterion (Sec. 2.1.2, Eq. (1), Fig. 2c).
  * For each frame and each candidate id: the symbol stream (prediction,
- * symbol map, ordering, 16-to-8-bit realign as (lo, hi) per symbol) is
+ * symbol map, ordering, 16-to-8-bit realign in the id's byte layout) is
  * sorted by the first byte of every rotation only, ties in generation
  * order; adjacent bytes of the last column form 16-bit values; their
  * histogram P_t gives score = sum_t P_t * L2(P_t), L2(c) = 2^32 log2(c) in

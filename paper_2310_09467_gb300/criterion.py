@@ -53,7 +53,9 @@ def study_frame(plan, lfc, frame_np, pitch, ids, block_bytes=720000, prev_np=Non
         _, sz, _ = plan.compress([d], pitch, prevs=None if dp is None else [dp], choice=ch)
         sizes.append(int(sz.cpu()[0]))
         z = plan.symbols(d, pitch, cid, prev=dp)
-        S = z.view(torch.uint8).reshape(-1)
+        S = z.view(torch.uint8).reshape(-1)  # (lo, hi) per symbol
+        if cid & 8:  # planar layout: the high bytes, then the low bytes
+            S = torch.cat([S[1::2], S[0::2]])
         n = S.numel()
         offs = list(range(0, n, block_bytes))
         L, ln, _ = plan.bwt_blocks(S, offs, [min(block_bytes, n - o) for o in offs])

@@ -32,8 +32,9 @@ int fail(lfc_plan P, int code, const std::string &what, cudaError_t e = cudaSucc
     } while (0)
 
 bool id_valid(int id) {
-    const int f = id & 15, dom = (id >> 4) & 3;
-    return id >= 0 && id < 256 && f <= 7 && dom <= 2 && !(f == 0 && dom != 0);
+    if (id < 0 || id > 255) return false;
+    const int f = id_f(id), dom = id_dom(id);
+    return dom <= 2 && !(f == 0 && dom != 0);
 }
 
 int64_t stream_bound(int64_t L) {
@@ -314,7 +315,7 @@ extern "C" int lfc_plan_create(const lfc_config *cfg, void *cuda_stream, lfc_pla
     const int JF = P->judge_frames_cap, BC = P->block_cap;
     const int64_t seg_min = chain_seg_bytes(16384);  // smallest tunable segment
     const int64_t segs_max = (n_max + seg_min - 1) / seg_min;
-    ws.summ_cap = (int64_t)JF * kMaxCand * segs_max;
+    ws.summ_cap = (int64_t)JF * K * segs_max;
     ws.cstream_kmax = K;
     ws.cstream_slot = (n_max + 255) & ~(int64_t)255;
     ws.stream_slot = (n_max + 255) & ~(int64_t)255;
@@ -324,7 +325,7 @@ extern "C" int lfc_plan_create(const lfc_config *cfg, void *cuda_stream, lfc_pla
     cudaError_t e = cudaSuccess;
 #define AL(ptr, count)                                           \
     if (e == cudaSuccess) e = dalloc(&ws.ptr, (size_t)(count));
-    AL(hist, (size_t)JF * kMaxCand * kHistBins);
+    AL(hist, (size_t)JF * K * kHistBins);
     AL(summ, (size_t)ws.summ_cap * 512);
     AL(scores, (size_t)F * 256);
     AL(choice, (size_t)F);
@@ -529,7 +530,7 @@ int build_judge(lfc_plan P, const lfc_frame *frames, int n, Arena &A, std::vecto
             if (tmp)
                 for (uint8_t id : P->ids_temporal) cand.push_back(id);
             for (size_t k = J.cand_off; k < cand.size(); k++) {
-                const int id = cand[k], f = id & 15, dom = (id >> 4) & 3;
+                const int id = cand[k], f = id_f(id), dom = id_dom(id);
                 if (f && dom != 1) fset[(id >> 7) & 1] |= 1u << f;
                 if (f) fall[(id >> 7) & 1] |= 1u << f;
             }

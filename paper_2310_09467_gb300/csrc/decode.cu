@@ -516,9 +516,12 @@ __global__ void inv_residual_kernel(InvFrame F) {
     const int64_t n = (int64_t)F.W * F.H;
     for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x) {
         const int y = (int)(k / F.W), x = (int)(k % F.W);
-        const uint32_t z = F.Z[stream_index(F, y, x)];
-        const int f = F.id & 15;
-        const bool tmp = (F.id >> 7) & 1;
+        const size_t si = stream_index(F, y, x);
+        // planar layout: high bytes of all symbols, then their low bytes
+        const uint8_t *Z8 = reinterpret_cast<const uint8_t *>(F.Z);
+        const uint32_t z = id_planar(F.id) ? ((uint32_t)Z8[si] << 8) | Z8[(size_t)n + si] : F.Z[si];
+        const int f = id_f(F.id);
+        const bool tmp = id_tmp(F.id);
         F.E[k] = (f == 0 && !tmp) ? (int32_t)z : as_s16(unzig(z));
     }
 }
@@ -531,7 +534,7 @@ __global__ void inv_inter_kernel(InvFrame F, int signed_field) {
     const int view = blockIdx.x * blockDim.x + threadIdx.x;
     if (view >= p * p) return;
     const int v = view / p, u = view % p;
-    const int f = F.id & 15;
+    const int f = id_f(F.id);
     for (int t = 0; t < Ny; t++) {
         for (int s = 0; s < Nx; s++) {
             const size_t k = (size_t)(t * p + v) * F.W + s * p + u;
@@ -550,7 +553,7 @@ __global__ void inv_intra_kernel(InvFrame F, int signed_field) {
     const int lens = blockIdx.x * blockDim.x + threadIdx.x;
     if (lens >= Nx * Ny) return;
     const int t = lens / Nx, s = lens % Nx;
-    const int f = F.id & 15;
+    const int f = id_f(F.id);
     for (int v = 0; v < p; v++) {
         for (int u = 0; u < p; u++) {
             const size_t k = (size_t)(t * p + v) * F.W + s * p + u;
@@ -591,8 +594,8 @@ cudaError_t launch_inverse_predict(lfc_plan P, const uint16_t *Z, const uint16_t
                                    int W, int H, int p, int id) {
     InvFrame F{Z, prev, X, E, W, H, p, id};
     cudaStream_t s = P->stream;
-    const int f = id & 15, dom = (id >> 4) & 3;
-    const bool tmp = (id >> 7) & 1;
+    const int f = id_f(id), dom = id_dom(id);
+    const bool tmp = id_tmp(id);
     inv_residual_kernel<<<1216, 256, 0, s>>>(F);
     int launches = 2;
     if (f != 0) {

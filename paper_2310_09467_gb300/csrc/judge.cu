@@ -93,8 +93,8 @@ __device__ __forceinline__ uint32_t phase_res(const FrameDev &F, int f, int y, i
 
 // Symbol of pixel (y, x) under candidate id.
 __device__ __forceinline__ uint32_t pixel_symbol(const FrameDev &F, int id, int y, int x) {
-    const int f = id & 15, dom = (id >> 4) & 3;
-    const bool tmp = (id >> 7) & 1;
+    const int f = id_f(id), dom = id_dom(id);
+    const bool tmp = id_tmp(id);
     uint32_t e;
     if (f == 0) {
         if (!tmp) return __ldg(F.X + (size_t)y * F.W + x);
@@ -122,14 +122,20 @@ __device__ __forceinline__ int col_to_raw_x(const FrameDev &F, int ord, int c) {
     return ord ? (c % F.Nx) * F.p + c / F.Nx : c;
 }
 
-// Last byte of stream row r - 1 (the byte before the row's first byte);
-// for r = 0 the stream's last byte (rotation 0 wraps around).
+// The judged byte string as rows: the (lo, hi) layout has H rows of 2W
+// bytes (stream row r); the planar layout 2H rows of W bytes, rows r < H the
+// high bytes of stream row r, rows H + r its low bytes.
+__device__ __forceinline__ int byte_rows(const FrameDev &F, int id) { return id_planar(id) ? 2 * F.H : F.H; }
+
+// Last byte of byte row r - 1 (the byte before the row's first byte); for
+// r = 0 the string's last byte (rotation 0 wraps around).
 __device__ __forceinline__ uint32_t byte_before_row(const FrameDev &F, int id, int r) {
-    const int ord = (id >> 6) & 1;
-    int rr = r == 0 ? F.H - 1 : r - 1;
-    int y = stream_row_to_y(F, ord, rr);
-    int x = col_to_raw_x(F, ord, F.W - 1);
-    return pixel_symbol(F, id, y, x) >> 8;
+    const int ord = id_ord(id);
+    const int rr = (r == 0 ? byte_rows(F, id) : r) - 1;
+    const int sr = rr % F.H;  // stream row
+    const uint32_t z = pixel_symbol(F, id, stream_row_to_y(F, ord, sr), col_to_raw_x(F, ord, F.W - 1));
+    const bool low = id_planar(id) && rr >= F.H;
+    return low ? (z & 0xFFu) : (z >> 8);
 }
 
 // ------------------------------------------------------------ the judge
@@ -161,18 +167,19 @@ judge_hist_kernel(const JudgeFrame *__restrict__ frames, int nframes, const uint
     const int64_t local = (int64_t)blockIdx.x - J.cta_base;
     const int ci = (int)(local / J.segs), seg = (int)(local % J.segs);
     const int id = cand[J.cand_off + ci];
-    const int ord = (id >> 6) & 1;
+    const int ord = id_ord(id);
+    const bool planar = id_planar(id);
     uint32_t *ghist = hist + (size_t)(J.hist_off + ci) * kHistBins;
 
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int r_seg0 = seg * J.rows_per_seg;
-    const int r_seg1 = min(F.H, r_seg0 + J.rows_per_seg);
+    const int r_seg1 = min(byte_rows(F, id), r_seg0 + J.rows_per_seg);
     const int rpw = (r_seg1 - r_seg0 + kJudgeWarps - 1) / kJudgeWarps;
     const int r0 = min(r_seg1, r_seg0 + w * rpw), r1 = min(r_seg1, r0 + rpw);
     uint16_t *zrow = sh_rows + (size_t)w * maxW;
     const uint8_t *zbytes = reinterpret_cast<const uint8_t *>(zrow);
     uint16_t *my_first = sh_first + w * 256, *my_last = sh_last + w * 256;
-    const int nb = 2 * F.W;
+    const int nb = planar ? F.W : 2 * F.W;  // bytes per row
 
     uint32_t carry0 = 0;
     if (r0 < r1) carry0 = byte_before_row(F, id, r0);  // uniform per warp
@@ -183,14 +190,17 @@ judge_hist_kernel(const JudgeFrame *__restrict__ frames, int nframes, const uint
         __syncthreads();
         uint32_t prev_byte = carry0;
         for (int r = r0; r < r1; r++) {
-            const int y = stream_row_to_y(F, ord, r);
+            const int sr = r % F.H;                                 // stream row of byte row r
+            const int sh = planar ? (r < F.H ? 8 : 0) : 0;          // planar: the high or the low bytes
+            const int y = stream_row_to_y(F, ord, sr);
             for (int x = lane; x < F.W; x += 32) zrow[raw_x_to_col(F, ord, x)] = (uint16_t)pixel_symbol(F, id, y, x);
             __syncwarp();
+            auto row_byte = [&](int q) -> uint32_t { return planar ? ((uint32_t)zrow[q] >> sh) & 0xFFu : zbytes[q]; };
             for (int base = 0; base < nb; base += 32) {
                 const int q = base + lane;
                 const bool valid = q < nb;
-                const uint32_t b = valid ? zbytes[q] : 0u;
-                const uint32_t a = valid ? (q > 0 ? (uint32_t)zbytes[q - 1] : prev_byte) : 0u;
+                const uint32_t b = valid ? row_byte(q) : 0u;
+                const uint32_t a = valid ? (q > 0 ? row_byte(q - 1) : prev_byte) : 0u;
                 const uint32_t m = __match_any_sync(LFC_FULL, valid ? b : 256u + lane);
                 const uint32_t lower = m & lanemask_lt();
                 const int pl = lower ? 31 - __clz(lower) : lane;
@@ -212,7 +222,7 @@ judge_hist_kernel(const JudgeFrame *__restrict__ frames, int nframes, const uint
                 const uint32_t hm = __match_any_sync(LFC_FULL, contrib ? (uint32_t)bin : 0x10000u + lane);
                 if (contrib && (hm & lanemask_lt()) == 0) atomicAdd(&sh_hist[bin & 0x7FFF], __popc(hm));
             }
-            prev_byte = zbytes[nb - 1];
+            prev_byte = row_byte(nb - 1);
             __syncwarp();
         }
         __syncthreads();
@@ -439,13 +449,21 @@ __global__ void emit_kernel(EmitArgs args, const uint8_t *__restrict__ choice, i
     const FrameDev F = args.F[f];
     int id = choice[f];
     if ((id & 0x80) && !F.prev) id &= 0x7F;  // no reference frame: never read through NULL
-    const int ord = (id >> 6) & 1;
+    const int ord = id_ord(id);
+    const bool planar = id_planar(id);
     const int64_t n = (int64_t)F.W * F.H;
     uint16_t *out = reinterpret_cast<uint16_t *>(args.dst[f]);
+    uint8_t *out8 = args.dst[f];
     for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x) {
         const int r = (int)(k / F.W), c = (int)(k % F.W);
         const int y = stream_row_to_y(F, ord, r), x = col_to_raw_x(F, ord, c);
-        out[k] = (uint16_t)pixel_symbol(F, id, y, x);
+        const uint32_t z = pixel_symbol(F, id, y, x);
+        if (planar) {
+            out8[k] = (uint8_t)(z >> 8);
+            out8[n + k] = (uint8_t)z;
+        } else {
+            out[k] = (uint16_t)z;
+        }
     }
 }
 
@@ -464,7 +482,7 @@ cudaError_t launch_emit(const FrameDev *h_frames, const uint8_t *d_choice, int n
 }
 
 __global__ void symbols_one_kernel(FrameDev F, int id, uint16_t *out) {
-    const int ord = (id >> 6) & 1;
+    const int ord = id_ord(id);
     const int64_t n = (int64_t)F.W * F.H;
     for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x) {
         const int r = (int)(k / F.W), c = (int)(k % F.W);
@@ -539,7 +557,7 @@ __global__ void noalloc_describe_kernel(NoAllocScratch *s, FrameDev F, IdList id
         J.K = 1;
         J.cand_off = i;
         J.segs = segs;
-        J.rows_per_seg = kNoAllocRowsPerSeg;
+        J.rows_per_seg = id_planar(ids.id[i]) ? 2 * kNoAllocRowsPerSeg : kNoAllocRowsPerSeg;  // 2H rows of W bytes
         J.cta_base = 0;
         J.hist_off = 0;
         J.summ_off = 0;
@@ -572,8 +590,8 @@ extern "C" int lfc_judge_noalloc(const lfc_frame *frame, const uint8_t *h_ids, i
     IdList ids;
     ids.n = n_ids;
     for (int i = 0; i < n_ids; i++) {
-        const int id = h_ids[i], f = id & 15, dom = (id >> 4) & 3;
-        if (f > 7 || dom > 2 || (f == 0 && dom != 0)) return LFC_ERR_INVALID_ARG;
+        const int id = h_ids[i], f = id_f(id), dom = id_dom(id);
+        if (dom > 2 || (f == 0 && dom != 0)) return LFC_ERR_INVALID_ARG;
         if ((id & 0x80) && !frame->prev) return LFC_ERR_INVALID_ARG;
         ids.id[i] = (uint8_t)id;
     }

@@ -70,10 +70,12 @@ size_t emit_all_smem_bytes(int p, int ts, int nslots) {
 // tile's pixels are computed once into shared memory (thread = pixel column,
 // p rows each), then every candidate of that f is written from there in
 // its ordering, consecutive threads on consecutive output positions.
-template <int kind>
+// PL: the candidate set holds planar-layout ids (otherwise their stores
+// compile away).
+template <int kind, bool PL>
 __device__ __forceinline__ void emit_all_body(const JudgeFrame *__restrict__ frames, const uint8_t *__restrict__ cand,
                                               uint8_t *__restrict__ cstream, int64_t cslot, int kmax, int TS,
-                                              uint8_t *esm, int16_t (*slot_of)[3][2], int8_t *eslot_of) {
+                                              uint8_t *esm, int16_t (*slot_of)[3][2][2], int8_t *eslot_of) {
     const int fi = blockIdx.y;
     const JudgeFrame &J = frames[fi];
     const FrameDev F = J.F;
@@ -91,7 +93,7 @@ __device__ __forceinline__ void emit_all_body(const JudgeFrame *__restrict__ fra
         const int id = cand[J.cand_off + k];
         if (((id >> 7) & 1) != kind || !cand_on(J, id)) continue;
         nc++;
-        const int f = id & 15, dom = (id >> 4) & 3;
+        const int f = id_f(id), dom = id_dom(id);
         fany |= 1u << f;
         if (f && dom != 1) fset |= 1u << f;
     }
@@ -101,12 +103,12 @@ __device__ __forceinline__ void emit_all_body(const JudgeFrame *__restrict__ fra
     int16_t *E = reinterpret_cast<int16_t *>(esm) + cells;
     uint16_t *Sy = reinterpret_cast<uint16_t *>(E + (size_t)nslots * cells);  // [3][npx]
     if (threadIdx.x == 0) {
-        for (int i = 0; i < 48; i++) (&slot_of[0][0][0])[i] = -1;
+        for (int i = 0; i < 96; i++) (&slot_of[0][0][0][0])[i] = -1;
         for (int f = 0; f < 8; f++) eslot_of[f] = (int8_t)__popc(fset & ((1u << f) - 1u));
         for (int k = 0; k < J.K; k++) {
             const int id = cand[J.cand_off + k];
             if (((id >> 7) & 1) != kind || !cand_on(J, id)) continue;
-            slot_of[id & 15][(id >> 4) & 3][(id >> 6) & 1] = (int16_t)k;
+            slot_of[id_f(id)][id_dom(id)][id_ord(id)][id_planar(id)] = (int16_t)k;
         }
     }
     const DivU16 div_p((uint32_t)p);
@@ -142,25 +144,39 @@ __device__ __forceinline__ void emit_all_body(const JudgeFrame *__restrict__ fra
         }
     }
     __syncthreads();
-    uint16_t *base = reinterpret_cast<uint16_t *>(cstream + (size_t)fi * kmax * (size_t)cslot);
+    uint8_t *base8 = cstream + (size_t)fi * kmax * (size_t)cslot;
+    uint16_t *base = reinterpret_cast<uint16_t *>(base8);
     const size_t cslot16 = (size_t)cslot / 2;
+    const size_t nsym = (size_t)W * F.H;  // a planar stream's low bytes start here
     // view-major write-out: thread j -> (u, si) = (j / ns, j % ns), rows v
     const DivU16 div_ns((uint32_t)ns);
     const int vm_j = threadIdx.x, vm_u = (int)div_ns.div((uint32_t)vm_j), vm_si = vm_j - vm_u * ns;
     // vector stores when every run start is aligned (slots are 256-byte aligned;
     // raw rows: W and the tile's first column multiples of 8 pixels keep every
-    // 8-pixel run on a 16-byte boundary)
+    // 8-pixel run on a 16-byte boundary, and its planar bytes on 8-byte ones)
     const bool raw8 = (W % 8) == 0 && ((s0 * p) % 8) == 0 && (nco % 8) == 0;
     const bool raw2 = (W % 2) == 0 && ((s0 * p) % 2) == 0 && (nco % 2) == 0;
     const bool vm8 = (ns % 8) == 0 && (W % 8) == 0 && (Nx % 8) == 0 && (s0 % 8) == 0;
     const DivU16 div_h((uint32_t)max(nco >> 1, 1)), div_h8((uint32_t)max(nco >> 3, 1)), div_hn((uint32_t)max(ns >> 3, 1));
+    // 8 symbols (4 words, two per word) as 8 high bytes and 8 low bytes
+    auto put8 = [&](uint8_t *hi, const uint4 &o) {
+        *reinterpret_cast<uint2 *>(hi) = make_uint2(__byte_perm(o.x, o.y, 0x7531), __byte_perm(o.z, o.w, 0x7531));
+        *reinterpret_cast<uint2 *>(hi + nsym) = make_uint2(__byte_perm(o.x, o.y, 0x6420), __byte_perm(o.z, o.w, 0x6420));
+    };
+    auto put1 = [&](uint8_t *hi, uint32_t v) {
+        hi[0] = (uint8_t)(v >> 8);
+        hi[nsym] = (uint8_t)v;
+    };
     // Writes the symbols get(r, c) of the tile's output pixels (row r of the
-    // lenslet row, column c) to candidate k0 in raw order and k1 in view-major
-    // order (view v = r, u = c mod p, lenslet s0 + c / p), consecutive threads
-    // on consecutive output positions.
-    auto write_both = [&](int k0, int k1, auto get) {
-        if (k0 >= 0) {
-            uint16_t *dst = base + (size_t)k0 * cslot16 + (size_t)(t * p) * W + (size_t)s0 * p;
+    // lenslet row, column c) in raw order to candidate k0 ((lo, hi) layout)
+    // and k0p (planar layout), and in view-major order (view v = r, u = c mod
+    // p, lenslet s0 + c / p) to k1 and k1p; consecutive threads on
+    // consecutive output positions, every symbol computed once.
+    auto write_both = [&](int k0, int k1, int k0p, int k1p, auto get) {
+        if (k0 >= 0 || k0p >= 0) {
+            const size_t i0 = (size_t)(t * p) * W + (size_t)s0 * p;  // symbol index of the tile's first pixel
+            uint16_t *dst = k0 >= 0 ? base + (size_t)k0 * cslot16 + i0 : nullptr;
+            uint8_t *dsp = PL && k0p >= 0 ? base8 + (size_t)k0p * cslot + i0 : nullptr;
             if (raw8) {  // 8 pixels per 16-byte store
                 const int h = nco >> 3;
                 for (int q = threadIdx.x; q < p * h; q += blockDim.x) {
@@ -170,22 +186,33 @@ __device__ __forceinline__ void emit_all_body(const JudgeFrame *__restrict__ fra
                     o.y = (uint32_t)get(r, c8 + 2) | ((uint32_t)get(r, c8 + 3) << 16);
                     o.z = (uint32_t)get(r, c8 + 4) | ((uint32_t)get(r, c8 + 5) << 16);
                     o.w = (uint32_t)get(r, c8 + 6) | ((uint32_t)get(r, c8 + 7) << 16);
-                    *reinterpret_cast<uint4 *>(dst + (size_t)r * W + c8) = o;
+                    if (dst) *reinterpret_cast<uint4 *>(dst + (size_t)r * W + c8) = o;
+                    if (dsp) put8(dsp + (size_t)r * W + c8, o);
                 }
             } else if (raw2) {
                 const int h = nco >> 1;
                 for (int q = threadIdx.x; q < p * h; q += blockDim.x) {
                     const int r = (int)div_h.div((uint32_t)q), c2 = 2 * (q - r * h);
-                    *reinterpret_cast<uint32_t *>(dst + (size_t)r * W + c2) =
-                        (uint32_t)get(r, c2) | ((uint32_t)get(r, c2 + 1) << 16);
+                    const uint32_t a = get(r, c2), b = get(r, c2 + 1);
+                    if (dst) *reinterpret_cast<uint32_t *>(dst + (size_t)r * W + c2) = a | (b << 16);
+                    if (dsp) {
+                        *reinterpret_cast<uint16_t *>(dsp + (size_t)r * W + c2) = (uint16_t)((a >> 8) | (b & 0xFF00u));
+                        *reinterpret_cast<uint16_t *>(dsp + nsym + (size_t)r * W + c2) = (uint16_t)((a & 0xFFu) | ((b & 0xFFu) << 8));
+                    }
                 }
             } else {
                 for (int r = 0; r < p; r++)
-                    for (int c = threadIdx.x; c < nco; c += blockDim.x) dst[(size_t)r * W + c] = get(r, c);
+                    for (int c = threadIdx.x; c < nco; c += blockDim.x) {
+                        const uint32_t v = get(r, c);
+                        if (dst) dst[(size_t)r * W + c] = (uint16_t)v;
+                        if (dsp) put1(dsp + (size_t)r * W + c, v);
+                    }
             }
         }
-        if (k1 >= 0) {
-            uint16_t *dst = base + (size_t)k1 * cslot16 + (size_t)t * W + s0;
+        if (k1 >= 0 || k1p >= 0) {
+            const size_t i1 = (size_t)t * W + s0;
+            uint16_t *dst = k1 >= 0 ? base + (size_t)k1 * cslot16 + i1 : nullptr;
+            uint8_t *dsp = PL && k1p >= 0 ? base8 + (size_t)k1p * cslot + i1 : nullptr;
             if (vm8) {
                 const int hn = ns >> 3, items = p * p * hn;
                 for (int q = threadIdx.x; q < items; q += blockDim.x) {
@@ -197,17 +224,26 @@ __device__ __forceinline__ void emit_all_body(const JudgeFrame *__restrict__ fra
                     o.y = (uint32_t)get(v, c + 2 * p) | ((uint32_t)get(v, c + 3 * p) << 16);
                     o.z = (uint32_t)get(v, c + 4 * p) | ((uint32_t)get(v, c + 5 * p) << 16);
                     o.w = (uint32_t)get(v, c + 6 * p) | ((uint32_t)get(v, c + 7 * p) << 16);
-                    *reinterpret_cast<uint4 *>(dst + (size_t)v * Ny * W + (size_t)u * Nx + 8 * hh) = o;
+                    const size_t e = (size_t)v * Ny * W + (size_t)u * Nx + 8 * hh;
+                    if (dst) *reinterpret_cast<uint4 *>(dst + e) = o;
+                    if (dsp) put8(dsp + e, o);
                 }
             } else if (p * ns <= (int)blockDim.x) {
                 if (vm_j < p * ns)
-                    for (int v = 0; v < p; v++)
-                        dst[(size_t)v * Ny * W + (size_t)vm_u * Nx + vm_si] = get(v, vm_si * p + vm_u);
+                    for (int v = 0; v < p; v++) {
+                        const uint32_t val = get(v, vm_si * p + vm_u);
+                        const size_t e = (size_t)v * Ny * W + (size_t)vm_u * Nx + vm_si;
+                        if (dst) dst[e] = (uint16_t)val;
+                        if (dsp) put1(dsp + e, val);
+                    }
             } else {
                 for (int v = 0; v < p; v++)
                     for (int j = threadIdx.x; j < p * ns; j += blockDim.x) {
                         const int u = (int)div_ns.div((uint32_t)j), si = j - u * ns;
-                        dst[(size_t)v * Ny * W + (size_t)u * Nx + si] = get(v, si * p + u);
+                        const uint32_t val = get(v, si * p + u);
+                        const size_t e = (size_t)v * Ny * W + (size_t)u * Nx + si;
+                        if (dst) dst[e] = (uint16_t)val;
+                        if (dsp) put1(dsp + e, val);
                     }
             }
         }
@@ -215,15 +251,17 @@ __device__ __forceinline__ void emit_all_body(const JudgeFrame *__restrict__ fra
     // raw candidates (no predictor) and intra-lenslet candidates straight from
     // the staged frame and the residual fields
     if (fany & 1u)
-        write_both(slot_of[0][0][0], slot_of[0][0][1], [&](int r, int c) -> uint16_t {
+        write_both(slot_of[0][0][0][0], slot_of[0][0][1][0], slot_of[0][0][0][1], slot_of[0][0][1][1], [&](int r, int c) -> uint16_t {
             const int32_t Xv = FVAL((p + r) * TC + p + c);
             return kind ? zz16(Xv) : (uint16_t)Xv;
         });
 #pragma unroll
     for (int f = 1; f < 8; f++) {
-        if (!((fset >> f) & 1u) || (slot_of[f][0][0] < 0 && slot_of[f][0][1] < 0)) continue;
+        if (!((fset >> f) & 1u) || (slot_of[f][0][0][0] < 0 && slot_of[f][0][1][0] < 0 && slot_of[f][0][0][1] < 0 &&
+                                    slot_of[f][0][1][1] < 0))
+            continue;
         const int16_t *Ef = E + (size_t)eslot_of[f] * cells;
-        write_both(slot_of[f][0][0], slot_of[f][0][1],
+        write_both(slot_of[f][0][0][0], slot_of[f][0][1][0], slot_of[f][0][0][1], slot_of[f][0][1][1],
                    [&](int r, int c) -> uint16_t { return zz16(Ef[(p + r) * TC + p + c]); });
     }
     // inter-lenslet candidates of every f in one pass over the pixels, then
@@ -235,7 +273,8 @@ __device__ __forceinline__ void emit_all_body(const JudgeFrame *__restrict__ fra
 #pragma unroll
         for (int f = 1; f < 8; f++) {
             plane[f] = -1;
-            if ((fany >> f) & 1u && (slot_of[f][dom][0] >= 0 || slot_of[f][dom][1] >= 0)) {
+            if ((fany >> f) & 1u && (slot_of[f][dom][0][0] >= 0 || slot_of[f][dom][1][0] >= 0 ||
+                                     slot_of[f][dom][0][1] >= 0 || slot_of[f][dom][1][1] >= 0)) {
                 fm |= 1u << f;
                 plane[f] = np++;
             }
@@ -273,7 +312,7 @@ __device__ __forceinline__ void emit_all_body(const JudgeFrame *__restrict__ fra
         for (int f = 1; f < 8; f++) {
             if (!((fm >> f) & 1u)) continue;
             const uint16_t *src = Sy + (size_t)plane[f] * npx;
-            write_both(slot_of[f][dom][0], slot_of[f][dom][1],
+            write_both(slot_of[f][dom][0][0], slot_of[f][dom][1][0], slot_of[f][dom][0][1], slot_of[f][dom][1][1],
                        [&](int r, int c) -> uint16_t { return src[r * nco + c]; });
         }
         __syncthreads();
@@ -281,14 +320,15 @@ __device__ __forceinline__ void emit_all_body(const JudgeFrame *__restrict__ fra
 #undef FVAL
 }
 
+template <bool PL>
 __global__ void __launch_bounds__(kEmitThreads) emit_all_kernel(const JudgeFrame *__restrict__ frames,
                                                                 const uint8_t *__restrict__ cand, uint8_t *__restrict__ cstream,
                                                                 int64_t cslot, int kmax, int TS) {
     extern __shared__ __align__(16) uint8_t esm[];
-    __shared__ int16_t slot_of[8][3][2];  // candidate index for (f, domain, ordering), -1 if absent
+    __shared__ int16_t slot_of[8][3][2][2];  // candidate index for (f, domain, ordering, layout), -1 if absent
     __shared__ int8_t eslot_of[8];        // intra residual field of f
-    if (blockIdx.z == 0) emit_all_body<0>(frames, cand, cstream, cslot, kmax, TS, esm, slot_of, eslot_of);
-    else emit_all_body<1>(frames, cand, cstream, cslot, kmax, TS, esm, slot_of, eslot_of);
+    if (blockIdx.z == 0) emit_all_body<0, PL>(frames, cand, cstream, cslot, kmax, TS, esm, slot_of, eslot_of);
+    else emit_all_body<1, PL>(frames, cand, cstream, cslot, kmax, TS, esm, slot_of, eslot_of);
 }
 
 // ------------------------------------------------------ pair-chain histogram
@@ -547,11 +587,15 @@ chain_hist_kernel(const JudgeFrame *__restrict__ frames, int nframes, const uint
 cudaError_t launch_emit_all(lfc_plan P, const JudgeFrame *d_frames, int nframes, const uint8_t *d_cand, int max_tiles,
                             int TS, int nslots_max, int any_temporal, int max_p) {
     const size_t smem = emit_all_smem_bytes(max_p, TS, nslots_max);
-    cudaError_t e = cudaFuncSetAttribute(emit_all_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    bool planar = false;
+    for (uint8_t id : P->ids_spatial) planar |= id_planar(id) != 0;
+    for (uint8_t id : P->ids_temporal) planar |= id_planar(id) != 0;
+    auto kern = planar ? emit_all_kernel<true> : emit_all_kernel<false>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     dim3 grid(max_tiles, nframes, any_temporal ? 2 : 1);
-    emit_all_kernel<<<grid, kEmitThreads, smem, P->stream>>>(d_frames, d_cand, P->ws.cstream, P->ws.cstream_slot,
-                                                             P->ws.cstream_kmax, TS);
+    kern<<<grid, kEmitThreads, smem, P->stream>>>(d_frames, d_cand, P->ws.cstream, P->ws.cstream_slot,
+                                                  P->ws.cstream_kmax, TS);
     count_launches(P, 1);
     return cudaGetLastError();
 }

@@ -24,7 +24,7 @@ constexpr int kMaxAlpha = 258;                       // bzip2 symbols: 256 MTF +
 constexpr int kMaxGroups = 6;
 constexpr int kMaxSelectors = 18002;
 constexpr int kHistBins = 65536;
-constexpr int kMaxCand = 52;                         // 26 spatial + 26 temporal by default
+constexpr int kMaxCand = 104;                        // candidates per frame: 26 default ids x 2 byte layouts x 2 (temporal)
 constexpr int kSortCtlHead = 16;                     // sort state words before the per-block tile offsets
 constexpr int kSortFaultWord = 5;                    // sort state word of the fault-injection test hook
 constexpr int kSortStickyWord = 9;                   // sort state word kept until lfc_plan_device_status reads it
@@ -104,6 +104,16 @@ __device__ __forceinline__ int block_excl_max(int v, int *sh) {
     return r;
 }
 
+// ------------------------------------------------------------ candidate ids
+// Fields of a candidate id (include/lfc.h): f bits 0-2, byte layout bit 3
+// (1: planar, high bytes then low bytes), domain bits 4-5, ordering bit 6,
+// temporal bit 7.
+__host__ __device__ __forceinline__ int id_f(int id) { return id & 7; }
+__host__ __device__ __forceinline__ int id_planar(int id) { return (id >> 3) & 1; }
+__host__ __device__ __forceinline__ int id_dom(int id) { return (id >> 4) & 3; }
+__host__ __device__ __forceinline__ int id_ord(int id) { return (id >> 6) & 1; }
+__host__ __device__ __forceinline__ int id_tmp(int id) { return (id >> 7) & 1; }
+
 // ------------------------------------------------------------- descriptors
 // One frame as the kernels see it.
 struct FrameDev {
@@ -157,7 +167,7 @@ static_assert(sizeof(BlockState) == 80, "BlockState layout");
 // ------------------------------------------------------------------ plan
 struct Workspace {
     // judge
-    uint32_t *hist = nullptr;      // judge_frames_cap * kMaxCand * 65536
+    uint32_t *hist = nullptr;      // judge_frames_cap * K * 65536
     uint16_t *summ = nullptr;      // per judge CTA: first[256], last[256]
     uint8_t *chain_first = nullptr;  // per SM: the chain kernel's first-predecessor bytes
     int chain_nsm = 0;               // SM slots of chain_first (%nsmid)

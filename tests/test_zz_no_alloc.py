@@ -142,6 +142,24 @@ print("ok")
 '''
 
 
+def test_noalloc_judge_planar_ids():
+    """The default ids and their planar twins (id bit 3: the judged string
+    is 2H rows of W high bytes, then W low bytes), against the oracle:
+    vector-width and odd-width frames, and 600 rows (5 segments)."""
+    import torch
+    from paper_2310_09467_gb300 import build, lfc
+    build.build()
+    lib = lfc.load()
+    ids = sorted(oracle.default_ids() + oracle.planar_ids())
+    for fr, p in ((synth.beads(195, 195, 13, peak=2000.0, seed=0), 13), (synth.cells(96, 102, 3, seed=8), 3),
+                  (synth.beads(300, 600, 15, peak=200.0, seed=21), 15)):
+        best, ref = oracle.judge(fr, p, ids)
+        d = lfc.to_device_frame(fr)
+        ch, got = _call(lib, torch, _frame_struct(lfc, d, fr.shape, p), ids)
+        assert got == ref
+        assert ch == best
+
+
 def test_noalloc_judge_after_device_reset():
     """The scratch array is re-created (zeroed, possibly elsewhere) when the
     device's context is: calls after cudaDeviceReset must still find it and
