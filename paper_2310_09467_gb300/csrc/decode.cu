@@ -5,9 +5,10 @@
 // against its length and every write against its buffer, so corrupt input
 // ends in an error flag, never an out-of-bounds access.
 //  1. thread 0: headers and tables; the CTA: a lookup table per Huffman
-//     table (codes up to 10 bits in one lookup); warp 0: Huffman decoding,
-//     inverse RUNA/RUNB and MTF (sequential by nature; the MTF list in the
-//     warp's registers) -> the BWT last column L;
+//     table (codes up to 10 bits in one lookup); then, pipelined through a
+//     ring in shared memory, thread 0 decodes the Huffman symbols and warp 1
+//     does inverse RUNA/RUNB and MTF (each sequential by nature; the MTF
+//     list in the warp's registers) -> the BWT last column L;
 //  2. the CTA: LF mapping T[j] = C[L[j]] + rank of j among equal bytes (a
 //     stable counting sort of L with per-warp counters);
 //  3. 1024 walkers invert the BWT: each starts at its own row (walker 0 at
@@ -26,8 +27,13 @@ constexpr uint32_t kPolyD = 0x04C11DB7u;
 
 enum : int32_t {
     DEC_OK = 0, DEC_BAD_MAGIC = 1, DEC_TRUNC = 2, DEC_BAD_TABLE = 3, DEC_BAD_DATA = 4,
-    DEC_OVERFLOW = 5, DEC_BAD_ORIG = 6, DEC_BAD_LEN = 7, DEC_BAD_CRC = 8, DEC_BAD_WALK = 9
+    DEC_OVERFLOW = 5, DEC_BAD_ORIG = 6, DEC_BAD_LEN = 7, DEC_BAD_CRC = 8, DEC_BAD_WALK = 9, DEC_TIMEOUT = 10
 };
+
+// Huffman decoding (thread 0) hands its symbols to the MTF warp (warp 1)
+// through a ring in shared memory; each side's wait is bounded.
+constexpr int kRing = 4096;                       // symbols in flight
+constexpr long long kDecWaitCycles = 4000000000ll; // about 2 s at the SM clock
 
 struct DecBlock {
     const uint8_t *src;   // one standalone bzip2 stream
@@ -114,7 +120,12 @@ struct DecShared {
     uint32_t red[32];
     int32_t status, nblock, orig, n_in_use, n_groups, n_sel, out_len;
     uint32_t stored_crc;
+    uint16_t ring[kRing];       // Huffman symbols from thread 0 to warp 1
+    int32_t prod, cons, stop, pstatus;  // symbols published / released, stop flag, the decoder's status
 };
+
+__device__ __forceinline__ int32_t vld(const int32_t &x) { return *reinterpret_cast<const volatile int32_t *>(&x); }
+__device__ __forceinline__ void vst(int32_t &x, int32_t v) { *reinterpret_cast<volatile int32_t *>(&x) = v; }
 
 // Workspace per block: sel (kMaxSelectors bytes), L (kBlockCap), T (int32
 // kBlockCap), rowmark (int32 kBlockCap, walker id or -1), blk (kBlockCap).
@@ -237,88 +248,147 @@ __global__ void __launch_bounds__(kDecThreads) bzip2_decode_kernel(const DecBloc
         S.lut[t][i] = e;
     }
     __syncthreads();
-    if (tid < 32) {
-        // warp 0 decodes: every lane keeps the same bit reader and takes the
-        // same branches (its loads are broadcasts); the MTF list lives in
+    if (tid == 0) {
+        S.prod = 0;
+        S.cons = 0;
+        S.stop = 0;
+        S.pstatus = DEC_OK;
+    }
+    __syncthreads();
+    if (tid == 0) {
+        // Huffman decoding: symbols into the ring, published every 32 and at
+        // the end; waits while the ring is full
+        BitReader br = S.br;
+        const int nsel = S.n_sel, alpha = S.alpha;
+        int st = DEC_OK, n = 0, cons_seen = 0, gi = 0, in_group = 0, t = 0;
+        for (;;) {
+            if (in_group == 0) {
+                if (gi >= nsel) { st = DEC_BAD_DATA; break; }
+                t = sel[gi++];
+                in_group = 50;
+            }
+            in_group--;
+            int sym = -1;
+            const uint32_t e = S.lut[t][br.peek(10)];
+            if (e) {
+                if (!br.skip(e & 31)) { st = DEC_TRUNC; break; }
+                sym = e >> 5;
+            } else {  // a code longer than 10 bits: canonical search from 11 bits
+                int32_t c = (int32_t)br.peek(10);
+                if (!br.skip(10)) { st = DEC_TRUNC; break; }
+                for (int l = 11; l <= 20; l++) {
+                    c = (c << 1) | (int32_t)br.get(1);
+                    if (br.err) break;
+                    const uint32_t d = (uint32_t)(c - S.first[t][l]);
+                    if (d < (uint32_t)S.count[t][l]) { sym = S.perm[t][S.pidx[t][l] + (int)d]; break; }
+                }
+                if (br.err) { st = DEC_TRUNC; break; }
+            }
+            if (sym < 0) { st = DEC_BAD_DATA; break; }
+            if (n - cons_seen >= kRing) {
+                const long long t0 = clock64();
+                while (n - (cons_seen = vld(S.cons)) >= kRing) {
+                    if (vld(S.stop)) break;
+                    if (clock64() - t0 > kDecWaitCycles) { st = DEC_TIMEOUT; break; }
+                }
+                if (st != DEC_OK || n - cons_seen >= kRing) break;  // timed out, or the MTF warp stopped
+            }
+            *reinterpret_cast<volatile uint16_t *>(&S.ring[n & (kRing - 1)]) = (uint16_t)sym;
+            n++;
+            if ((n & 31) == 0 || sym == alpha - 1) {
+                __threadfence_block();
+                vst(S.prod, n);
+                if (vld(S.stop)) break;
+            }
+            if (sym == alpha - 1) break;  // EOB
+        }
+        if (st != DEC_OK) {
+            vst(S.pstatus, st);
+            __threadfence_block();
+            vst(S.stop, 1);
+        }
+    } else if (tid >= 32 && tid < 64) {
+        // warp 1: inverse RUNA/RUNB and MTF. The MTF list lives in
         // registers, 8 bytes per lane (lane l holds positions 8l .. 8l + 7,
         // position 8l + k in bits 8k), so moving index j to the front is a
         // shift by one byte of positions 1 .. j with the byte carried in from
         // the lane below, whatever j is
-        const int lane = tid;
-        BitReader br = S.br;
-        const int niu = S.n_in_use, nsel = S.n_sel, alpha = S.alpha, block_max = S.block_max;
+        const int lane = tid - 32;
+        const int niu = S.n_in_use, alpha = S.alpha, block_max = S.block_max;
         uint64_t lst = 0;
         for (int k = 7; k >= 0; k--) {
             const int v = 8 * lane + k;
             lst = (lst << 8) | (uint64_t)(v < niu ? v : 0);
         }
         int st = DEC_OK;
-        int nblock = 0;
-        do {
-            int gi = 0, in_group = 0, t = 0;
-            int64_t run = 0, run_w = 1;
-            for (;;) {
-                if (in_group == 0) {
-                    if (gi >= nsel) { st = DEC_BAD_DATA; break; }
-                    t = sel[gi++];
-                    in_group = 50;
-                }
-                in_group--;
-                int s = -1;
-                const uint32_t e = S.lut[t][br.peek(10)];
-                if (e) {
-                    if (!br.skip(e & 31)) { st = DEC_TRUNC; break; }
-                    s = e >> 5;
-                } else {  // a code longer than 10 bits: canonical search from 11 bits
-                    int32_t c = (int32_t)br.peek(10);
-                    if (!br.skip(10)) { st = DEC_TRUNC; break; }
-                    for (int l = 11; l <= 20; l++) {
-                        c = (c << 1) | (int32_t)br.get(1);
-                        if (br.err) break;
-                        const uint32_t d = (uint32_t)(c - S.first[t][l]);
-                        if (d < (uint32_t)S.count[t][l]) { s = S.perm[t][S.pidx[t][l] + (int)d]; break; }
+        int nblock = 0, c = 0, avail = 0;
+        int64_t run = 0, run_w = 1;
+        for (;;) {
+            if (c == avail) {  // wait for published symbols (lane 0 polls, the warp follows)
+                int got = 0, code = DEC_OK;
+                if (lane == 0) {
+                    const long long t0 = clock64();
+                    for (;;) {
+                        const int pv = vld(S.prod);
+                        if (pv > c) { got = pv; break; }
+                        if (vld(S.stop)) {
+                            code = vld(S.pstatus);
+                            if (code == DEC_OK) code = DEC_BAD_DATA;
+                            break;
+                        }
+                        if (clock64() - t0 > kDecWaitCycles) { code = DEC_TIMEOUT; break; }
                     }
-                    if (br.err) { st = DEC_TRUNC; break; }
+                    __threadfence_block();
                 }
-                if (s < 0) { st = DEC_BAD_DATA; break; }
-                if (s <= 1) {
-                    run += (int64_t)(s + 1) * run_w;
-                    run_w <<= 1;
-                    if (run > block_max) { st = DEC_OVERFLOW; break; }
-                    continue;
-                }
-                if (run > 0) {
-                    if (nblock + run > block_max || nblock + run > kBlockCap) { st = DEC_OVERFLOW; break; }
-                    const uint8_t v = S.seq_to_unseq[__shfl_sync(LFC_FULL, (uint32_t)lst, 0) & 255u];
-                    for (int64_t q = lane; q < run; q += 32) L[nblock + q] = v;
-                    nblock += (int)run;
-                    run = 0;
-                    run_w = 1;
-                }
-                if (s == alpha - 1) break;  // EOB
-                const int j = s - 1;  // >= 1
-                if (j >= niu) { st = DEC_BAD_DATA; break; }
-                const uint64_t holder = __shfl_sync(LFC_FULL, lst, j >> 3);
-                const uint32_t v = (uint32_t)(holder >> (8 * (j & 7))) & 255u;
-                const uint64_t below = __shfl_up_sync(LFC_FULL, lst, 1) >> 56;  // position 8l - 1
-                const uint64_t shifted = (lst << 8) | (lane > 0 ? below : 0ull);
-                // this lane's positions 8l + k in [1, j]
-                const int k0 = lane == 0 ? 1 : 0, k1 = min(7, j - 8 * lane);
-                uint64_t msk = 0;
-                if (k1 >= k0) {
-                    const uint64_t upto = k1 == 7 ? ~0ull : ((1ull << (8 * (k1 + 1))) - 1ull);
-                    msk = upto & ~((1ull << (8 * k0)) - 1ull);
-                }
-                lst = (shifted & msk) | (lst & ~msk);
-                if (lane == 0) lst = (lst & ~0xFFull) | v;
-                if (nblock >= block_max || nblock >= kBlockCap) { st = DEC_OVERFLOW; break; }
-                if (lane == 0) L[nblock] = S.seq_to_unseq[v];
-                nblock++;
+                got = __shfl_sync(LFC_FULL, got, 0);
+                code = __shfl_sync(LFC_FULL, code, 0);
+                __syncwarp();  // the ring reads below come after lane 0 saw the count
+                if (code != DEC_OK) { st = code; break; }
+                avail = got;
             }
-            if (st != DEC_OK) break;
-            if (S.orig >= nblock) { st = DEC_BAD_ORIG; break; }
-        } while (0);
+            const int sym = *reinterpret_cast<const volatile uint16_t *>(&S.ring[c & (kRing - 1)]);
+            c++;
+            if ((c & 31) == 0) {
+                __syncwarp();
+                if (lane == 0) vst(S.cons, c);  // every lane has read its slots
+            }
+            if (sym <= 1) {
+                run += (int64_t)(sym + 1) * run_w;
+                run_w <<= 1;
+                if (run > block_max) { st = DEC_OVERFLOW; break; }
+                continue;
+            }
+            if (run > 0) {
+                if (nblock + run > block_max || nblock + run > kBlockCap) { st = DEC_OVERFLOW; break; }
+                const uint8_t v = S.seq_to_unseq[__shfl_sync(LFC_FULL, (uint32_t)lst, 0) & 255u];
+                for (int64_t q = lane; q < run; q += 32) L[nblock + q] = v;
+                nblock += (int)run;
+                run = 0;
+                run_w = 1;
+            }
+            if (sym == alpha - 1) break;  // EOB
+            const int j = sym - 1;  // >= 1
+            if (j >= niu) { st = DEC_BAD_DATA; break; }
+            const uint64_t holder = __shfl_sync(LFC_FULL, lst, j >> 3);
+            const uint32_t v = (uint32_t)(holder >> (8 * (j & 7))) & 255u;
+            const uint64_t below = __shfl_up_sync(LFC_FULL, lst, 1) >> 56;  // position 8l - 1
+            const uint64_t shifted = (lst << 8) | (lane > 0 ? below : 0ull);
+            // this lane's positions 8l + k in [1, j]
+            const int k0 = lane == 0 ? 1 : 0, k1 = min(7, j - 8 * lane);
+            uint64_t msk = 0;
+            if (k1 >= k0) {
+                const uint64_t upto = k1 == 7 ? ~0ull : ((1ull << (8 * (k1 + 1))) - 1ull);
+                msk = upto & ~((1ull << (8 * k0)) - 1ull);
+            }
+            lst = (shifted & msk) | (lst & ~msk);
+            if (lane == 0) lst = (lst & ~0xFFull) | v;
+            if (nblock >= block_max || nblock >= kBlockCap) { st = DEC_OVERFLOW; break; }
+            if (lane == 0) L[nblock] = S.seq_to_unseq[v];
+            nblock++;
+        }
+        if (st == DEC_OK && S.orig >= nblock) st = DEC_BAD_ORIG;
         if (lane == 0) {
+            if (st != DEC_OK) vst(S.stop, 1);  // lets a waiting decoder go
             S.status = st;
             S.nblock = nblock;
         }
@@ -526,17 +596,20 @@ __global__ void inv_residual_kernel(InvFrame F) {
     }
 }
 
-// Inter-lenslet inverse over the view grid of every (u, v): one thread per
-// view walks its Ny x Nx grid in raster order. signed_out: keep the result
-// as signed 16-bit (phase stage / temporal fields).
-__global__ void inv_inter_kernel(InvFrame F, int signed_field) {
+// Inter-lenslet inverse over the view grid of every (u, v): one CTA per
+// view restores its Ny x Nx grid by anti-diagonals (cell (t, s) needs the
+// cells left, above and above-left, all on the two previous diagonals), one
+// thread per cell of a diagonal. signed_out: keep the result as signed
+// 16-bit (phase stage / temporal fields).
+__global__ void __launch_bounds__(128) inv_inter_kernel(InvFrame F, int signed_field) {
     const int p = F.p, Nx = F.W / p, Ny = F.H / p;
-    const int view = blockIdx.x * blockDim.x + threadIdx.x;
-    if (view >= p * p) return;
+    const int view = blockIdx.x;
     const int v = view / p, u = view % p;
     const int f = id_f(F.id);
-    for (int t = 0; t < Ny; t++) {
-        for (int s = 0; s < Nx; s++) {
+    for (int d = 0; d < Nx + Ny - 1; d++) {
+        const int t_lo = max(0, d - (Nx - 1)), t_hi = min(Ny - 1, d);
+        for (int t = t_lo + (int)threadIdx.x; t <= t_hi; t += blockDim.x) {
+            const int s = d - t;
             const size_t k = (size_t)(t * p + v) * F.W + s * p + u;
             const int32_t A = s > 0 ? F.E[k - p] : 0;
             const int32_t B = t > 0 ? F.E[k - (size_t)p * F.W] : 0;
@@ -544,6 +617,7 @@ __global__ void inv_inter_kernel(InvFrame F, int signed_field) {
             const uint32_t val = ((uint32_t)F.E[k] + (uint32_t)gp(f, t, s, A, B, C)) & 0xFFFFu;
             F.E[k] = signed_field ? as_s16(val) : (int32_t)val;
         }
+        __syncthreads();
     }
 }
 
@@ -604,10 +678,10 @@ cudaError_t launch_inverse_predict(lfc_plan P, const uint16_t *Z, const uint16_t
             inv_intra_kernel<<<(nl + 127) / 128, 128, 0, s>>>(F, tmp ? 1 : 0);
             launches++;
         } else if (dom == 1) {
-            inv_inter_kernel<<<(nv + 63) / 64, 64, 0, s>>>(F, tmp ? 1 : 0);
+            inv_inter_kernel<<<nv, 128, 0, s>>>(F, tmp ? 1 : 0);
             launches++;
         } else {
-            inv_inter_kernel<<<(nv + 63) / 64, 64, 0, s>>>(F, 1);
+            inv_inter_kernel<<<nv, 128, 0, s>>>(F, 1);
             inv_intra_kernel<<<(nl + 127) / 128, 128, 0, s>>>(F, tmp ? 1 : 0);
             launches += 2;
         }
