@@ -129,7 +129,8 @@ __device__ __forceinline__ void vst(int32_t &x, int32_t v) { *reinterpret_cast<v
 
 // Workspace per block: sel (kMaxSelectors bytes), L (kBlockCap), T (int32
 // kBlockCap), rowmark (int32 kBlockCap, walker id or -1), blk (kBlockCap).
-__global__ void __launch_bounds__(kDecThreads) bzip2_decode_kernel(const DecBlock *__restrict__ blocks, int32_t *__restrict__ status,
+// 64 registers at most, so that a CTA of kDecThreads = 1024 fits an SM.
+__global__ void __maxnreg__(64) bzip2_decode_kernel(const DecBlock *__restrict__ blocks, int32_t *__restrict__ status,
                                                                    uint8_t *__restrict__ sel_all, uint8_t *__restrict__ L_all,
                                                                    int32_t *__restrict__ T_all, int32_t *__restrict__ mark_all,
                                                                    uint8_t *__restrict__ blk_all) {
@@ -288,6 +289,7 @@ __global__ void __launch_bounds__(kDecThreads) bzip2_decode_kernel(const DecBloc
             if (n - cons_seen >= kRing) {
                 const long long t0 = clock64();
                 while (n - (cons_seen = vld(S.cons)) >= kRing) {
+                    __nanosleep(32);
                     if (vld(S.stop)) break;
                     if (clock64() - t0 > kDecWaitCycles) { st = DEC_TIMEOUT; break; }
                 }
@@ -309,49 +311,58 @@ __global__ void __launch_bounds__(kDecThreads) bzip2_decode_kernel(const DecBloc
         }
     } else if (tid >= 32 && tid < 64) {
         // warp 1: inverse RUNA/RUNB and MTF. The MTF list lives in
-        // registers, 8 bytes per lane (lane l holds positions 8l .. 8l + 7,
-        // position 8l + k in bits 8k), so moving index j to the front is a
-        // shift by one byte of positions 1 .. j with the byte carried in from
-        // the lane below, whatever j is
+        // registers, 8 bytes per lane in two words (lane l holds positions
+        // 8l .. 8l + 7, position 8l + q in byte q of lo for q < 4, of hi
+        // otherwise), so moving index j to the front shifts positions 0 .. j
+        // up by one byte (v into position 0, each lane's lowest byte from the
+        // lane below) and keeps the rest: one byte permute per word, no
+        // branch on the lane. Symbols are read 32 at a time, one per lane,
+        // and handed round by shuffles.
         const int lane = tid - 32;
         const int niu = S.n_in_use, alpha = S.alpha, block_max = S.block_max;
-        uint64_t lst = 0;
-        for (int k = 7; k >= 0; k--) {
-            const int v = 8 * lane + k;
-            lst = (lst << 8) | (uint64_t)(v < niu ? v : 0);
+        uint32_t lo = 0, hi = 0;
+        for (int q = 3; q >= 0; q--) {
+            const int a = 8 * lane + q, a4 = a + 4;
+            lo = (lo << 8) | (uint32_t)(a < niu ? a : 0);
+            hi = (hi << 8) | (uint32_t)(a4 < niu ? a4 : 0);
         }
         int st = DEC_OK;
         int nblock = 0, c = 0, avail = 0;
+        uint32_t batch = 0;
         int64_t run = 0, run_w = 1;
         for (;;) {
-            if (c == avail) {  // wait for published symbols (lane 0 polls, the warp follows)
-                int got = 0, code = DEC_OK;
-                if (lane == 0) {
-                    const long long t0 = clock64();
-                    for (;;) {
-                        const int pv = vld(S.prod);
-                        if (pv > c) { got = pv; break; }
-                        if (vld(S.stop)) {
-                            code = vld(S.pstatus);
-                            if (code == DEC_OK) code = DEC_BAD_DATA;
-                            break;
+            if ((c & 31) == 0) {  // the next 32 symbols, one per lane
+                if (avail <= c) {  // wait for published symbols (lane 0 polls, the warp follows)
+                    int got = 0, code = DEC_OK;
+                    if (lane == 0) {
+                        const long long t0 = clock64();
+                        for (;;) {
+                            const int pv = vld(S.prod);
+                            if (pv > c) { got = pv; break; }
+                            __nanosleep(32);
+                            if (vld(S.stop)) {
+                                code = vld(S.pstatus);
+                                if (code == DEC_OK) code = DEC_BAD_DATA;
+                                break;
+                            }
+                            if (clock64() - t0 > kDecWaitCycles) { code = DEC_TIMEOUT; break; }
                         }
-                        if (clock64() - t0 > kDecWaitCycles) { code = DEC_TIMEOUT; break; }
+                        __threadfence_block();
                     }
-                    __threadfence_block();
+                    got = __shfl_sync(LFC_FULL, got, 0);
+                    code = __shfl_sync(LFC_FULL, code, 0);
+                    __syncwarp();  // the ring reads below come after lane 0 saw the count
+                    if (code != DEC_OK) { st = code; break; }
+                    avail = got;
                 }
-                got = __shfl_sync(LFC_FULL, got, 0);
-                code = __shfl_sync(LFC_FULL, code, 0);
-                __syncwarp();  // the ring reads below come after lane 0 saw the count
-                if (code != DEC_OK) { st = code; break; }
-                avail = got;
-            }
-            const int sym = *reinterpret_cast<const volatile uint16_t *>(&S.ring[c & (kRing - 1)]);
-            c++;
-            if ((c & 31) == 0) {
+                // published counts are multiples of 32 but for the last one
+                // (which ends in EOB), so lanes past avail are never used
+                batch = *reinterpret_cast<const volatile uint16_t *>(&S.ring[(c + lane) & (kRing - 1)]);
                 __syncwarp();
-                if (lane == 0) vst(S.cons, c);  // every lane has read its slots
+                if (lane == 0) vst(S.cons, min(avail, c + 32));  // these slots are held in registers
             }
+            const int sym = (int)__shfl_sync(LFC_FULL, batch, c & 31);
+            c++;
             if (sym <= 1) {
                 run += (int64_t)(sym + 1) * run_w;
                 run_w <<= 1;
@@ -360,7 +371,7 @@ __global__ void __launch_bounds__(kDecThreads) bzip2_decode_kernel(const DecBloc
             }
             if (run > 0) {
                 if (nblock + run > block_max || nblock + run > kBlockCap) { st = DEC_OVERFLOW; break; }
-                const uint8_t v = S.seq_to_unseq[__shfl_sync(LFC_FULL, (uint32_t)lst, 0) & 255u];
+                const uint8_t v = S.seq_to_unseq[__shfl_sync(LFC_FULL, lo, 0) & 255u];
                 for (int64_t q = lane; q < run; q += 32) L[nblock + q] = v;
                 nblock += (int)run;
                 run = 0;
@@ -369,19 +380,16 @@ __global__ void __launch_bounds__(kDecThreads) bzip2_decode_kernel(const DecBloc
             if (sym == alpha - 1) break;  // EOB
             const int j = sym - 1;  // >= 1
             if (j >= niu) { st = DEC_BAD_DATA; break; }
-            const uint64_t holder = __shfl_sync(LFC_FULL, lst, j >> 3);
-            const uint32_t v = (uint32_t)(holder >> (8 * (j & 7))) & 255u;
-            const uint64_t below = __shfl_up_sync(LFC_FULL, lst, 1) >> 56;  // position 8l - 1
-            const uint64_t shifted = (lst << 8) | (lane > 0 ? below : 0ull);
-            // this lane's positions 8l + k in [1, j]
-            const int k0 = lane == 0 ? 1 : 0, k1 = min(7, j - 8 * lane);
-            uint64_t msk = 0;
-            if (k1 >= k0) {
-                const uint64_t upto = k1 == 7 ? ~0ull : ((1ull << (8 * (k1 + 1))) - 1ull);
-                msk = upto & ~((1ull << (8 * k0)) - 1ull);
-            }
-            lst = (shifted & msk) | (lst & ~msk);
-            if (lane == 0) lst = (lst & ~0xFFull) | v;
+            const uint32_t holder = __shfl_sync(LFC_FULL, (j & 4) ? hi : lo, j >> 3);
+            const uint32_t v = (holder >> (8 * (j & 3))) & 255u;
+            const uint32_t below = __shfl_up_sync(LFC_FULL, hi, 1) >> 24;  // position 8l - 1
+            const uint32_t slo = (lo << 8) | (lane == 0 ? v : below), shi = __funnelshift_l(lo, hi, 8);
+            // this lane's positions up to j take the shifted byte: nibble q
+            // of a selector picks byte q of the shifted word, 4 + q the old one
+            const int cnt = min(8, max(0, j + 1 - 8 * lane));
+            const int cl = min(cnt, 4), ch = max(cnt - 4, 0);
+            lo = __byte_perm(slo, lo, 0x7654u - (0x4444u & ((1u << (4 * cl)) - 1u)));
+            hi = __byte_perm(shi, hi, 0x7654u - (0x4444u & ((1u << (4 * ch)) - 1u)));
             if (nblock >= block_max || nblock >= kBlockCap) { st = DEC_OVERFLOW; break; }
             if (lane == 0) L[nblock] = S.seq_to_unseq[v];
             nblock++;
@@ -502,8 +510,45 @@ __global__ void __launch_bounds__(kDecThreads) bzip2_decode_kernel(const DecBloc
     __syncthreads();
     // ---- 4. inverse RLE1 (thread 0), then CRC
     if (tid == 0) {
-        int o = 0, same = 0, last = -1, st = DEC_OK;
-        for (int i = 0; i < m && st == DEC_OK; i++) {
+        // 8 bytes at a time while no run reaches 4 inside them: bit k of mm
+        // says byte k equals the byte before it (__vcmpeq4), and a run
+        // reaches 4 where three such bits in a row end, counting the run
+        // carried in (same); such words are copied whole, the others (and
+        // the tail) byte by byte with the count byte after a run of 4
+        int o = 0, same = 0, last = -1, st = DEC_OK, i = 0;
+        // byte flags 0xFF / 0x00 of a word -> bits 0..3 (the product puts byte k's flag in bit 24 + k)
+        auto bits4 = [](uint32_t e) { return ((e & 0x01010101u) * 0x01020408u) >> 24; };
+        while (i < m && st == DEC_OK) {
+            if (i + 8 <= m && o + 8 <= D.expect) {
+                uint32_t xl = 0, xh = 0;
+#pragma unroll
+                for (int k = 0; k < 4; k++) {
+                    xl |= (uint32_t)blk[i + k] << (8 * k);
+                    xh |= (uint32_t)blk[i + 4 + k] << (8 * k);
+                }
+                const uint32_t pl = (xl << 8) | (uint32_t)(last & 255), ph = __funnelshift_l(xl, xh, 8);
+                uint32_t mm = bits4(__vcmpeq4(xl, pl)) | (bits4(__vcmpeq4(xh, ph)) << 4);
+                if (same == 0) mm &= ~1u;
+                const uint32_t M = (mm << 3) | (same == 2 ? 4u : (same == 3 ? 6u : 0u));
+                if ((((M & (M << 1) & (M << 2)) >> 3) & 255u) == 0u) {
+                    uint8_t *d8 = D.dst + o;
+                    if ((reinterpret_cast<uintptr_t>(d8) & 3) == 0) {
+                        reinterpret_cast<uint32_t *>(d8)[0] = xl;
+                        reinterpret_cast<uint32_t *>(d8)[1] = xh;
+                    } else {
+#pragma unroll
+                        for (int k = 0; k < 4; k++) {
+                            d8[k] = (uint8_t)(xl >> (8 * k));
+                            d8[4 + k] = (uint8_t)(xh >> (8 * k));
+                        }
+                    }
+                    o += 8;
+                    i += 8;
+                    last = (int)(xh >> 24);
+                    same = (mm & 0x80u) ? ((mm & 0x40u) ? 3 : 2) : 1;
+                    continue;
+                }
+            }
             const uint8_t v = blk[i];
             if (o >= D.expect) { st = DEC_BAD_LEN; break; }
             D.dst[o++] = v;
@@ -517,6 +562,7 @@ __global__ void __launch_bounds__(kDecThreads) bzip2_decode_kernel(const DecBloc
                 same = 0;
                 last = -1;
             }
+            i++;
         }
         if (st == DEC_OK && o != D.expect) st = DEC_BAD_LEN;
         S.status = st;
