@@ -60,9 +60,20 @@ struct BitReader {
         bcnt = 0;
         err = false;
     }
+    // Called with fewer bits buffered than a read needs (at most 32): 32
+    // more bits from four independent loads (one memory latency, not four);
+    // the last bytes of the string one by one
     __device__ __forceinline__ void refill() {
+        if (bcnt <= 32 && next + 4 <= nbytes) {
+            const uint32_t w = ((uint32_t)__ldg(p + next) << 24) | ((uint32_t)__ldg(p + next + 1) << 16) |
+                               ((uint32_t)__ldg(p + next + 2) << 8) | (uint32_t)__ldg(p + next + 3);
+            buf |= (uint64_t)w << (32 - bcnt);
+            bcnt += 32;
+            next += 4;
+            return;
+        }
         while (bcnt <= 56 && next < nbytes) {
-            buf |= (uint64_t)p[next++] << (56 - bcnt);
+            buf |= (uint64_t)__ldg(p + next++) << (56 - bcnt);
             bcnt += 8;
         }
     }
@@ -262,10 +273,13 @@ __global__ void __maxnreg__(64) bzip2_decode_kernel(const DecBlock *__restrict__
         BitReader br = S.br;
         const int nsel = S.n_sel, alpha = S.alpha;
         int st = DEC_OK, n = 0, cons_seen = 0, gi = 0, in_group = 0, t = 0;
+        int t_next = sel[0];  // the next group's table, loaded a group ahead
         for (;;) {
             if (in_group == 0) {
                 if (gi >= nsel) { st = DEC_BAD_DATA; break; }
-                t = sel[gi++];
+                t = t_next;
+                gi++;
+                t_next = gi < nsel ? sel[gi] : 0;
                 in_group = 50;
             }
             in_group--;
