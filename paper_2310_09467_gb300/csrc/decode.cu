@@ -33,6 +33,7 @@ enum : int32_t {
 // Huffman decoding (thread 0) hands its symbols to the MTF warp (warp 1)
 // through a ring in shared memory; each side's wait is bounded.
 constexpr int kRing = 4096;                       // symbols in flight
+constexpr int kStage = 128;                       // bytes of L staged per flush (4 per lane)
 constexpr long long kDecWaitCycles = 4000000000ll; // about 2 s at the SM clock
 
 struct DecBlock {
@@ -132,6 +133,7 @@ struct DecShared {
     int32_t status, nblock, orig, n_in_use, n_groups, n_sel, out_len;
     uint32_t stored_crc;
     uint16_t ring[kRing];       // Huffman symbols from thread 0 to warp 1
+    __align__(16) uint8_t stage[kStage];  // the MTF warp's output chunk
     int32_t prod, cons, stop, pstatus;  // symbols published / released, stop flag, the decoder's status
 };
 
@@ -343,6 +345,14 @@ __global__ void __maxnreg__(64) bzip2_decode_kernel(const DecBlock *__restrict__
         int st = DEC_OK;
         int nblock = 0, c = 0, avail = 0;
         uint32_t batch = 0;
+        // L is written through a 128-byte staging chunk in shared memory,
+        // one 4-byte store per lane per chunk, instead of a byte store per
+        // symbol
+        auto flush_stage = [&](int base) {
+            __syncwarp();
+            reinterpret_cast<uint32_t *>(L + base)[lane] = reinterpret_cast<const uint32_t *>(S.stage)[lane];
+            __syncwarp();
+        };
         int64_t run = 0, run_w = 1;
         for (;;) {
             if ((c & 31) == 0) {  // the next 32 symbols, one per lane
@@ -386,8 +396,14 @@ __global__ void __maxnreg__(64) bzip2_decode_kernel(const DecBlock *__restrict__
             if (run > 0) {
                 if (nblock + run > block_max || nblock + run > kBlockCap) { st = DEC_OVERFLOW; break; }
                 const uint8_t v = S.seq_to_unseq[__shfl_sync(LFC_FULL, lo, 0) & 255u];
-                for (int64_t q = lane; q < run; q += 32) L[nblock + q] = v;
-                nblock += (int)run;
+                int left = (int)run;
+                while (left > 0) {  // through the staging chunk, flushed whenever it fills
+                    const int at = nblock & (kStage - 1), take = min(left, kStage - at);
+                    for (int q = lane; q < take; q += 32) S.stage[at + q] = v;
+                    nblock += take;
+                    left -= take;
+                    if ((nblock & (kStage - 1)) == 0) flush_stage(nblock - kStage);
+                }
                 run = 0;
                 run_w = 1;
             }
@@ -405,9 +421,13 @@ __global__ void __maxnreg__(64) bzip2_decode_kernel(const DecBlock *__restrict__
             lo = __byte_perm(slo, lo, 0x7654u - (0x4444u & ((1u << (4 * cl)) - 1u)));
             hi = __byte_perm(shi, hi, 0x7654u - (0x4444u & ((1u << (4 * ch)) - 1u)));
             if (nblock >= block_max || nblock >= kBlockCap) { st = DEC_OVERFLOW; break; }
-            if (lane == 0) L[nblock] = S.seq_to_unseq[v];
+            if (lane == 0) S.stage[nblock & (kStage - 1)] = S.seq_to_unseq[v];
             nblock++;
+            if ((nblock & (kStage - 1)) == 0) flush_stage(nblock - kStage);
         }
+        // the last, partial chunk
+        __syncwarp();
+        for (int q = (nblock & ~(kStage - 1)) + lane; q < nblock; q += 32) L[q] = S.stage[q & (kStage - 1)];
         if (st == DEC_OK && S.orig >= nblock) st = DEC_BAD_ORIG;
         if (lane == 0) {
             if (st != DEC_OK) vst(S.stop, 1);  // lets a waiting decoder go
