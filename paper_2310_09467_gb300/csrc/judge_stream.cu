@@ -359,13 +359,14 @@ __global__ void __launch_bounds__(kEmitThreads) emit_all_kernel(const JudgeFrame
 // walk has no branch on the data.
 constexpr int kChainWarps = 10;
 constexpr int kChainThreads = kChainWarps * 32;
-constexpr int kHot = 128;              // hot corner side
+constexpr int kHotShift = 7;                    // table entries hold p << kHotShift
+constexpr int kHot = 1 << kHotShift;            // hot corner side
 constexpr int kChainTab = 128 * 32;    // table words of a warp (two 16-bit entries each)
 constexpr int kChainFirst = 256 * 32;  // first-predecessor bytes of a warp, [b][lane]
 constexpr uint32_t kNoPred = 0xFFFF;
 
 size_t chain_smem_bytes() { return (size_t)(kHot * kHot + 32) * 4 + (size_t)kChainWarps * kChainTab * 4; }
-constexpr uint32_t kHotBins = kHot * kHot;  // (p * 128 + a) for p, a < 128; then one slot per lane
+constexpr uint32_t kHotBins = kHot * kHot;  // (p * kHot + a) for p, a < kHot; then one slot per lane
 int64_t chain_seg_bytes(int range_bytes) { return (int64_t)kChainWarps * range_bytes; }
 size_t chain_first_bytes(int nsm) { return (size_t)nsm * kChainWarps * kChainFirst; }
 
@@ -399,15 +400,15 @@ __device__ __forceinline__ int find_frame_s(const JudgeFrame *fr, int n, int64_t
 }
 
 // Count the pair (p, a) of a chain: e the table entry of the previous
-// occurrence (p * 128, kNoPred: none, nothing counted), a the predecessor of
+// occurrence (p << kHotShift, kNoPred: none, nothing counted), a the predecessor of
 // this one. (0, 0) adds 1 to the lane's own slot, another pair of bytes
 // below kHot adds 1 to its hot-corner bin, every other lane adds 0 to its
 // slot; pairs outside the corner go to the global histogram.
 __device__ __forceinline__ void chain_count(uint32_t e, uint32_t a, uint32_t *hot, uint32_t *ghist, uint32_t slot) {
-    const uint32_t t = e + a;                              // p * 128 + a
-    const bool in_hot = (e | (a << 7)) < kHotBins;         // p < 128 and a < 128 (never for kNoPred)
+    const uint32_t t = e + a;                              // p * kHot + a
+    const bool in_hot = (e | (a << kHotShift)) < kHotBins;  // p < kHot and a < kHot (never for kNoPred)
     atomicAdd(&hot[(in_hot && t != 0u) ? t : slot], in_hot ? 1u : 0u);
-    if (e != kNoPred && !in_hot) atomicAdd(&ghist[(e << 1) | a], 1u);  // (p << 8) | a
+    if (e != kNoPred && !in_hot) atomicAdd(&ghist[(e << (8 - kHotShift)) | a], 1u);  // (p << 8) | a
 }
 
 __device__ __forceinline__ uint32_t byte_of(const uint32_t (&w)[8], int i) {
@@ -430,7 +431,7 @@ __device__ __forceinline__ void chain_walk32(const uint32_t (&w)[8], uint32_t &p
         const uint32_t a = i == 0 ? prev : byte_of(w, i - 1);
         uint16_t *en = chain_entry(tl, b);
         e[i] = *en;
-        *en = (uint16_t)(a << 7);
+        *en = (uint16_t)(a << kHotShift);
     }
 #pragma unroll
     for (int i = 0; i < 32; i++) {
@@ -497,7 +498,7 @@ chain_hist_kernel(const JudgeFrame *__restrict__ frames, int nframes, const uint
             const uint32_t b = L[k], a = prev;
             uint16_t *en = chain_entry(tl, b);
             const uint32_t e = *en;
-            *en = (uint16_t)(a << 7);
+            *en = (uint16_t)(a << kHotShift);
             if (e == kNoPred) fl[b * 32] = (uint8_t)a;
             chain_count(e, a, hot, ghist, slot);
             prev = b;
@@ -574,13 +575,13 @@ chain_hist_kernel(const JudgeFrame *__restrict__ frames, int nframes, const uint
             const uint32_t last = e & 0xFFFFu;  // p * 128
             if (last == kNoPred) continue;
             const uint32_t f = (e >> 16) & 255u;
-            if (cur != kNoPred) atomicAdd(&ghist[(cur << 1) | f], 1u);  // (p << 8) | f
+            if (cur != kNoPred) atomicAdd(&ghist[(cur << (8 - kHotShift)) | f], 1u);  // (p << 8) | f
             else f0 = f;
             cur = last;
         }
         uint16_t *out = summ + (size_t)(J.summ_off + (int64_t)ci * J.segs + seg) * 512;
         out[bv] = (uint16_t)f0;
-        out[256 + bv] = (uint16_t)(cur == kNoPred ? kNoPred : cur >> 7);
+        out[256 + bv] = (uint16_t)(cur == kNoPred ? kNoPred : cur >> kHotShift);
     }
 }
 
