@@ -59,13 +59,27 @@ class Clocks:
         self.gpu = gpu_index
 
     def start(self):
+        """Starts sampling every 50 ms and returns once the first sample is
+        written, so that the samples taken after this call fall inside the
+        timed region that follows."""
+        self.skip = 0
         try:
             self.f = open(self.path, "w")
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.Q,
-                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                          "--format=csv,noheader,nounits", "-lms", "50"],
                                          stdout=self.f, stderr=subprocess.DEVNULL)
         except Exception:
             self.proc = None
+            return
+        t0 = time.time()
+        while time.time() - t0 < 5.0:
+            self.f.flush()
+            with open(self.path) as g:
+                n = sum(1 for _ in g)
+            if n > 0:
+                self.skip = n
+                return
+            time.sleep(0.02)
 
     def stop(self):
         if self.proc is None:
@@ -78,7 +92,9 @@ class Clocks:
         self.f.close()
         sm, smax, reasons = [], [], set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for line in open(self.path):
+        lines = open(self.path).read().splitlines()
+        during = lines[self.skip:] or lines[-1:]  # samples of the timed region (else the last one before it)
+        for line in during:
             parts = [p.strip() for p in line.split(",")]
             if len(parts) < 9:
                 continue
