@@ -135,6 +135,7 @@ struct DecShared {
     uint16_t ring[kRing];       // Huffman symbols from thread 0 to warp 1
     __align__(16) uint8_t stage[kStage];  // the MTF warp's output chunk
     int32_t prod, cons, stop, pstatus;  // symbols published / released, stop flag, the decoder's status
+    int32_t scan_sh[33];        // block scan scratch
 };
 
 __device__ __forceinline__ int32_t vld(const int32_t &x) { return *reinterpret_cast<const volatile int32_t *>(&x); }
@@ -542,65 +543,72 @@ __global__ void __maxnreg__(64) bzip2_decode_kernel(const DecBlock *__restrict__
         }
     }
     __syncthreads();
-    // ---- 4. inverse RLE1 (thread 0), then CRC
-    if (tid == 0) {
-        // 8 bytes at a time while no run reaches 4 inside them: bit k of mm
-        // says byte k equals the byte before it (__vcmpeq4), and a run
-        // reaches 4 where three such bits in a row end, counting the run
-        // carried in (same); such words are copied whole, the others (and
-        // the tail) byte by byte with the count byte after a run of 4
-        int o = 0, same = 0, last = -1, st = DEC_OK, i = 0;
-        // byte flags 0xFF / 0x00 of a word -> bits 0..3 (the product puts byte k's flag in bit 24 + k)
-        auto bits4 = [](uint32_t e) { return ((e & 0x01010101u) * 0x01020408u) >> 24; };
-        while (i < m && st == DEC_OK) {
-            if (i + 8 <= m && o + 8 <= D.expect) {
-                uint32_t xl = 0, xh = 0;
-#pragma unroll
-                for (int k = 0; k < 4; k++) {
-                    xl |= (uint32_t)blk[i + k] << (8 * k);
-                    xh |= (uint32_t)blk[i + 4 + k] << (8 * k);
-                }
-                const uint32_t pl = (xl << 8) | (uint32_t)(last & 255), ph = __funnelshift_l(xl, xh, 8);
-                uint32_t mm = bits4(__vcmpeq4(xl, pl)) | (bits4(__vcmpeq4(xh, ph)) << 4);
-                if (same == 0) mm &= ~1u;
-                const uint32_t M = (mm << 3) | (same == 2 ? 4u : (same == 3 ? 6u : 0u));
-                if ((((M & (M << 1) & (M << 2)) >> 3) & 255u) == 0u) {
-                    uint8_t *d8 = D.dst + o;
-                    if ((reinterpret_cast<uintptr_t>(d8) & 3) == 0) {
-                        reinterpret_cast<uint32_t *>(d8)[0] = xl;
-                        reinterpret_cast<uint32_t *>(d8)[1] = xh;
-                    } else {
-#pragma unroll
-                        for (int k = 0; k < 4; k++) {
-                            d8[k] = (uint8_t)(xl >> (8 * k));
-                            d8[4 + k] = (uint8_t)(xh >> (8 * k));
-                        }
-                    }
-                    o += 8;
-                    i += 8;
-                    last = (int)(xh >> 24);
-                    same = (mm & 0x80u) ? ((mm & 0x40u) ? 3 : 2) : 1;
-                    continue;
+    // ---- 4. inverse RLE1, then CRC. A position q is a sync point when
+    // bytes q-2 and q-1 differ and bytes q-5 .. q-2 are not all equal: byte
+    // q-1 is then a literal (a count byte follows four equal literals) that
+    // starts a run, so decoding can start at q from (run 1, last = byte
+    // q-1). Every thread takes the first sync point of its chunk (thread 0:
+    // position 0, fresh) and decodes up to the next thread's: once to count
+    // its output bytes, once to write them at their prefix.
+    {
+        const int nth = blockDim.x;
+        const int ch = max(8, (m + nth - 1) / nth);
+        const int s0 = tid * ch, e0 = min(m, s0 + ch);
+        int p = m;  // this thread's segment start, m: none in its chunk
+        if (s0 < m) {
+            if (tid == 0) {
+                p = 0;
+            } else {
+                for (int q = max(s0, 5); q < e0; q++) {
+                    const uint8_t b1 = blk[q - 1], b2 = blk[q - 2];
+                    if (b1 != b2 && !(blk[q - 5] == b2 && blk[q - 4] == b2 && blk[q - 3] == b2)) { p = q; break; }
                 }
             }
-            const uint8_t v = blk[i];
-            if (o >= D.expect) { st = DEC_BAD_LEN; break; }
-            D.dst[o++] = v;
-            same = (v == last) ? same + 1 : 1;
-            last = v;
-            if (same == 4) {
-                if (i + 1 >= m) { st = DEC_BAD_DATA; break; }
-                const int extra = blk[++i];
-                if (o + extra > D.expect) { st = DEC_BAD_LEN; break; }
-                for (int q = 0; q < extra; q++) D.dst[o++] = v;
-                same = 0;
-                last = -1;
-            }
-            i++;
         }
-        if (st == DEC_OK && o != D.expect) st = DEC_BAD_LEN;
-        S.status = st;
-        S.out_len = o;
+        S.walk_len[tid] = p;
+        __syncthreads();
+        int end = m;  // the next segment start after this one
+        if (p < m)
+            for (int t2 = tid + 1; t2 < nth; t2++)
+                if (S.walk_len[t2] < m) { end = S.walk_len[t2]; break; }
+        int cnt = 0, st = DEC_OK;
+        for (int pass = 0; pass < 2; pass++) {
+            int off = 0;
+            if (pass == 1) {
+                int total = 0;
+                off = block_excl_sum<int>(cnt, S.scan_sh, &total);
+                if (total != D.expect) st = DEC_BAD_LEN;
+                if (__syncthreads_or(st != DEC_OK)) break;
+            }
+            if (p < m) {
+                int o = 0, same = tid == 0 ? 0 : 1, last = tid == 0 ? -1 : (int)blk[p - 1];
+                for (int i = p; i < end; i++) {
+                    const uint8_t v = blk[i];
+                    if (pass) D.dst[off + o] = v;
+                    o++;
+                    same = ((int)v == last) ? same + 1 : 1;
+                    last = v;
+                    if (same == 4) {
+                        if (i + 1 >= m) { st = DEC_BAD_DATA; break; }
+                        const int extra = blk[++i];
+                        if (pass && off + o + extra > D.expect) { st = DEC_BAD_LEN; break; }
+                        if (pass)
+                            for (int q = 0; q < extra; q++) D.dst[off + o + q] = v;
+                        o += extra;
+                        same = 0;
+                        last = -1;
+                    }
+                }
+                cnt = o;
+            }
+            if (__syncthreads_or(st != DEC_OK)) break;
+        }
+        if (tid == 0) {
+            S.status = DEC_OK;
+            S.out_len = D.expect;
+        }
+        __syncthreads();
+        if (st != DEC_OK) S.status = st;  // any failing thread (benign race: all write an error code)
     }
     __syncthreads();
     if (S.status != DEC_OK) {
