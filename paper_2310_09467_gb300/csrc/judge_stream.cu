@@ -113,17 +113,45 @@ __device__ __forceinline__ void emit_all_body(const JudgeFrame *__restrict__ fra
     }
     const DivU16 div_p((uint32_t)p);
     const int y0 = (t - 1) * p, x0 = (s0 - 1) * p;
-    for (int lx = threadIdx.x; lx < ncols; lx += blockDim.x) {  // column per thread, rows in a loop
-        const int x = x0 + lx;
-        for (int ly = 0; ly < TR; ly++) {
-            const int y = y0 + ly;
-            uint32_t v = 0;
-            if (y >= 0 && x >= 0) {
-                const size_t k = (size_t)y * W + x;
-                v = __ldg(F.X + k);
-                if (kind) v = (v - (uint32_t)__ldg(F.prev + k)) & 0xFFFFu;
+    // the tile's rows y0 .. y0 + TR - 1, columns x0 .. x0 + ncols - 1 (zero
+    // outside the frame): with 16-byte aligned rows, as 16-byte loads of 8
+    // pixels from the multiple of 8 at or below x0 (a chunk never straddles
+    // column 0 or the row end); otherwise pixel by pixel
+    const bool vec = (W % 8) == 0 && (reinterpret_cast<uintptr_t>(F.X) & 15) == 0 &&
+                     (!kind || (reinterpret_cast<uintptr_t>(F.prev) & 15) == 0);
+    if (vec) {
+        const int xa0 = x0 >= 0 ? (x0 & ~7) : -((7 - x0) & ~7);
+        const int nch = (x0 + ncols - xa0 + 7) >> 3;
+        for (int q = threadIdx.x; q < TR * nch; q += blockDim.x) {
+            const int ly = q / nch, xa = xa0 + 8 * (q - ly * nch), y = y0 + ly;
+            uint4 a = make_uint4(0, 0, 0, 0), b = a;
+            if (y >= 0 && xa >= 0) {
+                a = __ldg(reinterpret_cast<const uint4 *>(F.X + (size_t)y * W + xa));
+                if (kind) b = __ldg(reinterpret_cast<const uint4 *>(F.prev + (size_t)y * W + xa));
             }
-            Fb[ly * TC + lx] = (uint16_t)v;
+            const uint32_t aw[4] = {a.x, a.y, a.z, a.w}, bw[4] = {b.x, b.y, b.z, b.w};
+#pragma unroll
+            for (int j = 0; j < 8; j++) {
+                const int lx = xa + j - x0;
+                if (lx < 0 || lx >= ncols) continue;
+                uint32_t v = (aw[j >> 1] >> (16 * (j & 1))) & 0xFFFFu;
+                if (kind) v = (v - ((bw[j >> 1] >> (16 * (j & 1))) & 0xFFFFu)) & 0xFFFFu;
+                Fb[ly * TC + lx] = (uint16_t)v;
+            }
+        }
+    } else {
+        for (int lx = threadIdx.x; lx < ncols; lx += blockDim.x) {  // column per thread, rows in a loop
+            const int x = x0 + lx;
+            for (int ly = 0; ly < TR; ly++) {
+                const int y = y0 + ly;
+                uint32_t v = 0;
+                if (y >= 0 && x >= 0) {
+                    const size_t k = (size_t)y * W + x;
+                    v = __ldg(F.X + k);
+                    if (kind) v = (v - (uint32_t)__ldg(F.prev + k)) & 0xFFFFu;
+                }
+                Fb[ly * TC + lx] = (uint16_t)v;
+            }
         }
     }
     __syncthreads();
