@@ -93,12 +93,20 @@ __global__ void __launch_bounds__(32) mtf_encode_kernel(const BlockState *__rest
     __shared__ uint8_t lst[256];
     __shared__ uint8_t posof[256];
     __shared__ uint32_t WP[8];
+    __shared__ __align__(16) uint8_t seg[kTile];  // the segment's bytes, loaded at once
     const int b = blockIdx.y, g = blockIdx.x;
     const int m = st[b].m;
     const int s0 = g * kTile;
     if (s0 >= m) return;
     const int s1 = min(m, s0 + kTile);
     const int lane = threadIdx.x;
+    {
+        const uint8_t *Lb = L_all + (size_t)b * kBlockCap + s0;  // 16-byte aligned (block slots and tiles are)
+        const int nb = s1 - s0;
+        for (int q = lane; q < (nb >> 4); q += 32)
+            reinterpret_cast<uint4 *>(seg)[q] = __ldg(reinterpret_cast<const uint4 *>(Lb) + q);
+        for (int q = (nb & ~15) + lane; q < nb; q += 32) seg[q] = Lb[q];
+    }
     if (lane < 8) iush[lane] = st[b].in_use[lane];
     __syncwarp();
     build_seq_table(iush, seq);
@@ -109,13 +117,12 @@ __global__ void __launch_bounds__(32) mtf_encode_kernel(const BlockState *__rest
     __syncwarp();
     for (int q = lane; q < n_in_use; q += 32) posof[lst[q]] = (uint8_t)q;
     __syncwarp();
-    const uint8_t *L = L_all + (size_t)b * kBlockCap;
     uint8_t *out = idx_all + (size_t)b * kBlockCap;
     const uint32_t lt = lanemask_lt(), gt = lanemask_gt();
     for (int w0 = s0; w0 < s1; w0 += 32) {
         const int i = w0 + lane;
         const bool valid = i < s1;
-        const uint32_t s = valid ? (uint32_t)seq[L[i]] : 256u + lane;
+        const uint32_t s = valid ? (uint32_t)seq[seg[i - s0]] : 256u + lane;
         const uint32_t grp = __match_any_sync(LFC_FULL, s);
         const uint32_t lower = grp & lt;
         const bool fo = valid && lower == 0;
