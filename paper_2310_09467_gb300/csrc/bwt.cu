@@ -377,10 +377,17 @@ __global__ void __launch_bounds__(kSortThreads) key40_kernel(const int32_t *__re
     if (tile * kTile >= n) return;
     if (tile == 0 && threadIdx.x == 0) big[b] = 0;  // set again by the segmented sort if a group is too large
     const size_t bo = (size_t)b * kBlockCap;
+    // all elements first, then all rank gathers (independent loads in flight together)
+    int vv[kPerThread];
+#pragma unroll
     for (int r = 0; r < kPerThread; r++) {
         const int k = tile * kTile + r * kSortThreads + threadIdx.x;
-        if (k >= n) break;
-        const int v = V_all[bo + k];
+        vv[r] = k < n ? V_all[bo + k] : -1;
+    }
+#pragma unroll
+    for (int r = 0; r < kPerThread; r++) {
+        if (vv[r] < 0) continue;
+        const int k = tile * kTile + r * kSortThreads + threadIdx.x, v = vv[r];
         int j = v + h;
         if (j >= s.m) j -= s.m;
         K_all[bo + k] = ((uint64_t)(uint32_t)rank_all[bo + v] << 40) | ((uint64_t)(uint32_t)rank_all[bo + j] << 20) |

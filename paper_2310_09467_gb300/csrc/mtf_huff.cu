@@ -326,6 +326,10 @@ __global__ void __launch_bounds__(kRle2Threads) rle2_write_kernel(const BlockSta
                                                                   uint16_t *__restrict__ sym_all, uint32_t *__restrict__ freq_all) {
     __shared__ int sh[33];
     __shared__ uint32_t fq[kMaxAlpha];
+    // the tile's symbols: a zero run of r codes to at most r digits, and only
+    // the first run ending in the tile can hold zeros of earlier tiles (at
+    // most 20 digits: a block is below 2^20 positions)
+    __shared__ uint16_t ssym[kRle2Tile + 32];
     const int b = blockIdx.y, tile = blockIdx.x;
     const int m = st[b].m;
     const int ts = tile * kRle2Tile;
@@ -347,14 +351,17 @@ __global__ void __launch_bounds__(kRle2Threads) rle2_write_kernel(const BlockSta
         if ((nz >> q) & 1u) { cnt++; lz = a + q; }
         else if ((end >> q) & 1u) cnt += run_digits(a + q - lz);
     }
-    int o = off + block_excl_sum<int>(cnt, sh, nullptr);
+    // symbols staged in shared memory at their tile-local offsets, then
+    // written by consecutive threads on consecutive positions
+    int total = 0;
+    int o = block_excl_sum<int>(cnt, sh, &total);
     uint16_t *sym = sym_all + (size_t)b * kSymStride;
     lz = lz0;
 #pragma unroll
     for (int q = 0; q < 16; q++) {
         if ((nz >> q) & 1u) {
             const uint32_t s = (uint32_t)v[q] + 1u;
-            sym[o++] = (uint16_t)s;
+            ssym[o++] = (uint16_t)s;
             atomicAdd(&fq[s], 1u);
             lz = a + q;
         } else if ((end >> q) & 1u) {
@@ -362,12 +369,13 @@ __global__ void __launch_bounds__(kRle2Threads) rle2_write_kernel(const BlockSta
             const int nd = run_digits((int)r1);
             for (int k = 0; k < nd; k++) {
                 const uint32_t d = ((r1 + 1u) >> k) & 1u;
-                sym[o++] = (uint16_t)d;
+                ssym[o++] = (uint16_t)d;
                 atomicAdd(&fq[d], 1u);
             }
         }
     }
     __syncthreads();
+    for (int i = threadIdx.x; i < total; i += kRle2Threads) sym[off + i] = ssym[i];
     uint32_t *freq = freq_all + (size_t)b * kMaxAlpha;
     for (int i = threadIdx.x; i < kMaxAlpha; i += kRle2Threads)
         if (fq[i]) atomicAdd(&freq[i], fq[i]);
