@@ -635,29 +635,10 @@ __device__ __forceinline__ int digit_shift(int pass) { return (MODE == 0 ? 0 : 2
 // c[d] (flag "aggregate"; tile 0: "inclusive"), adds the published counts of
 // the block's earlier tiles back to the nearest "inclusive" one, publishes
 // its own inclusive count, and the run of digit d starts at (elements of the
-// block with a smaller digit, from the block's digit totals) + (elements of
-// digit d in earlier tiles). Tiles are placed in shared memory in digit
-// order and each digit's run is written with consecutive threads on
-// consecutive addresses.
-// A tile waits only on tiles taken from the queue before it, which are held
-// by running CTAs, so the waits always end; each is still bounded by
-// `budget` clock cycles, after which the CTA raises the abort word and every
-// sort kernel of this suffix sort returns at once (LFC_ERR_TIMEOUT).
-// Status words of the pass live in array par = pass parity; each tile clears
-// its words in the other array for the next pass (which runs on the same or
-// fewer tiles of every block).
-// One stable LSD pass of (key, element) pairs (MODE 0) or round words (MODE
-// 1, the element rides in the word) over every block of the pass.
-// Persistent: CTAs take tiles from the pass's work queue until it is empty
-// (tile-major order, see sort_items_kernel).
-// Per tile: warp w ranks elements [w*512, (w+1)*512) of the tile 32 at a
-// time in order (equal digits by __match_any_sync and a per-warp running
-// count), giving the tile's count c[d] of every digit d; thread d publishes
-// c[d] (flag "aggregate"; tile 0: "inclusive"), adds the published counts of
-// the block's earlier tiles back to the nearest "inclusive" one, publishes
-// its own inclusive count, and the run of digit d starts at (elements of the
-// block with a smaller digit, from the block's digit totals) + (elements of
-// digit d in earlier tiles). Tiles are placed in shared memory in digit
+// block with a smaller digit: in phase 1 the offsets sort_items_kernel
+// derived from the block's byte histogram, in a round a scan of the pass's
+// digit totals) + (elements of digit d in earlier tiles). A CTA takes its
+// next work item while it sorts the current one. Tiles are placed in shared memory in digit
 // order and each digit's run is written with consecutive threads on
 // consecutive addresses.
 // A tile waits only on tiles taken from the queue before it, which are held
