@@ -225,9 +225,7 @@ int lfc_plan_block_capacity(lfc_plan plan);
  * order. Every read of a container is bounds-checked, so a corrupt container
  * returns CORRUPT (bad header, block stream, block CRC or frame CRC) and
  * never reads or writes outside the buffers. Synchronous: the host reads
- * the headers. Errors: INVALID_ARG, CAPACITY, CORRUPT, CUDA, TIMEOUT (a
- * block decoder's hand-over between its Huffman and MTF stages waited about
- * two seconds without progress). */
+ * the headers. Errors: INVALID_ARG, CAPACITY, CORRUPT, CUDA. */
 int lfc_decompress(lfc_plan plan, const uint8_t *const *h_in, const uint64_t *h_in_sizes, int n,
                    uint16_t *const *h_out, const uint64_t *h_out_bytes, const uint16_t *const *h_prev);
 

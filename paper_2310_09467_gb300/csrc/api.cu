@@ -1032,7 +1032,6 @@ extern "C" int lfc_decompress(lfc_plan P, const uint8_t *const *h_in, const uint
         CK(cudaMemcpyAsync(st.data(), d_status, 4 * (size_t)nb, cudaMemcpyDeviceToHost, P->stream));
         CK(cudaStreamSynchronize(P->stream));
         for (int k = 0; k < nb; k++) {
-            if (st[k] == 10) return fail(P, LFC_ERR_TIMEOUT, "bzip2 block decode: a bounded wait gave up");
             if (st[k] != 0) return fail(P, LFC_ERR_CORRUPT, "bzip2 block failed to decode (code " + std::to_string(st[k]) + ")");
         }
         std::vector<const uint8_t *> outp;

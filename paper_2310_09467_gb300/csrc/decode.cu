@@ -17,6 +17,8 @@
 //     writing bytes from the end of the block backwards;
 //  4. thread 0: inverse RLE1; the CTA: CRC-32/BZIP2 of the output vs the
 //     stored block CRC.
+#include <climits>
+
 #include "lfc_common.cuh"
 
 namespace lfc {
@@ -27,14 +29,10 @@ constexpr uint32_t kPolyD = 0x04C11DB7u;
 
 enum : int32_t {
     DEC_OK = 0, DEC_BAD_MAGIC = 1, DEC_TRUNC = 2, DEC_BAD_TABLE = 3, DEC_BAD_DATA = 4,
-    DEC_OVERFLOW = 5, DEC_BAD_ORIG = 6, DEC_BAD_LEN = 7, DEC_BAD_CRC = 8, DEC_BAD_WALK = 9, DEC_TIMEOUT = 10
+    DEC_OVERFLOW = 5, DEC_BAD_ORIG = 6, DEC_BAD_LEN = 7, DEC_BAD_CRC = 8, DEC_BAD_WALK = 9
 };
 
-// Huffman decoding (thread 0) hands its symbols to the MTF warp (warp 1)
-// through a ring in shared memory; each side's wait is bounded.
-constexpr int kRing = 4096;                       // symbols in flight
-constexpr int kStage = 128;                       // bytes of L staged per flush (4 per lane)
-constexpr long long kDecWaitCycles = 4000000000ll; // about 2 s at the SM clock
+constexpr int kDecWarps = kDecThreads / 32;       // MTF segments per block
 
 struct DecBlock {
     const uint8_t *src;   // one standalone bzip2 stream
@@ -132,14 +130,31 @@ struct DecShared {
     uint32_t red[32];
     int32_t status, nblock, orig, n_in_use, n_groups, n_sel, out_len;
     uint32_t stored_crc;
-    uint16_t ring[kRing];       // Huffman symbols from thread 0 to warp 1
-    __align__(16) uint8_t stage[kStage];  // the MTF warp's output chunk
-    int32_t prod, cons, stop, pstatus;  // symbols published / released, stop flag, the decoder's status
+    int32_t nsym, ngroups_used;            // Huffman symbols up to EOB, groups holding them
+    int32_t seg_start[kDecWarps];          // MTF segment of warp w: [seg_start[w], next start)
+    int32_t seg_len[kDecWarps], seg_off[kDecWarps];  // its output bytes and their offset in L
+    int32_t seg_status[kDecWarps];
+    uint8_t seg_perm[kDecWarps][256];      // where the segment's MTF moves take each list position
+    uint8_t seg_list[kDecWarps][256];      // the list at the segment's start
     int32_t scan_sh[33];        // block scan scratch
 };
 
-__device__ __forceinline__ int32_t vld(const int32_t &x) { return *reinterpret_cast<const volatile int32_t *>(&x); }
-__device__ __forceinline__ void vst(int32_t &x, int32_t v) { *reinterpret_cast<volatile int32_t *>(&x) = v; }
+// One Huffman symbol with table t: the 10-bit lookup, else the canonical
+// search from 11 bits; -1 for a code that is not in the table or a stream
+// that ends first (br.err).
+__device__ __forceinline__ int huff_symbol(BitReader &br, const DecShared &S, int t) {
+    const uint32_t e = S.lut[t][br.peek(10)];
+    if (e) return br.skip(e & 31) ? (int)(e >> 5) : -1;
+    int32_t c = (int32_t)br.peek(10);
+    if (!br.skip(10)) return -1;
+    for (int l = 11; l <= 20; l++) {
+        c = (c << 1) | (int32_t)br.get(1);
+        if (br.err) return -1;
+        const uint32_t d = (uint32_t)(c - S.first[t][l]);
+        if (d < (uint32_t)S.count[t][l]) return S.perm[t][S.pidx[t][l] + (int)d];
+    }
+    return -1;
+}
 
 // Workspace per block: sel (kMaxSelectors bytes), L (kBlockCap), T (int32
 // kBlockCap), rowmark (int32 kBlockCap, walker id or -1), blk (kBlockCap).
@@ -263,178 +278,178 @@ __global__ void __maxnreg__(64) bzip2_decode_kernel(const DecBlock *__restrict__
         S.lut[t][i] = e;
     }
     __syncthreads();
+    // ---- 1b. Huffman: thread 0 walks the groups once to find where each
+    // starts in the stream (and where EOB is); then every thread decodes
+    // whole groups from their offsets into the symbol array
+    int32_t *gofs = T;                                  // group bit offsets (T is free until the LF mapping)
+    uint16_t *syms = reinterpret_cast<uint16_t *>(mark);  // symbols in order (mark is free until the walkers)
     if (tid == 0) {
-        S.prod = 0;
-        S.cons = 0;
-        S.stop = 0;
-        S.pstatus = DEC_OK;
-    }
-    __syncthreads();
-    if (tid == 0) {
-        // Huffman decoding: symbols into the ring, published every 32 and at
-        // the end; waits while the ring is full
         BitReader br = S.br;
         const int nsel = S.n_sel, alpha = S.alpha;
-        int st = DEC_OK, n = 0, cons_seen = 0, gi = 0, in_group = 0, t = 0;
-        int t_next = sel[0];  // the next group's table, loaded a group ahead
-        for (;;) {
-            if (in_group == 0) {
-                if (gi >= nsel) { st = DEC_BAD_DATA; break; }
-                t = t_next;
-                gi++;
-                t_next = gi < nsel ? sel[gi] : 0;
-                in_group = 50;
+        int st = DEC_OK, ns = 0, ngu = 0;
+        for (int g = 0; g < nsel && st == DEC_OK; g++) {
+            gofs[g] = (int32_t)(br.next * 8 - br.bcnt);
+            const int t = sel[g];
+            int k = 0;
+            for (; k < 50; k++) {
+                const int sym = huff_symbol(br, S, t);
+                if (sym < 0) { st = br.err ? DEC_TRUNC : DEC_BAD_DATA; break; }
+                if (sym == alpha - 1) break;  // EOB
             }
-            in_group--;
-            int sym = -1;
-            const uint32_t e = S.lut[t][br.peek(10)];
-            if (e) {
-                if (!br.skip(e & 31)) { st = DEC_TRUNC; break; }
-                sym = e >> 5;
-            } else {  // a code longer than 10 bits: canonical search from 11 bits
-                int32_t c = (int32_t)br.peek(10);
-                if (!br.skip(10)) { st = DEC_TRUNC; break; }
-                for (int l = 11; l <= 20; l++) {
-                    c = (c << 1) | (int32_t)br.get(1);
-                    if (br.err) break;
-                    const uint32_t d = (uint32_t)(c - S.first[t][l]);
-                    if (d < (uint32_t)S.count[t][l]) { sym = S.perm[t][S.pidx[t][l] + (int)d]; break; }
-                }
-                if (br.err) { st = DEC_TRUNC; break; }
+            if (st != DEC_OK) break;
+            if (k < 50) {
+                ns = g * 50 + k + 1;
+                ngu = g + 1;
+                break;
             }
-            if (sym < 0) { st = DEC_BAD_DATA; break; }
-            if (n - cons_seen >= kRing) {
-                const long long t0 = clock64();
-                while (n - (cons_seen = vld(S.cons)) >= kRing) {
-                    __nanosleep(32);
-                    if (vld(S.stop)) break;
-                    if (clock64() - t0 > kDecWaitCycles) { st = DEC_TIMEOUT; break; }
-                }
-                if (st != DEC_OK || n - cons_seen >= kRing) break;  // timed out, or the MTF warp stopped
-            }
-            *reinterpret_cast<volatile uint16_t *>(&S.ring[n & (kRing - 1)]) = (uint16_t)sym;
-            n++;
-            if ((n & 31) == 0 || sym == alpha - 1) {
-                __threadfence_block();
-                vst(S.prod, n);
-                if (vld(S.stop)) break;
-            }
-            if (sym == alpha - 1) break;  // EOB
+            if (g == nsel - 1) st = DEC_BAD_DATA;  // no EOB
         }
-        if (st != DEC_OK) {
-            vst(S.pstatus, st);
-            __threadfence_block();
-            vst(S.stop, 1);
+        S.nsym = ns;
+        S.ngroups_used = ngu;
+        S.status = st;
+    }
+    __syncthreads();
+    if (S.status != DEC_OK) {
+        if (tid == 0) status[b] = S.status;
+        return;
+    }
+    {
+        const int ns = S.nsym, ngu = S.ngroups_used;
+        for (int g = tid; g < ngu; g += blockDim.x) {
+            BitReader br;
+            br.init(D.src, D.src_len);
+            const int32_t bo = gofs[g];
+            br.next = bo >> 3;
+            br.skip(bo & 7);
+            const int t = sel[g], cnt = min(50, ns - g * 50);
+            for (int k = 0; k < cnt; k++) syms[g * 50 + k] = (uint16_t)huff_symbol(br, S, t);
         }
-    } else if (tid >= 32 && tid < 64) {
-        // warp 1: inverse RUNA/RUNB and MTF. The MTF list lives in
-        // registers, 8 bytes per lane in two words (lane l holds positions
-        // 8l .. 8l + 7, position 8l + q in byte q of lo for q < 4, of hi
-        // otherwise), so moving index j to the front shifts positions 0 .. j
-        // up by one byte (v into position 0, each lane's lowest byte from the
-        // lane below) and keeps the rest: one byte permute per word, no
-        // branch on the lane. Symbols are read 32 at a time, one per lane,
-        // and handed round by shuffles.
-        const int lane = tid - 32;
-        const int niu = S.n_in_use, alpha = S.alpha, block_max = S.block_max;
-        uint32_t lo = 0, hi = 0;
-        for (int q = 3; q >= 0; q--) {
-            const int a = 8 * lane + q, a4 = a + 4;
-            lo = (lo << 8) | (uint32_t)(a < niu ? a : 0);
-            hi = (hi << 8) | (uint32_t)(a4 < niu ? a4 : 0);
-        }
-        int st = DEC_OK;
-        int nblock = 0, c = 0, avail = 0;
-        uint32_t batch = 0;
-        // L is written through a 128-byte staging chunk in shared memory,
-        // one 4-byte store per lane per chunk, instead of a byte store per
-        // symbol
-        auto flush_stage = [&](int base) {
-            __syncwarp();
-            reinterpret_cast<uint32_t *>(L + base)[lane] = reinterpret_cast<const uint32_t *>(S.stage)[lane];
-            __syncwarp();
-        };
-        int64_t run = 0, run_w = 1;
-        for (;;) {
-            if ((c & 31) == 0) {  // the next 32 symbols, one per lane
-                if (avail <= c) {  // wait for published symbols (lane 0 polls, the warp follows)
-                    int got = 0, code = DEC_OK;
-                    if (lane == 0) {
-                        const long long t0 = clock64();
-                        for (;;) {
-                            const int pv = vld(S.prod);
-                            if (pv > c) { got = pv; break; }
-                            __nanosleep(32);
-                            if (vld(S.stop)) {
-                                code = vld(S.pstatus);
-                                if (code == DEC_OK) code = DEC_BAD_DATA;
-                                break;
-                            }
-                            if (clock64() - t0 > kDecWaitCycles) { code = DEC_TIMEOUT; break; }
-                        }
-                        __threadfence_block();
-                    }
-                    got = __shfl_sync(LFC_FULL, got, 0);
-                    code = __shfl_sync(LFC_FULL, code, 0);
-                    __syncwarp();  // the ring reads below come after lane 0 saw the count
-                    if (code != DEC_OK) { st = code; break; }
-                    avail = got;
-                }
-                // published counts are multiples of 32 but for the last one
-                // (which ends in EOB), so lanes past avail are never used
-                batch = *reinterpret_cast<const volatile uint16_t *>(&S.ring[(c + lane) & (kRing - 1)]);
-                __syncwarp();
-                if (lane == 0) vst(S.cons, min(avail, c + 32));  // these slots are held in registers
-            }
-            const int sym = (int)__shfl_sync(LFC_FULL, batch, c & 31);
-            c++;
-            if (sym <= 1) {
-                run += (int64_t)(sym + 1) * run_w;
-                run_w <<= 1;
-                if (run > block_max) { st = DEC_OVERFLOW; break; }
-                continue;
-            }
-            if (run > 0) {
-                if (nblock + run > block_max || nblock + run > kBlockCap) { st = DEC_OVERFLOW; break; }
-                const uint8_t v = S.seq_to_unseq[__shfl_sync(LFC_FULL, lo, 0) & 255u];
-                int left = (int)run;
-                while (left > 0) {  // through the staging chunk, flushed whenever it fills
-                    const int at = nblock & (kStage - 1), take = min(left, kStage - at);
-                    for (int q = lane; q < take; q += 32) S.stage[at + q] = v;
-                    nblock += take;
-                    left -= take;
-                    if ((nblock & (kStage - 1)) == 0) flush_stage(nblock - kStage);
-                }
-                run = 0;
-                run_w = 1;
-            }
-            if (sym == alpha - 1) break;  // EOB
-            const int j = sym - 1;  // >= 1
-            if (j >= niu) { st = DEC_BAD_DATA; break; }
-            const uint32_t holder = __shfl_sync(LFC_FULL, (j & 4) ? hi : lo, j >> 3);
-            const uint32_t v = (holder >> (8 * (j & 3))) & 255u;
-            const uint32_t below = __shfl_up_sync(LFC_FULL, hi, 1) >> 24;  // position 8l - 1
-            const uint32_t slo = (lo << 8) | (lane == 0 ? v : below), shi = __funnelshift_l(lo, hi, 8);
-            // this lane's positions up to j take the shifted byte: nibble q
-            // of a selector picks byte q of the shifted word, 4 + q the old one
-            const int cnt = min(8, max(0, j + 1 - 8 * lane));
-            const int cl = min(cnt, 4), ch = max(cnt - 4, 0);
-            lo = __byte_perm(slo, lo, 0x7654u - (0x4444u & ((1u << (4 * cl)) - 1u)));
-            hi = __byte_perm(shi, hi, 0x7654u - (0x4444u & ((1u << (4 * ch)) - 1u)));
-            if (nblock >= block_max || nblock >= kBlockCap) { st = DEC_OVERFLOW; break; }
-            if (lane == 0) S.stage[nblock & (kStage - 1)] = S.seq_to_unseq[v];
-            nblock++;
-            if ((nblock & (kStage - 1)) == 0) flush_stage(nblock - kStage);
-        }
-        // the last, partial chunk
-        __syncwarp();
-        for (int q = (nblock & ~(kStage - 1)) + lane; q < nblock; q += 32) L[q] = S.stage[q & (kStage - 1)];
-        if (st == DEC_OK && S.orig >= nblock) st = DEC_BAD_ORIG;
+    }
+    __syncthreads();
+    // ---- 1c. inverse RUNA/RUNB and MTF by segments. A segment's MTF moves
+    // permute list positions whatever the list holds, so each warp first
+    // finds its segment's permutation and output length (pass 1), warp 0
+    // chains the lists at the segment starts and the output offsets, and
+    // each warp decodes its segment from its own starting list (pass 2).
+    // Segments start right after a symbol that is not a run digit, so no
+    // run is split. The list lives in registers, 8 bytes per lane (lane l
+    // holds positions 8l .. 8l + 7, position 8l + q in byte q of lo for q <
+    // 4, of hi otherwise); moving index j to the front shifts positions
+    // 0 .. j up by one byte and keeps the rest: one byte permute per word.
+    {
+        const int ns = S.nsym, niu = S.n_in_use, alpha = S.alpha, block_max = S.block_max;
+        const int w = tid >> 5, lane = tid & 31;
         if (lane == 0) {
-            if (st != DEC_OK) vst(S.stop, 1);  // lets a waiting decoder go
-            S.status = st;
-            S.nblock = nblock;
+            const int per = (ns + kDecWarps - 1) / kDecWarps, s0 = w * per, e0 = min(ns, s0 + per);
+            int p = ns;
+            if (w == 0) {
+                p = 0;
+            } else {
+                for (int q = max(s0, 1); q < e0; q++)
+                    if (syms[q - 1] >= 2) { p = q; break; }
+            }
+            S.seg_start[w] = p;
         }
+        __syncthreads();
+        const int p0 = S.seg_start[w];
+        int p1 = ns;
+        for (int w2 = w + 1; w2 < kDecWarps; w2++)
+            if (S.seg_start[w2] < ns) { p1 = S.seg_start[w2]; break; }
+        for (int pass = 0; pass < 2; pass++) {
+            int st = DEC_OK;
+            int64_t outc = 0;
+            if (p0 < ns) {
+                uint32_t lo = 0, hi = 0;
+                for (int q = 3; q >= 0; q--) {  // positions (pass 0) or the list at the segment start (pass 1)
+                    const int a = 8 * lane + q, a4 = a + 4;
+                    const uint32_t va = pass ? S.seg_list[w][a] : (uint32_t)a;
+                    const uint32_t va4 = pass ? S.seg_list[w][a4] : (uint32_t)a4;
+                    lo = (lo << 8) | va;
+                    hi = (hi << 8) | va4;
+                }
+                const int64_t off = pass ? S.seg_off[w] : 0;
+                int64_t run = 0, run_w = 1;
+                uint32_t batch = 0;
+                for (int i = p0; i < p1; i++) {
+                    if (((i - p0) & 31) == 0) batch = i + lane < p1 ? syms[i + lane] : 0u;
+                    const int sym = (int)__shfl_sync(LFC_FULL, batch, (i - p0) & 31);
+                    if (sym <= 1) {
+                        run += (int64_t)(sym + 1) * run_w;
+                        run_w <<= 1;
+                        if (run > block_max) { st = DEC_OVERFLOW; break; }
+                        continue;
+                    }
+                    if (run > 0) {
+                        if (pass) {
+                            if (off + outc + run > S.nblock) { st = DEC_OVERFLOW; break; }
+                            const uint8_t v = S.seq_to_unseq[__shfl_sync(LFC_FULL, lo, 0) & 255u];
+                            for (int64_t q = lane; q < run; q += 32) L[off + outc + q] = v;
+                        }
+                        outc += run;
+                        run = 0;
+                        run_w = 1;
+                    }
+                    if (sym == alpha - 1) break;  // EOB
+                    const int j = sym - 1;  // >= 1
+                    if (j >= niu) { st = DEC_BAD_DATA; break; }
+                    const uint32_t holder = __shfl_sync(LFC_FULL, (j & 4) ? hi : lo, j >> 3);
+                    const uint32_t v = (holder >> (8 * (j & 3))) & 255u;
+                    const uint32_t below = __shfl_up_sync(LFC_FULL, hi, 1) >> 24;  // position 8l - 1
+                    const uint32_t slo = (lo << 8) | (lane == 0 ? v : below), shi = __funnelshift_l(lo, hi, 8);
+                    const int cnt = min(8, max(0, j + 1 - 8 * lane));
+                    const int cl = min(cnt, 4), ch = max(cnt - 4, 0);
+                    lo = __byte_perm(slo, lo, 0x7654u - (0x4444u & ((1u << (4 * cl)) - 1u)));
+                    hi = __byte_perm(shi, hi, 0x7654u - (0x4444u & ((1u << (4 * ch)) - 1u)));
+                    if (pass) {
+                        if (off + outc >= S.nblock) { st = DEC_OVERFLOW; break; }
+                        if (lane == 0) L[off + outc] = S.seq_to_unseq[v];
+                    }
+                    outc++;
+                    if (outc > block_max) { st = DEC_OVERFLOW; break; }
+                }
+                if (pass == 0) {  // where the moves took each position
+#pragma unroll
+                    for (int q = 0; q < 4; q++) {
+                        S.seg_perm[w][8 * lane + q] = (uint8_t)(lo >> (8 * q));
+                        S.seg_perm[w][8 * lane + 4 + q] = (uint8_t)(hi >> (8 * q));
+                    }
+                }
+            }
+            if (lane == 0) {
+                S.seg_len[w] = (int32_t)(outc < INT_MAX ? outc : INT_MAX);
+                S.seg_status[w] = st;
+            }
+            __syncthreads();
+            if (pass == 0 && w == 0) {
+                // lists at the segment starts and output offsets, in order
+                int st0 = DEC_OK;
+                for (int q = lane; q < 256; q += 32) S.seg_list[0][q] = (uint8_t)(q < niu ? q : 0);
+                int64_t total = 0;
+                int prev = -1;
+                for (int w2 = 0; w2 < kDecWarps; w2++) {
+                    if (S.seg_start[w2] >= ns) continue;
+                    if (S.seg_status[w2] != DEC_OK) st0 = S.seg_status[w2];
+                    if (prev >= 0) {
+                        __syncwarp();
+                        for (int q = lane; q < 256; q += 32) S.seg_list[w2][q] = S.seg_list[prev][S.seg_perm[prev][q]];
+                    }
+                    if (lane == 0) S.seg_off[w2] = (int32_t)(total < INT_MAX ? total : INT_MAX);
+                    total += S.seg_len[w2];
+                    prev = w2;
+                }
+                if (st0 == DEC_OK && (total > block_max || total > kBlockCap)) st0 = DEC_OVERFLOW;
+                if (st0 == DEC_OK && S.orig >= total) st0 = DEC_BAD_ORIG;
+                if (lane == 0) {
+                    S.status = st0;
+                    S.nblock = (int32_t)(total < INT_MAX ? total : INT_MAX);
+                }
+            }
+            __syncthreads();
+            if (S.status != DEC_OK) break;
+        }
+        if (tid == 0)
+            for (int w2 = 0; w2 < kDecWarps; w2++)
+                if (S.seg_status[w2] != DEC_OK) S.status = S.seg_status[w2];
     }
     __syncthreads();
     if (S.status != DEC_OK) {
