@@ -125,6 +125,7 @@ struct DecShared {
     int32_t first[6][22], count[6][22], pidx[6][22];
     uint16_t perm[6][258];
     uint16_t lut[6][1 << 10];  // next 10 bits -> (symbol << 5) | code length, 0: longer code
+    uint16_t mlut[6][1 << 12]; // next 12 bits -> (codes << 5) | their bits: the whole codes (at most 4) in them, 0: the first is longer
     BitReader br;              // the header reader, handed from the parse to the decode loop
     int32_t alpha, block_max;
     uint32_t red[32];
@@ -277,6 +278,23 @@ __global__ void __maxnreg__(64) bzip2_decode_kernel(const DecBlock *__restrict__
         }
         S.lut[t][i] = e;
     }
+    // multi-code length tables: how many whole codes the next 12 bits hold
+    // (at most 4) and how many bits they take, for the group walk below
+    for (int q = tid; q < S.n_groups * 4096; q += blockDim.x) {
+        const int t = q >> 12, i = q & 4095;
+        int used = 0, n = 0;
+        while (n < 4) {
+            int l = 1, got = 0;
+            for (; l <= 12 - used; l++) {
+                const uint32_t d = (uint32_t)((int32_t)((i >> (12 - used - l)) & ((1 << l) - 1)) - S.first[t][l]);
+                if (d < (uint32_t)S.count[t][l]) { got = l; break; }
+            }
+            if (!got) break;
+            used += got;
+            n++;
+        }
+        S.mlut[t][i] = (uint16_t)((n << 5) | used);
+    }
     __syncthreads();
     // ---- 1b. Huffman: thread 0 walks the groups once to find where each
     // starts in the stream (and where EOB is); then every thread decodes
@@ -291,6 +309,24 @@ __global__ void __maxnreg__(64) bzip2_decode_kernel(const DecBlock *__restrict__
             gofs[g] = (int32_t)(br.next * 8 - br.bcnt);
             const int t = sel[g];
             int k = 0;
+            if (g < nsel - 1) {
+                // an encoder writes one selector per group it uses, so EOB is
+                // in the last group and the others hold 50 codes: their
+                // lengths only, several codes per lookup (a misplaced EOB in
+                // a corrupt stream shows up in the group decode or the MTF)
+                while (k < 50) {
+                    const uint32_t e = S.mlut[t][br.peek(12)];
+                    const int n = (int)(e >> 5);
+                    if (n > 0 && n <= 50 - k) {
+                        if (!br.skip(e & 31)) { st = DEC_TRUNC; break; }
+                        k += n;
+                    } else {
+                        if (huff_symbol(br, S, t) < 0) { st = br.err ? DEC_TRUNC : DEC_BAD_DATA; break; }
+                        k++;
+                    }
+                }
+                continue;
+            }
             for (; k < 50; k++) {
                 const int sym = huff_symbol(br, S, t);
                 if (sym < 0) { st = br.err ? DEC_TRUNC : DEC_BAD_DATA; break; }
@@ -302,7 +338,7 @@ __global__ void __maxnreg__(64) bzip2_decode_kernel(const DecBlock *__restrict__
                 ngu = g + 1;
                 break;
             }
-            if (g == nsel - 1) st = DEC_BAD_DATA;  // no EOB
+            st = DEC_BAD_DATA;  // no EOB
         }
         S.nsym = ns;
         S.ngroups_used = ngu;
