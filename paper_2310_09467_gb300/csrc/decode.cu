@@ -140,10 +140,53 @@ struct DecShared {
     int32_t scan_sh[33];        // block scan scratch
 };
 
+// BitReader whose next 4 bytes are loaded one refill ahead, so a refill
+// does not wait for memory (for the one thread that walks all groups).
+struct AheadReader : BitReader {
+    uint32_t pf;  // bytes next .. next + 3, big-endian (when next + 4 <= nbytes)
+    __device__ __forceinline__ uint32_t load4(int64_t at) const {
+        return ((uint32_t)__ldg(p + at) << 24) | ((uint32_t)__ldg(p + at + 1) << 16) |
+               ((uint32_t)__ldg(p + at + 2) << 8) | (uint32_t)__ldg(p + at + 3);
+    }
+    __device__ void start(const BitReader &r) {
+        *static_cast<BitReader *>(this) = r;
+        pf = next + 4 <= nbytes ? load4(next) : 0u;
+    }
+    __device__ __forceinline__ void refill() {
+        if (bcnt <= 32 && next + 4 <= nbytes) {
+            buf |= (uint64_t)pf << (32 - bcnt);
+            bcnt += 32;
+            next += 4;
+            pf = next + 4 <= nbytes ? load4(next) : 0u;  // used at the next refill
+            return;
+        }
+        while (bcnt <= 56 && next < nbytes) {
+            buf |= (uint64_t)__ldg(p + next++) << (56 - bcnt);
+            bcnt += 8;
+        }
+    }
+    __device__ __forceinline__ uint32_t peek(int k) {
+        if (bcnt < k) refill();
+        return (uint32_t)(buf >> (64 - k));
+    }
+    __device__ __forceinline__ bool skip(int k) {
+        if (bcnt < k) refill();
+        if (bcnt < k) { err = true; bcnt = 0; buf = 0; return false; }
+        buf <<= k;
+        bcnt -= k;
+        return true;
+    }
+    __device__ __forceinline__ uint32_t get(int k) {
+        const uint32_t v = peek(k);
+        return skip(k) ? v : 0u;
+    }
+};
+
 // One Huffman symbol with table t: the 10-bit lookup, else the canonical
 // search from 11 bits; -1 for a code that is not in the table or a stream
 // that ends first (br.err).
-__device__ __forceinline__ int huff_symbol(BitReader &br, const DecShared &S, int t) {
+template <class Reader>
+__device__ __forceinline__ int huff_symbol(Reader &br, const DecShared &S, int t) {
     const uint32_t e = S.lut[t][br.peek(10)];
     if (e) return br.skip(e & 31) ? (int)(e >> 5) : -1;
     int32_t c = (int32_t)br.peek(10);
@@ -302,7 +345,8 @@ __global__ void __maxnreg__(64) bzip2_decode_kernel(const DecBlock *__restrict__
     int32_t *gofs = T;                                  // group bit offsets (T is free until the LF mapping)
     uint16_t *syms = reinterpret_cast<uint16_t *>(mark);  // symbols in order (mark is free until the walkers)
     if (tid == 0) {
-        BitReader br = S.br;
+        AheadReader br;
+        br.start(S.br);
         const int nsel = S.n_sel, alpha = S.alpha;
         int st = DEC_OK, ns = 0, ngu = 0;
         for (int g = 0; g < nsel && st == DEC_OK; g++) {
@@ -314,11 +358,14 @@ __global__ void __maxnreg__(64) bzip2_decode_kernel(const DecBlock *__restrict__
                 // in the last group and the others hold 50 codes: their
                 // lengths only, several codes per lookup (a misplaced EOB in
                 // a corrupt stream shows up in the group decode or the MTF)
+                const uint16_t *ml = S.mlut[t];
                 while (k < 50) {
-                    const uint32_t e = S.mlut[t][br.peek(12)];
-                    const int n = (int)(e >> 5);
-                    if (n > 0 && n <= 50 - k) {
-                        if (!br.skip(e & 31)) { st = DEC_TRUNC; break; }
+                    if (br.bcnt < 32) br.refill();  // then the whole step needs no other check
+                    const uint32_t e = ml[(uint32_t)(br.buf >> 52)];
+                    const int n = (int)(e >> 5), len = (int)(e & 31);
+                    if (n > 0 && n <= 50 - k && len <= br.bcnt) {
+                        br.buf <<= len;
+                        br.bcnt -= len;
                         k += n;
                     } else {
                         if (huff_symbol(br, S, t) < 0) { st = br.err ? DEC_TRUNC : DEC_BAD_DATA; break; }
