@@ -167,6 +167,19 @@ size_t lfc_max_compressed_bytes(int32_t width, int32_t height, int32_t block_byt
 int lfc_compress(lfc_plan plan, const lfc_frame *h_frames, int n, const uint8_t *d_choice,
                  uint8_t *d_out, size_t out_cap, uint64_t *d_out_sizes);
 
+/* lfc_compress on frames in host memory, the containers back in host memory
+ * (the whole round trip of a caller whose frames arrive on the host). Frame
+ * i's data (and prev) point to host memory; they are copied to device
+ * staging buffers that the plan allocates on the first call (max_frames
+ * frames of the plan's size, twice when frames carry prev), then
+ * compressed, and container i goes to h_out + the same offset as in
+ * lfc_compress, its size to h_out_sizes[i] (host). Pinned host memory
+ * makes the copies asynchronous. h_choice: host n ids, or NULL to judge.
+ * Synchronous. Errors: as lfc_compress; CAPACITY if out_cap is below the
+ * slot sum; NOMEM if the staging buffers cannot be allocated. */
+int lfc_compress_host(lfc_plan plan, const lfc_frame *h_frames, int n, const uint8_t *h_choice, uint8_t *h_out,
+                      size_t out_cap, uint64_t *h_out_sizes);
+
 /* A batch is one lfc_compress call captured once as a CUDA graph (with the
  * suffix-sort rounds as a device-driven WHILE node), so that a stream of
  * batches with the same frame buffers and geometry costs one cudaGraphLaunch

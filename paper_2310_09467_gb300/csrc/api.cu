@@ -254,7 +254,8 @@ static void free_ws(Workspace &w) {
     void *ptrs[] = {w.hist, w.summ, w.chain_first, w.scores, w.choice, w.jframes, w.cand, w.l2tab, w.stream, w.blocks, w.bstate,
                     w.rle, w.sa, w.sa2, w.rank, w.act, w.act2, w.val, w.val2, w.keys, w.keys2, w.lbstat, w.dhist, w.segbig, w.tileaux, w.bwt,
                     w.mtfidx, w.mtflists, w.mtfrec, w.mtfreclen, w.sym, w.freq, w.rfreq, w.sel, w.lens, w.codes, w.packed, w.cstream, w.masks, w.class_ids,
-                    w.act_total, w.block_dst, w.frame_crc, w.crc_part, w.crc_part2, w.chunk_desc, w.dec_tt};
+                    w.act_total, w.block_dst, w.frame_crc, w.crc_part, w.crc_part2, w.chunk_desc, w.dec_tt,
+                    w.hx_frames, w.hx_prev, w.hx_out, w.hx_choice, w.hx_sizes};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     if (w.h_act_total) cudaFreeHost(w.h_act_total);
@@ -872,6 +873,65 @@ extern "C" int lfc_compress(lfc_plan P, const lfc_frame *frames, int n, const ui
     r = stage_arena(P, D.arena);
     if (r) return r;
     return run_compress(P, D, reinterpret_cast<const uint8_t *>(P->ws.chunk_desc), d_choice, d_out, d_out_sizes);
+}
+
+extern "C" int lfc_compress_host(lfc_plan P, const lfc_frame *h_frames, int n, const uint8_t *h_choice, uint8_t *h_out,
+                                 size_t out_cap, uint64_t *h_out_sizes) {
+    if (!P || !h_frames || !h_out || !h_out_sizes || n < 1)
+        return fail(P, LFC_ERR_INVALID_ARG, "lfc_compress_host: bad arguments");
+    if (n > P->cfg.max_frames) return fail(P, LFC_ERR_INVALID_ARG, "lfc_compress_host: n > max_frames");
+    Workspace &ws = P->ws;
+    const int bb = block_bytes_of(P);
+    const size_t slot = 2 * (size_t)P->cfg.width * P->cfg.height;
+    // the containers' slots in h_out, as lfc_compress lays them out
+    std::vector<uint64_t> off(n);
+    uint64_t need = 0;
+    bool any_prev = false;
+    for (int i = 0; i < n; i++) {
+        const int r = check_frame(P, h_frames[i]);
+        if (r) return r;
+        off[i] = need;
+        need += container_bound(h_frames[i].width, h_frames[i].height, bb);
+        any_prev |= h_frames[i].prev != nullptr;
+    }
+    if (need > out_cap) return fail(P, LFC_ERR_CAPACITY, "lfc_compress_host: out_cap below the sum of container bounds");
+    // staging for the plan's largest call, allocated once
+    const int F = P->cfg.max_frames;
+    const size_t out_all = (size_t)F * container_bound(P->cfg.width, P->cfg.height, bb);
+    cudaError_t e = cudaSuccess;
+    if (!ws.hx_frames) e = cudaMalloc(reinterpret_cast<void **>(&ws.hx_frames), (size_t)F * slot);
+    if (e == cudaSuccess && any_prev && !ws.hx_prev) e = cudaMalloc(reinterpret_cast<void **>(&ws.hx_prev), (size_t)F * slot);
+    if (e == cudaSuccess && !ws.hx_out) {
+        e = cudaMalloc(reinterpret_cast<void **>(&ws.hx_out), out_all);
+        ws.hx_out_cap = out_all;
+    }
+    if (e == cudaSuccess && !ws.hx_sizes) e = cudaMalloc(reinterpret_cast<void **>(&ws.hx_sizes), (size_t)F * sizeof(uint64_t));
+    if (e == cudaSuccess && !ws.hx_choice) e = cudaMalloc(reinterpret_cast<void **>(&ws.hx_choice), (size_t)F);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(P, LFC_ERR_NOMEM, "lfc_compress_host: staging allocation", e);
+    }
+    // frames in, one copy each (pinned host memory makes them asynchronous)
+    std::vector<lfc_frame> dev(h_frames, h_frames + n);
+    for (int i = 0; i < n; i++) {
+        const size_t bytes = 2 * (size_t)h_frames[i].width * h_frames[i].height;
+        dev[i].data = reinterpret_cast<const uint16_t *>(ws.hx_frames + (size_t)i * slot);
+        CK(cudaMemcpyAsync(ws.hx_frames + (size_t)i * slot, h_frames[i].data, bytes, cudaMemcpyHostToDevice, P->stream));
+        if (h_frames[i].prev) {
+            dev[i].prev = reinterpret_cast<const uint16_t *>(ws.hx_prev + (size_t)i * slot);
+            CK(cudaMemcpyAsync(ws.hx_prev + (size_t)i * slot, h_frames[i].prev, bytes, cudaMemcpyHostToDevice, P->stream));
+        }
+    }
+    if (h_choice) CK(cudaMemcpyAsync(ws.hx_choice, h_choice, (size_t)n, cudaMemcpyHostToDevice, P->stream));
+    const int r = lfc_compress(P, dev.data(), n, h_choice ? ws.hx_choice : nullptr, ws.hx_out, ws.hx_out_cap, ws.hx_sizes);
+    if (r) return r;
+    // sizes, then each container's bytes, out
+    CK(cudaMemcpyAsync(h_out_sizes, ws.hx_sizes, (size_t)n * sizeof(uint64_t), cudaMemcpyDeviceToHost, P->stream));
+    CK(cudaStreamSynchronize(P->stream));
+    for (int i = 0; i < n; i++)
+        CK(cudaMemcpyAsync(h_out + off[i], ws.hx_out + off[i], (size_t)h_out_sizes[i], cudaMemcpyDeviceToHost, P->stream));
+    CK(cudaStreamSynchronize(P->stream));
+    return LFC_OK;
 }
 
 // ------------------------------------------------------------------ batches

@@ -178,6 +178,11 @@ struct Workspace {
     uint64_t *l2tab = nullptr;     // 65536
     int64_t summ_cap = 0;
     uint8_t *cstream = nullptr;    // candidate streams: judge_frames_cap * cstream_kmax slots
+    // lfc_compress_host staging, allocated on its first call: frames, previous
+    // frames, containers, sizes, given ids
+    uint8_t *hx_frames = nullptr, *hx_prev = nullptr, *hx_out = nullptr, *hx_choice = nullptr;
+    uint64_t *hx_sizes = nullptr;
+    size_t hx_out_cap = 0;
     uint64_t *masks = nullptr;     // proposal candidate masks, max_frames x 4
     uint8_t *class_ids = nullptr;  // proposal class -> candidate id (64)
     int64_t cstream_slot = 0;

@@ -32,7 +32,7 @@ EXPORTS = ["lfc_plan_create", "lfc_plan_destroy", "lfc_plan_last_error", "lfc_ju
            "lfc_cnn_create", "lfc_cnn_destroy", "lfc_cnn_last_error", "lfc_cnn_param_count", "lfc_cnn_set_params",
            "lfc_cnn_get_params", "lfc_cnn_thumbnails", "lfc_cnn_set_thumbnails", "lfc_cnn_forward", "lfc_cnn_backward",
            "lfc_cnn_adam_step", "lfc_plan_set_proposal", "lfc_propose", "lfc_plan_device_status",
-           "lfc_plan_inject_fault", "lfc_bwt_blocks"]
+           "lfc_plan_inject_fault", "lfc_bwt_blocks", "lfc_compress_host"]
 
 STAGES = ["judge_hist", "judge_score", "emit", "crc", "rle1", "bwt_sort8", "bwt_refine", "bwt_out", "mtf",
           "huffman", "pack", "container", "judge_emit", "bwt_keys"]
@@ -81,6 +81,7 @@ def load():
         "lfc_symbols": (i32, [P, ctypes.POINTER(Frame), i32, P]),
         "lfc_max_compressed_bytes": (sz, [ctypes.c_int32, ctypes.c_int32, ctypes.c_int32]),
         "lfc_compress": (i32, [P, ctypes.POINTER(Frame), i32, P, P, sz, P]),
+        "lfc_compress_host": (i32, [P, ctypes.POINTER(Frame), i32, P, P, sz, P]),
         "lfc_bzip2_encode": (i32, [P, P, ctypes.POINTER(u64), ctypes.POINTER(ctypes.c_uint32), i32, P, sz, P]),
         "lfc_max_stream_bytes": (sz, [ctypes.c_int32]),
         "lfc_plan_block_capacity": (i32, [P]),
@@ -282,6 +283,42 @@ class Plan:
             offs.append(o)
             o += max_compressed_bytes(f.shape[1], f.shape[0], self.block_bytes)
         return offs, o
+
+    def compress_host(self, frames, pitch, prevs=None, choice=None, out=None, sizes=None):
+        """lfc_compress_host: frames (and prevs) are CPU uint16/int16 tensors or
+        arrays (pinned memory copies fastest); returns (out host uint8 buffer,
+        sizes uint64[n] host, slot offsets)."""
+        import numpy as np
+        torch = _torch()
+
+        def host(x):
+            if isinstance(x, np.ndarray):
+                x = torch.from_numpy(np.ascontiguousarray(x))
+            assert not x.is_cuda and x.dim() == 2 and x.element_size() == 2 and x.is_contiguous()
+            return x
+        frames = [host(f) for f in frames]
+        prevs = None if prevs is None else [None if p is None else host(p) for p in prevs]
+        n = len(frames)
+        arr = (Frame * n)()
+        for i, f in enumerate(frames):
+            arr[i].data = f.data_ptr()
+            pv = None if prevs is None else prevs[i]
+            arr[i].prev = pv.data_ptr() if pv is not None else None
+            arr[i].height, arr[i].width = f.shape
+            arr[i].pitch = pitch if isinstance(pitch, int) else pitch[i]
+            arr[i].reserved = 0
+        offs, total = self.slots(frames)
+        if out is None:
+            out = torch.empty(total, dtype=torch.uint8)
+        if sizes is None:
+            sizes = np.zeros(n, dtype=np.uint64)
+        ch = None
+        if choice is not None:
+            ch = np.ascontiguousarray(np.asarray(choice, dtype=np.uint8))
+        rc = self.lib.lfc_compress_host(self.h, arr, n, ch.ctypes.data_as(ctypes.c_void_p) if ch is not None else None,
+                                        _ptr(out), out.numel(), sizes.ctypes.data_as(ctypes.c_void_p))
+        self._check(rc, "lfc_compress_host")
+        return out, sizes, offs
 
     def compress(self, frames, pitch, prevs=None, choice=None, out=None, sizes=None):
         """Compress on the device. Returns (out uint8 buffer, sizes int64[n], slot offsets)."""
