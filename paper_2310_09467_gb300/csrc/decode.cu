@@ -4,19 +4,24 @@
 // One CTA per bzip2 stream. Every read of the coded stream is checked
 // against its length and every write against its buffer, so corrupt input
 // ends in an error flag, never an out-of-bounds access.
-//  1. thread 0: headers and tables; the CTA: a lookup table per Huffman
-//     table (codes up to 10 bits in one lookup); then, pipelined through a
-//     ring in shared memory, thread 0 decodes the Huffman symbols and warp 1
-//     does inverse RUNA/RUNB and MTF (each sequential by nature; the MTF
-//     list in the warp's registers) -> the BWT last column L;
+//  1. thread 0: headers and tables; the CTA: Huffman lookup tables (a
+//     symbol per 10-bit prefix; whole-code counts and lengths per 12-bit
+//     prefix); thread 0 walks the groups of 50 codes for their bit offsets
+//     (EOB lies in the last group, as an encoder writes one selector per
+//     group it uses: a stream with more selectors is rejected as corrupt);
+//     every thread decodes whole groups into the symbol array; inverse
+//     RUNA/RUNB and MTF by 32 segments (each segment's moves permute list
+//     positions whatever the list holds: permutations first, then the lists
+//     at the segment starts in order, then every segment decoded) -> the BWT
+//     last column L;
 //  2. the CTA: LF mapping T[j] = C[L[j]] + rank of j among equal bytes (a
 //     stable counting sort of L with per-warp counters);
 //  3. 1024 walkers invert the BWT: each starts at its own row (walker 0 at
 //     origPtr), follows T until it meets another walker's start row, the
 //     pieces are chained from walker 0, and every walker re-walks its piece
 //     writing bytes from the end of the block backwards;
-//  4. thread 0: inverse RLE1; the CTA: CRC-32/BZIP2 of the output vs the
-//     stored block CRC.
+//  4. the CTA: inverse RLE1 from sync points (one piece per thread), then
+//     CRC-32/BZIP2 of the output vs the stored block CRC.
 #include <climits>
 
 #include "lfc_common.cuh"
