@@ -250,11 +250,11 @@ int lfc_decompress(lfc_plan plan, const uint8_t *const *h_in, const uint64_t *h_
  *   chain_range_bytes       upper bound on the bytes of a candidate stream
  *                           one warp of the pair-chain kernel walks (a 32nd
  *                           per lane): 16384, 32768, 65536, 131072 or 262144
- *                           (default 131072); each launch evens the ranges
+ *                           (default 262144); each launch evens the ranges
  *                           out below it so that its CTAs fill whole waves
  *                           of the device's SMs;
  *   judge_frames_per_launch frames per judge launch, 1 .. the plan's
- *                           min(max_frames, 8) (default: that maximum);
+ *                           min(max_frames, 16) (default: that maximum);
  *   wait_budget_ms          how long one bounded device wait may last
  *                           before the kernel gives up and the call returns
  *                           LFC_ERR_TIMEOUT, 1 .. 60000 (default 1000). The

@@ -11,7 +11,7 @@ using namespace lfc;
 
 namespace {
 
-constexpr int kJudgeFramesCap = 8;
+constexpr int kJudgeFramesCap = 16;
 constexpr int kDefaultWaitMs = 1000;  // bounded device waits give up after this long
 
 int fail(lfc_plan P, int code, const std::string &what, cudaError_t e = cudaSuccess) {
@@ -169,7 +169,7 @@ extern "C" int lfc_plan_set_tuning(lfc_plan P, const lfc_tuning *t) {
     }
     if (t->judge_frames_per_launch) {
         if (t->judge_frames_per_launch < 1 || t->judge_frames_per_launch > P->judge_frames_cap)
-            return fail(P, LFC_ERR_INVALID_ARG, "judge_frames_per_launch outside 1..min(max_frames, 8)");
+            return fail(P, LFC_ERR_INVALID_ARG, "judge_frames_per_launch outside 1..min(max_frames, 16)");
         v.judge_frames_per_launch = t->judge_frames_per_launch;
     }
     if (t->wait_budget_ms) {

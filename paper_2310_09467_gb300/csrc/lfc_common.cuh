@@ -250,7 +250,7 @@ struct lfc_plan_s {
     std::vector<uint8_t> ids_spatial;   // judged for every frame
     std::vector<uint8_t> ids_temporal;  // judged for frames with prev
     int judge_frames_cap = 0;           // frames per judge launch (allocated)
-    lfc_tuning tune{16, 131072, 0, 0};    // autotuned judge knobs
+    lfc_tuning tune{16, 262144, 0, 0};    // autotuned judge knobs
     lfc_cnn cnn = nullptr;              // learned proposal (optional)
     int topk = 0;
     float tau = 0.f;
