@@ -928,6 +928,9 @@ extern "C" int lfc_compress_host(lfc_plan P, const lfc_frame *h_frames, int n, c
     // sizes, then each container's bytes, out
     CK(cudaMemcpyAsync(h_out_sizes, ws.hx_sizes, (size_t)n * sizeof(uint64_t), cudaMemcpyDeviceToHost, P->stream));
     CK(cudaStreamSynchronize(P->stream));
+    for (int i = 0; i < n; i++)  // a size beyond its slot would overrun h_out: never copy it
+        if (h_out_sizes[i] > container_bound(h_frames[i].width, h_frames[i].height, bb))
+            return fail(P, LFC_ERR_CUDA, "lfc_compress_host: container size beyond its slot");
     for (int i = 0; i < n; i++)
         CK(cudaMemcpyAsync(h_out + off[i], ws.hx_out + off[i], (size_t)h_out_sizes[i], cudaMemcpyDeviceToHost, P->stream));
     CK(cudaStreamSynchronize(P->stream));
