@@ -119,6 +119,39 @@ def peaks():
     return 6800.0, "fallback"
 
 
+# Shared-memory wavefronts per stream byte of the pair-chain walk, from the ncu
+# capture of one 3-frame chain_hist_kernel launch (2040 x 2040, 26 candidates):
+# 166.2 M wavefronts of the shared-memory pipe for 649.2 M stream bytes (a table
+# read, a table rewrite and a hot-corner atomic per byte and lane, with the
+# atomics' bank conflicts). Conflict-free, the three accesses would take 3 / 32.
+CHAIN_WAVEFRONTS_PER_BYTE = 166.2e6 / 649.2e6
+CHAIN_WAVEFRONTS_PER_BYTE_IDEAL = 3.0 / 32.0
+# Warp instructions per stream byte of the same launch (776.6 M), against the
+# four warp instructions each SM can issue per clock.
+CHAIN_INSTR_PER_BYTE = 776.6e6 / 649.2e6
+
+
+def chain_smem_bound(pairs: float, stage_ms: float, n_sm: int, sm_mhz: float) -> dict:
+    """Pair increments per second of the judge's pair-chain stage beside the
+    ceilings that shared-memory throughput sets on them (one wavefront per SM
+    clock, at the measured wavefronts per stream byte, one increment per byte,
+    and at the conflict-free three accesses per byte) and that instruction
+    issue sets (four warp instructions per SM clock at the measured
+    instructions per byte)."""
+    achieved = pairs / (stage_ms / 1e3) if stage_ms > 0 else 0.0
+    clk = n_sm * sm_mhz * 1e6  # wavefronts per second over all SMs
+    bound = clk / CHAIN_WAVEFRONTS_PER_BYTE
+    ideal = clk / CHAIN_WAVEFRONTS_PER_BYTE_IDEAL
+    issue = 4.0 * clk / CHAIN_INSTR_PER_BYTE
+    return {"pair_increments_per_s": achieved, "smem_bound_per_s": bound, "frac_of_smem_bound": achieved / bound,
+            "smem_bound_conflict_free_per_s": ideal, "frac_of_conflict_free": achieved / ideal,
+            "issue_bound_per_s": issue, "frac_of_issue_bound": achieved / issue,
+            "how": "pairs = K (n - 1) per frame; smem bound = SMs x SM clock / shared-memory wavefronts per stream "
+                   "byte (%.3f measured by ncu on one 3-frame launch; 3/32 conflict-free); issue bound = 4 x SMs x SM "
+                   "clock / warp instructions per stream byte (%.3f, same capture)"
+                   % (CHAIN_WAVEFRONTS_PER_BYTE, CHAIN_INSTR_PER_BYTE)}
+
+
 def cpu_info():
     """Host core count and CPU model (read-only /proc and lscpu queries)."""
     model = None
@@ -604,6 +637,9 @@ def main():
                       "bytes_model": kmodel, "avg_launch_ms": kms / max(1, launches_), "launches_timed": launches_,
                       "stage_ms_per_step": kms / args.steps}
     dom = max(models, key=lambda k: stages[k][0])
+    n_sm = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+    lines["judge_hist"]["smem"] = chain_smem_bound(K * (raw_bytes - n) * args.steps, stages["judge_hist"][0], n_sm,
+                                                   clk.get("sm_mhz") or clk.get("sm_max_mhz") or 2070.0)
 
     # decompression through the API: the step's containers (device) back to
     # frames (device), checked bit-exact; lfc_decompress reads the headers on
