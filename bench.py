@@ -120,15 +120,16 @@ def peaks():
 
 
 # Shared-memory wavefronts per stream byte of the pair-chain walk, from the ncu
-# capture of one 3-frame chain_hist_kernel launch (2040 x 2040, 26 candidates):
-# 166.2 M wavefronts of the shared-memory pipe for 649.2 M stream bytes (a table
-# read, a table rewrite and a hot-corner atomic per byte and lane, with the
-# atomics' bank conflicts). Conflict-free, the three accesses would take 3 / 32.
-CHAIN_WAVEFRONTS_PER_BYTE = 166.2e6 / 649.2e6
+# capture of one 3-frame chain_hist_kernel launch (2040 x 2040, 26 candidates,
+# profiles/chain_hist_2040x3.md): 161.6 M wavefronts of the shared-memory pipe
+# for 649.2 M stream bytes (a table read, a table rewrite and a hot-corner
+# atomic per byte and lane, with the atomics' bank conflicts). Conflict-free,
+# the three accesses would take 3 / 32.
+CHAIN_WAVEFRONTS_PER_BYTE = 161.6e6 / 649.2e6
 CHAIN_WAVEFRONTS_PER_BYTE_IDEAL = 3.0 / 32.0
-# Warp instructions per stream byte of the same launch (776.6 M), against the
+# Warp instructions per stream byte of the same launch (688.7 M), against the
 # four warp instructions each SM can issue per clock.
-CHAIN_INSTR_PER_BYTE = 776.6e6 / 649.2e6
+CHAIN_INSTR_PER_BYTE = 688.7e6 / 649.2e6
 
 
 def chain_smem_bound(pairs: float, stage_ms: float, n_sm: int, sm_mhz: float) -> dict:
@@ -659,7 +660,7 @@ def main():
         dec_ms.append(1e3 * (time.perf_counter() - t0))
     decode = {"value": raw_bytes / 1e6 / (statistics.median(dec_ms) / 1e3), "unit": "MB/s (raw bytes restored)",
               "ms_per_step": statistics.median(dec_ms), "bit_exact": dec_ok,
-              "how": "lfc_decompress of the step's 12 device-resident containers into device frames"}
+              "how": "lfc_decompress of the step's %d device-resident containers into device frames" % n}
 
     # end to end through lfc_compress_host: pinned host frames in, sizes and
     # containers back in pinned host memory, copies inside the call
